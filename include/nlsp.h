@@ -1,0 +1,244 @@
+/*
+ * nlsp.h -- C ABI of the GB300 (sm_103a) spectral two-level preconditioned CG
+ * library (NeuraLSP, arXiv 2601.20174).
+ *
+ * The library solves sparse SPD systems A u = f (Sec. 3, Eq. discretized_pde)
+ * by preconditioned conjugate gradient (Sec. 4, "Two-grid Solver Evaluation")
+ * where every iteration applies the two-level preconditioner of Algorithm 1:
+ * weighted-Jacobi pre-smoothing, residual, restriction P^T rho through a dense
+ * n x k prolongation P, a k x k Galerkin coarse solve with A_c = P^T A P,
+ * prolongation z += P e_c and post-smoothing.  P is the span of the leading k
+ * left singular vectors of Jacobi-smoothed random vectors (Sec. 3,
+ * "Near-Nullspace Vectors" and "SVD-Centric Construction of Coarse Bases");
+ * the exact thin SVD stands in for the paper's learned map f_theta, whose
+ * global optima it is (Thm. 1, Cor. 2).
+ *
+ * Call order (Algorithm 1, setup then apply): nlsp_create ->
+ * nlsp_assemble_stencil -> nlsp_build_prolongation (or nlsp_prec_from_basis)
+ * -> nlsp_factor_coarse -> nlsp_solve / nlsp_apply_prec -> nlsp_free_* ->
+ * nlsp_destroy.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named dev_* are device pointers of the context's device; the
+ *     caller owns them, keeps them alive until the enqueued work completes,
+ *     and the library never frees them.  Other pointers are host pointers.
+ *   - Vectors over the grid are FP64, length n, node order x fastest
+ *     (2D: j*N + i; 3D: (l*N + j)*N + i).  Blocks of vectors are column-major
+ *     with a leading dimension ld >= n (in elements).
+ *   - The library owns nlsp_op / nlsp_prec objects (and the device memory
+ *     inside them) until nlsp_free_op / nlsp_free_prec.  An nlsp_prec keeps a
+ *     reference to the nlsp_op it was built for; free the prec first.
+ *   - All device work is enqueued on the context's stream.  Functions return
+ *     after enqueueing, except where "synchronises" is stated.
+ *   - Errors are returned as nlsp_status codes; nothing is thrown across the
+ *     ABI.  Device-side failures (non-positive pivot, CG breakdown) are
+ *     reported through status words that the synchronising calls read.
+ *     After NLSP_ERR_CUDA the context should be destroyed.
+ *   - Not thread-safe: one host thread per context at a time.
+ */
+#ifndef NLSP_H_
+#define NLSP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define NLSP_API __attribute__((visibility("default")))
+#else
+#define NLSP_API
+#endif
+
+typedef struct nlsp_ctx nlsp_ctx;
+typedef struct nlsp_op nlsp_op;
+typedef struct nlsp_prec nlsp_prec;
+
+typedef enum {
+  NLSP_OK = 0,
+  NLSP_NOT_CONVERGED = 1,   /* maxit reached; results and info are filled   */
+  NLSP_ERR_INVALID = -1,    /* bad argument, size or parameter combination   */
+  NLSP_ERR_CUDA = -2,       /* a CUDA runtime call failed                    */
+  NLSP_ERR_NOT_SPD = -3,    /* non-positive pivot in the Cholesky of A_c     */
+  NLSP_ERR_BREAKDOWN = -4,  /* p^T A p <= 0, r^T z <= 0 or non-finite scalar */
+  NLSP_ERR_TIMEOUT = -5,    /* a bounded device wait gave up                 */
+  NLSP_ERR_OOM = -6         /* device allocation failed                      */
+} nlsp_status;
+
+/* Arithmetic of the preconditioner (outer PCG recurrences are always FP64). */
+typedef enum {
+  NLSP_FP64 = 0,        /* everything FP64                                   */
+  NLSP_MIXED_FP32 = 1   /* setup and preconditioner FP32 (FP64 reductions),
+                           A_c Cholesky and the PCG recurrences FP64         */
+} nlsp_precision;
+
+/* Coefficient layouts for nlsp_assemble_stencil. */
+enum {
+  NLSP_COEF_CELL_KAPPA = 0,   /* cell-centred diffusion coefficient kappa > 0:
+                                 2D (N+1)^2 values [cj][ci], 3D (N+1)^3
+                                 values [cl][cj][ci] (x fastest)            */
+  NLSP_COEF_CONST_TENSOR = 1  /* constant 2D tensor {a_xx, a_yy, a_xy},
+                                 positive definite (9-point stencil)        */
+};
+
+/* Algorithm 1 inputs: K test vectors, rank k, weight omega, s1 smoothing
+   steps for the samples, nu1 / nu2 pre / post sweeps. */
+typedef struct {
+  int K;
+  int k;
+  int s1;
+  int nu1;
+  int nu2;
+  double omega;
+  int precision;  /* nlsp_precision */
+} nlsp_setup_params;
+
+typedef struct {
+  double tol;     /* stop when ||r||_2 <= tol ||b||_2 (recursive residual)  */
+  int maxit;      /* iteration cap (>= 1)                                    */
+  int flexible;   /* 1: Polak-Ribiere beta; 0: standard; -1: flexible iff
+                     the preconditioner is not FP64                         */
+  int graph_mode; /* 1: the whole loop is one CUDA graph with a device-side
+                     while node; 0: graph of one iteration relaunched by the
+                     host, checking convergence every few iterations        */
+} nlsp_solve_params;
+
+typedef struct {
+  int iterations;      /* products A p taken until the stop test passed     */
+  int status;          /* nlsp_status of this right-hand side               */
+  double relres;       /* recursive ||r|| / ||b|| at exit                    */
+  double true_relres;  /* ||b - A x|| / ||b|| recomputed in FP64 at exit     */
+} nlsp_solve_info;
+
+/* Human-readable name of a status code (static string). */
+NLSP_API const char* nlsp_status_string(int status);
+
+/* Message of the last failed CUDA runtime call on this host thread (static,
+   thread-local string; empty if none). */
+NLSP_API const char* nlsp_last_error(void);
+
+/* Creates a context on CUDA device `device`, enqueueing on `cuda_stream`
+   (a cudaStream_t, borrowed, not destroyed by the library; NULL = the legacy
+   default stream).  Errors: NLSP_ERR_INVALID (no such device),
+   NLSP_ERR_CUDA. */
+NLSP_API nlsp_status nlsp_create(nlsp_ctx** ctx_out, int device, void* cuda_stream);
+
+/* Replaces the stream that later calls enqueue on (borrowed). */
+NLSP_API nlsp_status nlsp_set_stream(nlsp_ctx* ctx, void* cuda_stream);
+
+/* Destroys the context; ops and precs must have been freed.  Synchronises. */
+NLSP_API void nlsp_destroy(nlsp_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Operator A (Sec. 3, Eq. discretized_pde; the diffusion / anisotropic PDE
+ * families of the Appendix on structured grids, Dirichlet nodes eliminated).
+ *   dim = 2, points = 5, layout CELL_KAPPA: -div(kappa grad u), edge weight =
+ *       mean kappa of the 2 cells sharing the edge, h = 1/(N+1), A scaled h^-2.
+ *   dim = 2, points = 9, layout CONST_TENSOR: -(a_xx u_xx + 2 a_xy u_xy +
+ *       a_yy u_yy) with the centred cross difference.
+ *   dim = 3, points = 7, layout CELL_KAPPA: edge weight = mean of 4 cells.
+ * grid = {N, N, N or 1}: only cubic / square grids (N >= 1).
+ * dev_coeffs: device FP64, read during the call (may be freed afterwards).
+ * Stores the operator coefficients in FP64 and FP32.  Synchronises.
+ * Errors: NLSP_ERR_INVALID (unsupported combination, non-positive diagonal),
+ * NLSP_ERR_OOM, NLSP_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+NLSP_API nlsp_status nlsp_assemble_stencil(nlsp_ctx* ctx, int dim, const int64_t grid[3], int points,
+                                  const double* dev_coeffs, int coeff_layout, nlsp_op** A_out);
+
+/* Number of unknowns n of the operator. */
+NLSP_API int64_t nlsp_op_size(const nlsp_op* A);
+
+/* Y = A X for m columns (FP64).  X is n x m (ldx), Y is n x m (ldy); X and Y
+   must not overlap.  Errors: NLSP_ERR_INVALID. */
+NLSP_API nlsp_status nlsp_op_apply(nlsp_ctx* ctx, const nlsp_op* A, int m, const double* dev_X, int64_t ldx,
+                          double* dev_Y, int64_t ldy);
+
+/* D = diag(A) (Algorithm 1 setup), n values FP64. */
+NLSP_API nlsp_status nlsp_op_diagonal(nlsp_ctx* ctx, const nlsp_op* A, double* dev_d);
+
+NLSP_API void nlsp_free_op(nlsp_op* A);
+
+/* ---------------------------------------------------------------------------
+ * Setup (Algorithm 1, setup).
+ * ------------------------------------------------------------------------- */
+
+/* S = (I - omega D^-1 A)^s1 S0 (Sec. 3, Near-Nullspace Vectors), computed in
+   `precision` and returned in FP64.  S0 and S are n x K column-major
+   (ld = n) and may be the same buffer.  Errors: NLSP_ERR_INVALID. */
+NLSP_API nlsp_status nlsp_smooth_samples(nlsp_ctx* ctx, const nlsp_op* A, int K, int s1, double omega,
+                                int precision, const double* dev_S0, double* dev_S);
+
+/* Builds a preconditioner for A from the random test vectors dev_S0 (n x K,
+   column-major, ld = n, read during the call): smooths them s1 times, takes
+   the leading k left singular vectors of S as P (thin SVD via the Gram
+   matrix S^T S, a Jacobi eigensolver and, in FP64, iterative refinement),
+   then forms and factors A_c = P^T A P for the full rank k (call
+   nlsp_factor_coarse to truncate).  Requires 1 <= k <= K <= 256, K <= n,
+   nu1 = nu2 >= 1 (PCG needs a symmetric preconditioner) and
+   0 < omega < 2.  Synchronises.  Errors: NLSP_ERR_INVALID, NLSP_ERR_NOT_SPD
+   (rank-deficient samples), NLSP_ERR_OOM, NLSP_ERR_CUDA. */
+NLSP_API nlsp_status nlsp_build_prolongation(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* params,
+                                    const double* dev_S0, nlsp_prec** M_out);
+
+/* Builds a preconditioner from a given basis dev_P (n x k column-major,
+   ld = n, FP64, read during the call), e.g. the output of a learned map
+   f_theta after its QR layer (Sec. 3, Algorithm 1 lines "P_hat = f_theta(S)",
+   "P = qf(P_hat)").  P need not be orthonormal, only of full column rank.
+   params->K and params->s1 are ignored.  Factors A_c for rank k.
+   Synchronises.  Errors as nlsp_build_prolongation. */
+NLSP_API nlsp_status nlsp_prec_from_basis(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* params,
+                                 const double* dev_P, int k, nlsp_prec** M_out);
+
+/* Truncates the coarse space to its first r columns (Algorithm 1 setup:
+   P_r = P[:, 1:r], A_c = P_r^T A P_r) and factors A_c = L L^T in FP64.
+   1 <= r <= k.  Synchronises.  Errors: NLSP_ERR_INVALID, NLSP_ERR_NOT_SPD. */
+NLSP_API nlsp_status nlsp_factor_coarse(nlsp_ctx* ctx, const nlsp_op* A, nlsp_prec* M, int r);
+
+/* Dimensions of a preconditioner: n, built rank k, active rank r, K (0 when
+   built from a basis) and precision.  Host pointers, any may be NULL. */
+NLSP_API nlsp_status nlsp_prec_dims(const nlsp_prec* M, int64_t* n, int* k, int* r, int* K, int* precision);
+
+/* Copies out P (n x k, column-major, ld = n, FP64; the stored basis,
+   converted from FP32 in mixed precision). */
+NLSP_API nlsp_status nlsp_prec_copy_basis(nlsp_ctx* ctx, const nlsp_prec* M, double* dev_P);
+
+/* Copies out the singular values sigma_1 >= ... >= sigma_K of S (K values,
+   FP64; zeros when built from a basis). */
+NLSP_API nlsp_status nlsp_prec_copy_sigma(nlsp_ctx* ctx, const nlsp_prec* M, double* dev_sigma);
+
+/* Copies out A_c (r x r) and its lower Cholesky factor L (r x r), both
+   column-major FP64 (either pointer may be NULL). */
+NLSP_API nlsp_status nlsp_prec_copy_coarse(nlsp_ctx* ctx, const nlsp_prec* M, double* dev_Ac, double* dev_L);
+
+NLSP_API void nlsp_free_prec(nlsp_prec* M);
+
+/* ---------------------------------------------------------------------------
+ * Apply and solve.
+ * ------------------------------------------------------------------------- */
+
+/* Z = B R for m columns: one application of the two-level preconditioner
+   (Algorithm 1, "Apply preconditioner to residual b").  R, Z FP64, n x m
+   (ldr, ldz >= n); must not overlap.  Computed in the prec's precision.
+   Errors: NLSP_ERR_INVALID. */
+NLSP_API nlsp_status nlsp_apply_prec(nlsp_ctx* ctx, const nlsp_prec* M, int m, const double* dev_R, int64_t ldr,
+                            double* dev_Z, int64_t ldz);
+
+/* Solves A X = B for m right-hand sides by PCG with the two-level
+   preconditioner M (Sec. 4; tolerance on the relative residual, x0 = 0 --
+   dev_X is output only).  Columns run independent recurrences; a converged
+   column is frozen.  infos: host array of m entries (may be NULL).
+   Synchronises.  Returns NLSP_OK when every column converged,
+   NLSP_NOT_CONVERGED if one hit maxit, NLSP_ERR_BREAKDOWN if one broke
+   down (per-column status in infos), NLSP_ERR_INVALID, NLSP_ERR_CUDA. */
+NLSP_API nlsp_status nlsp_solve(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec* M, int m, const double* dev_B,
+                       int64_t ldb, double* dev_X, int64_t ldx, const nlsp_solve_params* params,
+                       nlsp_solve_info* infos);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLSP_H_ */

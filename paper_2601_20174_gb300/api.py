@@ -1,0 +1,213 @@
+"""Python interface over the nlsp C ABI, taking and returning torch CUDA
+tensors.  PyTorch provides device memory and the stream; every computation is
+a call into libnlsp.so.
+
+Vectors are float64 tensors of shape (n,) or blocks of shape (n, m); they are
+handed to the library as column-major storage (a block is stored as its
+transpose, contiguous).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t: torch.Tensor) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+def _colmajor(X: torch.Tensor, n: int) -> tuple[torch.Tensor, int]:
+    """Returns (storage tensor of shape (m, n) contiguous, m)."""
+    if X.dtype != torch.float64 or not X.is_cuda:
+        raise TypeError("expected a CUDA float64 tensor")
+    if X.dim() == 1:
+        if X.shape[0] != n:
+            raise ValueError(f"length {X.shape[0]} != n = {n}")
+        return X.contiguous().view(1, n), 1
+    if X.dim() != 2 or X.shape[0] != n:
+        raise ValueError(f"expected shape (n, m) with n = {n}, got {tuple(X.shape)}")
+    return X.t().contiguous(), X.shape[1]
+
+
+def _out_like(store: torch.Tensor, one_d: bool) -> torch.Tensor:
+    return store.view(-1) if one_d else store.t()
+
+
+class Context:
+    """A library context on one CUDA device, enqueueing on a torch stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self._lib = L.load()
+        self.device = device
+        self.stream = stream or torch.cuda.current_stream(device)
+        h = C.c_void_p()
+        L.check(self._lib.nlsp_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream)), "nlsp_create")
+        self.h = h
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        L.check(self._lib.nlsp_set_stream(self.h, C.c_void_p(stream.cuda_stream)), "nlsp_set_stream")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.nlsp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    """SPD stencil operator A (nlsp_assemble_stencil)."""
+
+    def __init__(self, ctx: Context, dim: int, N: int, points: int, coeffs: torch.Tensor, layout: int):
+        self.ctx = ctx
+        self.dim, self.N, self.points, self.layout = dim, N, points, layout
+        coeffs = coeffs.to(device=f"cuda:{ctx.device}", dtype=torch.float64).contiguous()
+        grid = (C.c_int64 * 3)(N, N, N if dim == 3 else 1)
+        h = C.c_void_p()
+        L.check(ctx._lib.nlsp_assemble_stencil(ctx.h, dim, grid, points, _ptr(coeffs), layout, C.byref(h)),
+                "nlsp_assemble_stencil")
+        self.h = h
+        self.n = int(ctx._lib.nlsp_op_size(h))
+
+    @classmethod
+    def from_problem(cls, ctx: Context, problem) -> "Operator":
+        """From an inputs.Problem (its coefficients are uploaded)."""
+        coeffs = torch.as_tensor(problem.coeffs, dtype=torch.float64).reshape(-1)
+        return cls(ctx, problem.dim, problem.N, problem.points, coeffs.cuda(ctx.device), problem.layout)
+
+    def apply(self, X: torch.Tensor) -> torch.Tensor:
+        store, m = _colmajor(X, self.n)
+        out = torch.empty_like(store)
+        L.check(self.ctx._lib.nlsp_op_apply(self.ctx.h, self.h, m, _ptr(store), self.n, _ptr(out), self.n),
+                "nlsp_op_apply")
+        return _out_like(out, X.dim() == 1)
+
+    def diagonal(self) -> torch.Tensor:
+        d = torch.empty(self.n, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        L.check(self.ctx._lib.nlsp_op_diagonal(self.ctx.h, self.h, _ptr(d)), "nlsp_op_diagonal")
+        return d
+
+    def smooth_samples(self, S0: torch.Tensor, s1: int, omega: float, precision: int = L.NLSP_FP64) -> torch.Tensor:
+        store, K = _colmajor(S0, self.n)
+        out = torch.empty_like(store)
+        L.check(self.ctx._lib.nlsp_smooth_samples(self.ctx.h, self.h, K, s1, omega, precision, _ptr(store),
+                                                   _ptr(out)), "nlsp_smooth_samples")
+        return out.t()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx._lib.nlsp_free_op(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class SolveResult:
+    iterations: int
+    status: int
+    relres: float
+    true_relres: float
+
+
+class Preconditioner:
+    """Two-level preconditioner (nlsp_build_prolongation / nlsp_prec_from_basis)."""
+
+    def __init__(self, op: Operator, handle: C.c_void_p):
+        self.op = op
+        self.ctx = op.ctx
+        self.h = handle
+        n, k, r, K, prec = C.c_int64(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        L.check(self.ctx._lib.nlsp_prec_dims(handle, C.byref(n), C.byref(k), C.byref(r), C.byref(K),
+                                             C.byref(prec)), "nlsp_prec_dims")
+        self.n, self.k, self.K, self.precision = n.value, k.value, K.value, prec.value
+        self.r = r.value
+
+    @staticmethod
+    def _params(k, K, s1, nu, omega, precision):
+        return L.SetupParams(K=K, k=k, s1=s1, nu1=nu, nu2=nu, omega=omega, precision=precision)
+
+    @classmethod
+    def build(cls, op: Operator, S0: torch.Tensor, k: int, s1: int = 20, nu: int = 2, omega: float = 2.0 / 3.0,
+              precision: int = L.NLSP_FP64) -> "Preconditioner":
+        store, K = _colmajor(S0, op.n)
+        p = cls._params(k, K, s1, nu, omega, precision)
+        h = C.c_void_p()
+        L.check(op.ctx._lib.nlsp_build_prolongation(op.ctx.h, op.h, C.byref(p), _ptr(store), C.byref(h)),
+                "nlsp_build_prolongation")
+        return cls(op, h)
+
+    @classmethod
+    def from_basis(cls, op: Operator, P: torch.Tensor, nu: int = 2, omega: float = 2.0 / 3.0,
+                   precision: int = L.NLSP_FP64) -> "Preconditioner":
+        store, k = _colmajor(P, op.n)
+        p = cls._params(k, 0, 0, nu, omega, precision)
+        h = C.c_void_p()
+        L.check(op.ctx._lib.nlsp_prec_from_basis(op.ctx.h, op.h, C.byref(p), _ptr(store), k, C.byref(h)),
+                "nlsp_prec_from_basis")
+        return cls(op, h)
+
+    def factor(self, r: int):
+        L.check(self.ctx._lib.nlsp_factor_coarse(self.ctx.h, self.op.h, self.h, r), "nlsp_factor_coarse")
+        self.r = r
+
+    def basis(self) -> torch.Tensor:
+        out = torch.empty(self.k, self.n, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        L.check(self.ctx._lib.nlsp_prec_copy_basis(self.ctx.h, self.h, _ptr(out)), "nlsp_prec_copy_basis")
+        return out.t()
+
+    def sigma(self) -> torch.Tensor:
+        out = torch.zeros(max(self.K, 1), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        L.check(self.ctx._lib.nlsp_prec_copy_sigma(self.ctx.h, self.h, _ptr(out)), "nlsp_prec_copy_sigma")
+        return out[: self.K]
+
+    def coarse(self) -> tuple[torch.Tensor, torch.Tensor]:
+        r = self.r
+        Ac = torch.empty(r, r, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        Lf = torch.empty(r, r, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        L.check(self.ctx._lib.nlsp_prec_copy_coarse(self.ctx.h, self.h, _ptr(Ac), _ptr(Lf)), "nlsp_prec_copy_coarse")
+        return Ac.t(), Lf.t()  # stored column-major
+
+    def apply(self, R: torch.Tensor) -> torch.Tensor:
+        store, m = _colmajor(R, self.n)
+        out = torch.empty_like(store)
+        L.check(self.ctx._lib.nlsp_apply_prec(self.ctx.h, self.h, m, _ptr(store), self.n, _ptr(out), self.n),
+                "nlsp_apply_prec")
+        return _out_like(out, R.dim() == 1)
+
+    def solve(self, B: torch.Tensor, tol: float = 1e-8, maxit: int = 2000, flexible: int = -1,
+              graph_mode: int = 1):
+        """PCG for A X = B (x0 = 0).  Returns (X, [SolveResult per column])."""
+        store, m = _colmajor(B, self.n)
+        out = torch.empty_like(store)
+        infos = (L.SolveInfo * m)()
+        prm = L.SolveParams(tol=tol, maxit=maxit, flexible=flexible, graph_mode=graph_mode)
+        st = self.ctx._lib.nlsp_solve(self.ctx.h, self.op.h, self.h, m, _ptr(store), self.n, _ptr(out), self.n,
+                                      C.byref(prm), infos)
+        L.check(st, "nlsp_solve", allow=(L.NLSP_OK, L.NLSP_NOT_CONVERGED, L.NLSP_ERR_BREAKDOWN))
+        res = [SolveResult(i.iterations, i.status, i.relres, i.true_relres) for i in infos]
+        return _out_like(out, B.dim() == 1), res
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx._lib.nlsp_free_prec(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,178 @@
+// Shared definitions of the nlsp CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "nlsp.h"
+
+// ----------------------------------------------------------------------------
+// Error handling: every CUDA runtime call is checked; failures become
+// NLSP_ERR_CUDA (NLSP_ERR_OOM for allocation failures) and are never thrown.
+// ----------------------------------------------------------------------------
+#define NLSP_CUDA(call)                                                            \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      nlsp_record_cuda_error(e_, #call, __FILE__, __LINE__);                       \
+      return e_ == cudaErrorMemoryAllocation ? NLSP_ERR_OOM : NLSP_ERR_CUDA;       \
+    }                                                                              \
+  } while (0)
+
+#define NLSP_TRY(expr)                                                             \
+  do {                                                                             \
+    nlsp_status s_ = (expr);                                                       \
+    if (s_ < 0) return s_;                                                         \
+  } while (0)
+
+#define NLSP_LAUNCH_CHECK() NLSP_CUDA(cudaGetLastError())
+
+void nlsp_record_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// ----------------------------------------------------------------------------
+// Geometry and layouts
+// ----------------------------------------------------------------------------
+// Node tiles: P and the sample block S are stored as tiles of NLSP_TILE
+// consecutive nodes, each tile holding all columns contiguously:
+//   element (node i, column c) at ((i / W) * ncols + c) * W + (i % W).
+// One tile of one column is 512 B (FP32) / 1 KB (FP64): one coalesced warp
+// load of float4 / two of double2, and a whole tile (all columns) is a single
+// contiguous block for bulk copies.  n is padded to a multiple of W with zero
+// rows.
+constexpr int NLSP_TILE = 128;
+
+__host__ __device__ inline int64_t tiled_index(int64_t i, int c, int ncols) {
+  return ((i / NLSP_TILE) * ncols + c) * NLSP_TILE + (i % NLSP_TILE);
+}
+inline int64_t pad_tile(int64_t n) { return (n + NLSP_TILE - 1) / NLSP_TILE * NLSP_TILE; }
+
+enum StencilKind { ST_5PT = 0, ST_9PT = 1, ST_7PT = 2 };
+
+// Matrix-free view of A in one precision.
+//  5-point / 7-point: positive edge weights (h^-2 included) to the +x, +y, +z
+//  neighbour, zero where that neighbour is a boundary node, the diagonal and
+//  its inverse.  (A x)_i = d_i x_i - sum over neighbours of w_e x_nb.
+//  9-point constant: signed entries c[0] centre, c[1] E/W, c[2] N/S,
+//  c[3] NE/SW, c[4] NW/SE.
+template <typename T>
+struct StencilView {
+  int N;
+  int64_t n;
+  const T* diag;
+  const T* cx;
+  const T* cy;
+  const T* cz;
+  const T* dinv;
+  T c[5];
+  T cdinv;  // 1 / c[0] for the 9-point stencil
+};
+
+// ----------------------------------------------------------------------------
+// Library objects
+// ----------------------------------------------------------------------------
+struct nlsp_ctx {
+  int device;
+  cudaStream_t stream;
+  int num_sms;
+  size_t l2_bytes;
+};
+
+struct nlsp_op {
+  nlsp_ctx* ctx;
+  int device;  // kept so that freeing never touches a destroyed context
+  int dim, points, kind, N;
+  int64_t n;
+  double* a64;  // one allocation: diag, cx, cy, cz, dinv (n each)
+  float* a32;
+  double c9[5];
+  StencilView<double> v64;
+  StencilView<float> v32;
+};
+
+struct PcgWork;  // pcg.cu
+
+struct nlsp_prec {
+  nlsp_ctx* ctx;
+  int device;
+  const nlsp_op* A;
+  int precision;
+  int64_t n, n_pad;
+  int k, r, K;
+  int nu1, nu2;
+  double omega;
+  void* P;          // tiled [n_pad/W][k][W], float or double
+  double* sigma;    // K singular values (descending)
+  double* Ac;       // r x r column-major
+  double* L;        // r x r lower Cholesky factor, column-major
+  double* Ainv;     // r x r inverse of A_c (from the factor)
+  double* cpart;    // restriction partials [blocks][k]
+  double* ec;       // coarse correction (k, FP64)
+  unsigned* counter;
+  int* status;      // device status word (Cholesky pivots)
+  int rblocks;      // blocks of the restriction kernel
+  // apply workspace (precision T, n_pad each)
+  void* w0;
+  void* w1;
+  PcgWork* pcg;     // lazily built solver workspace and graphs
+};
+
+// ----------------------------------------------------------------------------
+// Device helpers
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block (blockDim.x a multiple of 32, <= 1024); result valid in
+// every thread.  Fixed order => deterministic.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* smem32) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) smem32[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  T t = (threadIdx.x < nw) ? smem32[threadIdx.x] : T(0);
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) smem32[0] = t;
+  __syncthreads();
+  T r = smem32[0];
+  __syncthreads();
+  return r;
+}
+
+// "Last block done": every block publishes its partial, then one arrival
+// counter decides which block is last; that block sees every partial
+// (threadfence before and after the counter) and resets the counter.
+__device__ __forceinline__ bool last_block_arrive(unsigned* counter, int* smem_flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    *smem_flag = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  bool last = *smem_flag != 0;
+  if (last) {
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+  return last;
+}
+
+// Deterministic sum of `count` partials (stride `stride`) by one block.
+__device__ __forceinline__ double block_sum_partials(const double* part, int count, int stride,
+                                                     double* smem32) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < count; b += blockDim.x) s += part[(int64_t)b * stride];
+  return block_sum(s, smem32);
+}
+
+template <typename T> __device__ __forceinline__ T ld_cg(const T* p) { return *p; }
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

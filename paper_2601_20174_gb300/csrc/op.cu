@@ -1,0 +1,278 @@
+// Context management and the operator A (Sec. 3, Eq. discretized_pde;
+// Algorithm 1 setup line D = diag(A)).
+#include <stdlib.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "stencil.cuh"
+#include "kernels.cuh"
+
+static thread_local char g_last_error[512];
+
+void nlsp_record_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file,
+           line);
+  if (getenv("NLSP_VERBOSE")) fprintf(stderr, "[nlsp] %s\n", g_last_error);
+}
+
+extern "C" const char* nlsp_last_error(void) { return g_last_error; }
+
+extern "C" const char* nlsp_status_string(int status) {
+  switch (status) {
+    case NLSP_OK: return "NLSP_OK";
+    case NLSP_NOT_CONVERGED: return "NLSP_NOT_CONVERGED";
+    case NLSP_ERR_INVALID: return "NLSP_ERR_INVALID";
+    case NLSP_ERR_CUDA: return "NLSP_ERR_CUDA";
+    case NLSP_ERR_NOT_SPD: return "NLSP_ERR_NOT_SPD";
+    case NLSP_ERR_BREAKDOWN: return "NLSP_ERR_BREAKDOWN";
+    case NLSP_ERR_TIMEOUT: return "NLSP_ERR_TIMEOUT";
+    case NLSP_ERR_OOM: return "NLSP_ERR_OOM";
+    default: return "NLSP_UNKNOWN_STATUS";
+  }
+}
+
+extern "C" nlsp_status nlsp_create(nlsp_ctx** ctx_out, int device, void* cuda_stream) {
+  if (!ctx_out) return NLSP_ERR_INVALID;
+  *ctx_out = nullptr;
+  int count = 0;
+  NLSP_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return NLSP_ERR_INVALID;
+  NLSP_CUDA(cudaSetDevice(device));
+  nlsp_ctx* c = new nlsp_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  int sms = 0, l2 = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+  c->num_sms = sms > 0 ? sms : 1;
+  c->l2_bytes = (size_t)l2;
+  *ctx_out = c;
+  return NLSP_OK;
+}
+
+extern "C" nlsp_status nlsp_set_stream(nlsp_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return NLSP_ERR_INVALID;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return NLSP_OK;
+}
+
+extern "C" void nlsp_destroy(nlsp_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+}
+
+// ----------------------------------------------------------------------------
+// Assembly kernels: cell kappa -> edge weights, diagonal and its inverse.
+// ----------------------------------------------------------------------------
+namespace {
+
+// 2D: x-edge between node columns i and i+1 of node row j lies in cell column
+// i+1 between cell rows j and j+1; y-edge between node rows j and j+1 of node
+// column i lies in cell row j+1 between cell columns i and i+1.  Weight = mean
+// of the two cells, scaled by h^-2.
+__global__ void k_assemble_5pt(int N, const double* __restrict__ kap, double* diag, double* cx, double* cy,
+                               double* dinv, int* bad) {
+  const int64_t n = (int64_t)N * N;
+  const int M = N + 1;
+  const double h2 = (double)M * (double)M;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / N), i = (int)(idx - (int64_t)j * N);
+    auto K = [&](int cj, int ci) { return kap[(int64_t)cj * M + ci]; };
+    const double west = 0.5 * (K(j, i) + K(j + 1, i)) * h2;
+    const double east = 0.5 * (K(j, i + 1) + K(j + 1, i + 1)) * h2;
+    const double south = 0.5 * (K(j, i) + K(j, i + 1)) * h2;
+    const double north = 0.5 * (K(j + 1, i) + K(j + 1, i + 1)) * h2;
+    const double d = west + east + south + north;
+    diag[idx] = d;
+    cx[idx] = (i < N - 1) ? east : 0.0;
+    cy[idx] = (j < N - 1) ? north : 0.0;
+    dinv[idx] = 1.0 / d;
+    if (!(d > 0.0) || !(west > 0.0) || !(east > 0.0) || !(south > 0.0) || !(north > 0.0) || !isfinite(d))
+      atomicOr(bad, 1);
+  }
+}
+
+// 3D: the x-edge between node columns i and i+1 at (j, l) lies in cell column
+// i+1 and is surrounded by cells (j|j+1, l|l+1); similarly for y and z.
+__global__ void k_assemble_7pt(int N, const double* __restrict__ kap, double* diag, double* cx, double* cy,
+                               double* cz, double* dinv, int* bad) {
+  const int64_t nn = (int64_t)N * N, n = nn * N;
+  const int M = N + 1;
+  const double h2 = (double)M * (double)M;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(idx / nn);
+    const int rem = (int)(idx - (int64_t)l * nn);
+    const int j = rem / N, i = rem - j * N;
+    auto K = [&](int cl, int cj, int ci) { return kap[((int64_t)cl * M + cj) * M + ci]; };
+    auto xedge = [&](int ci) { return 0.25 * (K(l, j, ci) + K(l, j + 1, ci) + K(l + 1, j, ci) + K(l + 1, j + 1, ci)) * h2; };
+    auto yedge = [&](int cj) { return 0.25 * (K(l, cj, i) + K(l, cj, i + 1) + K(l + 1, cj, i) + K(l + 1, cj, i + 1)) * h2; };
+    auto zedge = [&](int cl) { return 0.25 * (K(cl, j, i) + K(cl, j, i + 1) + K(cl, j + 1, i) + K(cl, j + 1, i + 1)) * h2; };
+    const double xw = xedge(i), xe = xedge(i + 1), ys = yedge(j), yn = yedge(j + 1), zd = zedge(l),
+                 zu = zedge(l + 1);
+    const double d = xw + xe + ys + yn + zd + zu;
+    diag[idx] = d;
+    cx[idx] = (i < N - 1) ? xe : 0.0;
+    cy[idx] = (j < N - 1) ? yn : 0.0;
+    cz[idx] = (l < N - 1) ? zu : 0.0;
+    dinv[idx] = 1.0 / d;
+    if (!(xw > 0.0) || !(xe > 0.0) || !(ys > 0.0) || !(yn > 0.0) || !(zd > 0.0) || !(zu > 0.0) || !isfinite(d))
+      atomicOr(bad, 1);
+  }
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+template <int KIND>
+__global__ void k_apply_cols(StencilView<double> A, int m, const double* __restrict__ X, int64_t ldx,
+                             double* __restrict__ Y, int64_t ldy) {
+  const int col = blockIdx.y;
+  const double* x = X + col * ldx;
+  double* y = Y + col * ldy;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < A.n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    NodeCoord c = node_coord<KIND>(idx, A.N);
+    y[idx] = stencil_apply<KIND>(A, idx, c, [&](int64_t m_) { return x[m_]; });
+  }
+}
+
+__global__ void k_diag_9pt(double d, double* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = d;
+}
+
+}  // namespace
+
+int grid_for(const nlsp_ctx* ctx, int64_t work, int threads, int per_sm) {
+  int64_t g = (work + threads - 1) / threads;
+  int64_t cap = (int64_t)ctx->num_sms * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+extern "C" nlsp_status nlsp_assemble_stencil(nlsp_ctx* ctx, int dim, const int64_t grid[3], int points,
+                                             const double* dev_coeffs, int coeff_layout, nlsp_op** A_out) {
+  if (!ctx || !grid || !dev_coeffs || !A_out) return NLSP_ERR_INVALID;
+  *A_out = nullptr;
+  int kind;
+  if (dim == 2 && points == 5 && coeff_layout == NLSP_COEF_CELL_KAPPA) kind = ST_5PT;
+  else if (dim == 2 && points == 9 && coeff_layout == NLSP_COEF_CONST_TENSOR) kind = ST_9PT;
+  else if (dim == 3 && points == 7 && coeff_layout == NLSP_COEF_CELL_KAPPA) kind = ST_7PT;
+  else return NLSP_ERR_INVALID;
+  const int64_t N = grid[0];
+  if (N < 1 || grid[1] != N || (dim == 3 ? grid[2] != N : (grid[2] != 1 && grid[2] != 0))) return NLSP_ERR_INVALID;
+  const int64_t n = dim == 3 ? N * N * N : N * N;
+  if (N > 65535 || n > ((int64_t)1 << 31) - 1) return NLSP_ERR_INVALID;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+
+  nlsp_op* op = new nlsp_op();
+  memset(op, 0, sizeof(*op));
+  op->ctx = ctx;
+  op->device = ctx->device;
+  op->dim = dim;
+  op->points = points;
+  op->kind = kind;
+  op->N = (int)N;
+  op->n = n;
+  cudaStream_t s = ctx->stream;
+  int* bad = nullptr;
+  auto fail = [&](nlsp_status e) {
+    if (bad) cudaFree(bad);
+    nlsp_free_op(op);
+    return e;
+  };
+  const double h2 = (double)(N + 1) * (double)(N + 1);
+  if (kind == ST_9PT) {
+    double t[3];
+    if (cudaMemcpy(t, dev_coeffs, sizeof(t), cudaMemcpyDeviceToHost) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+    const double axx = t[0], ayy = t[1], axy = t[2];
+    if (!(axx > 0.0) || !(ayy > 0.0) || !(axx * ayy > axy * axy)) return fail(NLSP_ERR_INVALID);
+    op->c9[0] = 2.0 * (axx + ayy) * h2;
+    op->c9[1] = -axx * h2;
+    op->c9[2] = -ayy * h2;
+    op->c9[3] = -0.5 * axy * h2;
+    op->c9[4] = 0.5 * axy * h2;
+  } else {
+    if (cudaMalloc(&op->a64, sizeof(double) * 5 * n) != cudaSuccess) return fail(NLSP_ERR_OOM);
+    if (cudaMalloc(&op->a32, sizeof(float) * 5 * n) != cudaSuccess) return fail(NLSP_ERR_OOM);
+    if (cudaMalloc(&bad, sizeof(int)) != cudaSuccess) return fail(NLSP_ERR_OOM);
+    if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+    if (cudaMemsetAsync(op->a64, 0, sizeof(double) * 5 * n, s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+    double* d = op->a64;
+    const int g = grid_for(ctx, n, 256, 8);
+    if (kind == ST_5PT)
+      k_assemble_5pt<<<g, 256, 0, s>>>((int)N, dev_coeffs, d, d + n, d + 2 * n, d + 4 * n, bad);
+    else
+      k_assemble_7pt<<<g, 256, 0, s>>>((int)N, dev_coeffs, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, bad);
+    k_to_float<<<grid_for(ctx, 5 * n, 256, 8), 256, 0, s>>>(op->a64, op->a32, 5 * n);
+    if (cudaGetLastError() != cudaSuccess) return fail(NLSP_ERR_CUDA);
+    int hbad = 0;
+    if (cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+    cudaFree(bad);
+    bad = nullptr;
+    if (hbad) return fail(NLSP_ERR_INVALID);
+  }
+  // views
+  StencilView<double>& v = op->v64;
+  StencilView<float>& w = op->v32;
+  v.N = w.N = (int)N;
+  v.n = w.n = n;
+  if (op->a64) {
+    v.diag = op->a64; v.cx = op->a64 + n; v.cy = op->a64 + 2 * n; v.cz = op->a64 + 3 * n; v.dinv = op->a64 + 4 * n;
+    w.diag = op->a32; w.cx = op->a32 + n; w.cy = op->a32 + 2 * n; w.cz = op->a32 + 3 * n; w.dinv = op->a32 + 4 * n;
+  }
+  for (int q = 0; q < 5; ++q) {
+    v.c[q] = op->c9[q];
+    w.c[q] = (float)op->c9[q];
+  }
+  v.cdinv = kind == ST_9PT ? 1.0 / op->c9[0] : 0.0;
+  w.cdinv = (float)v.cdinv;
+  *A_out = op;
+  return NLSP_OK;
+}
+
+extern "C" int64_t nlsp_op_size(const nlsp_op* A) { return A ? A->n : -1; }
+
+extern "C" nlsp_status nlsp_op_apply(nlsp_ctx* ctx, const nlsp_op* A, int m, const double* dev_X, int64_t ldx,
+                                     double* dev_Y, int64_t ldy) {
+  if (!ctx || !A || m < 0 || (m > 0 && (!dev_X || !dev_Y)) || ldx < A->n || ldy < A->n || m > 65535)
+    return NLSP_ERR_INVALID;
+  if (m == 0) return NLSP_OK;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  dim3 g(grid_for(ctx, A->n, 256, 8), m);
+  switch (A->kind) {
+    case ST_5PT: k_apply_cols<ST_5PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
+    case ST_9PT: k_apply_cols<ST_9PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
+    default: k_apply_cols<ST_7PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
+  }
+  NLSP_LAUNCH_CHECK();
+  return NLSP_OK;
+}
+
+extern "C" nlsp_status nlsp_op_diagonal(nlsp_ctx* ctx, const nlsp_op* A, double* dev_d) {
+  if (!ctx || !A || !dev_d) return NLSP_ERR_INVALID;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  if (A->kind == ST_9PT) {
+    k_diag_9pt<<<grid_for(ctx, A->n, 256, 8), 256, 0, ctx->stream>>>(A->c9[0], dev_d, A->n);
+    NLSP_LAUNCH_CHECK();
+  } else {
+    NLSP_CUDA(cudaMemcpyAsync(dev_d, A->a64, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  return NLSP_OK;
+}
+
+extern "C" void nlsp_free_op(nlsp_op* A) {
+  if (!A) return;
+  cudaSetDevice(A->device);
+  if (A->a64) cudaFree(A->a64);
+  if (A->a32) cudaFree(A->a32);
+  delete A;
+}

@@ -1,0 +1,917 @@
+// Setup of the two-level preconditioner (Algorithm 1, setup):
+//   S = (I - w D^-1 A)^s1 S0          sample smoothing (Sec. 3, Near-Nullspace Vectors)
+//   P = U_k of S                      thin SVD (Sec. 3, SVD-Centric Construction) via the
+//                                     Gram matrix S^T S: FP32 Jacobi eigensolver, then in
+//                                     FP64 mode Ogita-Aishima refinement and CholeskyQR
+//                                     (P = qf(.), Sec. 3)
+//   A_c = P_r^T A P_r, A_c = L L^T    Galerkin operator and FP64 Cholesky
+//
+// GB300 notes: FP64 runs at 1/62 of the FP32 rate on this part, so every
+// O(n K^2) and O(K^3) step of the mixed path is FP32 (with FP64 cross-block
+// sums), and the FP64 path solves the K x K eigenproblem in FP32 first and
+// refines it with FP64 matrix products instead of running FP64 Jacobi
+// rotations on one SM.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "stencil.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Layout conversion between column-major FP64 (ld = n) and tiled T.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_colmajor_to_tiled(const double* __restrict__ src, int64_t n, int64_t ld, int ncols,
+                                    int64_t n_pad, T* __restrict__ dst) {
+  const int64_t total = n_pad * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / ((int64_t)ncols * NLSP_TILE);
+    const int c = (int)((e / NLSP_TILE) % ncols);
+    const int64_t i = t * NLSP_TILE + (e % NLSP_TILE);
+    dst[e] = i < n ? (T)src[c * ld + i] : T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_tiled_to_colmajor(const T* __restrict__ src, int64_t n, int ncols, int ncols_out,
+                                    double* __restrict__ dst, int64_t ld) {
+  const int64_t total = n * ncols_out;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / n);
+    const int64_t i = e - (int64_t)c * n;
+    dst[c * ld + i] = (double)src[tiled_index(i, c, ncols)];
+  }
+}
+
+// One weighted-Jacobi sweep on A S = 0 for all K columns of a tiled block:
+// S_out = S_in - w D^-1 A S_in.  Padding rows are written as zero.
+template <int KIND, typename T>
+__global__ void k_smooth_sweep(StencilView<T> A, T omega, int ncols, int64_t n_pad, const T* __restrict__ Sin,
+                               T* __restrict__ Sout) {
+  const int64_t total = n_pad * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / ((int64_t)ncols * NLSP_TILE);
+    const int c = (int)((e / NLSP_TILE) % ncols);
+    const int64_t i = t * NLSP_TILE + (e % NLSP_TILE);
+    if (i >= A.n) {
+      Sout[e] = T(0);
+      continue;
+    }
+    const NodeCoord nc = node_coord<KIND>(i, A.N);
+    const T as = stencil_apply<KIND>(A, i, nc, [&](int64_t m) { return Sin[tiled_index(m, c, ncols)]; });
+    Sout[e] = Sin[e] - omega * stencil_dinv<KIND>(A, i) * as;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tall-skinny products over node tiles: partial[b] = sum over the tiles of
+// block b of X_t^T Y_t (ncx x ncy block of the first ncx / ncy columns), with
+// Y = X or Y = A X (evaluated on the fly from X's neighbour rows).  Thread
+// (ty, tx) of a TD x TD block owns an RB x RB register tile of the output.
+// The tile's node chunk is staged transposed in shared memory ([w][c]) so the
+// inner loop reads contiguous float4/double2 rows.  FP32 inputs accumulate in
+// FP32 within a block and leave as FP64 partials.
+// ---------------------------------------------------------------------------
+constexpr int GRAM_CW = 32;  // nodes per staged chunk
+
+template <typename T, int RB, int TD, int KIND, bool WITH_A>
+__global__ void __launch_bounds__(TD* TD) k_tsgemm(StencilView<T> A, const T* __restrict__ X, int ncols, int ncx,
+                                                  int64_t n_pad, double* __restrict__ partial) {
+  constexpr int KP = RB * TD;
+  constexpr int LDS = KP + (sizeof(T) == 4 ? 4 : 2);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);  // [CW][LDS]
+  T* ys = WITH_A ? xs + GRAM_CW * LDS : xs;
+  const int tx = threadIdx.x % TD, ty = threadIdx.x / TD;
+  T acc[RB][RB];
+#pragma unroll
+  for (int a = 0; a < RB; ++a)
+#pragma unroll
+    for (int b = 0; b < RB; ++b) acc[a][b] = T(0);
+
+  const int64_t ntiles = n_pad / NLSP_TILE;
+  const int nthreads = TD * TD;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int w0 = 0; w0 < NLSP_TILE; w0 += GRAM_CW) {
+      __syncthreads();
+      // stage X chunk (and A X chunk) transposed: element (w, c)
+      for (int e = threadIdx.x; e < GRAM_CW * KP; e += nthreads) {
+        const int c = e / GRAM_CW, w = e % GRAM_CW;
+        T xv = T(0), yv = T(0);
+        const int64_t i = t * NLSP_TILE + w0 + w;
+        if (c < ncx) {
+          xv = X[(t * ncols + c) * NLSP_TILE + w0 + w];
+          if (WITH_A && i < A.n) {
+            const NodeCoord nc = node_coord<KIND>(i, A.N);
+            yv = stencil_apply<KIND>(A, i, nc, [&](int64_t m) { return X[tiled_index(m, c, ncols)]; });
+          }
+        }
+        xs[w * LDS + c] = xv;
+        if (WITH_A) ys[w * LDS + c] = yv;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int w = 0; w < GRAM_CW; ++w) {
+        T xa[RB], yb[RB];
+#pragma unroll
+        for (int a = 0; a < RB; ++a) xa[a] = xs[w * LDS + ty * RB + a];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) yb[b] = ys[w * LDS + tx * RB + b];
+#pragma unroll
+        for (int a = 0; a < RB; ++a)
+#pragma unroll
+          for (int b = 0; b < RB; ++b) acc[a][b] += xa[a] * yb[b];
+      }
+    }
+  }
+  double* out = partial + (int64_t)blockIdx.x * ncx * ncx;
+#pragma unroll
+  for (int a = 0; a < RB; ++a) {
+    const int row = ty * RB + a;
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      const int col = tx * RB + b;
+      if (row < ncx && col < ncx) out[(int64_t)col * ncx + row] = (double)acc[a][b];
+    }
+  }
+}
+
+// out[e] = sum_b partial[b][e] in block order (deterministic), optionally
+// symmetrised: out = (M + M^T) / 2 for an m x m matrix.
+__global__ void k_sum_partials(const double* __restrict__ partial, int nblocks, int m, int symmetrize,
+                               double* __restrict__ out) {
+  const int mm = m * m;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * mm + e];
+    if (symmetrize) {
+      const int i = e % m, j = e / m;
+      double s2 = 0.0;
+      const int et = i * m + j;
+      for (int b = 0; b < nblocks; ++b) s2 += partial[(int64_t)b * mm + et];
+      s = 0.5 * (s + s2);
+    }
+    out[e] = s;
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Symmetric eigensolver for the K x K Gram matrix, one CTA, FP32: cyclic
+// Jacobi (Golub & Van Loan, sym.schur2 rotations) with the round-robin
+// ordering, so each round applies K/2 disjoint rotations at once.  With all
+// rotations of a round disjoint, G' = J^T G J acts on 2 x 2 blocks
+// independently: block (u, v) -> J_u^T B J_v, so a thread owning block
+// (u <= v) updates it and its mirror without synchronising with others.
+// Eigenvectors are accumulated as rows of Vt (V = Vt^T), sorted descending.
+// KP is the padded even order; a padded index has zero row/column and is
+// never rotated.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rr_pair(int KP, int r, int u, int* p, int* q) {
+  if (u == 0) {
+    *p = KP - 1;
+    *q = r;
+  } else {
+    *p = (r + u) % (KP - 1);
+    *q = (r - u + (KP - 1)) % (KP - 1);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ G, int K, int KP, int max_sweeps,
+                                                     float tol, double* __restrict__ evals,
+                                                     double* __restrict__ V) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LG = KP + 1;
+  float* g = reinterpret_cast<float*>(smem_raw);  // [KP][LG]
+  float* vt = g + KP * LG;                         // [KP][KP], row a = eigenvector a
+  float* cs = vt + KP * KP;                        // [KP/2][2]
+  int* pq = reinterpret_cast<int*>(cs + KP);       // [KP/2][2]
+  float* red = reinterpret_cast<float*>(pq + KP);  // [32]
+  __shared__ int converged;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int H = KP / 2;
+
+  for (int e = tid; e < KP * KP; e += nt) {
+    const int a = e / KP, b = e % KP;
+    g[a * LG + b] = (a < K && b < K) ? (float)G[(int64_t)b * K + a] : 0.0f;
+    vt[a * KP + b] = (a == b) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence test: off-diagonal mass against the diagonal
+    float off = 0.0f, dia = 0.0f;
+    for (int e = tid; e < KP * KP; e += nt) {
+      const int a = e / KP, b = e % KP;
+      const float x = g[a * LG + b];
+      if (a == b) dia += x * x; else off += x * x;
+    }
+    off = block_sum(off, red);
+    dia = block_sum(dia, red);
+    if (tid == 0) converged = (off <= tol * tol * dia);
+    __syncthreads();
+    if (converged) break;
+
+    for (int r = 0; r < KP - 1; ++r) {
+      for (int u = tid; u < H; u += nt) {
+        int p, q;
+        rr_pair(KP, r, u, &p, &q);
+        const float gpp = g[p * LG + p], gqq = g[q * LG + q], gpq = g[p * LG + q];
+        float c = 1.0f, s = 0.0f;
+        if (gpq != 0.0f && fabsf(gpq) > 1e-30f) {
+          const float tau = (gqq - gpp) / (2.0f * gpq);
+          const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+          c = rsqrtf(1.0f + t * t);
+          s = t * c;
+        }
+        cs[2 * u] = c;
+        cs[2 * u + 1] = s;
+        pq[2 * u] = p;
+        pq[2 * u + 1] = q;
+      }
+      __syncthreads();
+      // 2x2 block updates, u <= v
+      const int nblk = H * (H + 1) / 2;
+      for (int e = tid; e < nblk; e += nt) {
+        // invert the triangular index: e -> (u, v), u <= v
+        int u = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+        while (u * (u + 1) / 2 > e) --u;
+        while ((u + 1) * (u + 2) / 2 <= e) ++u;
+        const int v = e - u * (u + 1) / 2;  // v <= u
+        const int pu = pq[2 * u], qu = pq[2 * u + 1], pv = pq[2 * v], qv = pq[2 * v + 1];
+        const float cu = cs[2 * u], su = cs[2 * u + 1], cv = cs[2 * v], sv = cs[2 * v + 1];
+        if (u == v) {
+          const float gpp = g[pu * LG + pu], gqq = g[qu * LG + qu], gpq = g[pu * LG + qu];
+          const float t = su / cu;
+          g[pu * LG + pu] = gpp - t * gpq;
+          g[qu * LG + qu] = gqq + t * gpq;
+          g[pu * LG + qu] = 0.0f;
+          g[qu * LG + pu] = 0.0f;
+        } else {
+          const float b00 = g[pu * LG + pv], b01 = g[pu * LG + qv], b10 = g[qu * LG + pv], b11 = g[qu * LG + qv];
+          const float m00 = cu * b00 - su * b10, m01 = cu * b01 - su * b11;
+          const float m10 = su * b00 + cu * b10, m11 = su * b01 + cu * b11;
+          const float n00 = m00 * cv - m01 * sv, n01 = m00 * sv + m01 * cv;
+          const float n10 = m10 * cv - m11 * sv, n11 = m10 * sv + m11 * cv;
+          g[pu * LG + pv] = n00; g[pu * LG + qv] = n01; g[qu * LG + pv] = n10; g[qu * LG + qv] = n11;
+          g[pv * LG + pu] = n00; g[qv * LG + pu] = n01; g[pv * LG + qu] = n10; g[qv * LG + qu] = n11;
+        }
+      }
+      // V <- V J: rows p, q of Vt
+      for (int e = tid; e < H * KP; e += nt) {
+        const int u = e / KP, row = e % KP;
+        const int p = pq[2 * u], q = pq[2 * u + 1];
+        const float c = cs[2 * u], s = cs[2 * u + 1];
+        const float vp = vt[p * KP + row], vq = vt[q * KP + row];
+        vt[p * KP + row] = c * vp - s * vq;
+        vt[q * KP + row] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // sort descending (ties by index) and write out
+  for (int a = tid; a < K; a += nt) {
+    const float la = g[a * LG + a];
+    int pos = 0;
+    for (int b = 0; b < K; ++b) {
+      const float lb = g[b * LG + b];
+      pos += (lb > la) || (lb == la && b < a);
+    }
+    evals[pos] = (double)la;
+    for (int row = 0; row < K; ++row) V[(int64_t)pos * K + row] = (double)vt[a * KP + row];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small dense FP64 products for the K x K refinement: C = op(A) * B, all
+// column-major K x K; one block per output column.
+// ---------------------------------------------------------------------------
+__global__ void k_small_gemm(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
+                             int K, int transA) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* bcol = reinterpret_cast<double*>(smem_raw);
+  const int j = blockIdx.x;
+  for (int m = threadIdx.x; m < K; m += blockDim.x) bcol[m] = B[(int64_t)j * K + m];
+  __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double s = 0.0;
+    if (transA)
+      for (int m = 0; m < K; ++m) s += A[(int64_t)i * K + m] * bcol[m];
+    else
+      for (int m = 0; m < K; ++m) s += A[(int64_t)m * K + i] * bcol[m];
+    C[(int64_t)j * K + i] = s;
+  }
+}
+
+// Ogita & Aishima, "Iterative refinement for symmetric eigenvalue
+// decomposition" (Japan J. Indust. Appl. Math., 2018), one step, given
+// XtX = X^T X and S = X^T G X:  R = I - XtX, lambda_i = S_ii / (1 - R_ii),
+// E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i) when the gap exceeds
+// delta = 2 (||S - diag(lambda)|| + ||G|| ||R||), else R_ij / 2; E_ii = R_ii / 2.
+// Writes E and lambda; the caller forms X <- X + X E.  One block.
+__global__ void k_oa_step(const double* __restrict__ XtX, const double* __restrict__ S, int K, double* __restrict__ E,
+                          double* __restrict__ lam) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < K; i += nt) {
+    const double rii = 1.0 - XtX[(int64_t)i * K + i];
+    lam[i] = S[(int64_t)i * K + i] / (1.0 - rii);
+  }
+  __syncthreads();
+  double so = 0.0, rr = 0.0, lmax = 0.0;
+  for (int e = tid; e < K * K; e += nt) {
+    const int i = e % K, j = e / K;
+    const double r = (i == j ? 1.0 : 0.0) - XtX[e];
+    rr += r * r;
+    if (i != j) so += S[e] * S[e];
+  }
+  for (int i = tid; i < K; i += nt) {
+    const double d = S[(int64_t)i * K + i] - lam[i];
+    so += d * d;
+    lmax = fmax(lmax, fabs(lam[i]));
+  }
+  so = block_sum(so, red);
+  rr = block_sum(rr, red);
+  // max via sum of a one-hot is not possible; reduce max with a loop
+  __shared__ double mx;
+  if (tid == 0) mx = 0.0;
+  __syncthreads();
+  for (int i = 0; i < nt; ++i) {
+    if (tid == i) mx = fmax(mx, lmax);
+    __syncthreads();
+  }
+  const double delta = 2.0 * (sqrt(so) + mx * sqrt(rr));
+  for (int e = tid; e < K * K; e += nt) {
+    const int i = e % K, j = e / K;
+    const double r = (i == j ? 1.0 : 0.0) - XtX[e];
+    double v;
+    if (i == j) v = 0.5 * r;
+    else if (fabs(lam[j] - lam[i]) > delta) v = (S[e] + lam[j] * r) / (lam[j] - lam[i]);
+    else v = 0.5 * r;
+    E[e] = v;
+  }
+}
+
+__global__ void k_add(double* __restrict__ X, const double* __restrict__ Y, int count) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) X[e] += Y[e];
+}
+
+// Sorts eigenpairs descending: lam (K), X (K x K, columns) -> evals, V.
+__global__ void k_sort_eig(const double* __restrict__ lam, const double* __restrict__ X, int K,
+                           double* __restrict__ evals, double* __restrict__ V) {
+  for (int a = threadIdx.x; a < K; a += blockDim.x) {
+    const double la = lam[a];
+    int pos = 0;
+    for (int b = 0; b < K; ++b) pos += (lam[b] > la) || (lam[b] == la && b < a);
+    evals[pos] = la;
+    for (int row = 0; row < K; ++row) V[(int64_t)pos * K + row] = X[(int64_t)a * K + row];
+  }
+}
+
+// M = V[:, :k] diag(1 / sqrt(lambda)) as T (K x k, row-major: M[c * k + j]);
+// sigma = sqrt(lambda).  Flags a non-positive lambda_j (j < k).
+template <typename T>
+__global__ void k_make_basis_coeffs(const double* __restrict__ evals, const double* __restrict__ V, int K, int k,
+                                    T* __restrict__ M, double* __restrict__ sigma, int* status) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * k; e += gridDim.x * blockDim.x) {
+    const int c = e / k, j = e % k;
+    const double lj = evals[j];
+    M[e] = lj > 0.0 ? (T)(V[(int64_t)j * K + c] / sqrt(lj)) : T(0);
+  }
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+      const double lj = evals[j];
+      sigma[j] = lj > 0.0 ? sqrt(lj) : 0.0;
+      if (j < k && !(lj > 0.0)) atomicExch(status, (int)NLSP_ERR_NOT_SPD);
+    }
+}
+
+// Out_t = In_t * M for every node tile: In tiled with `ncin` columns, M is
+// ncin x k (row-major), Out tiled with k columns.  One thread per node of a
+// tile; outputs in register chunks of KC columns.
+template <typename T, int KC>
+__global__ void __launch_bounds__(NLSP_TILE) k_tile_times_small(const T* __restrict__ In, int ncin,
+                                                               const T* __restrict__ Mg, int k, int64_t n_pad,
+                                                               T* __restrict__ Out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* M = reinterpret_cast<T*>(smem_raw);
+  for (int e = threadIdx.x; e < ncin * k; e += blockDim.x) M[e] = Mg[e];
+  __syncthreads();
+  const int64_t ntiles = n_pad / NLSP_TILE;
+  const int w = threadIdx.x;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const T* in = In + t * ncin * NLSP_TILE + w;
+    T* out = Out + t * (int64_t)k * NLSP_TILE + w;
+    for (int j0 = 0; j0 < k; j0 += KC) {
+      T acc[KC];
+#pragma unroll
+      for (int j = 0; j < KC; ++j) acc[j] = T(0);
+      for (int c = 0; c < ncin; ++c) {
+        const T s = in[(int64_t)c * NLSP_TILE];
+        const T* mrow = M + c * k + j0;
+#pragma unroll
+        for (int j = 0; j < KC; ++j)
+          if (j0 + j < k) acc[j] += s * mrow[j];
+      }
+#pragma unroll
+      for (int j = 0; j < KC; ++j)
+        if (j0 + j < k) out[(int64_t)(j0 + j) * NLSP_TILE] = acc[j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense FP64 Cholesky A = L L^T of an m x m SPD matrix in one CTA (shared
+// memory, right-looking), then the inverse A^-1 = L^-T L^-1 column by column.
+// A non-positive or non-finite pivot sets NLSP_ERR_NOT_SPD.
+// ---------------------------------------------------------------------------
+__global__ void k_cholesky(const double* __restrict__ Ain, int m, double* __restrict__ Lout, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* a = reinterpret_cast<double*>(smem_raw);  // column-major m x m
+  __shared__ int bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < m * m; e += nt) a[e] = Ain[e];
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0) {
+      const double d = a[j * m + j];
+      if (!(d > 0.0) || !isfinite(d)) bad = 1;
+      else a[j * m + j] = sqrt(d);
+    }
+    __syncthreads();
+    if (bad) break;
+    const double ljj = a[j * m + j];
+    for (int i = j + 1 + tid; i < m; i += nt) a[j * m + i] /= ljj;
+    __syncthreads();
+    // trailing update of the lower triangle: a[i][c] -= a[i][j] a[c][j], j < c <= i
+    const int rem = m - j - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      const int c = j + 1 + e / rem, i = j + 1 + e % rem;
+      if (i >= c) a[c * m + i] -= a[j * m + i] * a[j * m + c];
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && bad) atomicExch(status, (int)NLSP_ERR_NOT_SPD);
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e % m, c = e / m;
+    Lout[e] = (i >= c && !bad) ? a[e] : 0.0;
+  }
+}
+
+// Column q of A^-1 = L^-T L^-1 e_q by one warp: forward then backward
+// substitution, each step a warp-parallel dot product.
+__global__ void k_spd_inverse_cols(const double* __restrict__ L, int m, double* __restrict__ Ainv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* y = reinterpret_cast<double*>(smem_raw);
+  const int q = blockIdx.x, lane = threadIdx.x;
+  for (int i = 0; i < m; ++i) {  // L y = e_q
+    double s = 0.0;
+    for (int c = lane; c < i; c += 32) s += L[(int64_t)c * m + i] * y[c];
+    s = warp_sum(s);
+    if (lane == 0) y[i] = ((i == q ? 1.0 : 0.0) - s) / L[(int64_t)i * m + i];
+    __syncwarp();
+  }
+  for (int i = m - 1; i >= 0; --i) {  // L^T x = y  (x overwrites y)
+    double s = 0.0;
+    for (int c = i + 1 + lane; c < m; c += 32) s += L[(int64_t)i * m + c] * y[c];
+    s = warp_sum(s);
+    if (lane == 0) y[i] = (y[i] - s) / L[(int64_t)i * m + i];
+    __syncwarp();
+  }
+  for (int i = lane; i < m; i += 32) Ainv[(int64_t)q * m + i] = y[i];
+}
+
+__global__ void k_symmetrize(double* __restrict__ M, int m) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int i = e % m, j = e / m;
+    if (i < j) {
+      const double v = 0.5 * (M[e] + M[(int64_t)i * m + j]);
+      M[e] = v;
+      M[(int64_t)i * m + j] = v;
+    }
+  }
+}
+
+}  // namespace
+
+// ============================================================================
+// Host orchestration
+// ============================================================================
+namespace {
+
+template <typename T>
+const StencilView<T>& view_of(const nlsp_op* A);
+template <>
+const StencilView<double>& view_of<double>(const nlsp_op* A) { return A->v64; }
+template <>
+const StencilView<float>& view_of<float>(const nlsp_op* A) { return A->v32; }
+
+nlsp_status set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return NLSP_OK;
+}
+
+// X_t^T Y_t summed over all tiles -> out (ncx x ncx FP64, column-major),
+// Y = X or A X.  partial: scratch of >= blocks * ncx^2 doubles.
+template <typename T, bool WITH_A>
+nlsp_status tsgemm(nlsp_ctx* ctx, const nlsp_op* A, const T* X, int ncols, int ncx, int64_t n_pad, double* partial,
+                   double* out, int symmetrize) {
+  const int blocks = ctx->num_sms;
+  cudaStream_t s = ctx->stream;
+#define NLSP_TSGEMM_LAUNCH(RB, TD)                                                                     \
+  do {                                                                                                \
+    constexpr int LDS_ = RB * TD + (sizeof(T) == 4 ? 4 : 2);                                          \
+    const size_t sm = (size_t)GRAM_CW * LDS_ * sizeof(T) * (WITH_A ? 2 : 1);                          \
+    NLSP_DISPATCH_KIND(A->kind, KD, {                                                                 \
+      auto fn = k_tsgemm<T, RB, TD, KD, WITH_A>;                                                      \
+      NLSP_TRY(set_smem((const void*)fn, sm));                                                        \
+      fn<<<blocks, TD * TD, sm, s>>>(view_of<T>(A), X, ncols, ncx, n_pad, partial);                   \
+    });                                                                                               \
+  } while (0)
+  if (ncx <= 32) NLSP_TSGEMM_LAUNCH(2, 16);
+  else if (ncx <= 64) NLSP_TSGEMM_LAUNCH(4, 16);
+  else if (ncx <= 128) NLSP_TSGEMM_LAUNCH(8, 16);
+  else return NLSP_ERR_INVALID;
+#undef NLSP_TSGEMM_LAUNCH
+  NLSP_LAUNCH_CHECK();
+  k_sum_partials<<<div_up((int64_t)ncx * ncx, 256), 256, 0, s>>>(partial, blocks, ncx, symmetrize, out);
+  NLSP_LAUNCH_CHECK();
+  return NLSP_OK;
+}
+
+template <typename T>
+nlsp_status tile_times_small(nlsp_ctx* ctx, const T* In, int ncin, const T* M, int k, int64_t n_pad, T* Out) {
+  const size_t sm = (size_t)ncin * k * sizeof(T);
+  auto fn = k_tile_times_small<T, 32>;
+  NLSP_TRY(set_smem((const void*)fn, sm));
+  const int64_t ntiles = n_pad / NLSP_TILE;
+  const int g = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 8);
+  fn<<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
+  NLSP_LAUNCH_CHECK();
+  return NLSP_OK;
+}
+
+// Smooths the tiled sample block in place (ping-pong through `tmp`); returns
+// the buffer holding the result.
+template <typename T>
+nlsp_status smooth_tiled(nlsp_ctx* ctx, const nlsp_op* A, int K, int s1, double omega, int64_t n_pad, T* a, T* tmp,
+                         T** result) {
+  T* src = a;
+  T* dst = tmp;
+  const int g = grid_for(ctx, n_pad * K, 256, 8);
+  for (int it = 0; it < s1; ++it) {
+    NLSP_DISPATCH_KIND(A->kind, KD, {
+      k_smooth_sweep<KD, T><<<g, 256, 0, ctx->stream>>>(view_of<T>(A), (T)omega, K, n_pad, src, dst);
+    });
+    NLSP_LAUNCH_CHECK();
+    std::swap(src, dst);
+  }
+  *result = src;
+  return NLSP_OK;
+}
+
+nlsp_status check_setup_params(const nlsp_op* A, const nlsp_setup_params* p, bool need_K) {
+  if (!A || !p) return NLSP_ERR_INVALID;
+  if (p->precision != NLSP_FP64 && p->precision != NLSP_MIXED_FP32) return NLSP_ERR_INVALID;
+  if (p->k < 1 || p->k > 128 || p->k > A->n) return NLSP_ERR_INVALID;
+  if (need_K && (p->K < p->k || p->K > 128 || p->K > A->n || p->s1 < 0)) return NLSP_ERR_INVALID;
+  if (p->nu1 < 1 || p->nu2 != p->nu1 || p->nu1 > 64) return NLSP_ERR_INVALID;
+  if (!(p->omega > 0.0) || !(p->omega < 2.0)) return NLSP_ERR_INVALID;
+  return NLSP_OK;
+}
+
+nlsp_prec* new_prec(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* p, int k, int K) {
+  nlsp_prec* M = new nlsp_prec();
+  memset(M, 0, sizeof(*M));
+  M->ctx = ctx;
+  M->device = ctx->device;
+  M->A = A;
+  M->precision = p->precision;
+  M->n = A->n;
+  M->n_pad = pad_tile(A->n);
+  M->k = k;
+  M->r = k;
+  M->K = K;
+  M->nu1 = p->nu1;
+  M->nu2 = p->nu2;
+  M->omega = p->omega;
+  M->rblocks = 2 * ctx->num_sms;
+  return M;
+}
+
+nlsp_status alloc_prec_storage(nlsp_prec* M) {
+  const size_t tsz = M->precision == NLSP_FP64 ? sizeof(double) : sizeof(float);
+  const int k = M->k;
+  NLSP_CUDA(cudaMalloc(&M->P, tsz * M->n_pad * k));
+  NLSP_CUDA(cudaMalloc(&M->sigma, sizeof(double) * std::max(M->K, 1)));
+  NLSP_CUDA(cudaMalloc(&M->Ac, sizeof(double) * k * k));
+  NLSP_CUDA(cudaMalloc(&M->L, sizeof(double) * k * k));
+  NLSP_CUDA(cudaMalloc(&M->Ainv, sizeof(double) * k * k));
+  NLSP_CUDA(cudaMalloc(&M->cpart, sizeof(double) * (size_t)M->rblocks * k));
+  NLSP_CUDA(cudaMalloc(&M->ec, sizeof(double) * k));
+  NLSP_CUDA(cudaMalloc(&M->counter, sizeof(unsigned) * 8));
+  NLSP_CUDA(cudaMalloc(&M->status, sizeof(int)));
+  NLSP_CUDA(cudaMalloc(&M->w0, tsz * M->n_pad));
+  NLSP_CUDA(cudaMalloc(&M->w1, tsz * M->n_pad));
+  NLSP_CUDA(cudaMemsetAsync(M->sigma, 0, sizeof(double) * std::max(M->K, 1), M->ctx->stream));
+  NLSP_CUDA(cudaMemsetAsync(M->counter, 0, sizeof(unsigned) * 8, M->ctx->stream));
+  NLSP_CUDA(cudaMemsetAsync(M->status, 0, sizeof(int), M->ctx->stream));
+  return NLSP_OK;
+}
+
+// Eigen-decomposition of the FP64 Gram matrix G (K x K): descending evals and
+// eigenvectors V (column-major).  refine = number of FP64 refinement steps.
+nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double* evals, double* V) {
+  cudaStream_t s = ctx->stream;
+  const int KP = K + (K & 1);
+  const size_t sm = (size_t)KP * (KP + 1) * 4 + (size_t)KP * KP * 4 + (size_t)KP * 4 + (size_t)KP * 4 + 32 * 4;
+  NLSP_TRY(set_smem((const void*)k_jacobi_eig, sm));
+  k_jacobi_eig<<<1, 1024, sm, s>>>(G, K, KP, 30, 2e-7f, evals, V);
+  NLSP_LAUNCH_CHECK();
+  if (refine > 0) {
+    DevBuf buf;
+    NLSP_TRY(buf.alloc(sizeof(double) * (size_t)K * K * 5 + sizeof(double) * K));
+    double* XtX = buf.as<double>();
+    double* GX = XtX + K * K;
+    double* S = GX + K * K;
+    double* E = S + K * K;
+    double* XE = E + K * K;
+    double* lam = XE + K * K;
+    const size_t gsm = sizeof(double) * K;
+    const int th = K < 128 ? 128 : 256;
+    for (int it = 0; it < refine; ++it) {
+      k_small_gemm<<<K, th, gsm, s>>>(V, V, XtX, K, 1);
+      k_small_gemm<<<K, th, gsm, s>>>(G, V, GX, K, 0);
+      k_small_gemm<<<K, th, gsm, s>>>(V, GX, S, K, 1);
+      k_oa_step<<<1, 256, 0, s>>>(XtX, S, K, E, lam);
+      k_small_gemm<<<K, th, gsm, s>>>(V, E, XE, K, 0);
+      k_add<<<div_up((int64_t)K * K, 256), 256, 0, s>>>(V, XE, K * K);
+      NLSP_LAUNCH_CHECK();
+    }
+    // eigenvalues of the refined basis: Rayleigh quotients of the final X
+    k_small_gemm<<<K, th, gsm, s>>>(V, V, XtX, K, 1);
+    k_small_gemm<<<K, th, gsm, s>>>(G, V, GX, K, 0);
+    k_small_gemm<<<K, th, gsm, s>>>(V, GX, S, K, 1);
+    k_oa_step<<<1, 256, 0, s>>>(XtX, S, K, E, lam);
+    DevBuf vcopy;
+    NLSP_TRY(vcopy.alloc(sizeof(double) * (size_t)K * K));
+    NLSP_CUDA(cudaMemcpyAsync(vcopy.p, V, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
+    k_sort_eig<<<1, 256, 0, s>>>(lam, vcopy.as<double>(), K, evals, V);
+    NLSP_LAUNCH_CHECK();
+    NLSP_CUDA(cudaStreamSynchronize(s));  // buffers are freed at scope exit
+  }
+  return NLSP_OK;
+}
+
+// P (tiled T, k columns) from the tiled smoothed samples S (K columns).
+template <typename T>
+nlsp_status basis_from_samples(nlsp_ctx* ctx, nlsp_prec* M, const T* S, double* partial) {
+  cudaStream_t s = ctx->stream;
+  const int K = M->K, k = M->k;
+  DevBuf gbuf;
+  NLSP_TRY(gbuf.alloc(sizeof(double) * ((size_t)K * K * 2 + K) + sizeof(T) * (size_t)K * k));
+  double* G = gbuf.as<double>();
+  double* V = G + K * K;
+  double* evals = V + K * K;
+  T* Mc = reinterpret_cast<T*>(evals + K);
+  NLSP_TRY((tsgemm<T, false>(ctx, M->A, S, K, K, M->n_pad, partial, G, 0)));
+  const int refine = M->precision == NLSP_FP64 ? 2 : 0;
+  NLSP_TRY(gram_eigen(ctx, G, K, refine, evals, V));
+  k_make_basis_coeffs<T><<<div_up((int64_t)K * k, 256), 256, 0, s>>>(evals, V, K, k, Mc, M->sigma, M->status);
+  NLSP_LAUNCH_CHECK();
+  NLSP_TRY(tile_times_small<T>(ctx, S, K, Mc, k, M->n_pad, (T*)M->P));
+  NLSP_CUDA(cudaStreamSynchronize(s));
+  return NLSP_OK;
+}
+
+// CholeskyQR re-orthonormalisation P <- P L^-T with P^T P = L L^T (the thin-Q
+// factor qf of Sec. 3, up to column signs).
+template <typename T>
+nlsp_status cholesky_qr(nlsp_ctx* ctx, nlsp_prec* M, double* partial) {
+  cudaStream_t s = ctx->stream;
+  const int k = M->k;
+  DevBuf buf, pbuf;
+  NLSP_TRY(buf.alloc(sizeof(double) * (size_t)k * k * 3 + sizeof(T) * (size_t)k * k));
+  double* Gp = buf.as<double>();
+  double* Lp = Gp + k * k;
+  double* Linv = Lp + k * k;
+  T* Mt = reinterpret_cast<T*>(Linv + k * k);
+  NLSP_TRY((tsgemm<T, false>(ctx, M->A, (const T*)M->P, k, k, M->n_pad, partial, Gp, 1)));
+  NLSP_TRY(set_smem((const void*)k_cholesky, sizeof(double) * k * k));
+  k_cholesky<<<1, 256, sizeof(double) * k * k, s>>>(Gp, k, Lp, M->status);
+  NLSP_LAUNCH_CHECK();
+  // With P^T P = L L^T:  (L L^T)^-1 L = L^-T, so P L^-T needs only the SPD
+  // inverse kernel and one small product.
+  NLSP_TRY(set_smem((const void*)k_spd_inverse_cols, sizeof(double) * k));
+  k_spd_inverse_cols<<<k, 32, sizeof(double) * k, s>>>(Lp, k, Linv);  // Linv := (L L^T)^-1
+  NLSP_LAUNCH_CHECK();
+  DevBuf wbuf;
+  NLSP_TRY(wbuf.alloc(sizeof(double) * (size_t)k * k));
+  k_small_gemm<<<k, 128, sizeof(double) * k, s>>>(Linv, Lp, wbuf.as<double>(), k, 0);  // L^-T
+  NLSP_LAUNCH_CHECK();
+  // Mt (row-major k x k: Mt[c * k + j]) = (L^-T)[c][j]
+  {
+    std::vector<double> hw((size_t)k * k);
+    NLSP_CUDA(cudaMemcpyAsync(hw.data(), wbuf.p, sizeof(double) * k * k, cudaMemcpyDeviceToHost, s));
+    NLSP_CUDA(cudaStreamSynchronize(s));
+    std::vector<T> hm((size_t)k * k);
+    for (int c = 0; c < k; ++c)
+      for (int j = 0; j < k; ++j) hm[(size_t)c * k + j] = (T)hw[(size_t)j * k + c];
+    NLSP_CUDA(cudaMemcpyAsync(Mt, hm.data(), sizeof(T) * k * k, cudaMemcpyHostToDevice, s));
+  }
+  NLSP_TRY(pbuf.alloc(sizeof(T) * M->n_pad * k));
+  NLSP_TRY(tile_times_small<T>(ctx, (const T*)M->P, k, Mt, k, M->n_pad, pbuf.as<T>()));
+  NLSP_CUDA(cudaStreamSynchronize(s));
+  cudaFree(M->P);
+  M->P = pbuf.release();
+  return NLSP_OK;
+}
+
+template <typename T>
+nlsp_status build_impl(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* p, const double* S0,
+                       nlsp_prec** out) {
+  nlsp_prec* M = new_prec(ctx, A, p, p->k, p->K);
+  nlsp_status st = alloc_prec_storage(M);
+  if (st != NLSP_OK) {
+    nlsp_free_prec(M);
+    return st;
+  }
+  auto fail = [&](nlsp_status e) {
+    nlsp_free_prec(M);
+    return e;
+  };
+  cudaStream_t s = ctx->stream;
+  const int K = p->K;
+  DevBuf sa, sb, part;
+  if ((st = sa.alloc(sizeof(T) * M->n_pad * K)) != NLSP_OK) return fail(st);
+  if ((st = sb.alloc(sizeof(T) * M->n_pad * K)) != NLSP_OK) return fail(st);
+  if ((st = part.alloc(sizeof(double) * (size_t)ctx->num_sms * 128 * 128)) != NLSP_OK) return fail(st);
+  k_colmajor_to_tiled<T><<<grid_for(ctx, M->n_pad * K, 256, 8), 256, 0, s>>>(S0, A->n, A->n, K, M->n_pad,
+                                                                               sa.as<T>());
+  if (cudaGetLastError() != cudaSuccess) return fail(NLSP_ERR_CUDA);
+  T* S = nullptr;
+  if ((st = smooth_tiled<T>(ctx, A, K, p->s1, p->omega, M->n_pad, sa.as<T>(), sb.as<T>(), &S)) != NLSP_OK)
+    return fail(st);
+  if ((st = basis_from_samples<T>(ctx, M, S, part.as<double>())) != NLSP_OK) return fail(st);
+  int hstat = 0;
+  if (cudaMemcpy(&hstat, M->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+  if (hstat != 0) return fail((nlsp_status)hstat);
+  if (p->precision == NLSP_FP64)
+    if ((st = cholesky_qr<T>(ctx, M, part.as<double>())) != NLSP_OK) return fail(st);
+  if ((st = nlsp_internal_factor(ctx, M, M->k)) != NLSP_OK) return fail(st);
+  *out = M;
+  return NLSP_OK;
+}
+
+template <typename T>
+nlsp_status from_basis_impl(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* p, const double* P, int k,
+                            nlsp_prec** out) {
+  nlsp_prec* M = new_prec(ctx, A, p, k, 0);
+  nlsp_status st = alloc_prec_storage(M);
+  if (st != NLSP_OK) {
+    nlsp_free_prec(M);
+    return st;
+  }
+  k_colmajor_to_tiled<T><<<grid_for(ctx, M->n_pad * k, 256, 8), 256, 0, ctx->stream>>>(P, A->n, A->n, k, M->n_pad,
+                                                                                         (T*)M->P);
+  if (cudaGetLastError() != cudaSuccess) {
+    nlsp_free_prec(M);
+    return NLSP_ERR_CUDA;
+  }
+  if ((st = nlsp_internal_factor(ctx, M, k)) != NLSP_OK) {
+    nlsp_free_prec(M);
+    return st;
+  }
+  *out = M;
+  return NLSP_OK;
+}
+
+}  // namespace
+
+// A_c = P_r^T A P_r (FP64 result), Cholesky and explicit inverse.
+nlsp_status nlsp_internal_factor(nlsp_ctx* ctx, nlsp_prec* M, int r) {
+  cudaStream_t s = ctx->stream;
+  DevBuf part;
+  NLSP_TRY(part.alloc(sizeof(double) * (size_t)ctx->num_sms * r * r));
+  NLSP_CUDA(cudaMemsetAsync(M->status, 0, sizeof(int), s));
+  if (M->precision == NLSP_FP64)
+    NLSP_TRY((tsgemm<double, true>(ctx, M->A, (const double*)M->P, M->k, r, M->n_pad, part.as<double>(), M->Ac, 1)));
+  else
+    NLSP_TRY((tsgemm<float, true>(ctx, M->A, (const float*)M->P, M->k, r, M->n_pad, part.as<double>(), M->Ac, 1)));
+  NLSP_TRY(set_smem((const void*)k_cholesky, sizeof(double) * r * r));
+  k_cholesky<<<1, 256, sizeof(double) * r * r, s>>>(M->Ac, r, M->L, M->status);
+  NLSP_LAUNCH_CHECK();
+  NLSP_TRY(set_smem((const void*)k_spd_inverse_cols, sizeof(double) * r));
+  k_spd_inverse_cols<<<r, 32, sizeof(double) * r, s>>>(M->L, r, M->Ainv);
+  k_symmetrize<<<div_up((int64_t)r * r, 256), 256, 0, s>>>(M->Ainv, r);
+  NLSP_LAUNCH_CHECK();
+  int hstat = 0;
+  NLSP_CUDA(cudaMemcpyAsync(&hstat, M->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NLSP_CUDA(cudaStreamSynchronize(s));
+  if (hstat != 0) return (nlsp_status)hstat;
+  M->r = r;
+  return NLSP_OK;
+}
+
+extern "C" nlsp_status nlsp_smooth_samples(nlsp_ctx* ctx, const nlsp_op* A, int K, int s1, double omega,
+                                           int precision, const double* dev_S0, double* dev_S) {
+  if (!ctx || !A || !dev_S0 || !dev_S || K < 1 || s1 < 0 || !(omega > 0.0) || !(omega < 2.0)) return NLSP_ERR_INVALID;
+  if (precision != NLSP_FP64 && precision != NLSP_MIXED_FP32) return NLSP_ERR_INVALID;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  const int64_t n_pad = pad_tile(A->n);
+  cudaStream_t s = ctx->stream;
+  const size_t tsz = precision == NLSP_FP64 ? 8 : 4;
+  DevBuf a, b;
+  NLSP_TRY(a.alloc(tsz * n_pad * K));
+  NLSP_TRY(b.alloc(tsz * n_pad * K));
+  const int g = grid_for(ctx, n_pad * K, 256, 8);
+  if (precision == NLSP_FP64) {
+    k_colmajor_to_tiled<double><<<g, 256, 0, s>>>(dev_S0, A->n, A->n, K, n_pad, a.as<double>());
+    double* r = nullptr;
+    NLSP_TRY(smooth_tiled<double>(ctx, A, K, s1, omega, n_pad, a.as<double>(), b.as<double>(), &r));
+    k_tiled_to_colmajor<double><<<g, 256, 0, s>>>(r, A->n, K, K, dev_S, A->n);
+  } else {
+    k_colmajor_to_tiled<float><<<g, 256, 0, s>>>(dev_S0, A->n, A->n, K, n_pad, a.as<float>());
+    float* r = nullptr;
+    NLSP_TRY(smooth_tiled<float>(ctx, A, K, s1, omega, n_pad, a.as<float>(), b.as<float>(), &r));
+    k_tiled_to_colmajor<float><<<g, 256, 0, s>>>(r, A->n, K, K, dev_S, A->n);
+  }
+  NLSP_LAUNCH_CHECK();
+  NLSP_CUDA(cudaStreamSynchronize(s));
+  return NLSP_OK;
+}
+
+extern "C" nlsp_status nlsp_build_prolongation(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* params,
+                                               const double* dev_S0, nlsp_prec** M_out) {
+  if (!ctx || !M_out || !dev_S0) return NLSP_ERR_INVALID;
+  *M_out = nullptr;
+  NLSP_TRY(check_setup_params(A, params, true));
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  if (params->precision == NLSP_FP64) return build_impl<double>(ctx, A, params, dev_S0, M_out);
+  return build_impl<float>(ctx, A, params, dev_S0, M_out);
+}
+
+extern "C" nlsp_status nlsp_prec_from_basis(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* params,
+                                            const double* dev_P, int k, nlsp_prec** M_out) {
+  if (!ctx || !M_out || !dev_P || !params) return NLSP_ERR_INVALID;
+  *M_out = nullptr;
+  nlsp_setup_params p = *params;
+  p.k = k;
+  NLSP_TRY(check_setup_params(A, &p, false));
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  if (p.precision == NLSP_FP64) return from_basis_impl<double>(ctx, A, &p, dev_P, k, M_out);
+  return from_basis_impl<float>(ctx, A, &p, dev_P, k, M_out);
+}
+
+extern "C" nlsp_status nlsp_factor_coarse(nlsp_ctx* ctx, const nlsp_op* A, nlsp_prec* M, int r) {
+  if (!ctx || !M || A != M->A || r < 1 || r > M->k) return NLSP_ERR_INVALID;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  return nlsp_internal_factor(ctx, M, r);
+}
+
+extern "C" nlsp_status nlsp_prec_dims(const nlsp_prec* M, int64_t* n, int* k, int* r, int* K, int* precision) {
+  if (!M) return NLSP_ERR_INVALID;
+  if (n) *n = M->n;
+  if (k) *k = M->k;
+  if (r) *r = M->r;
+  if (K) *K = M->K;
+  if (precision) *precision = M->precision;
+  return NLSP_OK;
+}
+
+extern "C" nlsp_status nlsp_prec_copy_basis(nlsp_ctx* ctx, const nlsp_prec* M, double* dev_P) {
+  if (!ctx || !M || !dev_P) return NLSP_ERR_INVALID;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  const int g = grid_for(ctx, M->n * M->k, 256, 8);
+  if (M->precision == NLSP_FP64)
+    k_tiled_to_colmajor<double><<<g, 256, 0, ctx->stream>>>((const double*)M->P, M->n, M->k, M->k, dev_P, M->n);
+  else
+    k_tiled_to_colmajor<float><<<g, 256, 0, ctx->stream>>>((const float*)M->P, M->n, M->k, M->k, dev_P, M->n);
+  NLSP_LAUNCH_CHECK();
+  return NLSP_OK;
+}
+
+extern "C" nlsp_status nlsp_prec_copy_sigma(nlsp_ctx* ctx, const nlsp_prec* M, double* dev_sigma) {
+  if (!ctx || !M || !dev_sigma) return NLSP_ERR_INVALID;
+  if (M->K > 0)
+    NLSP_CUDA(cudaMemcpyAsync(dev_sigma, M->sigma, sizeof(double) * M->K, cudaMemcpyDeviceToDevice, ctx->stream));
+  return NLSP_OK;
+}
+
+extern "C" nlsp_status nlsp_prec_copy_coarse(nlsp_ctx* ctx, const nlsp_prec* M, double* dev_Ac, double* dev_L) {
+  if (!ctx || !M) return NLSP_ERR_INVALID;
+  const size_t b = sizeof(double) * M->r * M->r;
+  if (dev_Ac) NLSP_CUDA(cudaMemcpyAsync(dev_Ac, M->Ac, b, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (dev_L) NLSP_CUDA(cudaMemcpyAsync(dev_L, M->L, b, cudaMemcpyDeviceToDevice, ctx->stream));
+  return NLSP_OK;
+}

@@ -1,0 +1,100 @@
+// Matrix-free stencil evaluation of A (Sec. 3, Eq. discretized_pde) on the
+// structured grids: 2D 5-point and 9-point, 3D 7-point, Dirichlet nodes
+// eliminated.  Every function evaluates in precision T and reads the vector in
+// its own storage type X (so an FP32 preconditioner can read FP64 residuals).
+#pragma once
+
+#include "common.cuh"
+
+struct NodeCoord {
+  int i, j, l;
+};
+
+template <int KIND>
+__device__ __forceinline__ NodeCoord node_coord(int64_t idx, int N) {
+  NodeCoord c;
+  if (KIND == ST_7PT) {
+    const int64_t nn = (int64_t)N * N;
+    c.l = (int)(idx / nn);
+    const int rem = (int)(idx - (int64_t)c.l * nn);
+    c.j = rem / N;
+    c.i = rem - c.j * N;
+  } else {
+    c.j = (int)(idx / N);
+    c.i = (int)(idx - (int64_t)c.j * N);
+    c.l = 0;
+  }
+  return c;
+}
+
+template <int KIND, typename T>
+__device__ __forceinline__ T stencil_diag(const StencilView<T>& A, int64_t idx) {
+  return KIND == ST_9PT ? A.c[0] : A.diag[idx];
+}
+
+template <int KIND, typename T>
+__device__ __forceinline__ T stencil_dinv(const StencilView<T>& A, int64_t idx) {
+  return KIND == ST_9PT ? A.cdinv : A.dinv[idx];
+}
+
+// (A x)_idx.  `get(m)` returns x at node m converted to T; it is only called
+// for nodes inside the grid.
+template <int KIND, typename T, typename Get>
+__device__ __forceinline__ T stencil_apply(const StencilView<T>& A, int64_t idx, NodeCoord c, Get get) {
+  const int N = A.N;
+  if (KIND == ST_9PT) {
+    T s = A.c[0] * get(idx);
+    const bool w = c.i > 0, e = c.i < N - 1, so = c.j > 0, no = c.j < N - 1;
+    T ew = T(0), ns = T(0), d1 = T(0), d2 = T(0);
+    if (w) ew += get(idx - 1);
+    if (e) ew += get(idx + 1);
+    if (so) ns += get(idx - N);
+    if (no) ns += get(idx + N);
+    if (e && no) d1 += get(idx + N + 1);
+    if (w && so) d1 += get(idx - N - 1);
+    if (w && no) d2 += get(idx + N - 1);
+    if (e && so) d2 += get(idx - N + 1);
+    s += A.c[1] * ew + A.c[2] * ns + A.c[3] * d1 + A.c[4] * d2;
+    return s;
+  } else {
+    T s = A.diag[idx] * get(idx);
+    if (c.i > 0) s -= A.cx[idx - 1] * get(idx - 1);
+    if (c.i < N - 1) s -= A.cx[idx] * get(idx + 1);
+    if (c.j > 0) s -= A.cy[idx - N] * get(idx - N);
+    if (c.j < N - 1) s -= A.cy[idx] * get(idx + N);
+    if (KIND == ST_7PT) {
+      const int64_t nn = (int64_t)N * N;
+      if (c.l > 0) s -= A.cz[idx - nn] * get(idx - nn);
+      if (c.l < N - 1) s -= A.cz[idx] * get(idx + nn);
+    }
+    return s;
+  }
+}
+
+// Visits the off-diagonal neighbours m of node idx: f(m, coord_m, a_idx_m)
+// with a_idx_m the (signed) matrix entry.
+template <int KIND, typename T, typename F>
+__device__ __forceinline__ void for_each_neighbour(const StencilView<T>& A, int64_t idx, NodeCoord c, F f) {
+  const int N = A.N;
+  const bool w = c.i > 0, e = c.i < N - 1, so = c.j > 0, no = c.j < N - 1;
+  if (KIND == ST_9PT) {
+    if (w) f(idx - 1, NodeCoord{c.i - 1, c.j, c.l}, A.c[1]);
+    if (e) f(idx + 1, NodeCoord{c.i + 1, c.j, c.l}, A.c[1]);
+    if (so) f(idx - N, NodeCoord{c.i, c.j - 1, c.l}, A.c[2]);
+    if (no) f(idx + N, NodeCoord{c.i, c.j + 1, c.l}, A.c[2]);
+    if (e && no) f(idx + N + 1, NodeCoord{c.i + 1, c.j + 1, c.l}, A.c[3]);
+    if (w && so) f(idx - N - 1, NodeCoord{c.i - 1, c.j - 1, c.l}, A.c[3]);
+    if (w && no) f(idx + N - 1, NodeCoord{c.i - 1, c.j + 1, c.l}, A.c[4]);
+    if (e && so) f(idx - N + 1, NodeCoord{c.i + 1, c.j - 1, c.l}, A.c[4]);
+  } else {
+    if (w) f(idx - 1, NodeCoord{c.i - 1, c.j, c.l}, -A.cx[idx - 1]);
+    if (e) f(idx + 1, NodeCoord{c.i + 1, c.j, c.l}, -A.cx[idx]);
+    if (so) f(idx - N, NodeCoord{c.i, c.j - 1, c.l}, -A.cy[idx - N]);
+    if (no) f(idx + N, NodeCoord{c.i, c.j + 1, c.l}, -A.cy[idx]);
+    if (KIND == ST_7PT) {
+      const int64_t nn = (int64_t)N * N;
+      if (c.l > 0) f(idx - nn, NodeCoord{c.i, c.j, c.l - 1}, -A.cz[idx - nn]);
+      if (c.l < N - 1) f(idx + nn, NodeCoord{c.i, c.j, c.l + 1}, -A.cz[idx]);
+    }
+  }
+}

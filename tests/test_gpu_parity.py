@@ -1,0 +1,201 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 kernels agree with the oracle to rounding (1e-12 relative on
+operator and preconditioner applications, which sum a handful of terms per
+entry; subspace agreement to 1e-8 given the singular-value gap).  The FP32
+preconditioner is judged by what the method fixes: the solve reaches the FP64
+true relative residual 1e-8 and the preconditioner error stays at FP32 level.
+"""
+import numpy as np
+import pytest
+import torch
+
+from helpers import projector_dist, rel, to_dev, to_np
+from oracle import operator as op, pcg as opcg, prec as oprec, setup as osetup
+from paper_2601_20174_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED = 0, 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_20174_gb300 import api
+    c = api.Context(0)
+    yield c
+    torch.cuda.synchronize()
+
+
+def _api():
+    from paper_2601_20174_gb300 import api
+    return api
+
+
+PROBLEMS = {
+    "poisson5": lambda: gen.poisson_2d(37, 8, 24, seed=1),
+    "grf5": lambda: gen.grf_diffusion_2d(N=45, k=12, K=32, seed=2),
+    "aniso9": lambda: gen.aniso_9pt_2d(N=29, k=10, K=24, m=1, seed=3),
+    "iid7": lambda: gen.iid_diffusion_3d(N=11, k=10, K=24, seed=4),
+}
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_operator_apply_and_diagonal(ctx, name):
+    p = PROBLEMS[name]()
+    A = op.assemble(p)
+    Aop = _api().Operator.from_problem(ctx, p)
+    X = np.random.default_rng(0).standard_normal((p.n, 3))
+    Y = to_np(Aop.apply(to_dev(X)))
+    ref = A @ X
+    assert np.max(np.abs(Y - ref)) <= 1e-13 * np.max(np.abs(ref))
+    assert np.array_equal(to_np(Aop.diagonal()), A.diagonal()) or \
+        np.max(np.abs(to_np(Aop.diagonal()) - A.diagonal())) <= 1e-15 * A.diagonal().max()
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_smooth_samples(ctx, name, precision):
+    p = PROBLEMS[name]()
+    A = op.assemble(p)
+    Aop = _api().Operator.from_problem(ctx, p)
+    S = to_np(Aop.smooth_samples(to_dev(p.S0), p.s1, p.omega, precision))
+    ref = osetup.smooth_samples(A, p.S0, p.omega, p.s1)
+    tol = 1e-12 if precision == FP64 else 2e-5
+    assert rel(S, ref) <= tol
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_setup_fp64_subspace_sigma_and_galerkin(ctx, name):
+    p = PROBLEMS[name]()
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    M = _api().Preconditioner.build(_api().Operator.from_problem(ctx, p), to_dev(p.S0), p.k, p.s1, p.nu, p.omega, FP64)
+    P = to_np(M.basis())
+    sig = to_np(M.sigma())
+    # The SVD goes through the Gram matrix S^T S, which resolves sigma_i only to
+    # ~eps sigma_1^2 / sigma_i; the leading k+1 values are the ones that matter.
+    s_ref = ref["sigma"][: p.k + 1]
+    tol_s = 1e-9 * s_ref + 1e-13 * s_ref[0] ** 2 / s_ref
+    assert np.all(np.abs(sig[: p.k + 1] - s_ref) <= tol_s), (sig[: p.k + 1] - s_ref) / s_ref
+    gap = (s_ref[p.k - 1] ** 2 - s_ref[p.k] ** 2) / s_ref[0] ** 2
+    dist = projector_dist(P, ref["P"])
+    assert dist <= max(1e-8, 1e-13 / gap), (dist, gap)
+    assert np.max(np.abs(P.T @ P - np.eye(p.k))) <= 1e-12, np.max(np.abs(P.T @ P - np.eye(p.k)))
+    Ac, Lf = (to_np(t) for t in M.coarse())
+    Ac_ref = osetup.galerkin(A, P)  # Galerkin product of the GPU's own basis
+    assert np.max(np.abs(Ac - Ac_ref)) <= 1e-12 * np.max(np.abs(Ac_ref))
+    assert np.max(np.abs(Lf @ Lf.T - Ac)) <= 1e-12 * np.max(np.abs(Ac))
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_apply_matches_algorithm1(ctx, name, precision):
+    # The oracle's basis is handed to the GPU so both apply the same B.
+    p = PROBLEMS[name]()
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    M = _api().Preconditioner.from_basis(_api().Operator.from_problem(ctx, p), to_dev(ref["P"]), p.nu, p.omega,
+                                         precision)
+    R = np.random.default_rng(5).standard_normal((p.n, 2))
+    Z = to_np(M.apply(to_dev(R)))
+    Zref = oprec.apply(A, ref["P"], ref["L"], R, p.omega, p.nu, p.nu)
+    tol = 1e-12 if precision == FP64 else 1e-4
+    assert rel(Z, Zref) <= tol
+
+
+def test_rank_truncation(ctx):
+    p = PROBLEMS["grf5"]()
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    M = _api().Preconditioner.from_basis(_api().Operator.from_problem(ctx, p), to_dev(ref["P"]), p.nu, p.omega, FP64)
+    r = 5
+    M.factor(r)
+    Pr = osetup.truncate(ref["P"], r)
+    Ac, _ = (to_np(t) for t in M.coarse())
+    assert np.max(np.abs(Ac - osetup.galerkin(A, Pr))) <= 1e-12 * np.max(np.abs(Ac))
+    R = np.random.default_rng(6).standard_normal(p.n)
+    Z = to_np(M.apply(to_dev(R)))
+    Zref = oprec.apply(A, Pr, osetup.coarse_factor(osetup.galerkin(A, Pr)), R, p.omega, p.nu, p.nu)
+    assert rel(Z, Zref) <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("graph_mode", [0, 1])
+def test_pcg_fp64_matches_oracle_iterates(ctx, name, graph_mode):
+    p = PROBLEMS[name]()
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    M = _api().Preconditioner.from_basis(_api().Operator.from_problem(ctx, p), to_dev(ref["P"]), p.nu, p.omega, FP64)
+    b = p.f[:, 0]
+    o = opcg.pcg(A, opcg.two_level_solver(A, ref["P"], ref["L"], p.omega, p.nu, p.nu), b, p.tol)
+    x, res = M.solve(to_dev(b), tol=p.tol, graph_mode=graph_mode)
+    assert res[0].status == 0
+    assert abs(res[0].iterations - o["iters"]) <= 1
+    assert rel(to_np(x), o["x"]) <= 1e-8
+    true = np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b)
+    assert true <= p.tol * 1.01 and abs(res[0].true_relres - true) <= 1e-3 * true
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_pcg_end_to_end_both_precisions(ctx, name):
+    p = PROBLEMS[name]()
+    p.tol = 1e-8
+    A = op.assemble(p)
+    o = opcg.solve_problem(p, A=A)
+    Aop = _api().Operator.from_problem(ctx, p)
+    for precision in (FP64, MIXED):
+        M = _api().Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, precision)
+        x, res = M.solve(to_dev(p.f[:, 0]), tol=p.tol)
+        true = np.linalg.norm(p.f[:, 0] - A @ to_np(x)) / np.linalg.norm(p.f[:, 0])
+        assert res[0].status == 0 and true <= 1e-8 * 1.01
+        if precision == FP64:
+            assert abs(res[0].iterations - o["results"][0]["iters"]) <= 1
+        else:
+            assert abs(res[0].iterations - o["results"][0]["iters"]) <= 2
+
+
+def test_multi_rhs_zero_and_scaled_columns(ctx):
+    p = PROBLEMS["grf5"]()
+    A = op.assemble(p)
+    M = _api().Preconditioner.build(_api().Operator.from_problem(ctx, p), to_dev(p.S0), p.k, p.s1, p.nu, p.omega,
+                                    FP64)
+    b = p.f[:, 0]
+    B = np.stack([b, np.zeros(p.n), 3.0 * b], axis=1)
+    X, res = M.solve(to_dev(B), tol=1e-9)
+    X = to_np(X)
+    assert res[1].iterations == 0 and res[1].status == 0 and np.all(X[:, 1] == 0)
+    assert res[0].iterations == res[2].iterations
+    assert rel(X[:, 2], 3.0 * X[:, 0]) <= 1e-10
+
+
+def test_full_rank_basis_one_iteration(ctx):
+    p = gen.iid_diffusion_2d(N=7, k=4, K=8, seed=9)
+    M = _api().Preconditioner.from_basis(_api().Operator.from_problem(ctx, p), to_dev(np.eye(p.n)), 2, p.omega, FP64)
+    x, res = M.solve(to_dev(p.f[:, 0]), tol=1e-10)
+    assert res[0].iterations == 1 and res[0].true_relres <= 1e-10
+
+
+def test_maxit_and_nonfinite_rhs(ctx):
+    p = PROBLEMS["grf5"]()
+    M = _api().Preconditioner.build(_api().Operator.from_problem(ctx, p), to_dev(p.S0), 2, p.s1, p.nu, p.omega, FP64)
+    x, res = M.solve(to_dev(p.f[:, 0]), tol=1e-14, maxit=3)
+    assert res[0].status == 1 and res[0].iterations == 3
+    bad = p.f[:, 0].copy()
+    bad[5] = np.nan
+    x, res = M.solve(to_dev(bad), tol=1e-8)
+    assert res[0].status == -4
+
+
+def test_invalid_arguments_rejected(ctx):
+    api = _api()
+    p = PROBLEMS["poisson5"]()
+    Aop = api.Operator.from_problem(ctx, p)
+    with pytest.raises(api.L.NlspError):
+        api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, 0, p.omega, FP64)  # nu = 0
+    with pytest.raises(api.L.NlspError):
+        api.Preconditioner.build(Aop, to_dev(p.S0), p.K + 1, p.s1, 2, p.omega, FP64)  # k > K
+    with pytest.raises(api.L.NlspError):
+        api.Operator(ctx, 2, 8, 5, -torch.ones(81, dtype=torch.float64).cuda(), 0)  # kappa < 0
