@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Benchmark: PCG solves/s to relative residual 1e-8 with the spectral
+two-level preconditioner, on one GB300 (or N replicas).
+
+Workload: 2D variable-coefficient diffusion, 5-point, 512 x 512 interior
+grid (n = 262144), log kappa a squared-exponential Gaussian random field
+(length 0.1, sigma 1), k = 64 from K = 128 Jacobi-smoothed N(0,1) samples
+(s1 = 20, omega = 2/3), nu1 = nu2 = 2, one right-hand side f ~ U[-1, 1],
+tolerance 1e-8.  Seeded synthetic inputs (no dataset exists for it).
+
+One step = assemble A + build P (smoothing, SVD, Galerkin, Cholesky) + PCG
+solve, through the library's public API, with the inputs already resident in
+HBM; L2 is flushed (256 MiB write) between timed steps.  The headline runs the
+mixed path (FP32 preconditioner, FP64 recurrences); the plain FP64 path and
+the solve-only throughput are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG solves/s to rel-res 1e-8 (mixed/batched vs plain FP64); % HBM roofline"
+UNIT = "solves/s"
+WL = dict(N=512, k=64, K=128, s1=20, nu=2, omega=2.0 / 3.0, tol=1e-8, seed=0)
+WORKLOAD_NAME = "grf_diffusion2d_N512_k64_K128_seed0"
+WORKLOAD_DESC = ("2D diffusion 5-point 512x512 (n=262144), GRF log-kappa (l=0.1, sigma=1), "
+                 "k=64 from K=128 smoothed samples (s1=20, omega=2/3), nu1=nu2=2, 1 RHS U[-1,1], tol 1e-8")
+FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int | None):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if self.gpu_index is not None:
+                cmd += ["-i", str(self.gpu_index)]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _gpu_index(torch, dev):
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        out = subprocess.run(["nvidia-smi", "--query-gpu=index,uuid", "--format=csv,noheader"], capture_output=True,
+                             text=True, timeout=20).stdout
+        for line in out.strip().splitlines():
+            idx, u = [x.strip() for x in line.split(",")]
+            if uuid.replace("GPU-", "") in u:
+                return int(idx)
+    except Exception:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ----------------------------------------------------------------------------
+def oracle_sample(pcg_iters_sample: int = 64, seed: int = 0):
+    """Times the oracle's setup plus `pcg_iters_sample` PCG iterations and
+    extrapolates to a full solve with the oracle's own iteration count for this
+    workload (tests/golden/bench_workloads.json, written by an oracle-only
+    script).  Returns (solves_per_s, detail dict)."""
+    from oracle import operator as op, pcg, setup as su
+    from paper_2601_20174_gb300 import inputs as gen
+    with open(os.path.join(ROOT, "tests", "golden", "bench_workloads.json")) as f:
+        iters_full = json.load(f)[WORKLOAD_NAME]["iters"]
+    p = gen.grf_diffusion_2d(WL["N"], WL["k"], WL["K"], seed=seed, tol=WL["tol"])
+    t0 = time.perf_counter()
+    A = op.assemble(p)
+    st = su.build(A, p.S0, p.k, p.omega, p.s1)
+    t1 = time.perf_counter()
+    pcg.pcg(A, pcg.two_level_solver(A, st["P"], st["L"], p.omega, p.nu, p.nu), p.f[:, 0], 0.0,
+            maxit=pcg_iters_sample)
+    t2 = time.perf_counter()
+    per_it = (t2 - t1) / pcg_iters_sample
+    total = (t1 - t0) + per_it * iters_full
+    return 1.0 / total, {"setup_s": round(t1 - t0, 3), "pcg_s_per_iter": per_it, "iters_full": iters_full,
+                         "sample_s": round(t2 - t0, 2), "extrapolated_solve_s": round(total, 3)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = os.cpu_count()
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(pcg_iters_sample=4)
+    vals, det = [], None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, det = oracle_sample()
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    sample = (f"per step: oracle setup (smoothing, numpy SVD, Galerkin, Cholesky) + 64 PCG iterations, "
+              f"extrapolated with the oracle's {det['iters_full']} iterations to rel-res 1e-8")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD_DESC, "impl": "FP64 CPU oracle (numpy/scipy)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "detail": det},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_20174_gb300 import _lib as L, api, inputs as gen
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    p = gen.grf_diffusion_2d(WL["N"], WL["k"], WL["K"], seed=WL["seed"] + rank, tol=WL["tol"])
+    n = p.n
+    kap_h = torch.as_tensor(p.coeffs.reshape(-1)).pin_memory()
+    S0_h = torch.as_tensor(np.ascontiguousarray(p.S0.T)).pin_memory()  # (K, n): column-major n x K
+    f_h = torch.as_tensor(p.f[:, 0].copy()).pin_memory()
+    kap, S0s, f = kap_h.to(dev), S0_h.to(dev), f_h.to(dev)
+    x_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush_src = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = api.Context(local)
+    stream = ctx.stream
+    mixed, fp64 = L.NLSP_MIXED_FP32, L.NLSP_FP64
+
+    def step(precision, kap_d, S0_d, f_d):
+        A = api.Operator(ctx, 2, WL["N"], 5, kap_d, L.NLSP_COEF_CELL_KAPPA)
+        M = api.Preconditioner.build(A, S0_d.t(), WL["k"], WL["s1"], WL["nu"], WL["omega"], precision)
+        x, res = M.solve(f_d, tol=WL["tol"], graph_mode=args.graph_mode)
+        return A, M, x, res[0]
+
+    def timed(fn, reps, flush_between=True, read_flush=False):
+        ms = []
+        out = None
+        for _ in range(reps):
+            out = None  # the previous step's objects are freed outside the timed region
+            if flush_between and read_flush:
+                flush_src.sum()  # evicts L2 with clean lines (no write-backs charged to the next kernel)
+            elif flush_between:
+                flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, out
+
+    # warm-up (also builds the solver graphs and grows the scratch slots)
+    for _ in range(args.warmup):
+        step(mixed, kap, S0s, f)
+    torch.cuda.synchronize()
+
+    # ---- headline: mixed path, full step --------------------------------
+    sampler = ClockSampler(_gpu_index(torch, local))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    l0 = ctx._lib.nlsp_launch_count(ctx.h)
+    ms, (A_m, M_m, x_m, res_m) = timed(lambda: step(mixed, kap, S0s, f), args.steps)
+    launches = int(ctx._lib.nlsp_launch_count(ctx.h) - l0)
+    clocks = sampler.stop()
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = world * args.steps / (total_ms / 1000.0)
+    true_m = float(torch.linalg.norm(f - A_m.apply(x_m)) / torch.linalg.norm(f))
+
+    # ---- solve only (preconditioner prebuilt) ---------------------------
+    so_ms, (x_s, res_s) = timed(lambda: M_m.solve(f, tol=WL["tol"], graph_mode=args.graph_mode), max(2, args.steps))
+    # ---- kernels for the roofline: cold-L2 replays of restrict / prolong ---
+    peak, peak_kind = _peaks()
+    kern = {}
+    r, k = WL["k"], WL["k"]
+    alg_bytes = {"restrict": n * (4 * r + 8 + 4 + 12), "prolong": n * (4 * r + 8)}
+    for which, name in ((0, "restrict"), (1, "prolong")):
+        kms, _ = timed(lambda: L.check(ctx._lib.nlsp_bench_kernel(ctx.h, M_m.h, which, 1), "bench"), 20,
+                       read_flush=True)
+        wms, _ = timed(lambda: L.check(ctx._lib.nlsp_bench_kernel(ctx.h, M_m.h, which, 20), "bench"), 3,
+                       flush_between=False)
+        avg = statistics.mean(kms) / 1000.0
+        kern[name] = {"avg_us_cold_l2": avg * 1e6, "avg_us_warm": min(wms) / 20 * 1000.0,
+                      "algorithmic_bytes": alg_bytes[name], "achieved_gbs": alg_bytes[name] / avg / 1e9}
+    dom = max(kern, key=lambda kname: kern[kname]["avg_us_cold_l2"])
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kern[dom]["achieved_gbs"] / peak, "traffic": None,
+            "peak_kind": f"{peak_kind} (copy, burst)",
+            "timing": "20 single launches replayed after the timed region, L2 evicted before each by reading "
+                      "256 MiB, CUDA events on the library stream"}
+
+    # ---- plain FP64 path, same step -------------------------------------
+    f64_ms, (_, _, x_d, res_d) = timed(lambda: step(fp64, kap, S0s, f), max(1, min(args.steps, 3)))
+
+    # ---- end to end from host buffers -----------------------------------
+    def e2e_step():
+        kap_d = kap_h.to(dev, non_blocking=True)
+        S0_d = S0_h.to(dev, non_blocking=True)
+        f_d = f_h.to(dev, non_blocking=True)
+        A, M, x, _ = step(mixed, kap_d, S0_d, f_d)
+        x_h.copy_(x, non_blocking=True)
+        return A, M, x_h
+
+    e2e_ms, _ = timed(e2e_step, max(2, args.steps))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_val = world * len(e2e_ms) / (e2e_total / 1000.0)
+    h2d = kap_h.numel() * 8 + S0_h.numel() * 8 + f_h.numel() * 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cv, det = oracle_sample()
+        cpu = {"value": cv, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "oracle setup (smoothing, numpy SVD, Galerkin, Cholesky) + 64 PCG iterations on the same "
+                         f"workload, extrapolated with the oracle's {det['iters_full']} iterations to 1e-8; numpy "
+                         "BLAS threads = cores, scipy sparse products single-threaded", "detail": det}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32-prec/f64-outer", "data": "synthetic",
+                "config": {"workload": WORKLOAD_DESC, "precision": "mixed (FP32 preconditioner, FP64 PCG)",
+                           "step": "assemble A + build P + factor A_c + PCG to 1e-8 through the C ABI",
+                           "l2": "flushed between timed steps (256 MiB write)",
+                           "graph_mode": args.graph_mode,
+                           "parallelism": f"replicas x{world} (independent instances, no collective)"},
+                "iterations": res_m.iterations, "true_relres": true_m,
+                "solve_only": {"value": 1000.0 / statistics.median(so_ms), "unit": UNIT,
+                               "ms": statistics.median(so_ms), "iterations": res_s[0].iterations,
+                               "us_per_iteration": 1000.0 * statistics.median(so_ms) / max(1, res_s[0].iterations)},
+                "fp64_plain": {"value": 1000.0 / statistics.median(f64_ms), "unit": UNIT,
+                               "ms_per_step": statistics.median(f64_ms), "iterations": res_d.iterations,
+                               "true_relres": res_d.true_relres},
+                "roofline": roof, "kernels": kern,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * 8},
+                "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph-mode", type=int, default=1, choices=[0, 1],
+                    help="1: PCG loop as one graph with a device-side while node (default); 0: one-iteration "
+                         "graph relaunched by the host (profilers see each kernel)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -237,6 +237,22 @@ NLSP_API nlsp_status nlsp_solve(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec
                        int64_t ldb, double* dev_X, int64_t ldx, const nlsp_solve_params* params,
                        nlsp_solve_info* infos);
 
+/* ---------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper).
+ * ------------------------------------------------------------------------- */
+
+/* Number of kernels this context has enqueued so far (host count, including
+   the kernels of every executed PCG graph iteration). */
+NLSP_API unsigned long long nlsp_launch_count(const nlsp_ctx* ctx);
+
+/* Enqueues `reps` back-to-back launches of one hot kernel of the
+   preconditioner apply on M's internal work vectors (their contents are
+   whatever the last apply or solve left; results are discarded), so that a
+   caller can time one launch with events recorded on the context stream.
+   which: 0 = residual + restriction P_r^T rho (with the coarse solve in its
+   last block), 1 = prolongation z += P_r e_c.  Errors: NLSP_ERR_INVALID. */
+NLSP_API nlsp_status nlsp_bench_kernel(nlsp_ctx* ctx, const nlsp_prec* M, int which, int reps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,8 @@ SIGNATURES = {
     "nlsp_free_prec": (None, [vp]),
     "nlsp_apply_prec": (ci, [vp, vp, ci, vp, i64, vp, i64]),
     "nlsp_solve": (ci, [vp, vp, vp, ci, vp, i64, vp, i64, C.POINTER(SolveParams), C.POINTER(SolveInfo)]),
+    "nlsp_launch_count": (C.c_ulonglong, [vp]),
+    "nlsp_bench_kernel": (ci, [vp, vp, ci, ci]),
 }
 
 _lib = None

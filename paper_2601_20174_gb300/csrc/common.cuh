@@ -43,8 +43,9 @@ void nlsp_record_cuda_error(cudaError_t e, const char* what, const char* file, i
 constexpr int NLSP_TILE = 128;
 
 __host__ __device__ inline int64_t tiled_index(int64_t i, int c, int ncols) {
-  return ((i / NLSP_TILE) * ncols + c) * NLSP_TILE + (i % NLSP_TILE);
+  return (((int64_t)((uint64_t)i >> 7)) * ncols + c) * NLSP_TILE + (int64_t)((uint64_t)i & 127u);
 }
+static_assert(NLSP_TILE == 128, "tiled_index assumes 128-node tiles");
 inline int64_t pad_tile(int64_t n) { return (n + NLSP_TILE - 1) / NLSP_TILE * NLSP_TILE; }
 
 enum StencilKind { ST_5PT = 0, ST_9PT = 1, ST_7PT = 2 };
@@ -71,12 +72,26 @@ struct StencilView {
 // ----------------------------------------------------------------------------
 // Library objects
 // ----------------------------------------------------------------------------
+// Grow-only device scratch slots owned by the context: setup and solve
+// temporaries are carved from them, so repeated calls allocate nothing once
+// the slots have grown to the working size.  Valid until the next call that
+// uses the same slot on this context.
+enum ScratchSlot { SLOT_SA = 0, SLOT_SB, SLOT_PART, SLOT_SMALL, SLOT_PNEW, SLOT_COUNT };
+
 struct nlsp_ctx {
   int device;
   cudaStream_t stream;
   int num_sms;
   size_t l2_bytes;
+  void* slot[SLOT_COUNT];
+  size_t slot_bytes[SLOT_COUNT];
+  unsigned long long launches;  // kernels this context has enqueued
 };
+
+// Returns slot `s` with at least `bytes` (grows it, synchronising the
+// device when it has to reallocate).  nullptr on allocation failure.
+void* ctx_slot(nlsp_ctx* ctx, int s, size_t bytes);
+inline void count_launches(nlsp_ctx* ctx, unsigned long long k) { ctx->launches += k; }
 
 struct nlsp_op {
   nlsp_ctx* ctx;
@@ -105,9 +120,10 @@ struct nlsp_prec {
   double* sigma;    // K singular values (descending)
   double* Ac;       // r x r column-major
   double* L;        // r x r lower Cholesky factor, column-major
-  double* Ainv;     // r x r inverse of A_c (from the factor)
-  double* cpart;    // restriction partials [blocks][k]
-  double* ec;       // coarse correction (k, FP64)
+  double* Ainv;     // r x r inverse of A_c (from the factor), FP64
+  void* AinvT;      // A_c^-1 in the preconditioner precision (== Ainv in FP64)
+  void* cpart;      // restriction partials [blocks][k], preconditioner precision
+  void* ec;         // coarse correction (k), preconditioner precision
   unsigned* counter;
   int* status;      // device status word (Cholesky pivots)
   int rblocks;      // blocks of the restriction kernel
@@ -115,6 +131,7 @@ struct nlsp_prec {
   void* w0;
   void* w1;
   PcgWork* pcg;     // lazily built solver workspace and graphs
+  void* storage;    // the single allocation holding the arrays above
 };
 
 // ----------------------------------------------------------------------------

@@ -39,6 +39,7 @@ extern "C" nlsp_status nlsp_create(nlsp_ctx** ctx_out, int device, void* cuda_st
   if (device < 0 || device >= count) return NLSP_ERR_INVALID;
   NLSP_CUDA(cudaSetDevice(device));
   nlsp_ctx* c = new nlsp_ctx();
+  memset(c, 0, sizeof(*c));
   c->device = device;
   c->stream = (cudaStream_t)cuda_stream;
   int sms = 0, l2 = 0;
@@ -60,8 +61,32 @@ extern "C" void nlsp_destroy(nlsp_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  for (int s = 0; s < SLOT_COUNT; ++s)
+    if (ctx->slot[s]) cudaFree(ctx->slot[s]);
   delete ctx;
 }
+
+void* ctx_slot(nlsp_ctx* ctx, int s, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (ctx->slot_bytes[s] >= bytes) return ctx->slot[s];
+  if (ctx->slot[s]) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->slot[s]);
+  }
+  ctx->slot[s] = nullptr;
+  ctx->slot_bytes[s] = 0;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    nlsp_record_cuda_error(e, "cudaMalloc (scratch)", __FILE__, __LINE__);
+    return nullptr;
+  }
+  ctx->slot[s] = p;
+  ctx->slot_bytes[s] = bytes;
+  return p;
+}
+
+extern "C" unsigned long long nlsp_launch_count(const nlsp_ctx* ctx) { return ctx ? ctx->launches : 0ull; }
 
 // ----------------------------------------------------------------------------
 // Assembly kernels: cell kappa -> edge weights, diagonal and its inverse.
@@ -212,6 +237,7 @@ extern "C" nlsp_status nlsp_assemble_stencil(nlsp_ctx* ctx, int dim, const int64
     else
       k_assemble_7pt<<<g, 256, 0, s>>>((int)N, dev_coeffs, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, bad);
     k_to_float<<<grid_for(ctx, 5 * n, 256, 8), 256, 0, s>>>(op->a64, op->a32, 5 * n);
+    count_launches(ctx, 2);
     if (cudaGetLastError() != cudaSuccess) return fail(NLSP_ERR_CUDA);
     int hbad = 0;
     if (cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
@@ -253,6 +279,7 @@ extern "C" nlsp_status nlsp_op_apply(nlsp_ctx* ctx, const nlsp_op* A, int m, con
     case ST_9PT: k_apply_cols<ST_9PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
     default: k_apply_cols<ST_7PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
   }
+  count_launches(ctx, 1);
   NLSP_LAUNCH_CHECK();
   return NLSP_OK;
 }

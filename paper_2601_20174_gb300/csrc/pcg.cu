@@ -1,18 +1,24 @@
 // Two-level preconditioner apply (Algorithm 1, "Apply preconditioner to
 // residual b") and preconditioned CG (Sec. 4, two-grid solver evaluation).
 //
-// One PCG iteration t is five kernels (plus extra sweeps when nu > 2):
-//   spmv    p_t = z_{t-1} + beta p_{t-1} (evaluated on the fly, also at the
-//           stencil neighbours), q = A p_t, p^T q;     last block: alpha
-//   pre     x += alpha p, r_t = r_{t-1} - alpha q, ||r_t||^2, and the first
-//           two Jacobi sweeps from z = 0 (z1 = w D^-1 r is elementwise, so
-//           z2 = z1 + w D^-1 (r - A z1) needs only neighbour values of r);
-//           last block: convergence test
-//   restrict  rho = r - A z, c = P^T rho;              last block: e_c = A_c^-1 c
-//   prolong   z += P e_c
-//   post    the post sweeps (FP32: two fused, the inner one recomputed at the
-//           neighbours), r^T z (and r^T z_old for flexible CG);
-//           last block: beta, loop condition
+// GB300 runs FP64 (including FP32<->FP64 conversions) at ~2 lanes/clk/SM,
+// 1/62 of FP32, so the iteration is arranged to spend FP64 only on the outer
+// recurrences and their dot products; everything inside the preconditioner
+// is FP32 in the mixed path, where recomputing stencil values is cheaper than
+// storing them.  One PCG iteration t:
+//   spmv      p_t = z_{t-1} + beta p_{t-1} (evaluated on the fly, also at the
+//             stencil neighbours), q = A p_t, p^T q;   last block: alpha
+//   pre       x += alpha p, r -= alpha q, ||r||^2, rT = r in the
+//             preconditioner precision;                last block: stop test
+//   restrict  the nu1 <= 2 pre-sweeps from z = 0 recomputed from rT
+//             (z1 = w D^-1 rT is elementwise, so z2 at a node needs rT only
+//             at its stencil neighbours), rho = rT - A z2, c = P_r^T rho,
+//             z2 stored;                                last block: e_c = A_c^-1 c
+//   prolong   z += P_r e_c
+//   post      the post sweeps (FP32: the last two fused, the inner one
+//             recomputed at the neighbours), z_t stored in FP64, r^T z_t
+//             (and r^T z_{t-1} for flexible CG); last block: beta, loop test
+// The FP64 path (T = double) stores the pre-sweeps instead of recomputing.
 // Vectors that a kernel reads at stencil neighbours while another block of
 // the same kernel writes them are double-buffered by iteration parity.
 // Scalar reductions are deterministic: per-block partials summed in block
@@ -27,6 +33,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 struct PcgState {
   double bnorm2, tol2bn, rz, pq, alpha, beta, rr, true_rr;
@@ -34,7 +41,7 @@ struct PcgState {
   int flexible, pad0;
 };
 
-// Vector bound to iteration parity: v[(t + shift) & 1].
+// Vector bound to iteration parity: v[t & 1].
 template <typename V>
 struct Pair {
   V* v[2];
@@ -43,7 +50,8 @@ struct Pair {
 
 namespace {
 
-constexpr int TPB = 256;  // threads per block for node-parallel kernels
+constexpr int TPB = 256;     // threads per block for node-parallel kernels
+constexpr int NODE_BPS = 8;  // node-kernel blocks per SM: one node per thread up to full occupancy
 
 struct RedSlots {
   double* part;       // [4][max_blocks]
@@ -59,28 +67,52 @@ __device__ __forceinline__ void mark_breakdown(PcgState* st) {
   st->done = 1;
 }
 
+// FP64 block sum with few FP64 instructions: partials go to shared memory and
+// one warp adds them (the FP64 pipe is charged per warp instruction).  The
+// result is valid in warp 0.  Fixed order => deterministic.
+__device__ __forceinline__ double block_sum_lean(double v, double* sm) {
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += sm[i];
+    s = warp_sum(s);
+  }
+  __syncthreads();
+  return s;
+}
+
+__device__ __forceinline__ double sum_partials_lean(const double* part, int count, double* sm) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < count; b += blockDim.x) s += part[b];
+  return block_sum_lean(s, sm);
+}
+
 // ----------------------------------------------------------------------------
-// PCG start: r_0 = b, x = 0, p = q = 0, ||b||^2.
+// PCG start: r_0 = b, rT = b, x = 0, p = q = 0, ||b||^2.
 // ----------------------------------------------------------------------------
-__global__ void k_pcg_init(int64_t n, const double* __restrict__ b, double* __restrict__ x, double* __restrict__ r0,
-                           double* __restrict__ p0, double* __restrict__ p1, double* __restrict__ q, PcgState* st,
-                           double tol, int maxit, int flexible, RedSlots red) {
-  __shared__ double sred[32];
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_pcg_init(int64_t n, const double* __restrict__ b, double* __restrict__ x,
+                                                  double* __restrict__ r, T* __restrict__ rT, double* __restrict__ p0,
+                                                  double* __restrict__ p1, double* __restrict__ q, PcgState* st,
+                                                  double tol, int maxit, int flexible, RedSlots red) {
+  __shared__ double sm[TPB];
   __shared__ int flag;
   double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double bi = b[i];
-    r0[i] = bi;
+    r[i] = bi;
+    if (sizeof(T) == 4) rT[i] = (T)bi;
     x[i] = 0.0;
     p0[i] = 0.0;
     p1[i] = 0.0;
     q[i] = 0.0;
     s += bi * bi;
   }
-  s = block_sum(s, sred);
+  s = block_sum_lean(s, sm);
   if (threadIdx.x == 0) red.part[blockIdx.x] = s;
   if (last_block_arrive(&red.counter[0], &flag)) {
-    const double bb = block_sum_partials(red.part, gridDim.x, 1, sred);
+    const double bb = sum_partials_lean(red.part, gridDim.x, sm);
     if (threadIdx.x == 0) {
       st->bnorm2 = bb;
       st->tol2bn = tol * tol * bb;
@@ -103,31 +135,31 @@ __global__ void k_pcg_init(int64_t n, const double* __restrict__ b, double* __re
 // ----------------------------------------------------------------------------
 // spmv: p_t = z_{t-1} + beta p_{t-1}; q = A p_t; p_t^T q.  FP64.
 // ----------------------------------------------------------------------------
-template <int KIND, typename T>
-__global__ void __launch_bounds__(TPB) k_pcg_spmv(StencilView<double> A, Pair<const T> Z, Pair<double> Pv,
+template <int KIND>
+__global__ void __launch_bounds__(TPB) k_pcg_spmv(StencilView<double> A, Pair<const double> Z, Pair<double> Pv,
                                                   double* __restrict__ q, PcgState* st, RedSlots red) {
-  __shared__ double sred[32];
+  __shared__ double sm[TPB];
   __shared__ int flag;
   if (load_done(st)) return;
   const int t = load_iter(st);  // number of completed A p products
   const double beta = st->beta;
-  const T* __restrict__ z = Z.at(t);
+  const double* __restrict__ z = Z.at(t);
   const double* __restrict__ pin = Pv.at(t);
   double* __restrict__ pout = Pv.at(t + 1);
   double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
     const NodeCoord c = node_coord<KIND>(i, A.N);
-    auto pv = [&](int64_t m) { return (double)z[m] + beta * pin[m]; };
+    auto pv = [&](int64_t m) { return fma(beta, pin[m], z[m]); };
     const double pi = pv(i);
     const double qi = stencil_apply<KIND>(A, i, c, pv);
     pout[i] = pi;
     q[i] = qi;
-    s += pi * qi;
+    s = fma(pi, qi, s);
   }
-  s = block_sum(s, sred);
+  s = block_sum_lean(s, sm);
   if (threadIdx.x == 0) red.part[blockIdx.x] = s;
   if (last_block_arrive(&red.counter[0], &flag)) {
-    const double pq = block_sum_partials(red.part, gridDim.x, 1, sred);
+    const double pq = sum_partials_lean(red.part, gridDim.x, sm);
     if (threadIdx.x == 0) {
       st->pq = pq;
       st->iter = t + 1;
@@ -138,249 +170,365 @@ __global__ void __launch_bounds__(TPB) k_pcg_spmv(StencilView<double> A, Pair<co
 }
 
 // ----------------------------------------------------------------------------
-// pre: CG update of x and r (loop mode), ||r||^2, first two Jacobi sweeps.
-//   INIT: start of the solve or a standalone apply: r is read, not updated.
+// pre: x += alpha p, r -= alpha q, ||r||^2, rT = r (preconditioner precision).
 // ----------------------------------------------------------------------------
-template <int KIND, typename T, bool INIT>
-__global__ void __launch_bounds__(TPB) k_pcg_pre(StencilView<T> A, T omega, int nu1, Pair<double> R,
-                                                 const double* __restrict__ q, Pair<const double> Pv,
-                                                 double* __restrict__ x, T* __restrict__ zout, PcgState* st,
-                                                 RedSlots red) {
-  __shared__ double sred[32];
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_pcg_pre(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                 T* __restrict__ rT, const double* __restrict__ q,
+                                                 Pair<const double> Pv, PcgState* st, RedSlots red) {
+  __shared__ double sm[TPB];
   __shared__ int flag;
   if (load_done(st)) return;
   const int t = load_iter(st);
-  const double alpha = INIT ? 0.0 : st->alpha;
-  const double* __restrict__ rin = INIT ? R.at(t) : R.at(t - 1);
-  double* __restrict__ rout = R.at(t);
+  const double alpha = st->alpha;
   const double* __restrict__ p = Pv.at(t);
   double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
-    double ri;
-    if (INIT) {
-      ri = rin[i];
-    } else {
-      x[i] += alpha * p[i];
-      ri = rin[i] - alpha * q[i];
-      rout[i] = ri;
-      s += ri * ri;
-    }
-    const T z1 = omega * stencil_dinv<KIND>(A, i) * (T)ri;
-    T zf = z1;
-    if (nu1 >= 2) {
-      const NodeCoord c = node_coord<KIND>(i, A.N);
-      auto z1at = [&](int64_t m) -> T {
-        if (m == i) return z1;
-        const double rm = INIT ? rin[m] : rin[m] - alpha * q[m];
-        return omega * stencil_dinv<KIND>(A, m) * (T)rm;
-      };
-      const T az = stencil_apply<KIND>(A, i, c, z1at);
-      zf = z1 + omega * stencil_dinv<KIND>(A, i) * ((T)ri - az);
-    }
-    zout[i] = zf;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    if (sizeof(T) == 4) rT[i] = (T)ri;
+    s = fma(ri, ri, s);
   }
-  if (!INIT && st) {
-    s = block_sum(s, sred);
-    if (threadIdx.x == 0) red.part[blockIdx.x] = s;
-    if (last_block_arrive(&red.counter[1], &flag)) {
-      const double rr = block_sum_partials(red.part, gridDim.x, 1, sred);
-      if (threadIdx.x == 0) {
-        st->rr = rr;
-        if (!isfinite(rr)) mark_breakdown(st);
-        else if (rr <= st->tol2bn) st->done = 1;  // converged: status stays NLSP_OK
-      }
+  s = block_sum_lean(s, sm);
+  if (threadIdx.x == 0) red.part[blockIdx.x] = s;
+  if (last_block_arrive(&red.counter[1], &flag)) {
+    const double rr = sum_partials_lean(red.part, gridDim.x, sm);
+    if (threadIdx.x == 0) {
+      st->rr = rr;
+      if (!isfinite(rr)) mark_breakdown(st);
+      else if (rr <= st->tol2bn) st->done = 1;  // converged: status stays NLSP_OK
     }
   }
 }
 
-// One extra Jacobi sweep: zout = zin + w D^-1 (r - A zin).
+// ----------------------------------------------------------------------------
+// Jacobi sweeps on A z = r (the residual in the preconditioner precision).
+// ----------------------------------------------------------------------------
+// z after `NU` (1 or 2) sweeps from z = 0, at node m with coordinates cm.
+template <int KIND, typename T, int NU>
+__device__ __forceinline__ T presmooth_at(const StencilView<T>& A, T omega, const T* __restrict__ rT, int64_t m,
+                                          NodeCoord cm) {
+  const T z1m = omega * stencil_dinv<KIND>(A, m) * rT[m];
+  if (NU == 1) return z1m;
+  const T az = stencil_apply<KIND>(A, m, cm, [&](int64_t mm) {
+    return mm == m ? z1m : omega * stencil_dinv<KIND>(A, mm) * rT[mm];
+  });
+  return z1m + omega * stencil_dinv<KIND>(A, m) * (rT[m] - az);
+}
+
+// zout = z after NU sweeps from zero (used when the pre-sweeps are stored).
+template <int KIND, typename T, int NU>
+__global__ void __launch_bounds__(TPB) k_presmooth(StencilView<T> A, T omega, const T* __restrict__ rT,
+                                                   T* __restrict__ zout, const PcgState* st) {
+  if (load_done(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x)
+    zout[i] = presmooth_at<KIND, T, NU>(A, omega, rT, i, node_coord<KIND>(i, A.N));
+}
+
+// One sweep: zout = zin + w D^-1 (rT - A zin).
 template <int KIND, typename T>
-__global__ void __launch_bounds__(TPB) k_sweep(StencilView<T> A, T omega, Pair<const double> R,
+__global__ void __launch_bounds__(TPB) k_sweep(StencilView<T> A, T omega, const T* __restrict__ rT,
                                                const T* __restrict__ zin, T* __restrict__ zout, const PcgState* st) {
   if (load_done(st)) return;
-  const double* __restrict__ r = R.at(load_iter(st));
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
     const NodeCoord c = node_coord<KIND>(i, A.N);
     const T az = stencil_apply<KIND>(A, i, c, [&](int64_t m) { return zin[m]; });
-    zout[i] = zin[i] + omega * stencil_dinv<KIND>(A, i) * ((T)r[i] - az);
+    zout[i] = zin[i] + omega * stencil_dinv<KIND>(A, i) * (rT[i] - az);
   }
 }
 
 // ----------------------------------------------------------------------------
-// restrict: rho = r - A z, c = P_r^T rho (per-block partials, FP64), and in the
-// last block c = sum of partials, e_c = A_c^-1 c (FP64).
-// Block = 8 warps; columns are split into NCH chunks of KC, each chunk handled
-// by 8/NCH warps, each warp one node tile at a time with 4 nodes per lane
+// restrict: rho = rT - A z, c = P_r^T rho (per-block partials in T), and in the
+// last block c = sum of partials, e_c = A_c^-1 c (in T, A_c^-1 rounded once
+// from the FP64 inverse of the FP64 Cholesky factor).
+//   ZMODE 0: z read from zin;  ZMODE 1 / 2: z = 1 / 2 pre-sweeps recomputed
+//   from rT and stored to zout.
+// Block = 8 warps; columns are split into NCH chunks of 32, each chunk handled
+// by 8/NCH warps, each warp one 128-node tile at a time with 4 nodes per lane
 // (one 16-byte load of P per lane per column for FP32).
 // ----------------------------------------------------------------------------
-template <typename T> struct Vec4;
-template <> struct Vec4<float> {
-  __device__ __forceinline__ static void load(const float* p, float v[4]) {
-    const float4 a = *reinterpret_cast<const float4*>(p);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+// Warp reduce-scatter of 32 per-lane values: afterwards lane l holds the sum
+// over the warp of value l (31 shuffle-adds per lane instead of 5 per value).
+template <typename T>
+__device__ __forceinline__ T warp_reduce_scatter32(T (&v)[32], int lane) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int j = 0; j < off; ++j) {
+      const T send = upper ? v[j] : v[j + off];
+      const T keep = upper ? v[j + off] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
   }
-};
-template <> struct Vec4<double> {
-  __device__ __forceinline__ static void load(const double* p, double v[4]) {
-    const double2 a = *reinterpret_cast<const double2*>(p);
-    const double2 b = *reinterpret_cast<const double2*>(p + 2);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-  }
+  return v[0];
+}
+
+// The two P-streaming kernels (restrict, prolong) run one CTA per SM over a
+// contiguous range of node tiles.  Thread 0 keeps NSTAGE tiles (the first r
+// columns of a tile are one contiguous block: r x 128 values) in flight with
+// bulk asynchronous copies into a shared-memory ring, completion tracked by
+// one mbarrier per stage; a CTA-wide barrier after each tile releases its
+// stage for the next copy.  Thread (w, h) of a CTA of 128 * NCH threads owns
+// node w of the tile and columns [32 h, 32 h + 32).
+struct StreamArgs {
+  int nstage;     // tiles in flight per CTA
+  int max_nodes;  // capacity of the per-CTA residual buffer (restrict)
 };
 
-template <int KIND, typename T, int KC, int NCH>
-__global__ void __launch_bounds__(TPB) k_restrict(StencilView<T> A, Pair<const double> R, const T* __restrict__ z,
-                                                  const T* __restrict__ P, int k, int r, const double* __restrict__ Ainv,
-                                                  double* __restrict__ cpart, double* __restrict__ ec,
-                                                  unsigned* counter, const PcgState* st) {
-  constexpr int TPG = 8 / NCH;  // tiles per group
-  __shared__ double sacc[8][KC];
-  __shared__ double cfull[128];
-  __shared__ int flag;
-  if (load_done(st)) return;
-  const double* __restrict__ rv = R.at(load_iter(st));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ch = warp / TPG, tw = warp % TPG;
-  const int c0 = ch * KC;
-  T acc[KC];
-#pragma unroll
-  for (int j = 0; j < KC; ++j) acc[j] = T(0);
-  const int64_t ntiles = (A.n + NLSP_TILE - 1) / NLSP_TILE;
-  const int64_t ngroups = (ntiles + TPG - 1) / TPG;
-  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-    const int64_t tt = g * TPG + tw;
-    if (tt >= ntiles) continue;
-    T rho[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t i = tt * NLSP_TILE + 4 * lane + u;
-      rho[u] = T(0);
-      if (i < A.n) {
-        const NodeCoord c = node_coord<KIND>(i, A.N);
-        rho[u] = (T)rv[i] - stencil_apply<KIND>(A, i, c, [&](int64_t m) { return z[m]; });
-      }
-    }
-    const T* pt = P + (tt * k) * NLSP_TILE + 4 * lane;
-#pragma unroll 8
-    for (int j = 0; j < KC; ++j) {
-      if (c0 + j < r) {
-        T pv[4];
-        Vec4<T>::load(pt + (int64_t)(c0 + j) * NLSP_TILE, pv);
-        acc[j] += rho[0] * pv[0] + rho[1] * pv[1] + rho[2] * pv[2] + rho[3] * pv[3];
-      }
-    }
+// Waits for stage `s` of iteration `it`; on a timeout records it in *abort_s.
+__device__ __forceinline__ void stream_wait(uint64_t* bar, int it, int nstage, int* abort_s) {
+  if (!tma::mbar_wait(&bar[it % nstage], (unsigned)((it / nstage) & 1))) *abort_s = 1;
+}
+
+// After a timeout: waits (bounded) for every copy still in flight, so that
+// no copy lands in shared memory after the CTA has moved on.
+__device__ __forceinline__ void stream_drain(uint64_t* bar, int it, int nt, int nstage) {
+  if (threadIdx.x == 0)
+    for (int j = it; j < nt && j < it + nstage; ++j) tma::mbar_wait(&bar[j % nstage], (unsigned)((j / nstage) & 1));
+}
+
+__device__ __forceinline__ void report_timeout(PcgState* st, int* err) {
+  if (threadIdx.x != 0) return;
+  if (st) {
+    st->status = (int)NLSP_ERR_TIMEOUT;
+    st->done = 1;
+  } else {
+    atomicExch(err, (int)NLSP_ERR_TIMEOUT);
   }
-#pragma unroll
-  for (int j = 0; j < KC; ++j) {
-    const double v = warp_sum((double)acc[j]);
-    if (lane == 0) sacc[warp][j] = v;
+}
+
+template <int KIND, typename T, int NCH, int ZMODE>
+__global__ void __launch_bounds__(128 * NCH) k_restrict(StencilView<T> A, T omega, const T* __restrict__ rT,
+                                                        const T* __restrict__ zin, T* __restrict__ zout,
+                                                        const T* __restrict__ P, int k, int r, StreamArgs sa,
+                                                        const T* __restrict__ Ainv, T* __restrict__ cpart,
+                                                        T* __restrict__ ec, unsigned* counter, PcgState* st,
+                                                        int* err) {
+  constexpr int NT = 128 * NCH;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[8];
+  __shared__ T sacc[NT / 32][32];
+  __shared__ T red[NT];
+  __shared__ T cfull[128];
+  __shared__ int flag, abort_s;
+  if (load_done(st)) return;
+  const int nstage = sa.nstage;
+  const int ntiles = (int)((A.n + NLSP_TILE - 1) / NLSP_TILE);
+  const int t0 = (int)((int64_t)ntiles * blockIdx.x / gridDim.x);
+  const int nt = (int)((int64_t)ntiles * (blockIdx.x + 1) / gridDim.x) - t0;
+  const unsigned tile_bytes = (unsigned)r * NLSP_TILE * (unsigned)sizeof(T);
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  T* rho_s = buf + (size_t)nstage * r * NLSP_TILE;
+  if (threadIdx.x == 0) {
+    abort_s = 0;
+    for (int s = 0; s < nstage; ++s) tma::mbar_init(&bar[s], 1);
+    tma::fence_barrier_init();
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < NCH * KC; e += blockDim.x) {
-    const int chh = e / KC, j = e % KC;
-    double s = 0.0;
-    for (int w = 0; w < TPG; ++w) s += sacc[chh * TPG + w][j];
-    const int col = chh * KC + j;
-    if (col < r) cpart[(int64_t)blockIdx.x * k + col] = s;
+  if (threadIdx.x == 0)
+    for (int s = 0; s < nstage && s < nt; ++s) {
+      tma::mbar_arrive_expect_tx(&bar[s], tile_bytes);
+      tma::bulk_g2s(buf + (size_t)s * r * NLSP_TILE, P + (size_t)(t0 + s) * k * NLSP_TILE, tile_bytes, &bar[s]);
+    }
+  // phase 1 (overlaps the first copies): rho = rT - A z for the CTA's nodes
+  for (int e = threadIdx.x; e < nt * NLSP_TILE; e += NT) {
+    const int i = t0 * NLSP_TILE + e;
+    T rho = T(0);
+    if (i < A.n) {
+      const NodeCoord c = node_coord<KIND>(i, A.N);
+      if (ZMODE == 0) {
+        rho = rT[i] - stencil_apply<KIND>(A, i, c, [&](int64_t m) { return zin[m]; });
+      } else {
+        const T zi = presmooth_at<KIND, T, ZMODE>(A, omega, rT, i, c);
+        T az = stencil_diag<KIND>(A, i) * zi;
+        for_each_neighbour<KIND>(A, i, c, [&](int64_t m, NodeCoord cm, T a) {
+          az += a * presmooth_at<KIND, T, ZMODE>(A, omega, rT, m, cm);
+        });
+        rho = rT[i] - az;
+        zout[i] = zi;
+      }
+    }
+    rho_s[e] = rho;
+  }
+  __syncthreads();
+  // phase 2: stream the tiles, acc[j] = sum over the CTA's nodes of rho * P
+  const int w = threadIdx.x & (NLSP_TILE - 1), h = threadIdx.x >> 7;
+  const int c0 = h * 32;
+  T acc[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc[j] = T(0);
+  for (int it = 0; it < nt; ++it) {
+    stream_wait(bar, it, nstage, &abort_s);
+    const T* tile = buf + (size_t)(it % nstage) * r * NLSP_TILE;
+    const T rho = rho_s[it * NLSP_TILE + w];
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < r) acc[j] += rho * tile[(c0 + j) * NLSP_TILE + w];
+    __syncthreads();
+    if (abort_s) {
+      stream_drain(bar, it, nt, nstage);
+      report_timeout(st, err);
+      break;
+    }
+    if (threadIdx.x == 0 && it + nstage < nt) {
+      const int s = it % nstage;
+      tma::mbar_arrive_expect_tx(&bar[s], tile_bytes);
+      tma::bulk_g2s(buf + (size_t)s * r * NLSP_TILE, P + (size_t)(t0 + it + nstage) * k * NLSP_TILE, tile_bytes,
+                    &bar[s]);
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  sacc[warp][lane] = warp_reduce_scatter32(acc, lane);  // column c0 + lane, summed over the warp
+  __syncthreads();
+  for (int col = threadIdx.x; col < r; col += NT) {
+    const int hh = col >> 5, j = col & 31;
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s += sacc[hh * 4 + q][j];
+    cpart[(int64_t)blockIdx.x * k + col] = s;
   }
   if (last_block_arrive(counter, &flag)) {
-    for (int col = threadIdx.x; col < r; col += blockDim.x) {
-      double s = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) s += cpart[(int64_t)b * k + col];
+    const int S = NT / r > 0 ? NT / r : 1;  // slices per column
+    T part = T(0);
+    if (threadIdx.x < S * r) {
+      const int col = threadIdx.x % r, sl = threadIdx.x / r;
+      for (int b = sl; b < (int)gridDim.x; b += S) part += cpart[(int64_t)b * k + col];
+    }
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int col = threadIdx.x; col < r; col += NT) {
+      T s = T(0);
+      for (int sl = 0; sl < S; ++sl) s += red[sl * r + col];
       cfull[col] = s;
     }
     __syncthreads();
-    for (int row = threadIdx.x; row < r; row += blockDim.x) {
-      double s = 0.0;
+    for (int row = threadIdx.x; row < r; row += NT) {
+      T s = T(0);
       for (int col = 0; col < r; ++col) s += Ainv[(int64_t)col * r + row] * cfull[col];
       ec[row] = s;
     }
   }
 }
 
-// prolong: z += P_r e_c.  Warp per tile, 4 nodes per lane.
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_prolong(int64_t n, const T* __restrict__ P, int k, int r,
-                                                 const double* __restrict__ ec, T* __restrict__ z, const PcgState* st) {
+// prolong: z += P_r e_c, streaming the tiles like restrict.
+template <typename T, int NCH>
+__global__ void __launch_bounds__(128 * NCH) k_prolong(int64_t n, const T* __restrict__ P, int k, int r,
+                                                       StreamArgs sa, const T* __restrict__ ec, T* __restrict__ z,
+                                                       PcgState* st, int* err) {
+  constexpr int NT = 128 * NCH;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[8];
+  __shared__ T zpart[2][NCH][NLSP_TILE];
   __shared__ T e[128];
+  __shared__ int abort_s;
   if (load_done(st)) return;
-  for (int j = threadIdx.x; j < r; j += blockDim.x) e[j] = (T)ec[j];
+  const int nstage = sa.nstage;
+  const int ntiles = (int)((n + NLSP_TILE - 1) / NLSP_TILE);
+  const int t0 = (int)((int64_t)ntiles * blockIdx.x / gridDim.x);
+  const int nt = (int)((int64_t)ntiles * (blockIdx.x + 1) / gridDim.x) - t0;
+  const unsigned tile_bytes = (unsigned)r * NLSP_TILE * (unsigned)sizeof(T);
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  for (int j = threadIdx.x; j < r; j += NT) e[j] = ec[j];
+  if (threadIdx.x == 0) {
+    abort_s = 0;
+    for (int s = 0; s < nstage; ++s) tma::mbar_init(&bar[s], 1);
+    tma::fence_barrier_init();
+  }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ntiles = (n + NLSP_TILE - 1) / NLSP_TILE;
-  for (int64_t tt = (int64_t)blockIdx.x * 8 + warp; tt < ntiles; tt += (int64_t)gridDim.x * 8) {
-    const T* pt = P + (tt * k) * NLSP_TILE + 4 * lane;
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-#pragma unroll 8
-    for (int j = 0; j < r; ++j) {
-      T pv[4];
-      Vec4<T>::load(pt + (int64_t)j * NLSP_TILE, pv);
-      const T ej = e[j];
-      a0 += pv[0] * ej;
-      a1 += pv[1] * ej;
-      a2 += pv[2] * ej;
-      a3 += pv[3] * ej;
+  if (threadIdx.x == 0)
+    for (int s = 0; s < nstage && s < nt; ++s) {
+      tma::mbar_arrive_expect_tx(&bar[s], tile_bytes);
+      tma::bulk_g2s(buf + (size_t)s * r * NLSP_TILE, P + (size_t)(t0 + s) * k * NLSP_TILE, tile_bytes, &bar[s]);
     }
-    const int64_t i0 = tt * NLSP_TILE + 4 * lane;
-    if (i0 + 0 < n) z[i0 + 0] += a0;
-    if (i0 + 1 < n) z[i0 + 1] += a1;
-    if (i0 + 2 < n) z[i0 + 2] += a2;
-    if (i0 + 3 < n) z[i0 + 3] += a3;
+  const int w = threadIdx.x & (NLSP_TILE - 1), h = threadIdx.x >> 7;
+  const int c0 = h * 32;
+  for (int it = 0; it < nt; ++it) {
+    stream_wait(bar, it, nstage, &abort_s);
+    const T* tile = buf + (size_t)(it % nstage) * r * NLSP_TILE;
+    T a = T(0);
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < r) a += tile[(c0 + j) * NLSP_TILE + w] * e[c0 + j];
+    zpart[it & 1][h][w] = a;
+    __syncthreads();
+    if (abort_s) {
+      stream_drain(bar, it, nt, nstage);
+      report_timeout(st, err);
+      return;
+    }
+    if (threadIdx.x == 0 && it + nstage < nt) {
+      const int s = it % nstage;
+      tma::mbar_arrive_expect_tx(&bar[s], tile_bytes);
+      tma::bulk_g2s(buf + (size_t)s * r * NLSP_TILE, P + (size_t)(t0 + it + nstage) * k * NLSP_TILE, tile_bytes,
+                    &bar[s]);
+    }
+    if (h == 0) {
+      T sum = zpart[it & 1][0][w];
+#pragma unroll
+      for (int q = 1; q < NCH; ++q) sum += zpart[it & 1][q][w];
+      const int64_t i = (int64_t)(t0 + it) * NLSP_TILE + w;
+      if (i < n) z[i] += sum;
+    }
   }
 }
 
 // ----------------------------------------------------------------------------
-// post: final post-smoothing sweep(s) into z_t, r^T z_t (and r^T z_{t-1}).
-//   FUSE2: two sweeps in one pass, the first recomputed at the neighbours.
+// post: final post-smoothing sweep(s), z_t stored in FP64, r^T z_t (and
+// r^T z_{t-1}).  FUSE2: two sweeps in one pass, the first recomputed at the
+// neighbours.  With st == nullptr (standalone apply) only z is written.
 // ----------------------------------------------------------------------------
-template <int KIND, typename T, bool FUSE2, bool INIT>
-__global__ void __launch_bounds__(TPB) k_pcg_post(StencilView<T> A, T omega, Pair<const double> R,
-                                                  const T* __restrict__ zin, Pair<T> Z, PcgState* st, RedSlots red,
-                                                  cudaGraphConditionalHandle cond, int set_cond) {
-  __shared__ double sred[32];
+template <int KIND, typename T, bool FUSE2, bool INIT, bool SET_COND>
+__global__ void __launch_bounds__(TPB) k_pcg_post(StencilView<T> A, T omega, const T* __restrict__ rT,
+                                                  const double* __restrict__ r, const T* __restrict__ zin,
+                                                  Pair<double> Z, PcgState* st, RedSlots red,
+                                                  cudaGraphConditionalHandle cond) {
+  __shared__ double sm[TPB];
   __shared__ int flag;
   if (load_done(st)) {
-    if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    if (SET_COND && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     return;
   }
   const int t = load_iter(st);
-  const double* __restrict__ r = R.at(t);
-  T* __restrict__ zout = Z.at(t);
-  const T* __restrict__ zold = Z.at(t + 1);  // z_{t-1}
+  double* __restrict__ zout = Z.at(t);
+  const double* __restrict__ zold = Z.at(t + 1);  // z_{t-1}
   const bool flex = st && !INIT && st->flexible;
   double s_rz = 0.0, s_ro = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
     const NodeCoord c = node_coord<KIND>(i, A.N);
     T zf;
     if (FUSE2) {
       auto z4at = [&](int64_t m, NodeCoord cm) -> T {
         const T az = stencil_apply<KIND>(A, m, cm, [&](int64_t mm) { return zin[mm]; });
-        return zin[m] + omega * stencil_dinv<KIND>(A, m) * ((T)r[m] - az);
+        return zin[m] + omega * stencil_dinv<KIND>(A, m) * (rT[m] - az);
       };
       const T z4i = z4at(i, c);
       T az4 = stencil_diag<KIND>(A, i) * z4i;
       for_each_neighbour<KIND>(A, i, c, [&](int64_t m, NodeCoord cm, T a) { az4 += a * z4at(m, cm); });
-      zf = z4i + omega * stencil_dinv<KIND>(A, i) * ((T)r[i] - az4);
+      zf = z4i + omega * stencil_dinv<KIND>(A, i) * (rT[i] - az4);
     } else {
       const T az = stencil_apply<KIND>(A, i, c, [&](int64_t m) { return zin[m]; });
-      zf = zin[i] + omega * stencil_dinv<KIND>(A, i) * ((T)r[i] - az);
+      zf = zin[i] + omega * stencil_dinv<KIND>(A, i) * (rT[i] - az);
     }
-    zout[i] = zf;
+    const double zd = (double)zf;
+    zout[i] = zd;
     if (st) {
-      s_rz += r[i] * (double)zf;
-      if (flex) s_ro += r[i] * (double)zold[i];
+      const double ri = r[i];
+      s_rz = fma(ri, zd, s_rz);
+      if (flex) s_ro = fma(ri, zold[i], s_ro);
     }
   }
   if (!st) return;
-  s_rz = block_sum(s_rz, sred);
-  if (flex) s_ro = block_sum(s_ro, sred);
+  s_rz = block_sum_lean(s_rz, sm);
+  if (flex) s_ro = block_sum_lean(s_ro, sm);
   if (threadIdx.x == 0) {
     red.part[2 * red.max_blocks + blockIdx.x] = s_rz;
     red.part[3 * red.max_blocks + blockIdx.x] = s_ro;
   }
   if (last_block_arrive(&red.counter[2], &flag)) {
-    const double rz = block_sum_partials(red.part + 2 * red.max_blocks, gridDim.x, 1, sred);
-    const double ro = flex ? block_sum_partials(red.part + 3 * red.max_blocks, gridDim.x, 1, sred) : 0.0;
+    const double rz = sum_partials_lean(red.part + 2 * red.max_blocks, gridDim.x, sm);
+    const double ro = flex ? sum_partials_lean(red.part + 3 * red.max_blocks, gridDim.x, sm) : 0.0;
     if (threadIdx.x == 0) {
       if (!(rz > 0.0) || !isfinite(rz)) {
         mark_breakdown(st);
@@ -392,7 +540,7 @@ __global__ void __launch_bounds__(TPB) k_pcg_post(StencilView<T> A, T omega, Pai
         st->status = (int)NLSP_NOT_CONVERGED;
         st->done = 1;
       }
-      if (set_cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+      if (SET_COND) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
     }
   }
 }
@@ -401,26 +549,26 @@ __global__ void __launch_bounds__(TPB) k_pcg_post(StencilView<T> A, T omega, Pai
 template <int KIND>
 __global__ void __launch_bounds__(TPB) k_true_residual(StencilView<double> A, const double* __restrict__ b,
                                                        const double* __restrict__ x, PcgState* st, RedSlots red) {
-  __shared__ double sred[32];
+  __shared__ double sm[TPB];
   __shared__ int flag;
   double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
     const NodeCoord c = node_coord<KIND>(i, A.N);
     const double ri = b[i] - stencil_apply<KIND>(A, i, c, [&](int64_t m) { return x[m]; });
-    s += ri * ri;
+    s = fma(ri, ri, s);
   }
-  s = block_sum(s, sred);
+  s = block_sum_lean(s, sm);
   if (threadIdx.x == 0) red.part[blockIdx.x] = s;
   if (last_block_arrive(&red.counter[3], &flag)) {
-    const double tr = block_sum_partials(red.part, gridDim.x, 1, sred);
+    const double tr = sum_partials_lean(red.part, gridDim.x, sm);
     if (threadIdx.x == 0) st->true_rr = tr;
   }
 }
 
 template <typename T>
-__global__ void k_to_double(const T* __restrict__ a, double* __restrict__ b, int64_t n) {
+__global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
+    b[i] = (T)a[i];
 }
 
 }  // namespace
@@ -431,12 +579,12 @@ __global__ void k_to_double(const T* __restrict__ a, double* __restrict__ b, int
 struct PcgWork {
   int64_t n = 0;
   int tsize = 0;
-  double* vec = nullptr;   // R[2], Pv[2], q, x  (n each)
-  void* zbuf = nullptr;    // Z[2] in the preconditioner precision
+  double* vec = nullptr;   // x, r, q, Pv[2], Z[2]  (n each, FP64)
+  void* rT = nullptr;      // residual in the preconditioner precision (FP32 path)
   double* part = nullptr;  // [4][max_blocks]
   unsigned* counter = nullptr;
   int max_blocks = 0;
-  PcgState* st = nullptr;  // the state the graph works on
+  PcgState* st = nullptr;  // the state the graphs work on
   PcgState* st_all = nullptr;
   int st_cap = 0;
   PcgState* h_st = nullptr;  // pinned
@@ -445,6 +593,7 @@ struct PcgWork {
   cudaGraphExec_t x_while = nullptr, x_iter = nullptr;
   cudaGraphConditionalHandle cond = 0;
   int built_r = -1;
+  int body_launches = 0;  // kernels in one iteration body
 };
 
 namespace {
@@ -465,7 +614,7 @@ void free_work(PcgWork* w) {
   if (!w) return;
   destroy_graphs(w);
   if (w->vec) cudaFree(w->vec);
-  if (w->zbuf) cudaFree(w->zbuf);
+  if (w->rT) cudaFree(w->rT);
   if (w->part) cudaFree(w->part);
   if (w->counter) cudaFree(w->counter);
   if (w->st_all) cudaFree(w->st_all);
@@ -474,20 +623,22 @@ void free_work(PcgWork* w) {
   delete w;
 }
 
+int node_grid(const nlsp_ctx* ctx, int64_t n) { return grid_for(ctx, n, TPB, NODE_BPS); }
+
 nlsp_status ensure_work(nlsp_prec* M, int m) {
   nlsp_ctx* ctx = M->ctx;
   if (!M->pcg) {
     PcgWork* w = new PcgWork();
     w->n = M->n;
     w->tsize = M->precision == NLSP_FP64 ? 8 : 4;
-    w->max_blocks = ctx->num_sms * 8;
+    w->max_blocks = ctx->num_sms * NODE_BPS;
     M->pcg = w;
-    NLSP_CUDA(cudaMalloc(&w->vec, sizeof(double) * M->n * 6));
-    NLSP_CUDA(cudaMalloc(&w->zbuf, (size_t)w->tsize * M->n * 2));
+    NLSP_CUDA(cudaMalloc(&w->vec, sizeof(double) * M->n * 7));
+    NLSP_CUDA(cudaMemsetAsync(w->vec, 0, sizeof(double) * M->n * 7, ctx->stream));
+    NLSP_CUDA(cudaMalloc(&w->rT, (size_t)w->tsize * M->n));
     NLSP_CUDA(cudaMalloc(&w->part, sizeof(double) * 4 * w->max_blocks));
     NLSP_CUDA(cudaMalloc(&w->counter, sizeof(unsigned) * 4));
     NLSP_CUDA(cudaMemsetAsync(w->counter, 0, sizeof(unsigned) * 4, ctx->stream));
-    NLSP_CUDA(cudaMemsetAsync(w->zbuf, 0, (size_t)w->tsize * M->n * 2, ctx->stream));
     NLSP_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
   }
   PcgWork* w = M->pcg;
@@ -508,88 +659,213 @@ nlsp_status ensure_work(nlsp_prec* M, int m) {
 
 RedSlots red_of(PcgWork* w) { return RedSlots{w->part, w->counter, w->max_blocks}; }
 
-int node_grid(const nlsp_ctx* ctx, int64_t n) { return grid_for(ctx, n, TPB, 8); }
+template <typename T>
+const StencilView<T>& view_T(const nlsp_op* A) {
+  return *reinterpret_cast<const StencilView<T>*>(sizeof(T) == 8 ? (const void*)&A->v64 : (const void*)&A->v32);
+}
 
-// Enqueues one preconditioner application on stream s.
-//  loop = false: z = B r with r = R.at(iter) (start of a solve, or standalone)
-//  loop = true:  the PCG iteration body after the spmv kernel
+// Launch plan of the P-streaming kernels: two CTAs per SM (more when a CTA's
+// residual buffer would exceed 32 KB), as many tiles in flight as fit in
+// ~100 KB of shared memory per CTA (at most 4).
+struct StreamPlan {
+  int grid, nch;
+  StreamArgs sa;
+  size_t smem_restrict, smem_prolong;
+};
+
+template <typename T>
+StreamPlan stream_plan(const nlsp_prec* M) {
+  StreamPlan pl;
+  const int ntiles = (int)((M->n + NLSP_TILE - 1) / NLSP_TILE);
+  pl.grid = std::max(std::min(ntiles, 2 * M->ctx->num_sms), div_up((int64_t)ntiles * NLSP_TILE, 8192));
+  pl.grid = std::min(pl.grid, M->rblocks);
+  pl.nch = (M->r + 31) / 32;
+  const size_t tile = (size_t)M->r * NLSP_TILE * sizeof(T);
+  pl.sa.max_nodes = div_up(ntiles, pl.grid) * NLSP_TILE;
+  const size_t rho = (size_t)pl.sa.max_nodes * sizeof(T);
+  const size_t budget = std::max<size_t>(100 * 1024, tile + rho);
+  pl.sa.nstage = (int)std::max<size_t>(1, std::min<size_t>(4, (budget - std::min(budget - tile, rho)) / tile));
+  pl.smem_restrict = (size_t)pl.sa.nstage * tile + rho;
+  pl.smem_prolong = (size_t)pl.sa.nstage * tile;
+  return pl;
+}
+
+// Raises a kernel's dynamic shared-memory limit to what the device allows
+// beside its static shared memory.  Called before any stream capture.
+template <typename F>
+nlsp_status allow_max_smem(F fn) {
+  cudaFuncAttributes fa;
+  NLSP_CUDA(cudaFuncGetAttributes(&fa, fn));
+  int dev = 0, optin = 0;
+  NLSP_CUDA(cudaGetDevice(&dev));
+  NLSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+  return NLSP_OK;
+}
+
 template <int KIND, typename T>
-nlsp_status enqueue_apply(const nlsp_prec* M, cudaStream_t s, bool loop, Pair<double> R, const double* q,
-                          Pair<const double> Pv, double* x, Pair<T> Z, PcgState* st, RedSlots red,
-                          cudaGraphConditionalHandle cond, int set_cond) {
+nlsp_status prepare_stream_kernels() {
+  static bool done = false;  // once per instantiation and process (one device)
+  if (done) return NLSP_OK;
+  NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 1, 0>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 1, 1>));
+  NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 1, 2>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 2, 0>));
+  NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 2, 1>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 2, 2>));
+  NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 3, 0>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 3, 1>));
+  NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 3, 2>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 4, 0>));
+  NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 4, 1>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 4, 2>));
+  NLSP_TRY(allow_max_smem(k_prolong<T, 1>)); NLSP_TRY(allow_max_smem(k_prolong<T, 2>));
+  NLSP_TRY(allow_max_smem(k_prolong<T, 3>)); NLSP_TRY(allow_max_smem(k_prolong<T, 4>));
+  done = true;
+  return NLSP_OK;
+}
+
+template <int KIND, typename T, int NCH>
+nlsp_status launch_restrict_n(const nlsp_prec* M, cudaStream_t s, const StreamPlan& pl, int zm, const T* rT, T* z,
+                              PcgState* st) {
+  const StencilView<T>& A = view_T<T>(M->A);
+  auto go = [&](auto fn) -> nlsp_status {
+    fn<<<pl.grid, 128 * NCH, pl.smem_restrict, s>>>(A, (T)M->omega, rT, z, z, (const T*)M->P, M->k, M->r, pl.sa,
+                                                    (const T*)M->AinvT, (T*)M->cpart, (T*)M->ec, M->counter, st,
+                                                    M->status);
+    return NLSP_OK;
+  };
+  if (zm == 0) return go(k_restrict<KIND, T, NCH, 0>);
+  if (zm == 1) return go(k_restrict<KIND, T, NCH, 1>);
+  return go(k_restrict<KIND, T, NCH, 2>);
+}
+
+template <int KIND, typename T>
+nlsp_status launch_restrict(const nlsp_prec* M, cudaStream_t s, const StreamPlan& pl, int zm, const T* rT, T* z,
+                            PcgState* st) {
+  switch (pl.nch) {
+    case 1: return launch_restrict_n<KIND, T, 1>(M, s, pl, zm, rT, z, st);
+    case 2: return launch_restrict_n<KIND, T, 2>(M, s, pl, zm, rT, z, st);
+    case 3: return launch_restrict_n<KIND, T, 3>(M, s, pl, zm, rT, z, st);
+    default: return launch_restrict_n<KIND, T, 4>(M, s, pl, zm, rT, z, st);
+  }
+}
+
+template <typename T>
+nlsp_status launch_prolong(const nlsp_prec* M, cudaStream_t s, const StreamPlan& pl, T* z, PcgState* st) {
+  auto go = [&](auto fn, int nt) -> nlsp_status {
+    fn<<<pl.grid, nt, pl.smem_prolong, s>>>(M->n, (const T*)M->P, M->k, M->r, pl.sa, (const T*)M->ec, z, st,
+                                            M->status);
+    return NLSP_OK;
+  };
+  switch (pl.nch) {
+    case 1: return go(k_prolong<T, 1>, 128);
+    case 2: return go(k_prolong<T, 2>, 256);
+    case 3: return go(k_prolong<T, 3>, 384);
+    default: return go(k_prolong<T, 4>, 512);
+  }
+}
+
+// Enqueues the preconditioner application z = B r on stream s: rT holds r in
+// the preconditioner precision; the result goes to Z.at(iter) in FP64, with
+// r^T z (and flexible terms) reduced into st when st != nullptr.
+// Returns the number of kernels enqueued in *nlaunch.
+template <int KIND, typename T>
+nlsp_status enqueue_prec(const nlsp_prec* M, cudaStream_t s, bool init, const T* rT, const double* r, Pair<double> Z,
+                         PcgState* st, RedSlots red, cudaGraphConditionalHandle cond, int set_cond, int* nlaunch) {
   const nlsp_ctx* ctx = M->ctx;
-  const StencilView<T>& A = *reinterpret_cast<const StencilView<T>*>(
-      sizeof(T) == 8 ? (const void*)&M->A->v64 : (const void*)&M->A->v32);
+  const StencilView<T>& A = view_T<T>(M->A);
   const T omega = (T)M->omega;
   const int g = node_grid(ctx, M->n);
   T* cur = (T*)M->w0;
   T* oth = (T*)M->w1;
-  Pair<const double> Rc{{R.v[0], R.v[1]}};
-  if (loop)
-    k_pcg_pre<KIND, T, false><<<g, TPB, 0, s>>>(A, omega, M->nu1, R, q, Pv, x, cur, st, red);
-  else
-    k_pcg_pre<KIND, T, true><<<g, TPB, 0, s>>>(A, omega, M->nu1, R, q, Pv, x, cur, st, red);
-  for (int sw = 2; sw < M->nu1; ++sw) {
-    k_sweep<KIND, T><<<g, TPB, 0, s>>>(A, omega, Rc, cur, oth, st);
+  int nl = 0;
+  constexpr bool FP32 = sizeof(T) == 4;
+  const StreamPlan pl = stream_plan<T>(M);
+  // pre-smoothing (+ restriction)
+  const bool fused_pre = FP32 && M->nu1 <= 2;
+  if (!fused_pre) {
+    if (M->nu1 == 1) k_presmooth<KIND, T, 1><<<g, TPB, 0, s>>>(A, omega, rT, cur, st);
+    else k_presmooth<KIND, T, 2><<<g, TPB, 0, s>>>(A, omega, rT, cur, st);
+    ++nl;
+    for (int sw = 2; sw < M->nu1; ++sw, ++nl) {
+      k_sweep<KIND, T><<<g, TPB, 0, s>>>(A, omega, rT, cur, oth, st);
+      std::swap(cur, oth);
+    }
+  }
+  NLSP_TRY((launch_restrict<KIND, T>(M, s, pl, fused_pre ? M->nu1 : 0, rT, cur, st)));
+  NLSP_TRY(launch_prolong<T>(M, s, pl, cur, st));
+  nl += 2;
+  // post-smoothing
+  const int nfinal = (FP32 && M->nu2 >= 2) ? 2 : 1;
+  for (int sw = nfinal; sw < M->nu2; ++sw, ++nl) {
+    k_sweep<KIND, T><<<g, TPB, 0, s>>>(A, omega, rT, cur, oth, st);
     std::swap(cur, oth);
   }
-  // restriction + coarse solve
-  const int r = M->r, k = M->k;
-  const int64_t ntiles = (M->n + NLSP_TILE - 1) / NLSP_TILE;
-  const int nch = r <= 32 ? 1 : (r <= 64 ? 2 : 4);
-  const int64_t ngroups = (ntiles + (8 / nch) - 1) / (8 / nch);
-  const int rg = (int)std::min<int64_t>(ngroups, M->rblocks);
-  const T* P = (const T*)M->P;
-  if (nch == 1)
-    k_restrict<KIND, T, 32, 1><<<rg, TPB, 0, s>>>(A, Rc, cur, P, k, r, M->Ainv, M->cpart, M->ec, M->counter, st);
-  else if (nch == 2)
-    k_restrict<KIND, T, 32, 2><<<rg, TPB, 0, s>>>(A, Rc, cur, P, k, r, M->Ainv, M->cpart, M->ec, M->counter, st);
-  else
-    k_restrict<KIND, T, 32, 4><<<rg, TPB, 0, s>>>(A, Rc, cur, P, k, r, M->Ainv, M->cpart, M->ec, M->counter, st);
-  const int pg = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + 7) / 8, (int64_t)ctx->num_sms * 8));
-  k_prolong<T><<<pg, TPB, 0, s>>>(M->n, P, k, r, M->ec, cur, st);
-  constexpr bool FUSE2 = sizeof(T) == 4;
-  const int nfinal = (FUSE2 && M->nu2 >= 2) ? 2 : 1;
-  for (int sw = nfinal; sw < M->nu2; ++sw) {
-    k_sweep<KIND, T><<<g, TPB, 0, s>>>(A, omega, Rc, cur, oth, st);
-    std::swap(cur, oth);
-  }
-  Pair<const double> Rp{{R.v[0], R.v[1]}};
+#define NLSP_POST(F2_, INIT_, SC_) \
+  k_pcg_post<KIND, T, F2_, INIT_, SC_><<<g, TPB, 0, s>>>(A, omega, rT, r, cur, Z, st, red, cond)
   if (nfinal == 2) {
-    if (loop) k_pcg_post<KIND, T, true, false><<<g, TPB, 0, s>>>(A, omega, Rp, cur, Z, st, red, cond, set_cond);
-    else k_pcg_post<KIND, T, true, true><<<g, TPB, 0, s>>>(A, omega, Rp, cur, Z, st, red, cond, set_cond);
+    if (init) NLSP_POST(true, true, false); else if (set_cond) NLSP_POST(true, false, true); else NLSP_POST(true, false, false);
   } else {
-    if (loop) k_pcg_post<KIND, T, false, false><<<g, TPB, 0, s>>>(A, omega, Rp, cur, Z, st, red, cond, set_cond);
-    else k_pcg_post<KIND, T, false, true><<<g, TPB, 0, s>>>(A, omega, Rp, cur, Z, st, red, cond, set_cond);
+    if (init) NLSP_POST(false, true, false); else if (set_cond) NLSP_POST(false, false, true); else NLSP_POST(false, false, false);
   }
+#undef NLSP_POST
+  ++nl;
   NLSP_LAUNCH_CHECK();
+  *nlaunch = nl;
   return NLSP_OK;
 }
 
 template <int KIND, typename T>
 struct Solver {
-  static Pair<double> Rpair(PcgWork* w) { return Pair<double>{{w->vec, w->vec + w->n}}; }
-  static Pair<double> Ppair(PcgWork* w) { return Pair<double>{{w->vec + 2 * w->n, w->vec + 3 * w->n}}; }
-  static double* q(PcgWork* w) { return w->vec + 4 * w->n; }
-  static double* x(PcgWork* w) { return w->vec + 5 * w->n; }
-  static Pair<T> Zpair(PcgWork* w) { return Pair<T>{{(T*)w->zbuf, (T*)w->zbuf + w->n}}; }
+  static double* x(PcgWork* w) { return w->vec; }
+  static double* r(PcgWork* w) { return w->vec + w->n; }
+  static double* q(PcgWork* w) { return w->vec + 2 * w->n; }
+  static Pair<double> Ppair(PcgWork* w) { return Pair<double>{{w->vec + 3 * w->n, w->vec + 4 * w->n}}; }
+  static Pair<double> Zpair(PcgWork* w) { return Pair<double>{{w->vec + 5 * w->n, w->vec + 6 * w->n}}; }
+  // residual in the preconditioner precision (the FP64 path uses r itself)
+  static T* rT(PcgWork* w) { return sizeof(T) == 8 ? (T*)r(w) : (T*)w->rT; }
 
-  // One PCG iteration body (spmv, pre, restrict, prolong, post).
-  static nlsp_status enqueue_body(const nlsp_prec* M, cudaStream_t s, int set_cond) {
+  // One PCG iteration (spmv, pre, then the preconditioner).
+  static nlsp_status enqueue_body(const nlsp_prec* M, cudaStream_t s, int set_cond, int* nlaunch) {
     PcgWork* w = M->pcg;
     const int g = node_grid(M->ctx, M->n);
-    Pair<const T> Zc{{(const T*)w->zbuf, (const T*)w->zbuf + w->n}};
-    k_pcg_spmv<KIND, T><<<g, TPB, 0, s>>>(M->A->v64, Zc, Ppair(w), q(w), w->st, red_of(w));
+    Pair<double> Z = Zpair(w), P2 = Ppair(w);
+    Pair<const double> Zc{{Z.v[0], Z.v[1]}}, Pc{{P2.v[0], P2.v[1]}};
+    k_pcg_spmv<KIND><<<g, TPB, 0, s>>>(M->A->v64, Zc, P2, q(w), w->st, red_of(w));
+    k_pcg_pre<T><<<g, TPB, 0, s>>>(M->n, x(w), r(w), rT(w), q(w), Pc, w->st, red_of(w));
     NLSP_LAUNCH_CHECK();
-    Pair<double> P2 = Ppair(w);
-    Pair<const double> Pc{{P2.v[0], P2.v[1]}};
-    return enqueue_apply<KIND, T>(M, s, true, Rpair(w), q(w), Pc, x(w), Zpair(w), w->st, red_of(w), w->cond,
-                                  set_cond);
+    int na = 0;
+    nlsp_status st = enqueue_prec<KIND, T>(M, s, false, rT(w), r(w), Z, w->st, red_of(w), w->cond, set_cond, &na);
+    *nlaunch = 2 + na;
+    return st;
+  }
+
+  // Keeps P resident in L2 while the iteration graphs run: the captured
+  // kernel nodes inherit an access-policy window over P from the capture
+  // stream (P is read twice per iteration).  The persisting-L2 limit is a
+  // setting of this process's context only.
+  static nlsp_status set_l2_window(nlsp_prec* M) {
+    PcgWork* w = M->pcg;
+    int dev = 0, max_persist = 0, max_window = 0;
+    NLSP_CUDA(cudaGetDevice(&dev));
+    NLSP_CUDA(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev));
+    NLSP_CUDA(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev));
+    if (max_persist <= 0 || max_window <= 0) return NLSP_OK;
+    const size_t pbytes = (size_t)M->n_pad * M->k * sizeof(T);
+    size_t limit = 0;
+    NLSP_CUDA(cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize));
+    const size_t want = std::min<size_t>(pbytes, (size_t)max_persist);
+    if (limit < want) NLSP_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+    cudaStreamAttrValue v;
+    memset(&v, 0, sizeof(v));
+    v.accessPolicyWindow.base_ptr = M->P;
+    v.accessPolicyWindow.num_bytes = std::min<size_t>(pbytes, (size_t)max_window);
+    v.accessPolicyWindow.hitRatio = (float)std::min(1.0, (double)want / (double)v.accessPolicyWindow.num_bytes);
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    NLSP_CUDA(cudaStreamSetAttribute(w->cap, cudaStreamAttributeAccessPolicyWindow, &v));
+    return NLSP_OK;
   }
 
   static nlsp_status build_graphs(nlsp_prec* M) {
     PcgWork* w = M->pcg;
     destroy_graphs(w);
+    NLSP_TRY(set_l2_window(M));
     // while-loop graph: a single conditional node whose body is one iteration
     NLSP_CUDA(cudaGraphCreate(&w->g_while, 0));
     NLSP_CUDA(cudaGraphConditionalHandleCreate(&w->cond, w->g_while, 1u, cudaGraphCondAssignDefault));
@@ -601,15 +877,16 @@ struct Solver {
     NLSP_CUDA(cudaGraphAddNode(&node, w->g_while, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     NLSP_CUDA(cudaStreamBeginCaptureToGraph(w->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    nlsp_status st = enqueue_body(M, w->cap, 1);
+    nlsp_status st = enqueue_body(M, w->cap, 1, &w->body_launches);
     cudaGraph_t dummy = nullptr;
     cudaError_t e = cudaStreamEndCapture(w->cap, &dummy);
     if (st != NLSP_OK) return st;
     NLSP_CUDA(e);
     NLSP_CUDA(cudaGraphInstantiate(&w->x_while, w->g_while, 0));
-    // single-iteration graph for host-checked mode
+    // single-iteration graph for the host-checked mode
     NLSP_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
-    st = enqueue_body(M, w->cap, 0);
+    int nb = 0;
+    st = enqueue_body(M, w->cap, 0, &nb);
     e = cudaStreamEndCapture(w->cap, &w->g_iter);
     if (st != NLSP_OK) return st;
     NLSP_CUDA(e);
@@ -623,18 +900,20 @@ struct Solver {
     nlsp_ctx* ctx = M->ctx;
     cudaStream_t s = ctx->stream;
     NLSP_TRY(ensure_work(M, m));
+    NLSP_TRY((prepare_stream_kernels<KIND, T>()));
     PcgWork* w = M->pcg;
     if (!w->x_while || w->built_r != M->r) NLSP_TRY(build_graphs(M));
     const int flexible = prm->flexible < 0 ? (M->precision != NLSP_FP64) : (prm->flexible != 0);
     const int g = node_grid(ctx, M->n);
     for (int col = 0; col < m; ++col) {
       const double* b = B + col * ldb;
-      Pair<double> R = Rpair(w), P2 = Ppair(w);
-      k_pcg_init<<<g, TPB, 0, s>>>(M->n, b, x(w), R.v[0], P2.v[0], P2.v[1], q(w), w->st, prm->tol, prm->maxit,
-                                   flexible, red_of(w));
+      Pair<double> P2 = Ppair(w);
+      k_pcg_init<T><<<g, TPB, 0, s>>>(M->n, b, x(w), r(w), rT(w), P2.v[0], P2.v[1], q(w), w->st, prm->tol,
+                                      prm->maxit, flexible, red_of(w));
       NLSP_LAUNCH_CHECK();
-      Pair<const double> Pc{{P2.v[0], P2.v[1]}};
-      NLSP_TRY((enqueue_apply<KIND, T>(M, s, false, R, q(w), Pc, x(w), Zpair(w), w->st, red_of(w), 0, 0)));
+      int na = 0;
+      NLSP_TRY((enqueue_prec<KIND, T>(M, s, true, rT(w), r(w), Zpair(w), w->st, red_of(w), 0, 0, &na)));
+      count_launches(ctx, 2 + na);  // init, preconditioner, true residual
       if (prm->graph_mode == 1) {
         NLSP_CUDA(cudaGraphLaunch(w->x_while, s));
       } else {
@@ -642,6 +921,7 @@ struct Solver {
         while (done_iters < prm->maxit) {
           const int chunk = std::min(8, prm->maxit - done_iters);
           for (int c = 0; c < chunk; ++c) NLSP_CUDA(cudaGraphLaunch(w->x_iter, s));
+          count_launches(ctx, (unsigned long long)chunk * w->body_launches);
           done_iters += chunk;
           NLSP_CUDA(cudaMemcpyAsync(w->h_st, w->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
           NLSP_CUDA(cudaStreamSynchronize(s));
@@ -658,6 +938,7 @@ struct Solver {
     nlsp_status worst = NLSP_OK;
     for (int col = 0; col < m; ++col) {
       const PcgState& h = w->h_st[col];
+      if (prm->graph_mode == 1) count_launches(ctx, (unsigned long long)std::max(h.iter, 1) * w->body_launches);
       int stc = h.status;
       if (stc == NLSP_OK && !h.done) stc = NLSP_NOT_CONVERGED;
       if (infos) {
@@ -672,20 +953,25 @@ struct Solver {
     return worst;
   }
 
-  static nlsp_status apply(nlsp_prec* M, int m, const double* Rin, int64_t ldr, double* Z, int64_t ldz) {
+  static nlsp_status apply(nlsp_prec* M, int m, const double* Rin, int64_t ldr, double* Zout, int64_t ldz) {
     nlsp_ctx* ctx = M->ctx;
     cudaStream_t s = ctx->stream;
     NLSP_TRY(ensure_work(M, 1));
+    NLSP_TRY((prepare_stream_kernels<KIND, T>()));
     PcgWork* w = M->pcg;
-    T* zout = (T*)w->zbuf;
     for (int col = 0; col < m; ++col) {
-      double* rc = const_cast<double*>(Rin + col * ldr);
-      Pair<double> R{{rc, rc}};
-      Pair<const double> Pc{{nullptr, nullptr}};
-      Pair<T> Zp{{zout, zout}};
-      NLSP_TRY((enqueue_apply<KIND, T>(M, s, false, R, nullptr, Pc, nullptr, Zp, nullptr, red_of(w), 0, 0)));
-      k_to_double<T><<<node_grid(ctx, M->n), TPB, 0, s>>>(zout, Z + col * ldz, M->n);
-      NLSP_LAUNCH_CHECK();
+      const double* rc = Rin + col * ldr;
+      const T* rt = (const T*)rc;
+      if (sizeof(T) == 4) {
+        k_convert<T><<<node_grid(ctx, M->n), TPB, 0, s>>>(rc, (T*)w->rT, M->n);
+        rt = (const T*)w->rT;
+        count_launches(ctx, 1);
+      }
+      double* zc = Zout + col * ldz;
+      Pair<double> Zp{{zc, zc}};
+      int na = 0;
+      NLSP_TRY((enqueue_prec<KIND, T>(M, s, true, rt, rc, Zp, nullptr, red_of(w), 0, 0, &na)));
+      count_launches(ctx, na);
     }
     return NLSP_OK;
   }
@@ -705,6 +991,25 @@ nlsp_status dispatch(const nlsp_prec* M, F f) {
     case ST_9PT: return f(Solver<ST_9PT, float>());
     default: return f(Solver<ST_7PT, float>());
   }
+}
+
+// Back-to-back launches of one hot kernel on the current buffers (timing).
+template <int KIND, typename T>
+nlsp_status bench_launch(nlsp_prec* M, int which, int reps) {
+  PcgWork* w = M->pcg;
+  cudaStream_t s = M->ctx->stream;
+  NLSP_TRY((prepare_stream_kernels<KIND, T>()));
+  const StreamPlan pl = stream_plan<T>(M);
+  T* z = (T*)M->w0;
+  const T* rT = Solver<KIND, T>::rT(w);
+  constexpr int ZM = sizeof(T) == 4 ? 2 : 0;
+  for (int i = 0; i < reps; ++i) {
+    if (which == 0) NLSP_TRY((launch_restrict<KIND, T>(M, s, pl, ZM, rT, z, nullptr)));
+    else NLSP_TRY(launch_prolong<T>(M, s, pl, z, nullptr));
+  }
+  NLSP_LAUNCH_CHECK();
+  count_launches(M->ctx, reps);
+  return NLSP_OK;
 }
 
 }  // namespace
@@ -740,8 +1045,25 @@ extern "C" void nlsp_free_prec(nlsp_prec* M) {
   cudaSetDevice(M->device);
   cudaDeviceSynchronize();  // the context (and its stream) may already be gone
   free_work(M->pcg);
-  void* bufs[] = {M->P, M->sigma, M->Ac, M->L, M->Ainv, M->cpart, M->ec, M->counter, M->status, M->w0, M->w1};
-  for (void* b : bufs)
-    if (b) cudaFree(b);
+  if (M->storage) cudaFree(M->storage);
   delete M;
+}
+
+extern "C" nlsp_status nlsp_bench_kernel(nlsp_ctx* ctx, const nlsp_prec* Mc, int which, int reps) {
+  if (!ctx || !Mc || reps < 0 || which < 0 || which > 1) return NLSP_ERR_INVALID;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  nlsp_prec* M = const_cast<nlsp_prec*>(Mc);
+  NLSP_TRY(ensure_work(M, 1));
+  if (M->precision == NLSP_FP64) {
+    switch (M->A->kind) {
+      case ST_5PT: return bench_launch<ST_5PT, double>(M, which, reps);
+      case ST_9PT: return bench_launch<ST_9PT, double>(M, which, reps);
+      default: return bench_launch<ST_7PT, double>(M, which, reps);
+    }
+  }
+  switch (M->A->kind) {
+    case ST_5PT: return bench_launch<ST_5PT, float>(M, which, reps);
+    case ST_9PT: return bench_launch<ST_9PT, float>(M, which, reps);
+    default: return bench_launch<ST_7PT, float>(M, which, reps);
+  }
 }

@@ -50,22 +50,36 @@ __global__ void k_tiled_to_colmajor(const T* __restrict__ src, int64_t n, int nc
 }
 
 // One weighted-Jacobi sweep on A S = 0 for all K columns of a tiled block:
-// S_out = S_in - w D^-1 A S_in.  Padding rows are written as zero.
-template <int KIND, typename T>
-__global__ void k_smooth_sweep(StencilView<T> A, T omega, int ncols, int64_t n_pad, const T* __restrict__ Sin,
-                               T* __restrict__ Sout) {
-  const int64_t total = n_pad * ncols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = e / ((int64_t)ncols * NLSP_TILE);
-    const int c = (int)((e / NLSP_TILE) % ncols);
-    const int64_t i = t * NLSP_TILE + (e % NLSP_TILE);
+// S_out = S_in - w D^-1 A S_in.  Grid: x over the padded nodes, y over groups
+// of CPT columns (the index arithmetic and the coefficients of a node are
+// shared by its CPT columns); padding rows are written as zero.
+template <int KIND, typename T, int CPT>
+__global__ void __launch_bounds__(256) k_smooth_sweep(StencilView<T> A, T omega, int ncols, int n_pad,
+                                                      const T* __restrict__ Sin, T* __restrict__ Sout) {
+  const int cbase = blockIdx.y * CPT;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
+    const int64_t e0 = tiled_index(i, cbase, ncols);
     if (i >= A.n) {
-      Sout[e] = T(0);
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+        if (cbase + c < ncols) Sout[e0 + (int64_t)c * NLSP_TILE] = T(0);
       continue;
     }
     const NodeCoord nc = node_coord<KIND>(i, A.N);
-    const T as = stencil_apply<KIND>(A, i, nc, [&](int64_t m) { return Sin[tiled_index(m, c, ncols)]; });
-    Sout[e] = Sin[e] - omega * stencil_dinv<KIND>(A, i) * as;
+    const T wd = omega * stencil_dinv<KIND>(A, i);
+    T as[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      as[c] = cbase + c < ncols ? stencil_diag<KIND>(A, i) * Sin[e0 + (int64_t)c * NLSP_TILE] : T(0);
+    for_each_neighbour<KIND>(A, i, nc, [&](int64_t m, NodeCoord, T a) {
+      const int64_t em = tiled_index(m, cbase, ncols);
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+        if (cbase + c < ncols) as[c] += a * Sin[em + (int64_t)c * NLSP_TILE];
+    });
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (cbase + c < ncols) Sout[e0 + (int64_t)c * NLSP_TILE] = Sin[e0 + (int64_t)c * NLSP_TILE] - wd * as[c];
   }
 }
 
@@ -196,9 +210,13 @@ __global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ 
   float* cs = vt + KP * KP;                        // [KP/2][2]
   int* pq = reinterpret_cast<int*>(cs + KP);       // [KP/2][2]
   float* red = reinterpret_cast<float*>(pq + KP);  // [32]
+  short2* uv = reinterpret_cast<short2*>(red + 32);  // [H (H + 1) / 2] blocks (u >= v)
   __shared__ int converged;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int H = KP / 2;
+  const int nblk = H * (H + 1) / 2;
+  for (int u = tid; u < H; u += nt)
+    for (int v = 0; v <= u; ++v) uv[u * (u + 1) / 2 + v] = make_short2((short)u, (short)v);
 
   for (int e = tid; e < KP * KP; e += nt) {
     const int a = e / KP, b = e % KP;
@@ -239,14 +257,10 @@ __global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ 
         pq[2 * u + 1] = q;
       }
       __syncthreads();
-      // 2x2 block updates, u <= v
-      const int nblk = H * (H + 1) / 2;
+      // 2x2 block updates (u >= v, mirrored)
       for (int e = tid; e < nblk; e += nt) {
-        // invert the triangular index: e -> (u, v), u <= v
-        int u = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-        while (u * (u + 1) / 2 > e) --u;
-        while ((u + 1) * (u + 2) / 2 <= e) ++u;
-        const int v = e - u * (u + 1) / 2;  // v <= u
+        const short2 b = uv[e];
+        const int u = b.x, v = b.y;  // v <= u
         const int pu = pq[2 * u], qu = pq[2 * u + 1], pv = pq[2 * v], qv = pq[2 * v + 1];
         const float cu = cs[2 * u], su = cs[2 * u + 1], cv = cs[2 * v], sv = cs[2 * v + 1];
         if (u == v) {
@@ -505,7 +519,10 @@ __global__ void k_symmetrize(double* __restrict__ M, int m) {
 }  // namespace
 
 // ============================================================================
-// Host orchestration
+// Host orchestration.  Temporaries live in the context's grow-only scratch
+// slots: SA/SB the two tiled sample blocks, PART the per-block partial
+// products, SMALL the K x K work of the eigensolver, PNEW the re-orthonormal
+// basis.
 // ============================================================================
 namespace {
 
@@ -521,13 +538,20 @@ nlsp_status set_smem(const void* fn, size_t bytes) {
   return NLSP_OK;
 }
 
+template <typename T>
+T* slot_as(nlsp_ctx* ctx, int s, size_t count) {
+  return reinterpret_cast<T*>(ctx_slot(ctx, s, sizeof(T) * count));
+}
+
 // X_t^T Y_t summed over all tiles -> out (ncx x ncx FP64, column-major),
-// Y = X or A X.  partial: scratch of >= blocks * ncx^2 doubles.
+// Y = X or A X.
 template <typename T, bool WITH_A>
-nlsp_status tsgemm(nlsp_ctx* ctx, const nlsp_op* A, const T* X, int ncols, int ncx, int64_t n_pad, double* partial,
-                   double* out, int symmetrize) {
+nlsp_status tsgemm(nlsp_ctx* ctx, const nlsp_op* A, const T* X, int ncols, int ncx, int64_t n_pad, double* out,
+                   int symmetrize) {
   const int blocks = ctx->num_sms;
   cudaStream_t s = ctx->stream;
+  double* partial = slot_as<double>(ctx, SLOT_PART, (size_t)blocks * ncx * ncx);
+  if (!partial) return NLSP_ERR_OOM;
 #define NLSP_TSGEMM_LAUNCH(RB, TD)                                                                     \
   do {                                                                                                \
     constexpr int LDS_ = RB * TD + (sizeof(T) == 4 ? 4 : 2);                                          \
@@ -546,6 +570,7 @@ nlsp_status tsgemm(nlsp_ctx* ctx, const nlsp_op* A, const T* X, int ncols, int n
   NLSP_LAUNCH_CHECK();
   k_sum_partials<<<div_up((int64_t)ncx * ncx, 256), 256, 0, s>>>(partial, blocks, ncx, symmetrize, out);
   NLSP_LAUNCH_CHECK();
+  count_launches(ctx, 2);
   return NLSP_OK;
 }
 
@@ -558,24 +583,27 @@ nlsp_status tile_times_small(nlsp_ctx* ctx, const T* In, int ncin, const T* M, i
   const int g = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 8);
   fn<<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
   NLSP_LAUNCH_CHECK();
+  count_launches(ctx, 1);
   return NLSP_OK;
 }
 
-// Smooths the tiled sample block in place (ping-pong through `tmp`); returns
-// the buffer holding the result.
+// Smooths the tiled sample block (ping-pong between a and tmp); *result is
+// the buffer holding S.
 template <typename T>
 nlsp_status smooth_tiled(nlsp_ctx* ctx, const nlsp_op* A, int K, int s1, double omega, int64_t n_pad, T* a, T* tmp,
                          T** result) {
   T* src = a;
   T* dst = tmp;
-  const int g = grid_for(ctx, n_pad * K, 256, 8);
+  constexpr int CPT = 4;
+  const dim3 g((unsigned)div_up(n_pad, 256), (unsigned)div_up(K, CPT));
   for (int it = 0; it < s1; ++it) {
     NLSP_DISPATCH_KIND(A->kind, KD, {
-      k_smooth_sweep<KD, T><<<g, 256, 0, ctx->stream>>>(view_of<T>(A), (T)omega, K, n_pad, src, dst);
+      k_smooth_sweep<KD, T, CPT><<<g, 256, 0, ctx->stream>>>(view_of<T>(A), (T)omega, K, (int)n_pad, src, dst);
     });
     NLSP_LAUNCH_CHECK();
     std::swap(src, dst);
   }
+  count_launches(ctx, s1);
   *result = src;
   return NLSP_OK;
 }
@@ -605,48 +633,59 @@ nlsp_prec* new_prec(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* p,
   M->nu1 = p->nu1;
   M->nu2 = p->nu2;
   M->omega = p->omega;
-  M->rblocks = 2 * ctx->num_sms;
+  const int ntiles = (int)(M->n_pad / NLSP_TILE);
+  M->rblocks = std::max(2 * ctx->num_sms, div_up((int64_t)ntiles * NLSP_TILE, 16384));
   return M;
 }
 
+// The preconditioner's own storage: one allocation carved into its arrays.
 nlsp_status alloc_prec_storage(nlsp_prec* M) {
   const size_t tsz = M->precision == NLSP_FP64 ? sizeof(double) : sizeof(float);
-  const int k = M->k;
-  NLSP_CUDA(cudaMalloc(&M->P, tsz * M->n_pad * k));
-  NLSP_CUDA(cudaMalloc(&M->sigma, sizeof(double) * std::max(M->K, 1)));
-  NLSP_CUDA(cudaMalloc(&M->Ac, sizeof(double) * k * k));
-  NLSP_CUDA(cudaMalloc(&M->L, sizeof(double) * k * k));
-  NLSP_CUDA(cudaMalloc(&M->Ainv, sizeof(double) * k * k));
-  NLSP_CUDA(cudaMalloc(&M->cpart, sizeof(double) * (size_t)M->rblocks * k));
-  NLSP_CUDA(cudaMalloc(&M->ec, sizeof(double) * k));
-  NLSP_CUDA(cudaMalloc(&M->counter, sizeof(unsigned) * 8));
-  NLSP_CUDA(cudaMalloc(&M->status, sizeof(int)));
-  NLSP_CUDA(cudaMalloc(&M->w0, tsz * M->n_pad));
-  NLSP_CUDA(cudaMalloc(&M->w1, tsz * M->n_pad));
-  NLSP_CUDA(cudaMemsetAsync(M->sigma, 0, sizeof(double) * std::max(M->K, 1), M->ctx->stream));
-  NLSP_CUDA(cudaMemsetAsync(M->counter, 0, sizeof(unsigned) * 8, M->ctx->stream));
-  NLSP_CUDA(cudaMemsetAsync(M->status, 0, sizeof(int), M->ctx->stream));
+  const size_t k = M->k;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t sizes[] = {up(tsz * M->n_pad * k), up(sizeof(double) * std::max(M->K, 1)), up(sizeof(double) * k * k),
+                          up(sizeof(double) * k * k), up(sizeof(double) * k * k),
+                          up(tsz * (size_t)M->rblocks * k), up(tsz * k),
+                          up(sizeof(unsigned) * 8), up(sizeof(int)), up(tsz * M->n_pad), up(tsz * M->n_pad),
+                          up(tsz * k * k)};
+  size_t total = 0;
+  for (size_t b : sizes) total += b;
+  char* base = nullptr;
+  NLSP_CUDA(cudaMalloc(&base, total));
+  M->storage = base;
+  void** dst[] = {&M->P, (void**)&M->sigma, (void**)&M->Ac, (void**)&M->L, (void**)&M->Ainv, &M->cpart,
+                  &M->ec, (void**)&M->counter, (void**)&M->status, &M->w0, &M->w1, &M->AinvT};
+  size_t off = 0;
+  for (int i = 0; i < 12; ++i) {
+    *dst[i] = base + off;
+    off += sizes[i];
+  }
+  NLSP_CUDA(cudaMemsetAsync(M->sigma, 0, sizes[1], M->ctx->stream));
+  NLSP_CUDA(cudaMemsetAsync(M->counter, 0, sizes[7], M->ctx->stream));
+  NLSP_CUDA(cudaMemsetAsync(M->status, 0, sizes[8], M->ctx->stream));
   return NLSP_OK;
 }
 
 // Eigen-decomposition of the FP64 Gram matrix G (K x K): descending evals and
 // eigenvectors V (column-major).  refine = number of FP64 refinement steps.
-nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double* evals, double* V) {
+// work: 6 K^2 + K doubles.
+nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double* evals, double* V, double* work) {
   cudaStream_t s = ctx->stream;
   const int KP = K + (K & 1);
-  const size_t sm = (size_t)KP * (KP + 1) * 4 + (size_t)KP * KP * 4 + (size_t)KP * 4 + (size_t)KP * 4 + 32 * 4;
+  const size_t sm = (size_t)KP * (KP + 1) * 4 + (size_t)KP * KP * 4 + (size_t)KP * 4 + (size_t)KP * 4 + 32 * 4 +
+                    (size_t)(KP / 2) * (KP / 2 + 1) / 2 * 4;
   NLSP_TRY(set_smem((const void*)k_jacobi_eig, sm));
-  k_jacobi_eig<<<1, 1024, sm, s>>>(G, K, KP, 30, 2e-7f, evals, V);
+  k_jacobi_eig<<<1, 1024, sm, s>>>(G, K, KP, 30, 4e-6f, evals, V);
   NLSP_LAUNCH_CHECK();
+  count_launches(ctx, 1);
   if (refine > 0) {
-    DevBuf buf;
-    NLSP_TRY(buf.alloc(sizeof(double) * (size_t)K * K * 5 + sizeof(double) * K));
-    double* XtX = buf.as<double>();
+    double* XtX = work;
     double* GX = XtX + K * K;
     double* S = GX + K * K;
     double* E = S + K * K;
     double* XE = E + K * K;
-    double* lam = XE + K * K;
+    double* vcopy = XE + K * K;
+    double* lam = vcopy + K * K;
     const size_t gsm = sizeof(double) * K;
     const int th = K < 128 ? 128 : 256;
     for (int it = 0; it < refine; ++it) {
@@ -658,82 +697,77 @@ nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double
       k_add<<<div_up((int64_t)K * K, 256), 256, 0, s>>>(V, XE, K * K);
       NLSP_LAUNCH_CHECK();
     }
-    // eigenvalues of the refined basis: Rayleigh quotients of the final X
+    // eigenvalues of the refined basis (Rayleigh quotients), then sort
     k_small_gemm<<<K, th, gsm, s>>>(V, V, XtX, K, 1);
     k_small_gemm<<<K, th, gsm, s>>>(G, V, GX, K, 0);
     k_small_gemm<<<K, th, gsm, s>>>(V, GX, S, K, 1);
     k_oa_step<<<1, 256, 0, s>>>(XtX, S, K, E, lam);
-    DevBuf vcopy;
-    NLSP_TRY(vcopy.alloc(sizeof(double) * (size_t)K * K));
-    NLSP_CUDA(cudaMemcpyAsync(vcopy.p, V, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
-    k_sort_eig<<<1, 256, 0, s>>>(lam, vcopy.as<double>(), K, evals, V);
+    NLSP_CUDA(cudaMemcpyAsync(vcopy, V, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
+    k_sort_eig<<<1, 256, 0, s>>>(lam, vcopy, K, evals, V);
     NLSP_LAUNCH_CHECK();
-    NLSP_CUDA(cudaStreamSynchronize(s));  // buffers are freed at scope exit
+    count_launches(ctx, 6 * refine + 5);
   }
   return NLSP_OK;
 }
 
 // P (tiled T, k columns) from the tiled smoothed samples S (K columns).
 template <typename T>
-nlsp_status basis_from_samples(nlsp_ctx* ctx, nlsp_prec* M, const T* S, double* partial) {
+nlsp_status basis_from_samples(nlsp_ctx* ctx, nlsp_prec* M, const T* S) {
   cudaStream_t s = ctx->stream;
   const int K = M->K, k = M->k;
-  DevBuf gbuf;
-  NLSP_TRY(gbuf.alloc(sizeof(double) * ((size_t)K * K * 2 + K) + sizeof(T) * (size_t)K * k));
-  double* G = gbuf.as<double>();
+  const size_t nsmall = (size_t)K * K * 2 + K + (6 * (size_t)K * K + K) + (size_t)K * k + 8;
+  double* G = slot_as<double>(ctx, SLOT_SMALL, nsmall);
+  if (!G) return NLSP_ERR_OOM;
   double* V = G + K * K;
   double* evals = V + K * K;
-  T* Mc = reinterpret_cast<T*>(evals + K);
-  NLSP_TRY((tsgemm<T, false>(ctx, M->A, S, K, K, M->n_pad, partial, G, 0)));
+  double* work = evals + K;
+  T* Mc = reinterpret_cast<T*>(work + 6 * K * K + K);
+  NLSP_TRY((tsgemm<T, false>(ctx, M->A, S, K, K, M->n_pad, G, 0)));
   const int refine = M->precision == NLSP_FP64 ? 2 : 0;
-  NLSP_TRY(gram_eigen(ctx, G, K, refine, evals, V));
+  NLSP_TRY(gram_eigen(ctx, G, K, refine, evals, V, work));
   k_make_basis_coeffs<T><<<div_up((int64_t)K * k, 256), 256, 0, s>>>(evals, V, K, k, Mc, M->sigma, M->status);
   NLSP_LAUNCH_CHECK();
+  count_launches(ctx, 1);
   NLSP_TRY(tile_times_small<T>(ctx, S, K, Mc, k, M->n_pad, (T*)M->P));
-  NLSP_CUDA(cudaStreamSynchronize(s));
   return NLSP_OK;
+}
+
+// Transposes the column-major k x k FP64 matrix W into row-major T.
+template <typename T>
+__global__ void k_transpose_to(const double* __restrict__ W, int k, T* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    const int c = e / k, j = e % k;  // out[c][j] = W(c, j)
+    out[e] = (T)W[(int64_t)j * k + c];
+  }
 }
 
 // CholeskyQR re-orthonormalisation P <- P L^-T with P^T P = L L^T (the thin-Q
 // factor qf of Sec. 3, up to column signs).
 template <typename T>
-nlsp_status cholesky_qr(nlsp_ctx* ctx, nlsp_prec* M, double* partial) {
+nlsp_status cholesky_qr(nlsp_ctx* ctx, nlsp_prec* M) {
   cudaStream_t s = ctx->stream;
   const int k = M->k;
-  DevBuf buf, pbuf;
-  NLSP_TRY(buf.alloc(sizeof(double) * (size_t)k * k * 3 + sizeof(T) * (size_t)k * k));
-  double* Gp = buf.as<double>();
+  double* Gp = slot_as<double>(ctx, SLOT_SMALL, (size_t)k * k * 5 + 8);
+  if (!Gp) return NLSP_ERR_OOM;
   double* Lp = Gp + k * k;
   double* Linv = Lp + k * k;
-  T* Mt = reinterpret_cast<T*>(Linv + k * k);
-  NLSP_TRY((tsgemm<T, false>(ctx, M->A, (const T*)M->P, k, k, M->n_pad, partial, Gp, 1)));
+  double* W = Linv + k * k;
+  T* Mt = reinterpret_cast<T*>(W + k * k);
+  T* Pnew = slot_as<T>(ctx, SLOT_PNEW, (size_t)M->n_pad * k);
+  if (!Pnew) return NLSP_ERR_OOM;
+  NLSP_TRY((tsgemm<T, false>(ctx, M->A, (const T*)M->P, k, k, M->n_pad, Gp, 1)));
   NLSP_TRY(set_smem((const void*)k_cholesky, sizeof(double) * k * k));
   k_cholesky<<<1, 256, sizeof(double) * k * k, s>>>(Gp, k, Lp, M->status);
-  NLSP_LAUNCH_CHECK();
   // With P^T P = L L^T:  (L L^T)^-1 L = L^-T, so P L^-T needs only the SPD
   // inverse kernel and one small product.
   NLSP_TRY(set_smem((const void*)k_spd_inverse_cols, sizeof(double) * k));
-  k_spd_inverse_cols<<<k, 32, sizeof(double) * k, s>>>(Lp, k, Linv);  // Linv := (L L^T)^-1
+  k_spd_inverse_cols<<<k, 32, sizeof(double) * k, s>>>(Lp, k, Linv);  // (L L^T)^-1
+  k_small_gemm<<<k, 128, sizeof(double) * k, s>>>(Linv, Lp, W, k, 0);  // L^-T
+  k_transpose_to<T><<<div_up((int64_t)k * k, 256), 256, 0, s>>>(W, k, Mt);
   NLSP_LAUNCH_CHECK();
-  DevBuf wbuf;
-  NLSP_TRY(wbuf.alloc(sizeof(double) * (size_t)k * k));
-  k_small_gemm<<<k, 128, sizeof(double) * k, s>>>(Linv, Lp, wbuf.as<double>(), k, 0);  // L^-T
-  NLSP_LAUNCH_CHECK();
-  // Mt (row-major k x k: Mt[c * k + j]) = (L^-T)[c][j]
-  {
-    std::vector<double> hw((size_t)k * k);
-    NLSP_CUDA(cudaMemcpyAsync(hw.data(), wbuf.p, sizeof(double) * k * k, cudaMemcpyDeviceToHost, s));
-    NLSP_CUDA(cudaStreamSynchronize(s));
-    std::vector<T> hm((size_t)k * k);
-    for (int c = 0; c < k; ++c)
-      for (int j = 0; j < k; ++j) hm[(size_t)c * k + j] = (T)hw[(size_t)j * k + c];
-    NLSP_CUDA(cudaMemcpyAsync(Mt, hm.data(), sizeof(T) * k * k, cudaMemcpyHostToDevice, s));
-  }
-  NLSP_TRY(pbuf.alloc(sizeof(T) * M->n_pad * k));
-  NLSP_TRY(tile_times_small<T>(ctx, (const T*)M->P, k, Mt, k, M->n_pad, pbuf.as<T>()));
-  NLSP_CUDA(cudaStreamSynchronize(s));
-  cudaFree(M->P);
-  M->P = pbuf.release();
+  count_launches(ctx, 4);
+  NLSP_TRY(tile_times_small<T>(ctx, (const T*)M->P, k, Mt, k, M->n_pad, Pnew));
+  NLSP_CUDA(cudaMemcpyAsync(M->P, Pnew, sizeof(T) * M->n_pad * k, cudaMemcpyDeviceToDevice, s));
   return NLSP_OK;
 }
 
@@ -742,32 +776,24 @@ nlsp_status build_impl(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params*
                        nlsp_prec** out) {
   nlsp_prec* M = new_prec(ctx, A, p, p->k, p->K);
   nlsp_status st = alloc_prec_storage(M);
-  if (st != NLSP_OK) {
-    nlsp_free_prec(M);
-    return st;
-  }
   auto fail = [&](nlsp_status e) {
     nlsp_free_prec(M);
     return e;
   };
+  if (st != NLSP_OK) return fail(st);
   cudaStream_t s = ctx->stream;
   const int K = p->K;
-  DevBuf sa, sb, part;
-  if ((st = sa.alloc(sizeof(T) * M->n_pad * K)) != NLSP_OK) return fail(st);
-  if ((st = sb.alloc(sizeof(T) * M->n_pad * K)) != NLSP_OK) return fail(st);
-  if ((st = part.alloc(sizeof(double) * (size_t)ctx->num_sms * 128 * 128)) != NLSP_OK) return fail(st);
-  k_colmajor_to_tiled<T><<<grid_for(ctx, M->n_pad * K, 256, 8), 256, 0, s>>>(S0, A->n, A->n, K, M->n_pad,
-                                                                               sa.as<T>());
+  T* sa = slot_as<T>(ctx, SLOT_SA, (size_t)M->n_pad * K);
+  T* sb = slot_as<T>(ctx, SLOT_SB, (size_t)M->n_pad * K);
+  if (!sa || !sb) return fail(NLSP_ERR_OOM);
+  k_colmajor_to_tiled<T><<<grid_for(ctx, M->n_pad * K, 256, 8), 256, 0, s>>>(S0, A->n, A->n, K, M->n_pad, sa);
   if (cudaGetLastError() != cudaSuccess) return fail(NLSP_ERR_CUDA);
+  count_launches(ctx, 1);
   T* S = nullptr;
-  if ((st = smooth_tiled<T>(ctx, A, K, p->s1, p->omega, M->n_pad, sa.as<T>(), sb.as<T>(), &S)) != NLSP_OK)
-    return fail(st);
-  if ((st = basis_from_samples<T>(ctx, M, S, part.as<double>())) != NLSP_OK) return fail(st);
-  int hstat = 0;
-  if (cudaMemcpy(&hstat, M->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return fail(NLSP_ERR_CUDA);
-  if (hstat != 0) return fail((nlsp_status)hstat);
+  if ((st = smooth_tiled<T>(ctx, A, K, p->s1, p->omega, M->n_pad, sa, sb, &S)) != NLSP_OK) return fail(st);
+  if ((st = basis_from_samples<T>(ctx, M, S)) != NLSP_OK) return fail(st);
   if (p->precision == NLSP_FP64)
-    if ((st = cholesky_qr<T>(ctx, M, part.as<double>())) != NLSP_OK) return fail(st);
+    if ((st = cholesky_qr<T>(ctx, M)) != NLSP_OK) return fail(st);
   if ((st = nlsp_internal_factor(ctx, M, M->k)) != NLSP_OK) return fail(st);
   *out = M;
   return NLSP_OK;
@@ -788,6 +814,7 @@ nlsp_status from_basis_impl(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_pa
     nlsp_free_prec(M);
     return NLSP_ERR_CUDA;
   }
+  count_launches(ctx, 1);
   if ((st = nlsp_internal_factor(ctx, M, k)) != NLSP_OK) {
     nlsp_free_prec(M);
     return st;
@@ -798,23 +825,26 @@ nlsp_status from_basis_impl(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_pa
 
 }  // namespace
 
-// A_c = P_r^T A P_r (FP64 result), Cholesky and explicit inverse.
+// A_c = P_r^T A P_r (FP64 result), Cholesky and explicit inverse.  Reads the
+// status word (synchronises).
 nlsp_status nlsp_internal_factor(nlsp_ctx* ctx, nlsp_prec* M, int r) {
   cudaStream_t s = ctx->stream;
-  DevBuf part;
-  NLSP_TRY(part.alloc(sizeof(double) * (size_t)ctx->num_sms * r * r));
-  NLSP_CUDA(cudaMemsetAsync(M->status, 0, sizeof(int), s));
   if (M->precision == NLSP_FP64)
-    NLSP_TRY((tsgemm<double, true>(ctx, M->A, (const double*)M->P, M->k, r, M->n_pad, part.as<double>(), M->Ac, 1)));
+    NLSP_TRY((tsgemm<double, true>(ctx, M->A, (const double*)M->P, M->k, r, M->n_pad, M->Ac, 1)));
   else
-    NLSP_TRY((tsgemm<float, true>(ctx, M->A, (const float*)M->P, M->k, r, M->n_pad, part.as<double>(), M->Ac, 1)));
+    NLSP_TRY((tsgemm<float, true>(ctx, M->A, (const float*)M->P, M->k, r, M->n_pad, M->Ac, 1)));
   NLSP_TRY(set_smem((const void*)k_cholesky, sizeof(double) * r * r));
   k_cholesky<<<1, 256, sizeof(double) * r * r, s>>>(M->Ac, r, M->L, M->status);
   NLSP_LAUNCH_CHECK();
   NLSP_TRY(set_smem((const void*)k_spd_inverse_cols, sizeof(double) * r));
   k_spd_inverse_cols<<<r, 32, sizeof(double) * r, s>>>(M->L, r, M->Ainv);
   k_symmetrize<<<div_up((int64_t)r * r, 256), 256, 0, s>>>(M->Ainv, r);
+  if (M->precision == NLSP_FP64)
+    NLSP_CUDA(cudaMemcpyAsync(M->AinvT, M->Ainv, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, s));
+  else
+    k_transpose_to<float><<<div_up((int64_t)r * r, 256), 256, 0, s>>>(M->Ainv, r, (float*)M->AinvT);  // symmetric
   NLSP_LAUNCH_CHECK();
+  count_launches(ctx, M->precision == NLSP_FP64 ? 3 : 4);
   int hstat = 0;
   NLSP_CUDA(cudaMemcpyAsync(&hstat, M->status, sizeof(int), cudaMemcpyDeviceToHost, s));
   NLSP_CUDA(cudaStreamSynchronize(s));
@@ -830,23 +860,21 @@ extern "C" nlsp_status nlsp_smooth_samples(nlsp_ctx* ctx, const nlsp_op* A, int 
   NLSP_CUDA(cudaSetDevice(ctx->device));
   const int64_t n_pad = pad_tile(A->n);
   cudaStream_t s = ctx->stream;
-  const size_t tsz = precision == NLSP_FP64 ? 8 : 4;
-  DevBuf a, b;
-  NLSP_TRY(a.alloc(tsz * n_pad * K));
-  NLSP_TRY(b.alloc(tsz * n_pad * K));
   const int g = grid_for(ctx, n_pad * K, 256, 8);
-  if (precision == NLSP_FP64) {
-    k_colmajor_to_tiled<double><<<g, 256, 0, s>>>(dev_S0, A->n, A->n, K, n_pad, a.as<double>());
-    double* r = nullptr;
-    NLSP_TRY(smooth_tiled<double>(ctx, A, K, s1, omega, n_pad, a.as<double>(), b.as<double>(), &r));
-    k_tiled_to_colmajor<double><<<g, 256, 0, s>>>(r, A->n, K, K, dev_S, A->n);
-  } else {
-    k_colmajor_to_tiled<float><<<g, 256, 0, s>>>(dev_S0, A->n, A->n, K, n_pad, a.as<float>());
-    float* r = nullptr;
-    NLSP_TRY(smooth_tiled<float>(ctx, A, K, s1, omega, n_pad, a.as<float>(), b.as<float>(), &r));
-    k_tiled_to_colmajor<float><<<g, 256, 0, s>>>(r, A->n, K, K, dev_S, A->n);
-  }
-  NLSP_LAUNCH_CHECK();
+  auto run = [&](auto tag) -> nlsp_status {
+    using T = decltype(tag);
+    T* a = slot_as<T>(ctx, SLOT_SA, (size_t)n_pad * K);
+    T* b = slot_as<T>(ctx, SLOT_SB, (size_t)n_pad * K);
+    if (!a || !b) return NLSP_ERR_OOM;
+    k_colmajor_to_tiled<T><<<g, 256, 0, s>>>(dev_S0, A->n, A->n, K, n_pad, a);
+    T* r = nullptr;
+    NLSP_TRY(smooth_tiled<T>(ctx, A, K, s1, omega, n_pad, a, b, &r));
+    k_tiled_to_colmajor<T><<<g, 256, 0, s>>>(r, A->n, K, K, dev_S, A->n);
+    NLSP_LAUNCH_CHECK();
+    count_launches(ctx, 2);
+    return NLSP_OK;
+  };
+  NLSP_TRY(precision == NLSP_FP64 ? run(double()) : run(float()));
   NLSP_CUDA(cudaStreamSynchronize(s));
   return NLSP_OK;
 }
@@ -898,6 +926,7 @@ extern "C" nlsp_status nlsp_prec_copy_basis(nlsp_ctx* ctx, const nlsp_prec* M, d
   else
     k_tiled_to_colmajor<float><<<g, 256, 0, ctx->stream>>>((const float*)M->P, M->n, M->k, M->k, dev_P, M->n);
   NLSP_LAUNCH_CHECK();
+  count_launches(ctx, 1);
   return NLSP_OK;
 }
 

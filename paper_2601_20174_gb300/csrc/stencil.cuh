@@ -10,18 +10,20 @@ struct NodeCoord {
   int i, j, l;
 };
 
+// Grid coordinates of node idx (n < 2^31: 32-bit unsigned division only).
 template <int KIND>
 __device__ __forceinline__ NodeCoord node_coord(int64_t idx, int N) {
   NodeCoord c;
+  const unsigned u = (unsigned)idx, un = (unsigned)N;
   if (KIND == ST_7PT) {
-    const int64_t nn = (int64_t)N * N;
-    c.l = (int)(idx / nn);
-    const int rem = (int)(idx - (int64_t)c.l * nn);
-    c.j = rem / N;
-    c.i = rem - c.j * N;
+    const unsigned nn = un * un;
+    c.l = (int)(u / nn);
+    const unsigned rem = u - (unsigned)c.l * nn;
+    c.j = (int)(rem / un);
+    c.i = (int)(rem - (unsigned)c.j * un);
   } else {
-    c.j = (int)(idx / N);
-    c.i = (int)(idx - (int64_t)c.j * N);
+    c.j = (int)(u / un);
+    c.i = (int)(u - (unsigned)c.j * un);
     c.l = 0;
   }
   return c;

@@ -1,0 +1,45 @@
+"""A short run of the benchmark workload for profilers.
+
+Builds the 512 x 512 GRF diffusion system (k = 64 from K = 128 smoothed
+samples, nu = 2, omega = 2/3), sets up the preconditioner and runs a few PCG
+iterations with the host-relaunched iteration graph, so that a profiler sees
+every kernel of the setup and of the iteration as separate launches.
+
+    python -m paper_2601_20174_gb300.profile_case [--precision mixed|fp64] [--iters 4] [--N 512]
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+import torch
+
+from . import _lib as L, api, inputs as gen
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--iters", type=int, default=4)
+    ap.add_argument("--N", type=int, default=512)
+    ap.add_argument("--k", type=int, default=64)
+    ap.add_argument("--K", type=int, default=128)
+    args = ap.parse_args()
+    p = gen.grf_diffusion_2d(args.N, args.k, args.K, seed=0)
+    ctx = api.Context(0)
+    A = api.Operator.from_problem(ctx, p)
+    S0 = torch.as_tensor(np.ascontiguousarray(p.S0.T)).cuda()
+    prec = L.NLSP_MIXED_FP32 if args.precision == "mixed" else L.NLSP_FP64
+    M = api.Preconditioner.build(A, S0.t(), p.k, p.s1, p.nu, p.omega, prec)
+    f = torch.as_tensor(p.f[:, 0].copy()).cuda()
+    _, res = M.solve(f, tol=1e-8, maxit=args.iters, graph_mode=0)
+    torch.cuda.synchronize()
+    print(f"profile case: n={p.n} k={p.k} iterations={res[0].iterations} status={res[0].status}")
+    M.close()
+    A.close()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
