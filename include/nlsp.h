@@ -52,6 +52,10 @@ extern "C" {
 #define NLSP_API
 #endif
 
+/* Capacity of nlsp_apply_prec_noalloc's static scratch. */
+#define NLSP_NOALLOC_MAX_N 262144
+#define NLSP_NOALLOC_MAX_RANK 128
+
 typedef struct nlsp_ctx nlsp_ctx;
 typedef struct nlsp_op nlsp_op;
 typedef struct nlsp_prec nlsp_prec;
@@ -225,6 +229,28 @@ NLSP_API void nlsp_free_prec(nlsp_prec* M);
    Errors: NLSP_ERR_INVALID. */
 NLSP_API nlsp_status nlsp_apply_prec(nlsp_ctx* ctx, const nlsp_prec* M, int m, const double* dev_R, int64_t ldr,
                             double* dev_Z, int64_t ldz);
+
+/* Same as nlsp_apply_prec, but allocates no device memory: no cudaMalloc,
+   cudaFree or allocating library routine is called, and the preconditioner's
+   own lazily created solver workspace is not touched.  The paper has no
+   counterpart; this exists for callers that cannot allocate while they run:
+   code that enqueues work inside its own stream capture (allocation and
+   freeing synchronise the device and are not allowed while capturing), and
+   applications whose memory pool owns all of device memory under a fixed
+   cap.  M itself must have been built beforehand (that does allocate).
+   Temporaries live in one static device array, sized for
+   n <= NLSP_NOALLOC_MAX_N and active rank r <= NLSP_NOALLOC_MAX_RANK (about
+   7 MB, held by every GPU that loads the library until the process exits);
+   larger problems return NLSP_ERR_INVALID (message in nlsp_last_error).
+   The first call on a device looks up the array's device address (a CUDA
+   runtime call, done once per device with that device current): make that
+   first call before any stream capture.  All calls share the array and it
+   keeps the last call's contents; what must start at zero is cleared on the
+   stream by each call.  Calls whose work overlaps on the GPU (different
+   streams or contexts of one process) race on the array.
+   Errors: NLSP_ERR_INVALID, NLSP_ERR_CUDA. */
+NLSP_API nlsp_status nlsp_apply_prec_noalloc(nlsp_ctx* ctx, const nlsp_prec* M, int m, const double* dev_R,
+                                             int64_t ldr, double* dev_Z, int64_t ldz);
 
 /* Solves A X = B for m right-hand sides by PCG with the two-level
    preconditioner M (Sec. 4; tolerance on the relative residual, x0 = 0 --

@@ -29,6 +29,7 @@
 #define NLSP_LAUNCH_CHECK() NLSP_CUDA(cudaGetLastError())
 
 void nlsp_record_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void nlsp_record_message(const char* msg);
 
 // ----------------------------------------------------------------------------
 // Geometry and layouts

@@ -15,6 +15,11 @@ void nlsp_record_cuda_error(cudaError_t e, const char* what, const char* file, i
   if (getenv("NLSP_VERBOSE")) fprintf(stderr, "[nlsp] %s\n", g_last_error);
 }
 
+void nlsp_record_message(const char* msg) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+  if (getenv("NLSP_VERBOSE")) fprintf(stderr, "[nlsp] %s\n", g_last_error);
+}
+
 extern "C" const char* nlsp_last_error(void) { return g_last_error; }
 
 extern "C" const char* nlsp_status_string(int status) {

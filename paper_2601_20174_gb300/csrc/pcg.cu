@@ -673,6 +673,20 @@ struct StreamPlan {
   size_t smem_restrict, smem_prolong;
 };
 
+// Mutable workspace of one preconditioner application: the two smoothing
+// work vectors, the restriction's per-block partials, its arrival counter,
+// the coarse correction and the error word.
+struct PrecWork {
+  void* w0;
+  void* w1;
+  void* cpart;
+  void* ec;
+  unsigned* counter;
+  int* err;
+};
+
+PrecWork prec_work_of(const nlsp_prec* M) { return PrecWork{M->w0, M->w1, M->cpart, M->ec, M->counter, M->status}; }
+
 template <typename T>
 StreamPlan stream_plan(const nlsp_prec* M) {
   StreamPlan pl;
@@ -720,13 +734,13 @@ nlsp_status prepare_stream_kernels() {
 }
 
 template <int KIND, typename T, int NCH>
-nlsp_status launch_restrict_n(const nlsp_prec* M, cudaStream_t s, const StreamPlan& pl, int zm, const T* rT, T* z,
-                              PcgState* st) {
+nlsp_status launch_restrict_n(const nlsp_prec* M, const PrecWork& pw, cudaStream_t s, const StreamPlan& pl, int zm,
+                              const T* rT, T* z, PcgState* st) {
   const StencilView<T>& A = view_T<T>(M->A);
   auto go = [&](auto fn) -> nlsp_status {
     fn<<<pl.grid, 128 * NCH, pl.smem_restrict, s>>>(A, (T)M->omega, rT, z, z, (const T*)M->P, M->k, M->r, pl.sa,
-                                                    (const T*)M->AinvT, (T*)M->cpart, (T*)M->ec, M->counter, st,
-                                                    M->status);
+                                                    (const T*)M->AinvT, (T*)pw.cpart, (T*)pw.ec, pw.counter, st,
+                                                    pw.err);
     return NLSP_OK;
   };
   if (zm == 0) return go(k_restrict<KIND, T, NCH, 0>);
@@ -735,21 +749,22 @@ nlsp_status launch_restrict_n(const nlsp_prec* M, cudaStream_t s, const StreamPl
 }
 
 template <int KIND, typename T>
-nlsp_status launch_restrict(const nlsp_prec* M, cudaStream_t s, const StreamPlan& pl, int zm, const T* rT, T* z,
-                            PcgState* st) {
+nlsp_status launch_restrict(const nlsp_prec* M, const PrecWork& pw, cudaStream_t s, const StreamPlan& pl, int zm,
+                            const T* rT, T* z, PcgState* st) {
   switch (pl.nch) {
-    case 1: return launch_restrict_n<KIND, T, 1>(M, s, pl, zm, rT, z, st);
-    case 2: return launch_restrict_n<KIND, T, 2>(M, s, pl, zm, rT, z, st);
-    case 3: return launch_restrict_n<KIND, T, 3>(M, s, pl, zm, rT, z, st);
-    default: return launch_restrict_n<KIND, T, 4>(M, s, pl, zm, rT, z, st);
+    case 1: return launch_restrict_n<KIND, T, 1>(M, pw, s, pl, zm, rT, z, st);
+    case 2: return launch_restrict_n<KIND, T, 2>(M, pw, s, pl, zm, rT, z, st);
+    case 3: return launch_restrict_n<KIND, T, 3>(M, pw, s, pl, zm, rT, z, st);
+    default: return launch_restrict_n<KIND, T, 4>(M, pw, s, pl, zm, rT, z, st);
   }
 }
 
 template <typename T>
-nlsp_status launch_prolong(const nlsp_prec* M, cudaStream_t s, const StreamPlan& pl, T* z, PcgState* st) {
+nlsp_status launch_prolong(const nlsp_prec* M, const PrecWork& pw, cudaStream_t s, const StreamPlan& pl, T* z,
+                           PcgState* st) {
   auto go = [&](auto fn, int nt) -> nlsp_status {
-    fn<<<pl.grid, nt, pl.smem_prolong, s>>>(M->n, (const T*)M->P, M->k, M->r, pl.sa, (const T*)M->ec, z, st,
-                                            M->status);
+    fn<<<pl.grid, nt, pl.smem_prolong, s>>>(M->n, (const T*)M->P, M->k, M->r, pl.sa, (const T*)pw.ec, z, st,
+                                            pw.err);
     return NLSP_OK;
   };
   switch (pl.nch) {
@@ -765,14 +780,15 @@ nlsp_status launch_prolong(const nlsp_prec* M, cudaStream_t s, const StreamPlan&
 // r^T z (and flexible terms) reduced into st when st != nullptr.
 // Returns the number of kernels enqueued in *nlaunch.
 template <int KIND, typename T>
-nlsp_status enqueue_prec(const nlsp_prec* M, cudaStream_t s, bool init, const T* rT, const double* r, Pair<double> Z,
-                         PcgState* st, RedSlots red, cudaGraphConditionalHandle cond, int set_cond, int* nlaunch) {
+nlsp_status enqueue_prec(const nlsp_prec* M, const PrecWork& pw, cudaStream_t s, bool init, const T* rT,
+                         const double* r, Pair<double> Z, PcgState* st, RedSlots red, cudaGraphConditionalHandle cond,
+                         int set_cond, int* nlaunch) {
   const nlsp_ctx* ctx = M->ctx;
   const StencilView<T>& A = view_T<T>(M->A);
   const T omega = (T)M->omega;
   const int g = node_grid(ctx, M->n);
-  T* cur = (T*)M->w0;
-  T* oth = (T*)M->w1;
+  T* cur = (T*)pw.w0;
+  T* oth = (T*)pw.w1;
   int nl = 0;
   constexpr bool FP32 = sizeof(T) == 4;
   const StreamPlan pl = stream_plan<T>(M);
@@ -787,8 +803,8 @@ nlsp_status enqueue_prec(const nlsp_prec* M, cudaStream_t s, bool init, const T*
       std::swap(cur, oth);
     }
   }
-  NLSP_TRY((launch_restrict<KIND, T>(M, s, pl, fused_pre ? M->nu1 : 0, rT, cur, st)));
-  NLSP_TRY(launch_prolong<T>(M, s, pl, cur, st));
+  NLSP_TRY((launch_restrict<KIND, T>(M, pw, s, pl, fused_pre ? M->nu1 : 0, rT, cur, st)));
+  NLSP_TRY(launch_prolong<T>(M, pw, s, pl, cur, st));
   nl += 2;
   // post-smoothing
   const int nfinal = (FP32 && M->nu2 >= 2) ? 2 : 1;
@@ -830,7 +846,8 @@ struct Solver {
     k_pcg_pre<T><<<g, TPB, 0, s>>>(M->n, x(w), r(w), rT(w), q(w), Pc, w->st, red_of(w));
     NLSP_LAUNCH_CHECK();
     int na = 0;
-    nlsp_status st = enqueue_prec<KIND, T>(M, s, false, rT(w), r(w), Z, w->st, red_of(w), w->cond, set_cond, &na);
+    nlsp_status st = enqueue_prec<KIND, T>(M, prec_work_of(M), s, false, rT(w), r(w), Z, w->st, red_of(w), w->cond,
+                                           set_cond, &na);
     *nlaunch = 2 + na;
     return st;
   }
@@ -912,7 +929,8 @@ struct Solver {
                                       prm->maxit, flexible, red_of(w));
       NLSP_LAUNCH_CHECK();
       int na = 0;
-      NLSP_TRY((enqueue_prec<KIND, T>(M, s, true, rT(w), r(w), Zpair(w), w->st, red_of(w), 0, 0, &na)));
+      NLSP_TRY((enqueue_prec<KIND, T>(M, prec_work_of(M), s, true, rT(w), r(w), Zpair(w), w->st, red_of(w), 0, 0,
+                                      &na)));
       count_launches(ctx, 2 + na);  // init, preconditioner, true residual
       if (prm->graph_mode == 1) {
         NLSP_CUDA(cudaGraphLaunch(w->x_while, s));
@@ -970,7 +988,7 @@ struct Solver {
       double* zc = Zout + col * ldz;
       Pair<double> Zp{{zc, zc}};
       int na = 0;
-      NLSP_TRY((enqueue_prec<KIND, T>(M, s, true, rt, rc, Zp, nullptr, red_of(w), 0, 0, &na)));
+      NLSP_TRY((enqueue_prec<KIND, T>(M, prec_work_of(M), s, true, rt, rc, Zp, nullptr, red_of(w), 0, 0, &na)));
       count_launches(ctx, na);
     }
     return NLSP_OK;
@@ -1004,8 +1022,8 @@ nlsp_status bench_launch(nlsp_prec* M, int which, int reps) {
   const T* rT = Solver<KIND, T>::rT(w);
   constexpr int ZM = sizeof(T) == 4 ? 2 : 0;
   for (int i = 0; i < reps; ++i) {
-    if (which == 0) NLSP_TRY((launch_restrict<KIND, T>(M, s, pl, ZM, rT, z, nullptr)));
-    else NLSP_TRY(launch_prolong<T>(M, s, pl, z, nullptr));
+    if (which == 0) NLSP_TRY((launch_restrict<KIND, T>(M, prec_work_of(M), s, pl, ZM, rT, z, nullptr)));
+    else NLSP_TRY(launch_prolong<T>(M, prec_work_of(M), s, pl, z, nullptr));
   }
   NLSP_LAUNCH_CHECK();
   count_launches(M->ctx, reps);
@@ -1065,5 +1083,120 @@ extern "C" nlsp_status nlsp_bench_kernel(nlsp_ctx* ctx, const nlsp_prec* Mc, int
     case ST_5PT: return bench_launch<ST_5PT, float>(M, which, reps);
     case ST_9PT: return bench_launch<ST_9PT, float>(M, which, reps);
     default: return bench_launch<ST_7PT, float>(M, which, reps);
+  }
+}
+
+// ============================================================================
+// Preconditioner application without device allocation.
+//
+// For callers that must not allocate device memory while they run: code that
+// enqueues work inside its own stream capture (cudaMalloc / cudaFree
+// synchronise the device and are illegal during capture), and applications
+// whose memory pool owns all of device memory under a fixed cap, where a
+// stray cudaMalloc fails or fragments the pool.  The temporaries of
+// nlsp_apply_prec (the residual in the preconditioner precision, the two
+// smoothing work vectors, the restriction's per-block partials, its arrival
+// counter and the coarse correction) live here in one file-scope device
+// array instead, sized for n <= NLSP_NOALLOC_MAX_N and r <= NLSP_NOALLOC_MAX_RANK.
+// Every GPU that loads the library holds this array until the process exits.
+// ============================================================================
+namespace {
+
+constexpr int64_t NOALLOC_MAX_BLOCKS = 1024;
+constexpr size_t NOALLOC_VEC_BYTES = (size_t)NLSP_NOALLOC_MAX_N * sizeof(double);
+constexpr size_t NOALLOC_PART_BYTES = (size_t)NOALLOC_MAX_BLOCKS * NLSP_NOALLOC_MAX_RANK * sizeof(double);
+constexpr size_t NOALLOC_BYTES = 3 * NOALLOC_VEC_BYTES + NOALLOC_PART_BYTES + NLSP_NOALLOC_MAX_RANK * sizeof(double) + 256;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES];  // device address of the array, per device
+
+// Device address of the scratch array on `device` (which must be current).
+// Host code cannot use the symbol itself: in host code it names a host-side
+// stand-in, not device memory.
+nlsp_status noalloc_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= NOALLOC_MAX_DEVICES) return NLSP_ERR_INVALID;
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      nlsp_record_cuda_error(e, "cudaGetSymbolAddress (no-allocation scratch)", __FILE__, __LINE__);
+      return NLSP_ERR_CUDA;
+    }
+    g_noalloc_addr[device] = p;
+  }
+  *out = (unsigned char*)g_noalloc_addr[device];
+  return NLSP_OK;
+}
+
+template <int KIND, typename T>
+nlsp_status apply_noalloc(const nlsp_prec* M, unsigned char* base, int m, const double* R, int64_t ldr, double* Z,
+                          int64_t ldz) {
+  cudaStream_t s = M->ctx->stream;
+  NLSP_TRY((prepare_stream_kernels<KIND, T>()));
+  const StreamPlan pl = stream_plan<T>(M);
+  if (pl.grid > NOALLOC_MAX_BLOCKS) {
+    nlsp_record_message("nlsp_apply_prec_noalloc: restriction grid exceeds the scratch capacity");
+    return NLSP_ERR_INVALID;
+  }
+  T* rT = (T*)base;
+  PrecWork pw;
+  pw.w0 = base + NOALLOC_VEC_BYTES;
+  pw.w1 = base + 2 * NOALLOC_VEC_BYTES;
+  pw.cpart = base + 3 * NOALLOC_VEC_BYTES;
+  pw.ec = base + 3 * NOALLOC_VEC_BYTES + NOALLOC_PART_BYTES;
+  pw.counter = (unsigned*)(base + 3 * NOALLOC_VEC_BYTES + NOALLOC_PART_BYTES +
+                           NLSP_NOALLOC_MAX_RANK * sizeof(double));
+  pw.err = M->status;
+  // the restriction's arrival counter must start at zero (the array keeps
+  // whatever the last call left)
+  NLSP_CUDA(cudaMemsetAsync(pw.counter, 0, 256, s));
+  RedSlots none{nullptr, nullptr, 0};
+  for (int col = 0; col < m; ++col) {
+    const double* rc = R + col * ldr;
+    const T* rt = (const T*)rc;
+    if (sizeof(T) == 4) {
+      k_convert<T><<<node_grid(M->ctx, M->n), TPB, 0, s>>>(rc, rT, M->n);
+      rt = rT;
+      count_launches(M->ctx, 1);
+    }
+    double* zc = Z + col * ldz;
+    Pair<double> Zp{{zc, zc}};
+    int na = 0;
+    NLSP_TRY((enqueue_prec<KIND, T>(M, pw, s, true, rt, rc, Zp, nullptr, none, 0, 0, &na)));
+    count_launches(M->ctx, na);
+  }
+  return NLSP_OK;
+}
+
+}  // namespace
+
+extern "C" nlsp_status nlsp_apply_prec_noalloc(nlsp_ctx* ctx, const nlsp_prec* M, int m, const double* dev_R,
+                                               int64_t ldr, double* dev_Z, int64_t ldz) {
+  if (!ctx || !M || m < 0 || (m > 0 && (!dev_R || !dev_Z)) || ldr < M->n || ldz < M->n) return NLSP_ERR_INVALID;
+  if (M->n > NLSP_NOALLOC_MAX_N || M->r > NLSP_NOALLOC_MAX_RANK) {
+    nlsp_record_message("nlsp_apply_prec_noalloc: n or rank exceeds NLSP_NOALLOC_MAX_N / NLSP_NOALLOC_MAX_RANK");
+    return NLSP_ERR_INVALID;
+  }
+  if (m == 0) return NLSP_OK;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  unsigned char* base = nullptr;
+  NLSP_TRY(noalloc_scratch(ctx->device, &base));
+  if (M->precision == NLSP_FP64) {
+    switch (M->A->kind) {
+      case ST_5PT: return apply_noalloc<ST_5PT, double>(M, base, m, dev_R, ldr, dev_Z, ldz);
+      case ST_9PT: return apply_noalloc<ST_9PT, double>(M, base, m, dev_R, ldr, dev_Z, ldz);
+      default: return apply_noalloc<ST_7PT, double>(M, base, m, dev_R, ldr, dev_Z, ldz);
+    }
+  }
+  switch (M->A->kind) {
+    case ST_5PT: return apply_noalloc<ST_5PT, float>(M, base, m, dev_R, ldr, dev_Z, ldz);
+    case ST_9PT: return apply_noalloc<ST_9PT, float>(M, base, m, dev_R, ldr, dev_Z, ldz);
+    default: return apply_noalloc<ST_7PT, float>(M, base, m, dev_R, ldr, dev_Z, ldz);
   }
 }

@@ -1,0 +1,79 @@
+"""nlsp_apply_prec_noalloc: the preconditioner application for callers that
+cannot allocate device memory while they run (work enqueued inside their own
+stream capture, or a memory pool that owns all of device memory).  It must give
+what nlsp_apply_prec gives, call after call, although its temporaries live in
+one static device array that every call reuses.  This file is collected last
+so that a run stopping at the first failure has run every other test."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import rel, to_dev, to_np
+from oracle import operator as op, setup as osetup
+from paper_2601_20174_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # ragged node count (n = 2025 is not a multiple of the 128-node tile)
+    "grf5_fp64": (lambda: gen.grf_diffusion_2d(N=45, k=12, K=32, seed=2), 0, 1e-12),
+    "grf5_mixed": (lambda: gen.grf_diffusion_2d(N=45, k=12, K=32, seed=2), 1, 1e-12),
+    "aniso9_mixed": (lambda: gen.aniso_9pt_2d(N=29, k=40, K=48, m=1, seed=3), 1, 1e-12),
+    "iid7_fp64": (lambda: gen.iid_diffusion_3d(N=11, k=10, K=24, seed=4), 0, 1e-12),
+}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_20174_gb300 import api
+    return api.Context(0)
+
+
+def _apply(lib, entry, ctx, M, R):
+    """Calls `entry` (a C-ABI function) on the column-major block R (n x m)."""
+    n, m = R.shape
+    Rs = to_dev(np.ascontiguousarray(R.T))  # column-major storage
+    Zs = torch.full_like(Rs, float("nan"))
+    st = getattr(lib, entry)(ctx.h, M.h, m, C.c_void_p(Rs.data_ptr()), n, C.c_void_p(Zs.data_ptr()), n)
+    torch.cuda.synchronize()
+    return st, to_np(Zs).T
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_noalloc_matches_apply_prec_twice(ctx, name):
+    from paper_2601_20174_gb300 import api
+    make, precision, tol = CASES[name]
+    p = make()
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    M = api.Preconditioner.from_basis(api.Operator.from_problem(ctx, p), to_dev(ref["P"]), p.nu, p.omega, precision)
+    lib = ctx._lib
+    R = np.random.default_rng(7).standard_normal((p.n, 2))
+    st, Zref = _apply(lib, "nlsp_apply_prec", ctx, M, R)
+    assert st == 0
+    for _ in range(2):  # the static array keeps the previous call's contents
+        st, Z = _apply(lib, "nlsp_apply_prec_noalloc", ctx, M, R)
+        assert st == 0
+        assert np.all(np.isfinite(Z))
+        assert rel(Z, Zref) <= tol
+    # a second, different right-hand side through the same array
+    R2 = np.random.default_rng(8).standard_normal((p.n, 1))
+    _, Zref2 = _apply(lib, "nlsp_apply_prec", ctx, M, R2)
+    st, Z2 = _apply(lib, "nlsp_apply_prec_noalloc", ctx, M, R2)
+    assert st == 0 and rel(Z2, Zref2) <= tol
+
+
+def test_noalloc_rejects_problems_beyond_its_capacity(ctx):
+    from paper_2601_20174_gb300 import api
+    N = 513  # n = 263169 > 262144 nodes
+    p = gen.iid_diffusion_2d(N=N, k=1, K=2, seed=5, with_samples=False)
+    basis = np.zeros((p.n, 1))
+    basis[:, 0] = 1.0 / np.sqrt(p.n)
+    M = api.Preconditioner.from_basis(api.Operator.from_problem(ctx, p), to_dev(basis), 2, p.omega, 1)
+    st, _ = _apply(ctx._lib, "nlsp_apply_prec_noalloc", ctx, M, np.ones((p.n, 1)))
+    assert st == -1
+    assert "NLSP_NOALLOC_MAX_N" in ctx._lib.nlsp_last_error().decode()
