@@ -328,9 +328,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--graph-mode", type=int, default=1, choices=[0, 1],
-                    help="1: PCG loop as one graph with a device-side while node (default); 0: one-iteration "
-                         "graph relaunched by the host (profilers see each kernel)")
+    ap.add_argument("--graph-mode", type=int, default=2, choices=[0, 1, 2],
+                    help="2: one persistent cooperative kernel per solve (default); 1: PCG loop as one graph "
+                         "with a device-side while node; 0: one-iteration graph relaunched by the host "
+                         "(profilers see each kernel)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

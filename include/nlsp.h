@@ -104,9 +104,13 @@ typedef struct {
   int maxit;      /* iteration cap (>= 1)                                    */
   int flexible;   /* 1: Polak-Ribiere beta; 0: standard; -1: flexible iff
                      the preconditioner is not FP64                         */
-  int graph_mode; /* 1: the whole loop is one CUDA graph with a device-side
-                     while node; 0: graph of one iteration relaunched by the
-                     host, checking convergence every few iterations        */
+  int graph_mode; /* 2: one persistent cooperative kernel per right-hand
+                     side runs the whole solve (phases separated by a
+                     bounded grid barrier; NLSP_ERR_TIMEOUT if a barrier
+                     wait gives up); 1: the loop is one CUDA graph with a
+                     device-side while node; 0: graph of one iteration
+                     relaunched by the host, checking convergence every
+                     few iterations (profilers see each kernel)            */
 } nlsp_solve_params;
 
 typedef struct {
@@ -278,6 +282,15 @@ NLSP_API unsigned long long nlsp_launch_count(const nlsp_ctx* ctx);
    which: 0 = residual + restriction P_r^T rho (with the coarse solve in its
    last block), 1 = prolongation z += P_r e_c.  Errors: NLSP_ERR_INVALID. */
 NLSP_API nlsp_status nlsp_bench_kernel(nlsp_ctx* ctx, const nlsp_prec* M, int which, int reps);
+
+/* Phase timers of the persistent solver (graph_mode 2), accumulated over the
+   solves since the last call and then reset: out_ns[2 p] = time CTA 0 spent
+   in phase p before its grid barrier, out_ns[2 p + 1] = its wait at that
+   barrier, for p = spmv, pre, stored sweeps, restrict, prolong, post, other
+   (14 values).  Recording is enabled by the environment variable
+   NLSP_PHASE_TIMERS=1 when the solver workspace is first created; otherwise
+   zeros.  Synchronises. */
+NLSP_API nlsp_status nlsp_prec_phase_times(nlsp_ctx* ctx, const nlsp_prec* M, double* out_ns, int count);
 
 #ifdef __cplusplus
 }

@@ -72,6 +72,7 @@ SIGNATURES = {
     "nlsp_solve": (ci, [vp, vp, vp, ci, vp, i64, vp, i64, C.POINTER(SolveParams), C.POINTER(SolveInfo)]),
     "nlsp_launch_count": (C.c_ulonglong, [vp]),
     "nlsp_apply_prec_noalloc": (ci, [vp, vp, ci, vp, i64, vp, i64]),
+    "nlsp_prec_phase_times": (ci, [vp, vp, C.POINTER(C.c_double), ci]),
     "nlsp_bench_kernel": (ci, [vp, vp, ci, ci]),
 }
 

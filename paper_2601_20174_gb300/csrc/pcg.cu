@@ -25,6 +25,7 @@
 // order by the last block to arrive.  The loop runs as a CUDA graph whose
 // while node is driven by the post kernel, so a solve needs no host round
 // trip until it finishes.
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -206,9 +207,10 @@ __global__ void __launch_bounds__(TPB) k_pcg_pre(int64_t n, double* __restrict__
 // Jacobi sweeps on A z = r (the residual in the preconditioner precision).
 // ----------------------------------------------------------------------------
 // z after `NU` (1 or 2) sweeps from z = 0, at node m with coordinates cm.
+// rT is not __restrict__: the persistent solver rewrites it between phases of
+// one launch, so its loads must not take the read-only (non-coherent) path.
 template <int KIND, typename T, int NU>
-__device__ __forceinline__ T presmooth_at(const StencilView<T>& A, T omega, const T* __restrict__ rT, int64_t m,
-                                          NodeCoord cm) {
+__device__ __forceinline__ T presmooth_at(const StencilView<T>& A, T omega, const T* rT, int64_t m, NodeCoord cm) {
   const T z1m = omega * stencil_dinv<KIND>(A, m) * rT[m];
   if (NU == 1) return z1m;
   const T az = stencil_apply<KIND>(A, m, cm, [&](int64_t mm) {
@@ -574,6 +576,490 @@ __global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, int64
 }  // namespace
 
 // ============================================================================
+// Persistent solver: the whole PCG solve of one right-hand side in one
+// cooperative launch.  One CTA per SM owns a contiguous range of node tiles;
+// the phases of an iteration are separated by a grid-wide barrier instead of
+// kernel boundaries (a kernel boundary plus a last-block reduction costs
+// several microseconds on GB300, a barrier about one).  Every CTA reduces the
+// per-CTA partials of each dot product itself, in the same order, so all CTAs
+// take the same control decisions.  Iteration t+1:
+//   spmv     p = z + beta p, q = A p, p^T q            | barrier
+//   pre      alpha; x += alpha p, r -= alpha q, rT, r^T r | barrier; stop test
+//   [pre-sweeps stored, FP64 path / nu1 > 2]             | barrier each
+//   restrict z2, rho = rT - A z2, c = P^T rho (TMA ring) | barrier
+//   prolong  e_c = A_c^-1 sum(c); z += P e_c (TMA ring) | barrier
+//   [post-sweeps stored]                                 | barrier each
+//   post     last sweep(s), z in FP64, r^T z (r^T z_old)| barrier; beta
+// ============================================================================
+namespace {
+
+constexpr int PT = 512;  // threads per CTA of the persistent solver
+
+enum { RED_BB = 0, RED_PQ, RED_RR, RED_RZ, RED_RO, RED_TRUE, RED_COUNT };
+
+template <typename T>
+struct PersistArgs {
+  StencilView<double> A64;
+  StencilView<T> AT;
+  T omega;
+  int nu1, nu2, flexible, maxit;
+  double tol;
+  const double* b;
+  double* x;
+  double* r;
+  double* q;
+  double* p0;
+  double* p1;
+  double* z0;
+  double* z1;
+  T* rT;    // residual in the preconditioner precision (== r for FP64)
+  T* zw;    // preconditioner work vectors
+  T* zw2;
+  const T* P;
+  int k, rr_;  // stored rank, active rank
+  const T* Ainv;
+  double* part;   // [RED_COUNT][grid]
+  T* cpart;       // [grid][k]
+  unsigned* ctr;  // grid barrier arrival counter (zero at launch)
+  int* abort;     // set when a barrier wait gave up
+  PcgState* st;   // written by CTA 0 at the end
+  StreamArgs sa;
+  unsigned long long* ptimes;  // optional phase timers [PH_COUNT][2] (work, barrier wait) ns, CTA 0's view
+};
+
+enum { PH_SPMV = 0, PH_PRE, PH_SMOOTH, PH_RESTRICT, PH_PROLONG, PH_POST, PH_OTHER, PH_COUNT };
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier (all CTAs are co-resident: cooperative launch).  The
+// arrival counter grows monotonically, barrier number `gen` waits for
+// gen * gridDim.x arrivals.  A wait longer than 2 s, or one that sees the
+// abort flag, gives up and returns false in every thread of the CTA.
+__device__ __forceinline__ bool grid_sync(unsigned* ctr, int* abort, unsigned& gen, int* ok_s) {
+  ++gen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned target = gen * gridDim.x;
+    int ok = 1;
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    const unsigned long long t0 = tma::now_ns();
+    while (ld_acquire_u32(ctr) < target) {
+      if (*((volatile int*)abort)) {
+        ok = 0;
+        break;
+      }
+      if (tma::now_ns() - t0 > tma::WAIT_LIMIT_NS) {
+        atomicExch(abort, 1);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    if (ok && *((volatile int*)abort)) ok = 0;  // another CTA gave up earlier
+    *ok_s = ok;
+  }
+  __syncthreads();
+  return *ok_s != 0;
+}
+
+// Sum of the grid's partials of one dot product, in CTA order (same value in
+// every CTA).  Result valid in all threads.
+__device__ __forceinline__ double grid_total(const double* part, double* sm_d, double* bc) {
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += 32) s += __ldcg(part + c);
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *bc = s;
+  }
+  __syncthreads();
+  const double v = *bc;
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ void put_partial(double s, double* part, double* sm_d) {
+  s = block_sum_lean(s, sm_d);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Streams the CTA's P tiles through the ring: copy number j (running over the
+// whole kernel) uses stage j % nstage with parity (j / nstage) & 1.
+template <typename T>
+__device__ __forceinline__ void ring_issue(uint64_t* bar, T* buf, const T* P, int k, int r, int nstage, unsigned j,
+                                           int tile) {
+  const unsigned bytes = (unsigned)r * NLSP_TILE * (unsigned)sizeof(T);
+  const int s = (int)(j % (unsigned)nstage);
+  tma::mbar_arrive_expect_tx(&bar[s], bytes);
+  tma::bulk_g2s(buf + (size_t)s * r * NLSP_TILE, P + (size_t)tile * k * NLSP_TILE, bytes, &bar[s]);
+}
+
+__device__ __forceinline__ bool ring_wait(uint64_t* bar, int nstage, unsigned j) {
+  return tma::mbar_wait(&bar[j % (unsigned)nstage], (j / (unsigned)nstage) & 1u);
+}
+
+template <int KIND, typename T, int NCH>
+__global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar[8];
+  __shared__ double sm_d[PT];
+  __shared__ T red_t[PT];
+  __shared__ T sacc[PT / 32][32];
+  __shared__ T cfull[128];
+  __shared__ T e_s[128];
+  __shared__ T zpart[2][4][NLSP_TILE];
+  __shared__ double bc[2];
+  __shared__ int ok_s, abort_s;
+
+  constexpr bool FP32 = sizeof(T) == 4;
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int n = (int)a.AT.n, N = a.AT.N;
+  const int ntiles = (n + NLSP_TILE - 1) / NLSP_TILE;
+  const int t0 = (int)((int64_t)ntiles * cta / G);
+  const int nt = (int)((int64_t)ntiles * (cta + 1) / G) - t0;
+  const int i0 = t0 * NLSP_TILE, i1 = min((t0 + nt) * NLSP_TILE, n);
+  const int nstage = a.sa.nstage, r = a.rr_, k = a.k;
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  T* rho_s = buf + (size_t)nstage * r * NLSP_TILE;
+  const T omega = a.omega;
+  unsigned gen = 0, jc = 0;
+  bool ok = true;
+  (void)N;
+
+  if (tid == 0) {
+    abort_s = 0;
+    for (int s = 0; s < nstage; ++s) tma::mbar_init(&mbar[s], 1);
+    tma::fence_barrier_init();
+  }
+  __syncthreads();
+
+  unsigned long long t_last = (a.ptimes && cta == 0 && tid == 0) ? tma::now_ns() : 0ull;
+  auto sync = [&](int phase) -> bool {
+    const bool timed = a.ptimes && cta == 0 && tid == 0;
+    const unsigned long long t_arr = timed ? tma::now_ns() : 0ull;
+    ok = ok && grid_sync(a.ctr, a.abort, gen, &ok_s);
+    if (timed) {
+      const unsigned long long t_rel = tma::now_ns();
+      a.ptimes[2 * phase] += t_arr - t_last;
+      a.ptimes[2 * phase + 1] += t_rel - t_arr;
+      t_last = t_rel;
+    }
+    return ok;
+  };
+
+  // ---- the two P-streaming phases --------------------------------------
+  // restrict: rho for the own nodes (z recomputed from rT when ZM > 0), then
+  // c_cta = P^T rho over the own tiles -> a.cpart[cta]
+  auto restrict_phase = [&](int zm, const T* zin) {
+    for (int s = 0; s < nstage && s < nt; ++s)
+      if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, t0 + s);
+    for (int e = tid; e < nt * NLSP_TILE; e += PT) {
+      const int i = i0 + e;
+      T rho = T(0);
+      if (i < n) {
+        const NodeCoord c = node_coord<KIND>(i, a.AT.N);
+        if (zm == 0) {
+          rho = a.rT[i] - stencil_apply<KIND>(a.AT, i, c, [&](int64_t m) { return zin[m]; });
+        } else {
+          T zi, az;
+          if (zm == 1) {
+            zi = presmooth_at<KIND, T, 1>(a.AT, omega, a.rT, i, c);
+            az = stencil_diag<KIND>(a.AT, i) * zi;
+            for_each_neighbour<KIND>(a.AT, i, c, [&](int64_t m, NodeCoord cm, T w) {
+              az += w * presmooth_at<KIND, T, 1>(a.AT, omega, a.rT, m, cm);
+            });
+          } else {
+            zi = presmooth_at<KIND, T, 2>(a.AT, omega, a.rT, i, c);
+            az = stencil_diag<KIND>(a.AT, i) * zi;
+            for_each_neighbour<KIND>(a.AT, i, c, [&](int64_t m, NodeCoord cm, T w) {
+              az += w * presmooth_at<KIND, T, 2>(a.AT, omega, a.rT, m, cm);
+            });
+          }
+          rho = a.rT[i] - az;
+          a.zw[i] = zi;
+        }
+      }
+      rho_s[e] = rho;
+    }
+    __syncthreads();
+    const int w = tid & (NLSP_TILE - 1), h = tid >> 7;
+    const int c0 = h * 32;
+    T acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = T(0);
+    for (int it = 0; it < nt; ++it) {
+      if (!ring_wait(mbar, nstage, jc + it)) abort_s = 1;
+      const T* tile = buf + (size_t)((jc + it) % (unsigned)nstage) * r * NLSP_TILE;
+      if (h < NCH) {
+        const T rho = rho_s[it * NLSP_TILE + w];
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < r) acc[j] += rho * tile[(c0 + j) * NLSP_TILE + w];
+      }
+      __syncthreads();
+      if (abort_s) {
+        stream_drain(mbar, (int)(jc + it), (int)(jc + nt), nstage);
+        if (tid == 0) atomicExch(a.abort, 1);
+        break;
+      }
+      if (tid == 0 && it + nstage < nt) ring_issue(mbar, buf, a.P, k, r, nstage, jc + it + nstage, t0 + it + nstage);
+    }
+    jc += nt;
+    const int warp = tid >> 5, lane = tid & 31;
+    sacc[warp][lane] = warp_reduce_scatter32(acc, lane);
+    __syncthreads();
+    for (int col = tid; col < r; col += PT) {
+      const int hh = col >> 5, j = col & 31;
+      T s = T(0);
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) s += sacc[hh * 4 + qq][j];
+      a.cpart[(int64_t)cta * k + col] = s;
+    }
+  };
+
+  // prolong: e_c = A_c^-1 (sum of the CTAs' c), z += P e_c on the own tiles
+  auto prolong_phase = [&](T* z) {
+    for (int s = 0; s < nstage && s < nt; ++s)
+      if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, t0 + s);
+    {
+      const int S = PT / r > 0 ? PT / r : 1;
+      T part = T(0);
+      if (tid < S * r) {
+        const int col = tid % r, sl = tid / r;
+        for (int c = sl; c < G; c += S) part += __ldcg(a.cpart + (int64_t)c * k + col);
+      }
+      red_t[tid] = part;
+      __syncthreads();
+      for (int col = tid; col < r; col += PT) {
+        T s = T(0);
+        for (int sl = 0; sl < S; ++sl) s += red_t[sl * r + col];
+        cfull[col] = s;
+      }
+      __syncthreads();
+      for (int row = tid; row < r; row += PT) {
+        T s = T(0);
+        for (int col = 0; col < r; ++col) s += a.Ainv[(int64_t)col * r + row] * cfull[col];
+        e_s[row] = s;
+      }
+      __syncthreads();
+    }
+    const int w = tid & (NLSP_TILE - 1), h = tid >> 7;
+    const int c0 = h * 32;
+    for (int it = 0; it < nt; ++it) {
+      if (!ring_wait(mbar, nstage, jc + it)) abort_s = 1;
+      const T* tile = buf + (size_t)((jc + it) % (unsigned)nstage) * r * NLSP_TILE;
+      T s = T(0);
+      if (h < NCH) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < r) s += tile[(c0 + j) * NLSP_TILE + w] * e_s[c0 + j];
+      }
+      zpart[it & 1][h][w] = s;
+      __syncthreads();
+      if (abort_s) {
+        stream_drain(mbar, (int)(jc + it), (int)(jc + nt), nstage);
+        if (tid == 0) atomicExch(a.abort, 1);
+        break;
+      }
+      if (tid == 0 && it + nstage < nt) ring_issue(mbar, buf, a.P, k, r, nstage, jc + it + nstage, t0 + it + nstage);
+      if (h == 0) {
+        T sum = zpart[it & 1][0][w];
+#pragma unroll
+        for (int qq = 1; qq < NCH; ++qq) sum += zpart[it & 1][qq][w];
+        const int i = (t0 + it) * NLSP_TILE + w;
+        if (i < n) z[i] += sum;
+      }
+    }
+    jc += nt;
+  };
+
+  auto sweep_phase = [&](const T* zin, T* zout) {
+    for (int i = i0 + tid; i < i1; i += PT) {
+      const NodeCoord c = node_coord<KIND>(i, a.AT.N);
+      const T az = stencil_apply<KIND>(a.AT, i, c, [&](int64_t m) { return zin[m]; });
+      zout[i] = zin[i] + omega * stencil_dinv<KIND>(a.AT, i) * (a.rT[i] - az);
+    }
+  };
+
+  // The preconditioner on the current residual: z (FP64) -> zout64, with
+  // r^T z and r^T zold64 accumulated into the RED_RZ / RED_RO partials.
+  auto apply = [&](double* zout64, const double* zold64, bool flex) -> bool {
+    T* cur = a.zw;
+    T* oth = a.zw2;
+    const bool fused_pre = FP32 && a.nu1 <= 2;
+    if (!fused_pre) {
+      for (int i = i0 + tid; i < i1; i += PT) {
+        const NodeCoord c = node_coord<KIND>(i, a.AT.N);
+        cur[i] = a.nu1 == 1 ? presmooth_at<KIND, T, 1>(a.AT, omega, a.rT, i, c)
+                            : presmooth_at<KIND, T, 2>(a.AT, omega, a.rT, i, c);
+      }
+      if (!sync(PH_SMOOTH)) return false;
+      for (int sw = 2; sw < a.nu1; ++sw) {
+        sweep_phase(cur, oth);
+        T* tmp = cur; cur = oth; oth = tmp;
+        if (!sync(PH_SMOOTH)) return false;
+      }
+    }
+    restrict_phase(fused_pre ? a.nu1 : 0, cur);
+    if (!sync(PH_RESTRICT)) return false;
+    prolong_phase(cur);
+    if (!sync(PH_PROLONG)) return false;
+    const int nfinal = (FP32 && a.nu2 >= 2) ? 2 : 1;
+    for (int sw = nfinal; sw < a.nu2; ++sw) {
+      sweep_phase(cur, oth);
+      T* tmp = cur; cur = oth; oth = tmp;
+      if (!sync(PH_SMOOTH)) return false;
+    }
+    double s_rz = 0.0, s_ro = 0.0;
+    for (int i = i0 + tid; i < i1; i += PT) {
+      const NodeCoord c = node_coord<KIND>(i, a.AT.N);
+      T zf;
+      if (nfinal == 2) {
+        auto z4at = [&](int64_t m, NodeCoord cm) -> T {
+          const T az = stencil_apply<KIND>(a.AT, m, cm, [&](int64_t mm) { return cur[mm]; });
+          return cur[m] + omega * stencil_dinv<KIND>(a.AT, m) * (a.rT[m] - az);
+        };
+        const T z4i = z4at(i, c);
+        T az4 = stencil_diag<KIND>(a.AT, i) * z4i;
+        for_each_neighbour<KIND>(a.AT, i, c, [&](int64_t m, NodeCoord cm, T w) { az4 += w * z4at(m, cm); });
+        zf = z4i + omega * stencil_dinv<KIND>(a.AT, i) * (a.rT[i] - az4);
+      } else {
+        const T az = stencil_apply<KIND>(a.AT, i, c, [&](int64_t m) { return cur[m]; });
+        zf = cur[i] + omega * stencil_dinv<KIND>(a.AT, i) * (a.rT[i] - az);
+      }
+      const double zd = (double)zf;
+      const double ri = a.r[i];
+      zout64[i] = zd;
+      s_rz = fma(ri, zd, s_rz);
+      if (flex) s_ro = fma(ri, zold64[i], s_ro);
+    }
+    put_partial(s_rz, a.part + RED_RZ * G, sm_d);
+    if (flex) put_partial(s_ro, a.part + RED_RO * G, sm_d);
+    return sync(PH_POST);
+  };
+
+  // ---- start: r = b, x = 0, p = 0 ---------------------------------------
+  int status = (int)NLSP_OK, iter = 0;
+  double bb, tol2bn, rz = 0.0, rr = 0.0, beta = 0.0;
+  {
+    double s = 0.0;
+    for (int i = i0 + tid; i < i1; i += PT) {
+      const double bi = a.b[i];
+      a.r[i] = bi;
+      if (FP32) a.rT[i] = (T)bi;
+      a.x[i] = 0.0;
+      a.p0[i] = 0.0;
+      a.p1[i] = 0.0;
+      s = fma(bi, bi, s);
+    }
+    put_partial(s, a.part + RED_BB * G, sm_d);
+  }
+  bool done = false;
+  if (sync(PH_OTHER)) {
+    bb = grid_total(a.part + RED_BB * G, sm_d, bc);
+    tol2bn = a.tol * a.tol * bb;
+    rr = bb;
+    if (bb == 0.0) done = true;
+    else if (!isfinite(bb)) { status = (int)NLSP_ERR_BREAKDOWN; done = true; }
+  } else {
+    bb = 0.0;
+    tol2bn = 0.0;
+    done = true;
+  }
+  // initial preconditioner application z_0 = B r_0
+  if (!done) {
+    if (apply(a.z0, a.z1, false)) {
+      rz = grid_total(a.part + RED_RZ * G, sm_d, bc);
+      if (!(rz > 0.0) || !isfinite(rz)) { status = (int)NLSP_ERR_BREAKDOWN; done = true; }
+    } else {
+      done = true;
+    }
+  }
+  // ---- iterations --------------------------------------------------------
+  while (!done && ok) {
+    const int t = iter;
+    const double* zc = (t & 1) ? a.z1 : a.z0;
+    const double* pin = (t & 1) ? a.p1 : a.p0;
+    double* pout = (t & 1) ? a.p0 : a.p1;
+    {  // spmv
+      double s = 0.0;
+      for (int i = i0 + tid; i < i1; i += PT) {
+        const NodeCoord c = node_coord<KIND>(i, a.A64.N);
+        auto pv = [&](int64_t m) { return fma(beta, __ldcg(pin + m), __ldcg(zc + m)); };
+        const double pi = pv(i);
+        const double qi = stencil_apply<KIND>(a.A64, i, c, pv);
+        pout[i] = pi;
+        a.q[i] = qi;
+        s = fma(pi, qi, s);
+      }
+      put_partial(s, a.part + RED_PQ * G, sm_d);
+    }
+    if (!sync(PH_SPMV)) break;
+    const double pq = grid_total(a.part + RED_PQ * G, sm_d, bc);
+    iter = t + 1;
+    if (!(pq > 0.0) || !isfinite(pq)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
+    const double alpha = rz / pq;
+    {  // pre: x, r update
+      double s = 0.0;
+      for (int i = i0 + tid; i < i1; i += PT) {
+        a.x[i] = fma(alpha, pout[i], a.x[i]);
+        const double ri = fma(-alpha, a.q[i], a.r[i]);
+        a.r[i] = ri;
+        if (FP32) a.rT[i] = (T)ri;
+        s = fma(ri, ri, s);
+      }
+      put_partial(s, a.part + RED_RR * G, sm_d);
+    }
+    if (!sync(PH_PRE)) break;
+    rr = grid_total(a.part + RED_RR * G, sm_d, bc);
+    if (!isfinite(rr)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
+    if (rr <= tol2bn) break;  // converged
+    double* zn = (iter & 1) ? a.z1 : a.z0;
+    const double* zo = (iter & 1) ? a.z0 : a.z1;
+    const bool flex = a.flexible != 0;
+    if (!apply(zn, zo, flex)) break;
+    const double rzn = grid_total(a.part + RED_RZ * G, sm_d, bc);
+    const double ro = flex ? grid_total(a.part + RED_RO * G, sm_d, bc) : 0.0;
+    if (!(rzn > 0.0) || !isfinite(rzn)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
+    beta = (rzn - ro) / rz;
+    rz = rzn;
+    if (iter >= a.maxit) { status = (int)NLSP_NOT_CONVERGED; break; }
+  }
+  if (!ok) status = (int)NLSP_ERR_TIMEOUT;
+  // ---- true residual ------------------------------------------------------
+  double trr = 0.0;
+  if (ok) {
+    double s = 0.0;
+    for (int i = i0 + tid; i < i1; i += PT) {
+      const NodeCoord c = node_coord<KIND>(i, a.A64.N);
+      const double ri = a.b[i] - stencil_apply<KIND>(a.A64, i, c, [&](int64_t m) { return __ldcg(a.x + m); });
+      s = fma(ri, ri, s);
+    }
+    put_partial(s, a.part + RED_TRUE * G, sm_d);
+    if (sync(PH_OTHER)) trr = grid_total(a.part + RED_TRUE * G, sm_d, bc);
+  }
+  if (cta == 0 && tid == 0) {
+    PcgState* st = a.st;
+    st->bnorm2 = bb;
+    st->tol2bn = tol2bn;
+    st->rz = rz;
+    st->rr = rr;
+    st->true_rr = trr;
+    st->iter = iter;
+    st->status = ok ? status : (int)NLSP_ERR_TIMEOUT;
+    st->done = 1;
+    st->maxit = a.maxit;
+    st->flexible = a.flexible;
+  }
+}
+
+}  // namespace
+
+// ============================================================================
 // Host side
 // ============================================================================
 struct PcgWork {
@@ -594,6 +1080,7 @@ struct PcgWork {
   cudaGraphConditionalHandle cond = 0;
   int built_r = -1;
   int body_launches = 0;  // kernels in one iteration body
+  unsigned long long* ptimes = nullptr;  // phase timers of the persistent solver (NLSP_PHASE_TIMERS=1)
 };
 
 namespace {
@@ -617,6 +1104,7 @@ void free_work(PcgWork* w) {
   if (w->rT) cudaFree(w->rT);
   if (w->part) cudaFree(w->part);
   if (w->counter) cudaFree(w->counter);
+  if (w->ptimes) cudaFree(w->ptimes);
   if (w->st_all) cudaFree(w->st_all);
   if (w->h_st) cudaFreeHost(w->h_st);
   if (w->cap) cudaStreamDestroy(w->cap);
@@ -640,6 +1128,11 @@ nlsp_status ensure_work(nlsp_prec* M, int m) {
     NLSP_CUDA(cudaMalloc(&w->counter, sizeof(unsigned) * 4));
     NLSP_CUDA(cudaMemsetAsync(w->counter, 0, sizeof(unsigned) * 4, ctx->stream));
     NLSP_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+    const char* pt = getenv("NLSP_PHASE_TIMERS");
+    if (pt && pt[0] == '1') {
+      NLSP_CUDA(cudaMalloc(&w->ptimes, sizeof(unsigned long long) * 2 * PH_COUNT));
+      NLSP_CUDA(cudaMemsetAsync(w->ptimes, 0, sizeof(unsigned long long) * 2 * PH_COUNT, ctx->stream));
+    }
   }
   PcgWork* w = M->pcg;
   if (w->st_cap < m + 1) {
@@ -729,6 +1222,8 @@ nlsp_status prepare_stream_kernels() {
   NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 4, 1>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 4, 2>));
   NLSP_TRY(allow_max_smem(k_prolong<T, 1>)); NLSP_TRY(allow_max_smem(k_prolong<T, 2>));
   NLSP_TRY(allow_max_smem(k_prolong<T, 3>)); NLSP_TRY(allow_max_smem(k_prolong<T, 4>));
+  NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 1>)); NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 2>));
+  NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 3>)); NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 4>));
   done = true;
   return NLSP_OK;
 }
@@ -830,6 +1325,7 @@ template <int KIND, typename T>
 struct Solver {
   static double* x(PcgWork* w) { return w->vec; }
   static double* r(PcgWork* w) { return w->vec + w->n; }
+  static double* r_(PcgWork* w) { return r(w); }
   static double* q(PcgWork* w) { return w->vec + 2 * w->n; }
   static Pair<double> Ppair(PcgWork* w) { return Pair<double>{{w->vec + 3 * w->n, w->vec + 4 * w->n}}; }
   static Pair<double> Zpair(PcgWork* w) { return Pair<double>{{w->vec + 5 * w->n, w->vec + 6 * w->n}}; }
@@ -912,6 +1408,76 @@ struct Solver {
     return NLSP_OK;
   }
 
+  // The persistent cooperative solver (graph_mode 2): one launch per column.
+  static nlsp_status launch_persistent(nlsp_prec* M, const double* b, double* xout, const nlsp_solve_params* prm,
+                                       int flexible, PcgState* st_out) {
+    nlsp_ctx* ctx = M->ctx;
+    PcgWork* w = M->pcg;
+    cudaStream_t s = ctx->stream;
+    const int G = ctx->num_sms;
+    const int ntiles = (int)((M->n + NLSP_TILE - 1) / NLSP_TILE);
+    const int r = M->r;
+    const size_t tile = (size_t)r * NLSP_TILE * sizeof(T);
+    const int max_nodes = div_up(ntiles, G) * NLSP_TILE;
+    const size_t rho = (size_t)max_nodes * sizeof(T);
+    const size_t budget = 180 * 1024;
+    StreamArgs sa;
+    sa.max_nodes = max_nodes;
+    sa.nstage = (int)std::max<size_t>(1, std::min<size_t>(4, budget > rho + tile ? (budget - rho) / tile : 1));
+    const size_t smem = (size_t)sa.nstage * tile + rho;
+    PersistArgs<T> a;
+    a.A64 = M->A->v64;
+    a.AT = view_T<T>(M->A);
+    a.omega = (T)M->omega;
+    a.nu1 = M->nu1;
+    a.nu2 = M->nu2;
+    a.flexible = flexible;
+    a.maxit = prm->maxit;
+    a.tol = prm->tol;
+    a.b = b;
+    a.x = x(w);
+    a.r = r_(w);
+    a.q = q(w);
+    Pair<double> P2 = Ppair(w), Z2 = Zpair(w);
+    a.p0 = P2.v[0];
+    a.p1 = P2.v[1];
+    a.z0 = Z2.v[0];
+    a.z1 = Z2.v[1];
+    a.rT = rT(w);
+    a.zw = (T*)M->w0;
+    a.zw2 = (T*)M->w1;
+    a.P = (const T*)M->P;
+    a.k = M->k;
+    a.rr_ = r;
+    a.Ainv = (const T*)M->AinvT;
+    a.part = w->part;
+    a.cpart = (T*)M->cpart;
+    a.ctr = w->counter;
+    a.abort = (int*)(w->counter + 1);
+    a.st = st_out;
+    a.sa = sa;
+    a.ptimes = w->ptimes;
+    const void* fn;
+    const int nch = (r + 31) / 32;
+    if (nch == 1) fn = (const void*)k_pcg_persistent<KIND, T, 1>;
+    else if (nch == 2) fn = (const void*)k_pcg_persistent<KIND, T, 2>;
+    else if (nch == 3) fn = (const void*)k_pcg_persistent<KIND, T, 3>;
+    else fn = (const void*)k_pcg_persistent<KIND, T, 4>;
+    int per_sm = 0;
+    NLSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PT, smem));
+    if (per_sm < 1) {
+      nlsp_record_message("persistent solver: one CTA per SM does not fit (shared memory or registers)");
+      return NLSP_ERR_INVALID;
+    }
+    if ((int64_t)RED_COUNT * G > 4 * (int64_t)w->max_blocks || G > M->rblocks) return NLSP_ERR_INVALID;
+    NLSP_CUDA(cudaMemsetAsync(w->counter, 0, sizeof(unsigned) * 2, s));
+    void* args[] = {&a};
+    NLSP_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PT), args, smem, s));
+    count_launches(ctx, 1);
+    NLSP_CUDA(cudaMemcpyAsync(xout, x(w), sizeof(double) * M->n, cudaMemcpyDeviceToDevice, s));
+    return NLSP_OK;
+  }
+
   static nlsp_status solve(nlsp_prec* M, int m, const double* B, int64_t ldb, double* X, int64_t ldx,
                            const nlsp_solve_params* prm, nlsp_solve_info* infos) {
     nlsp_ctx* ctx = M->ctx;
@@ -919,6 +1485,14 @@ struct Solver {
     NLSP_TRY(ensure_work(M, m));
     NLSP_TRY((prepare_stream_kernels<KIND, T>()));
     PcgWork* w = M->pcg;
+    if (prm->graph_mode == 2) {
+      const int flexible = prm->flexible < 0 ? (M->precision != NLSP_FP64) : (prm->flexible != 0);
+      for (int col = 0; col < m; ++col)
+        NLSP_TRY(launch_persistent(M, B + col * ldb, X + col * ldx, prm, flexible, w->st_all + col));
+      NLSP_CUDA(cudaMemcpyAsync(w->h_st, w->st_all, sizeof(PcgState) * m, cudaMemcpyDeviceToHost, s));
+      NLSP_CUDA(cudaStreamSynchronize(s));
+      return summarize(w, m, infos, 0);
+    }
     if (!w->x_while || w->built_r != M->r) NLSP_TRY(build_graphs(M));
     const int flexible = prm->flexible < 0 ? (M->precision != NLSP_FP64) : (prm->flexible != 0);
     const int g = node_grid(ctx, M->n);
@@ -953,10 +1527,16 @@ struct Solver {
     }
     NLSP_CUDA(cudaMemcpyAsync(w->h_st, w->st_all, sizeof(PcgState) * m, cudaMemcpyDeviceToHost, s));
     NLSP_CUDA(cudaStreamSynchronize(s));
+    if (prm->graph_mode == 1)
+      for (int col = 0; col < m; ++col)
+        count_launches(ctx, (unsigned long long)std::max(w->h_st[col].iter, 1) * w->body_launches);
+    return summarize(w, m, infos, 0);
+  }
+
+  static nlsp_status summarize(PcgWork* w, int m, nlsp_solve_info* infos, int) {
     nlsp_status worst = NLSP_OK;
     for (int col = 0; col < m; ++col) {
       const PcgState& h = w->h_st[col];
-      if (prm->graph_mode == 1) count_launches(ctx, (unsigned long long)std::max(h.iter, 1) * w->body_launches);
       int stc = h.status;
       if (stc == NLSP_OK && !h.done) stc = NLSP_NOT_CONVERGED;
       if (infos) {
@@ -965,7 +1545,7 @@ struct Solver {
         infos[col].relres = h.bnorm2 > 0 ? sqrt(h.rr / h.bnorm2) : 0.0;
         infos[col].true_relres = h.bnorm2 > 0 ? sqrt(h.true_rr / h.bnorm2) : 0.0;
       }
-      if (stc == NLSP_ERR_BREAKDOWN) worst = NLSP_ERR_BREAKDOWN;
+      if (stc == NLSP_ERR_BREAKDOWN || stc == NLSP_ERR_TIMEOUT) worst = (nlsp_status)stc;
       else if (stc == NLSP_NOT_CONVERGED && worst == NLSP_OK) worst = NLSP_NOT_CONVERGED;
     }
     return worst;
@@ -1050,7 +1630,7 @@ extern "C" nlsp_status nlsp_solve(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_pr
                                   nlsp_solve_info* infos) {
   if (!ctx || !A || !Mc || !params || Mc->A != A || m < 0 || ldb < A->n || ldx < A->n) return NLSP_ERR_INVALID;
   if (m > 0 && (!dev_B || !dev_X)) return NLSP_ERR_INVALID;
-  if (!(params->tol >= 0.0) || params->maxit < 1 || (params->graph_mode != 0 && params->graph_mode != 1))
+  if (!(params->tol >= 0.0) || params->maxit < 1 || params->graph_mode < 0 || params->graph_mode > 2)
     return NLSP_ERR_INVALID;
   if (m == 0) return NLSP_OK;
   NLSP_CUDA(cudaSetDevice(ctx->device));
@@ -1065,6 +1645,18 @@ extern "C" void nlsp_free_prec(nlsp_prec* M) {
   free_work(M->pcg);
   if (M->storage) cudaFree(M->storage);
   delete M;
+}
+
+extern "C" nlsp_status nlsp_prec_phase_times(nlsp_ctx* ctx, const nlsp_prec* M, double* out_ns, int count) {
+  if (!ctx || !M || !out_ns || count < 0) return NLSP_ERR_INVALID;
+  for (int i = 0; i < count; ++i) out_ns[i] = 0.0;
+  if (!M->pcg || !M->pcg->ptimes) return NLSP_OK;
+  unsigned long long h[2 * PH_COUNT];
+  NLSP_CUDA(cudaMemcpyAsync(h, M->pcg->ptimes, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  NLSP_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < count && i < 2 * PH_COUNT; ++i) out_ns[i] = (double)h[i];
+  NLSP_CUDA(cudaMemsetAsync(M->pcg->ptimes, 0, sizeof(h), ctx->stream));
+  return NLSP_OK;
 }
 
 extern "C" nlsp_status nlsp_bench_kernel(nlsp_ctx* ctx, const nlsp_prec* Mc, int which, int reps) {

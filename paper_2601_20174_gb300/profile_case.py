@@ -2,10 +2,12 @@
 
 Builds the 512 x 512 GRF diffusion system (k = 64 from K = 128 smoothed
 samples, nu = 2, omega = 2/3), sets up the preconditioner and runs a few PCG
-iterations with the host-relaunched iteration graph, so that a profiler sees
-every kernel of the setup and of the iteration as separate launches.
+iterations.  With --mode 0 (default) the iterations use the host-relaunched
+iteration graph, so that a profiler sees every kernel as a separate launch;
+with --mode 2 and NLSP_PHASE_TIMERS=1 in the environment the persistent
+solver's per-phase times are printed (microseconds per iteration).
 
-    python -m paper_2601_20174_gb300.profile_case [--precision mixed|fp64] [--iters 4] [--N 512]
+    python -m paper_2601_20174_gb300.profile_case [--precision mixed|fp64] [--iters 4] [--N 512] [--mode 0|1|2]
 """
 from __future__ import annotations
 
@@ -24,6 +26,7 @@ def main() -> int:
     ap.add_argument("--N", type=int, default=512)
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--K", type=int, default=128)
+    ap.add_argument("--mode", type=int, default=0, choices=[0, 1, 2])
     args = ap.parse_args()
     p = gen.grf_diffusion_2d(args.N, args.k, args.K, seed=0)
     ctx = api.Context(0)
@@ -32,9 +35,17 @@ def main() -> int:
     prec = L.NLSP_MIXED_FP32 if args.precision == "mixed" else L.NLSP_FP64
     M = api.Preconditioner.build(A, S0.t(), p.k, p.s1, p.nu, p.omega, prec)
     f = torch.as_tensor(p.f[:, 0].copy()).cuda()
-    _, res = M.solve(f, tol=1e-8, maxit=args.iters, graph_mode=0)
+    _, res = M.solve(f, tol=1e-8, maxit=args.iters, graph_mode=args.mode)
     torch.cuda.synchronize()
     print(f"profile case: n={p.n} k={p.k} iterations={res[0].iterations} status={res[0].status}")
+    if args.mode == 2:
+        import ctypes as C
+        out = (C.c_double * 14)()
+        L.check(ctx._lib.nlsp_prec_phase_times(ctx.h, M.h, out, 14), "nlsp_prec_phase_times")
+        names = ["spmv", "pre", "stored sweeps", "restrict", "prolong", "post", "other"]
+        it = max(1, res[0].iterations)
+        for i, name in enumerate(names):
+            print(f"  {name:14s} work {out[2 * i] / 1e3 / it:8.2f} us/it   barrier wait {out[2 * i + 1] / 1e3 / it:8.2f} us/it")
     M.close()
     A.close()
     ctx.close()

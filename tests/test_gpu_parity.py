@@ -123,7 +123,7 @@ def test_rank_truncation(ctx):
 
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
-@pytest.mark.parametrize("graph_mode", [0, 1])
+@pytest.mark.parametrize("graph_mode", [0, 1, 2])
 def test_pcg_fp64_matches_oracle_iterates(ctx, name, graph_mode):
     p = PROBLEMS[name]()
     A = op.assemble(p)
@@ -140,7 +140,8 @@ def test_pcg_fp64_matches_oracle_iterates(ctx, name, graph_mode):
 
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
-def test_pcg_end_to_end_both_precisions(ctx, name):
+@pytest.mark.parametrize("graph_mode", [1, 2])
+def test_pcg_end_to_end_both_precisions(ctx, name, graph_mode):
     p = PROBLEMS[name]()
     p.tol = 1e-8
     A = op.assemble(p)
@@ -148,7 +149,7 @@ def test_pcg_end_to_end_both_precisions(ctx, name):
     Aop = _api().Operator.from_problem(ctx, p)
     for precision in (FP64, MIXED):
         M = _api().Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, precision)
-        x, res = M.solve(to_dev(p.f[:, 0]), tol=p.tol)
+        x, res = M.solve(to_dev(p.f[:, 0]), tol=p.tol, graph_mode=graph_mode)
         true = np.linalg.norm(p.f[:, 0] - A @ to_np(x)) / np.linalg.norm(p.f[:, 0])
         assert res[0].status == 0 and true <= 1e-8 * 1.01
         if precision == FP64:
@@ -157,35 +158,38 @@ def test_pcg_end_to_end_both_precisions(ctx, name):
             assert abs(res[0].iterations - o["results"][0]["iters"]) <= 2
 
 
-def test_multi_rhs_zero_and_scaled_columns(ctx):
+@pytest.mark.parametrize("graph_mode", [1, 2])
+def test_multi_rhs_zero_and_scaled_columns(ctx, graph_mode):
     p = PROBLEMS["grf5"]()
     A = op.assemble(p)
     M = _api().Preconditioner.build(_api().Operator.from_problem(ctx, p), to_dev(p.S0), p.k, p.s1, p.nu, p.omega,
                                     FP64)
     b = p.f[:, 0]
     B = np.stack([b, np.zeros(p.n), 3.0 * b], axis=1)
-    X, res = M.solve(to_dev(B), tol=1e-9)
+    X, res = M.solve(to_dev(B), tol=1e-9, graph_mode=graph_mode)
     X = to_np(X)
     assert res[1].iterations == 0 and res[1].status == 0 and np.all(X[:, 1] == 0)
     assert res[0].iterations == res[2].iterations
     assert rel(X[:, 2], 3.0 * X[:, 0]) <= 1e-10
 
 
-def test_full_rank_basis_one_iteration(ctx):
+@pytest.mark.parametrize("graph_mode", [1, 2])
+def test_full_rank_basis_one_iteration(ctx, graph_mode):
     p = gen.iid_diffusion_2d(N=7, k=4, K=8, seed=9)
     M = _api().Preconditioner.from_basis(_api().Operator.from_problem(ctx, p), to_dev(np.eye(p.n)), 2, p.omega, FP64)
-    x, res = M.solve(to_dev(p.f[:, 0]), tol=1e-10)
+    x, res = M.solve(to_dev(p.f[:, 0]), tol=1e-10, graph_mode=graph_mode)
     assert res[0].iterations == 1 and res[0].true_relres <= 1e-10
 
 
-def test_maxit_and_nonfinite_rhs(ctx):
+@pytest.mark.parametrize("graph_mode", [1, 2])
+def test_maxit_and_nonfinite_rhs(ctx, graph_mode):
     p = PROBLEMS["grf5"]()
     M = _api().Preconditioner.build(_api().Operator.from_problem(ctx, p), to_dev(p.S0), 2, p.s1, p.nu, p.omega, FP64)
-    x, res = M.solve(to_dev(p.f[:, 0]), tol=1e-14, maxit=3)
+    x, res = M.solve(to_dev(p.f[:, 0]), tol=1e-14, maxit=3, graph_mode=graph_mode)
     assert res[0].status == 1 and res[0].iterations == 3
     bad = p.f[:, 0].copy()
     bad[5] = np.nan
-    x, res = M.solve(to_dev(bad), tol=1e-8)
+    x, res = M.solve(to_dev(bad), tol=1e-8, graph_mode=graph_mode)
     assert res[0].status == -4
 
 
