@@ -277,6 +277,8 @@ __device__ __forceinline__ T warp_reduce_scatter32(T (&v)[32], int lane) {
 struct StreamArgs {
   int nstage;     // tiles in flight per CTA
   int max_nodes;  // capacity of the per-CTA residual buffer (restrict)
+  int n_tm;       // persistent solver: tiles per CTA kept in tensor memory
+  int n_sm;       // persistent solver: tiles per CTA kept in shared memory
 };
 
 // Waits for stage `s` of iteration `it`; on a timeout records it in *abort_s.
@@ -702,7 +704,11 @@ __device__ __forceinline__ bool ring_wait(uint64_t* bar, int nstage, unsigned j)
   return tma::mbar_wait(&bar[j % (unsigned)nstage], (j / (unsigned)nstage) & 1u);
 }
 
-template <int KIND, typename T, int NCH>
+// CPG = columns of P per warp group (4 groups of 4 warps; r_pad = 4 CPG).
+// The CTA's first n_tm tiles of P live in tensor memory (FP32 path), the next
+// n_sm in shared memory, both loaded once per solve; only the rest is
+// streamed through the TMA ring in every restriction and prolongation.
+template <int KIND, typename T, int CPG>
 __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[8];
@@ -714,8 +720,10 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
   __shared__ T zpart[2][4][NLSP_TILE];
   __shared__ double bc[2];
   __shared__ int ok_s, abort_s;
+  __shared__ unsigned tbase_s;
 
   constexpr bool FP32 = sizeof(T) == 4;
+  constexpr int RPAD = 4 * CPG;
   const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
   const int n = (int)a.AT.n, N = a.AT.N;
   const int ntiles = (n + NLSP_TILE - 1) / NLSP_TILE;
@@ -723,9 +731,15 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
   const int nt = (int)((int64_t)ntiles * (cta + 1) / G) - t0;
   const int i0 = t0 * NLSP_TILE, i1 = min((t0 + nt) * NLSP_TILE, n);
   const int nstage = a.sa.nstage, r = a.rr_, k = a.k;
+  const int ntm = FP32 ? min(nt, a.sa.n_tm) : 0;    // tiles in tensor memory
+  const int nsm = min(nt - ntm, a.sa.n_sm);         // tiles resident in shared memory
+  const int nst = nt - ntm - nsm;                   // tiles streamed per phase
+  const int tst = t0 + ntm + nsm;                   // first streamed tile
   T* buf = reinterpret_cast<T*>(smem_raw);
-  T* rho_s = buf + (size_t)nstage * r * NLSP_TILE;
+  T* res = buf + (size_t)nstage * r * NLSP_TILE;
+  T* rho_s = res + (size_t)a.sa.n_sm * r * NLSP_TILE;
   const T omega = a.omega;
+  const int warp = tid >> 5, lane = tid & 31, q = warp & 3, g = warp >> 2, nd = 32 * q + lane;
   unsigned gen = 0, jc = 0;
   bool ok = true;
   (void)N;
@@ -734,6 +748,28 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
     abort_s = 0;
     for (int s = 0; s < nstage; ++s) tma::mbar_init(&mbar[s], 1);
     tma::fence_barrier_init();
+  }
+  if (ntm > 0 && warp == 0) tmem::alloc(&tbase_s, 512);
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  const unsigned tlane = (unsigned)(32 * q) << 16;
+  const unsigned tbase = ntm > 0 ? tbase_s : 0u;
+  // one-time loads of the resident tiles
+  for (int ti = 0; ti < ntm; ++ti) {
+    float v[CPG];
+    const T* src = a.P + ((size_t)(t0 + ti) * k) * NLSP_TILE + nd;
+#pragma unroll
+    for (int j = 0; j < CPG; ++j) {
+      const int col = g * CPG + j;
+      v[j] = col < r ? (float)src[(size_t)col * NLSP_TILE] : 0.0f;
+    }
+    if (FP32) tmem::Io<CPG>::st(tbase + tlane + (unsigned)(ti * RPAD + g * CPG), v);
+  }
+  for (int ts = 0; ts < nsm; ++ts) {
+    const T* src = a.P + ((size_t)(t0 + ntm + ts) * k) * NLSP_TILE;
+    T* dst = res + (size_t)ts * r * NLSP_TILE;
+    for (int e = tid; e < r * NLSP_TILE; e += PT) dst[e] = src[e];
   }
   __syncthreads();
 
@@ -751,12 +787,13 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
     return ok;
   };
 
-  // ---- the two P-streaming phases --------------------------------------
-  // restrict: rho for the own nodes (z recomputed from rT when ZM > 0), then
-  // c_cta = P^T rho over the own tiles -> a.cpart[cta]
+  // ---- the two phases that read P ----------------------------------------
+  // restrict: rho for the own nodes (z recomputed from rT when zm > 0), then
+  // c_cta = P^T rho over the own tiles -> a.cpart[cta].  Thread (g, q, lane)
+  // accumulates columns [g CPG, g CPG + CPG) for node 32 q + lane of each tile.
   auto restrict_phase = [&](int zm, const T* zin) {
-    for (int s = 0; s < nstage && s < nt; ++s)
-      if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, t0 + s);
+    for (int s = 0; s < nstage && s < nst; ++s)
+      if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, tst + s);
     for (int e = tid; e < nt * NLSP_TILE; e += PT) {
       const int i = i0 + e;
       T rho = T(0);
@@ -786,45 +823,61 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
       rho_s[e] = rho;
     }
     __syncthreads();
-    const int w = tid & (NLSP_TILE - 1), h = tid >> 7;
-    const int c0 = h * 32;
     T acc[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = T(0);
-    for (int it = 0; it < nt; ++it) {
+    for (int ti = 0; ti < ntm; ++ti) {
+      float v[CPG];
+      tmem::Io<CPG>::ld(tbase + tlane + (unsigned)(ti * RPAD + g * CPG), v);
+      const T rho = rho_s[ti * NLSP_TILE + nd];
+#pragma unroll
+      for (int j = 0; j < CPG; ++j) acc[j] += rho * (T)v[j];
+    }
+    for (int ts = 0; ts < nsm; ++ts) {
+      const T* tile = res + (size_t)ts * r * NLSP_TILE;
+      const T rho = rho_s[(ntm + ts) * NLSP_TILE + nd];
+#pragma unroll
+      for (int j = 0; j < CPG; ++j) {
+        const int col = g * CPG + j;
+        if (col < r) acc[j] += rho * tile[col * NLSP_TILE + nd];
+      }
+    }
+    for (int it = 0; it < nst; ++it) {
       if (!ring_wait(mbar, nstage, jc + it)) abort_s = 1;
       const T* tile = buf + (size_t)((jc + it) % (unsigned)nstage) * r * NLSP_TILE;
-      if (h < NCH) {
-        const T rho = rho_s[it * NLSP_TILE + w];
+      const T rho = rho_s[(ntm + nsm + it) * NLSP_TILE + nd];
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < r) acc[j] += rho * tile[(c0 + j) * NLSP_TILE + w];
+      for (int j = 0; j < CPG; ++j) {
+        const int col = g * CPG + j;
+        if (col < r) acc[j] += rho * tile[col * NLSP_TILE + nd];
       }
       __syncthreads();
       if (abort_s) {
-        stream_drain(mbar, (int)(jc + it), (int)(jc + nt), nstage);
+        stream_drain(mbar, (int)(jc + it), (int)(jc + nst), nstage);
         if (tid == 0) atomicExch(a.abort, 1);
         break;
       }
-      if (tid == 0 && it + nstage < nt) ring_issue(mbar, buf, a.P, k, r, nstage, jc + it + nstage, t0 + it + nstage);
+      if (tid == 0 && it + nstage < nst) ring_issue(mbar, buf, a.P, k, r, nstage, jc + it + nstage, tst + it + nstage);
     }
-    jc += nt;
-    const int warp = tid >> 5, lane = tid & 31;
-    sacc[warp][lane] = warp_reduce_scatter32(acc, lane);
+    jc += nst;
+    sacc[warp][lane] = warp_reduce_scatter32(acc, lane);  // column g CPG + lane (lane < CPG)
     __syncthreads();
     for (int col = tid; col < r; col += PT) {
-      const int hh = col >> 5, j = col & 31;
+      const int gg = col / CPG, j = col % CPG;
       T s = T(0);
 #pragma unroll
-      for (int qq = 0; qq < 4; ++qq) s += sacc[hh * 4 + qq][j];
+      for (int qq = 0; qq < 4; ++qq) s += sacc[gg * 4 + qq][j];
       a.cpart[(int64_t)cta * k + col] = s;
     }
   };
 
-  // prolong: e_c = A_c^-1 (sum of the CTAs' c), z += P e_c on the own tiles
+  // prolong: e_c = A_c^-1 (sum of the CTAs' c), z += P e_c on the own tiles.
+  // Resident tiles: warp group g takes tiles g, g + 4, ... and each thread
+  // its node's whole row; streamed tiles: the (g, q, lane) split with a
+  // shared-memory combine.
   auto prolong_phase = [&](T* z) {
-    for (int s = 0; s < nstage && s < nt; ++s)
-      if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, t0 + s);
+    for (int s = 0; s < nstage && s < nst; ++s)
+      if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, tst + s);
     {
       const int S = PT / r > 0 ? PT / r : 1;
       T part = T(0);
@@ -840,41 +893,55 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
         cfull[col] = s;
       }
       __syncthreads();
-      for (int row = tid; row < r; row += PT) {
+      for (int row = tid; row < RPAD; row += PT) {
         T s = T(0);
-        for (int col = 0; col < r; ++col) s += a.Ainv[(int64_t)col * r + row] * cfull[col];
-        e_s[row] = s;
+        if (row < r)
+          for (int col = 0; col < r; ++col) s += a.Ainv[(int64_t)col * r + row] * cfull[col];
+        e_s[row] = s;  // zero beyond r
       }
       __syncthreads();
     }
-    const int w = tid & (NLSP_TILE - 1), h = tid >> 7;
-    const int c0 = h * 32;
-    for (int it = 0; it < nt; ++it) {
+    for (int tl = g; tl < ntm + nsm; tl += 4) {
+      T s = T(0);
+      if (tl < ntm) {
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          float v[CPG];
+          tmem::Io<CPG>::ld(tbase + tlane + (unsigned)(tl * RPAD + cc * CPG), v);
+#pragma unroll
+          for (int j = 0; j < CPG; ++j) s += (T)v[j] * e_s[cc * CPG + j];
+        }
+      } else {
+        const T* tile = res + (size_t)(tl - ntm) * r * NLSP_TILE;
+        for (int col = 0; col < r; ++col) s += tile[col * NLSP_TILE + nd] * e_s[col];
+      }
+      const int i = (t0 + tl) * NLSP_TILE + nd;
+      if (i < n) z[i] += s;
+    }
+    for (int it = 0; it < nst; ++it) {
       if (!ring_wait(mbar, nstage, jc + it)) abort_s = 1;
       const T* tile = buf + (size_t)((jc + it) % (unsigned)nstage) * r * NLSP_TILE;
       T s = T(0);
-      if (h < NCH) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < r) s += tile[(c0 + j) * NLSP_TILE + w] * e_s[c0 + j];
+      for (int j = 0; j < CPG; ++j) {
+        const int col = g * CPG + j;
+        if (col < r) s += tile[col * NLSP_TILE + nd] * e_s[col];
       }
-      zpart[it & 1][h][w] = s;
+      zpart[it & 1][g][nd] = s;
       __syncthreads();
       if (abort_s) {
-        stream_drain(mbar, (int)(jc + it), (int)(jc + nt), nstage);
+        stream_drain(mbar, (int)(jc + it), (int)(jc + nst), nstage);
         if (tid == 0) atomicExch(a.abort, 1);
         break;
       }
-      if (tid == 0 && it + nstage < nt) ring_issue(mbar, buf, a.P, k, r, nstage, jc + it + nstage, t0 + it + nstage);
-      if (h == 0) {
-        T sum = zpart[it & 1][0][w];
-#pragma unroll
-        for (int qq = 1; qq < NCH; ++qq) sum += zpart[it & 1][qq][w];
-        const int i = (t0 + it) * NLSP_TILE + w;
+      if (tid == 0 && it + nstage < nst) ring_issue(mbar, buf, a.P, k, r, nstage, jc + it + nstage, tst + it + nstage);
+      if (g == 0) {
+        const T sum = zpart[it & 1][0][nd] + zpart[it & 1][1][nd] + zpart[it & 1][2][nd] + zpart[it & 1][3][nd];
+        const int i = (tst + it) * NLSP_TILE + nd;
         if (i < n) z[i] += sum;
       }
     }
-    jc += nt;
+    jc += nst;
   };
 
   auto sweep_phase = [&](const T* zin, T* zout) {
@@ -1042,6 +1109,10 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
     put_partial(s, a.part + RED_TRUE * G, sm_d);
     if (sync(PH_OTHER)) trr = grid_total(a.part + RED_TRUE * G, sm_d, bc);
   }
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  if (ntm > 0 && warp == 0) tmem::dealloc(tbase, 512);
   if (cta == 0 && tid == 0) {
     PcgState* st = a.st;
     st->bnorm2 = bb;
@@ -1125,8 +1196,10 @@ nlsp_status ensure_work(nlsp_prec* M, int m) {
     NLSP_CUDA(cudaMemsetAsync(w->vec, 0, sizeof(double) * M->n * 7, ctx->stream));
     NLSP_CUDA(cudaMalloc(&w->rT, (size_t)w->tsize * M->n));
     NLSP_CUDA(cudaMalloc(&w->part, sizeof(double) * 4 * w->max_blocks));
-    NLSP_CUDA(cudaMalloc(&w->counter, sizeof(unsigned) * 4));
-    NLSP_CUDA(cudaMemsetAsync(w->counter, 0, sizeof(unsigned) * 4, ctx->stream));
+    // [0..3]: last-block arrival counters of the graph kernels;
+    // [4], [5]: grid-barrier counter and abort flag of the persistent solver
+    NLSP_CUDA(cudaMalloc(&w->counter, sizeof(unsigned) * 8));
+    NLSP_CUDA(cudaMemsetAsync(w->counter, 0, sizeof(unsigned) * 8, ctx->stream));
     NLSP_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
     const char* pt = getenv("NLSP_PHASE_TIMERS");
     if (pt && pt[0] == '1') {
@@ -1222,8 +1295,8 @@ nlsp_status prepare_stream_kernels() {
   NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 4, 1>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 4, 2>));
   NLSP_TRY(allow_max_smem(k_prolong<T, 1>)); NLSP_TRY(allow_max_smem(k_prolong<T, 2>));
   NLSP_TRY(allow_max_smem(k_prolong<T, 3>)); NLSP_TRY(allow_max_smem(k_prolong<T, 4>));
-  NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 1>)); NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 2>));
-  NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 3>)); NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 4>));
+  NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 8>)); NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 16>));
+  NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 32>));
   done = true;
   return NLSP_OK;
 }
@@ -1417,14 +1490,32 @@ struct Solver {
     const int G = ctx->num_sms;
     const int ntiles = (int)((M->n + NLSP_TILE - 1) / NLSP_TILE);
     const int r = M->r;
+    const int cpg = r <= 32 ? 8 : (r <= 64 ? 16 : 32);
+    const void* fn = cpg == 8 ? (const void*)k_pcg_persistent<KIND, T, 8>
+                   : cpg == 16 ? (const void*)k_pcg_persistent<KIND, T, 16>
+                               : (const void*)k_pcg_persistent<KIND, T, 32>;
+    // residency plan: tensor memory (FP32), then shared memory, then the ring
+    cudaFuncAttributes fa;
+    NLSP_CUDA(cudaFuncGetAttributes(&fa, fn));
+    int dev = 0, optin = 0;
+    NLSP_CUDA(cudaGetDevice(&dev));
+    NLSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const size_t tile = (size_t)r * NLSP_TILE * sizeof(T);
-    const int max_nodes = div_up(ntiles, G) * NLSP_TILE;
-    const size_t rho = (size_t)max_nodes * sizeof(T);
-    const size_t budget = 180 * 1024;
+    const int max_tiles = div_up(ntiles, G);
+    const size_t rho = (size_t)max_tiles * NLSP_TILE * sizeof(T);
+    const int64_t avail = (int64_t)optin - (int64_t)fa.sharedSizeBytes - (int64_t)rho - 1024;
     StreamArgs sa;
-    sa.max_nodes = max_nodes;
-    sa.nstage = (int)std::max<size_t>(1, std::min<size_t>(4, budget > rho + tile ? (budget - rho) / tile : 1));
-    const size_t smem = (size_t)sa.nstage * tile + rho;
+    sa.max_nodes = max_tiles * NLSP_TILE;
+    sa.n_tm = sizeof(T) == 4 ? std::min(max_tiles, 512 / (4 * cpg)) : 0;
+    const int rem = max_tiles - sa.n_tm;
+    sa.nstage = rem > 0 ? 2 : 1;
+    if (avail < (int64_t)(sa.nstage * tile)) sa.nstage = 1;
+    if (avail < (int64_t)tile) {
+      nlsp_record_message("persistent solver: one P tile does not fit in shared memory");
+      return NLSP_ERR_INVALID;
+    }
+    sa.n_sm = rem > 0 ? (int)std::min<int64_t>(rem, (avail - (int64_t)sa.nstage * tile) / (int64_t)tile) : 0;
+    const size_t smem = (size_t)(sa.nstage + sa.n_sm) * tile + rho;
     PersistArgs<T> a;
     a.A64 = M->A->v64;
     a.AT = view_T<T>(M->A);
@@ -1452,17 +1543,11 @@ struct Solver {
     a.Ainv = (const T*)M->AinvT;
     a.part = w->part;
     a.cpart = (T*)M->cpart;
-    a.ctr = w->counter;
-    a.abort = (int*)(w->counter + 1);
+    a.ctr = w->counter + 4;
+    a.abort = (int*)(w->counter + 5);
     a.st = st_out;
     a.sa = sa;
     a.ptimes = w->ptimes;
-    const void* fn;
-    const int nch = (r + 31) / 32;
-    if (nch == 1) fn = (const void*)k_pcg_persistent<KIND, T, 1>;
-    else if (nch == 2) fn = (const void*)k_pcg_persistent<KIND, T, 2>;
-    else if (nch == 3) fn = (const void*)k_pcg_persistent<KIND, T, 3>;
-    else fn = (const void*)k_pcg_persistent<KIND, T, 4>;
     int per_sm = 0;
     NLSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PT, smem));
     if (per_sm < 1) {
@@ -1470,7 +1555,7 @@ struct Solver {
       return NLSP_ERR_INVALID;
     }
     if ((int64_t)RED_COUNT * G > 4 * (int64_t)w->max_blocks || G > M->rblocks) return NLSP_ERR_INVALID;
-    NLSP_CUDA(cudaMemsetAsync(w->counter, 0, sizeof(unsigned) * 2, s));
+    NLSP_CUDA(cudaMemsetAsync(w->counter + 4, 0, sizeof(unsigned) * 2, s));
     void* args[] = {&a};
     NLSP_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PT), args, smem, s));
     count_launches(ctx, 1);

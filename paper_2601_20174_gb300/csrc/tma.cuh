@@ -68,3 +68,81 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 }
 
 }  // namespace tma
+
+// Tensor memory (TMEM, 128 lanes x 512 columns x 32 bit per SM) used as a
+// resident store for P: allocation by one warp, and 32-lane x NC-column
+// stores/loads where warp w of the CTA reaches lanes 32 (w % 4) .. + 31.
+// Each load/store asm waits for its own completion, so the registers are
+// valid (or the data written) when the statement ends.
+namespace tmem {
+
+__device__ __forceinline__ void alloc(unsigned* dst_smem, unsigned ncols) {  // one full warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tma::smem_addr(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void dealloc(unsigned taddr, unsigned ncols) {  // one full warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int NC>
+struct Io;
+
+template <>
+struct Io<8> {
+  __device__ __forceinline__ static void st(unsigned ta, const float (&v)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
+        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+        : "memory");
+  }
+  __device__ __forceinline__ static void ld(unsigned ta, float (&v)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "r"(ta)
+        : "memory");
+  }
+};
+
+template <>
+struct Io<16> {
+  __device__ __forceinline__ static void st(unsigned ta, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
+        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+        "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+        : "memory");
+  }
+  __device__ __forceinline__ static void ld(unsigned ta, float (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
+          "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+        : "r"(ta)
+        : "memory");
+  }
+};
+
+template <>
+struct Io<32> {
+  __device__ __forceinline__ static void st(unsigned ta, const float (&v)[32]) {
+    Io<16>::st(ta, reinterpret_cast<const float(&)[16]>(v[0]));
+    Io<16>::st(ta + 16, reinterpret_cast<const float(&)[16]>(v[16]));
+  }
+  __device__ __forceinline__ static void ld(unsigned ta, float (&v)[32]) {
+    Io<16>::ld(ta, reinterpret_cast<float(&)[16]>(v[0]));
+    Io<16>::ld(ta + 16, reinterpret_cast<float(&)[16]>(v[16]));
+  }
+};
+
+}  // namespace tmem

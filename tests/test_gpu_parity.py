@@ -203,3 +203,30 @@ def test_invalid_arguments_rejected(ctx):
         api.Preconditioner.build(Aop, to_dev(p.S0), p.K + 1, p.s1, 2, p.omega, FP64)  # k > K
     with pytest.raises(api.L.NlspError):
         api.Operator(ctx, 2, 8, 5, -torch.ones(81, dtype=torch.float64).cuda(), 0)  # kappa < 0
+
+
+@pytest.mark.parametrize("case", ["bench512_k64", "iid1024_k32"])
+def test_persistent_solver_large_grids(ctx, case):
+    # Full-size grids: the persistent solver keeps P in tensor memory, shared
+    # memory and a streamed remainder (all three tiers at n = 1024^2, k = 32).
+    # Checked by what holds at any size: the FP64 true residual computed by
+    # the oracle's own operator, and agreement with the graph-driven solver.
+    if case == "bench512_k64":
+        p = gen.grf_diffusion_2d(512, 64, 128, seed=0, tol=1e-8)
+    else:
+        p = gen.iid_diffusion_2d(1024, 32, 64, seed=3, tol=1e-8)
+    A = op.assemble(p)
+    Aop = _api().Operator.from_problem(ctx, p)
+    M = _api().Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, MIXED)
+    b = p.f[:, 0]
+    x2, r2 = M.solve(to_dev(b), tol=p.tol, maxit=5000, graph_mode=2)
+    x1, r1 = M.solve(to_dev(b), tol=p.tol, maxit=5000, graph_mode=1)
+    true2 = np.linalg.norm(b - A @ to_np(x2)) / np.linalg.norm(b)
+    assert r2[0].status == 0 and true2 <= 1e-8 * 1.01, (r2[0], true2)
+    assert abs(r2[0].iterations - r1[0].iterations) <= max(2, r1[0].iterations // 100)
+    assert abs(r2[0].true_relres - true2) <= 1e-3 * true2
+    if case == "bench512_k64":
+        import json, os
+        golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "bench_workloads.json")))
+        it_oracle = golden["grf_diffusion2d_N512_k64_K128_seed0"]["iters"]
+        assert abs(r2[0].iterations - it_oracle) <= 8
