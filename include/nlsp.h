@@ -96,8 +96,13 @@ typedef struct {
   int nu1;
   int nu2;
   double omega;
-  int precision;  /* nlsp_precision */
+  int precision;            /* nlsp_precision */
+  unsigned long long seed;  /* S0 stream seed when no S0 is passed */
 } nlsp_setup_params;
+
+/* Stream number of the random test vectors S0 in the counter-based generator
+   (SplitMix64 counter streams, Box-Muller normals). */
+#define NLSP_STREAM_S0 3
 
 typedef struct {
   double tol;     /* stop when ||r||_2 <= tol ||b||_2 (recursive residual)  */
@@ -180,7 +185,10 @@ NLSP_API nlsp_status nlsp_smooth_samples(nlsp_ctx* ctx, const nlsp_op* A, int K,
                                 int precision, const double* dev_S0, double* dev_S);
 
 /* Builds a preconditioner for A from the random test vectors dev_S0 (n x K,
-   column-major, ld = n, read during the call): smooths them s1 times, takes
+   column-major, ld = n, read during the call; NULL: drawn on the device as
+   N(0,1) from the counter-based generator of nlsp_random_normal with
+   params->seed and stream NLSP_STREAM_S0, element (i, c) being normal number
+   c n + i): smooths them s1 times, takes
    the leading k left singular vectors of S as P (thin SVD via the Gram
    matrix S^T S, a Jacobi eigensolver and, in FP64, iterative refinement),
    then forms and factors A_c = P^T A P for the full rank k (call
@@ -199,6 +207,17 @@ NLSP_API nlsp_status nlsp_build_prolongation(nlsp_ctx* ctx, const nlsp_op* A, co
    Synchronises.  Errors as nlsp_build_prolongation. */
 NLSP_API nlsp_status nlsp_prec_from_basis(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* params,
                                  const double* dev_P, int k, nlsp_prec** M_out);
+
+/* Draws normals offset .. offset + count - 1 of a counter-based stream into
+   dev_out (FP64): the i-th uniform of stream s under seed q is the top 53
+   bits of SplitMix64 output i + 1 started at base(q, s) =
+   fin(q ^ s * 0xD1B54A32D192ED03 + 0x9E3779B97F4A7C15) (fin = the SplitMix64
+   finaliser); normals 2j, 2j+1 are sqrt(-2 log(1 - u_2j)) * (cos, sin)(2 pi
+   u_2j+1) (Box-Muller).  This is the definition the host-side input
+   generator implements; the random test vectors S0 of Sec. 3 come from it.
+   Errors: NLSP_ERR_INVALID. */
+NLSP_API nlsp_status nlsp_random_normal(nlsp_ctx* ctx, unsigned long long seed, unsigned long long stream,
+                                        unsigned long long offset, int64_t count, double* dev_out);
 
 /* Truncates the coarse space to its first r columns (Algorithm 1 setup:
    P_r = P[:, 1:r], A_c = P_r^T A P_r) and factors A_c = L L^T in FP64.
@@ -266,6 +285,39 @@ NLSP_API nlsp_status nlsp_apply_prec_noalloc(nlsp_ctx* ctx, const nlsp_prec* M, 
 NLSP_API nlsp_status nlsp_solve(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec* M, int m, const double* dev_B,
                        int64_t ldb, double* dev_X, int64_t ldx, const nlsp_solve_params* params,
                        nlsp_solve_info* infos);
+
+/* Batched solve: instance i solves A_i x_i = b_i by PCG with its own
+   preconditioner M[i] (Sec. 4 per instance; the paper solves its instances
+   one after another and has no batched counterpart).  One cooperative launch
+   of the persistent solver runs every instance on a team of consecutive
+   CTAs (one CTA per SM); the team plan is the one nlsp_plan_teams returns
+   for the instances' node counts, tiles_per_cta and the device's SM count.
+   M: host array of `count` distinct preconditioners of this context, all
+   of one stencil kind and one precision.  dev_b, dev_x: host arrays of
+   `count` device pointers to FP64 vectors of length n_i; x0 = 0 and x_i is
+   output only (must not be b_i).  params: tol, maxit and flexible as in
+   nlsp_solve (graph_mode is ignored).  tiles_per_cta: target number of
+   128-node tiles per CTA of a team (0: 16).  infos: host array of `count`
+   entries (may be NULL).  Synchronises.  A team barrier that waits longer
+   than 2 s ends its instance with NLSP_ERR_TIMEOUT.  Returns as nlsp_solve
+   (the worst per-instance status), or NLSP_ERR_INVALID, NLSP_ERR_CUDA,
+   NLSP_ERR_OOM. */
+NLSP_API nlsp_status nlsp_solve_batched(nlsp_ctx* ctx, int count, nlsp_prec* const* M, const double* const* dev_b,
+                                        double* const* dev_x, const nlsp_solve_params* params, int tiles_per_cta,
+                                        nlsp_solve_info* infos);
+
+/* The batched solver's team plan (host computation only, no device work).
+   Instance i of n[i] nodes (n[i] >= 1) gets team_size[i] =
+   clamp(ceil(ceil(n[i] / 128) / tiles_per_cta), 1, min(num_ctas,
+   ceil(n[i] / 128))) consecutive CTAs starting at first_cta[i]; start[i] is
+   its planned start time in a tile-iteration cost model.  Teams are placed
+   largest estimated area first, each in the window of CTAs that frees
+   earliest.  Each CTA runs its instances in (start, instance) order, which
+   is the same order for every CTA of a team; that is what makes the
+   launch free of deadlock.  tiles_per_cta = 0 means 16.  Output arrays
+   hold `count` entries.  Errors: NLSP_ERR_INVALID. */
+NLSP_API nlsp_status nlsp_plan_teams(int count, const int64_t* n, int num_ctas, int tiles_per_cta, int* first_cta,
+                                     int* team_size, double* start);
 
 /* ---------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper).

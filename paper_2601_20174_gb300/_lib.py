@@ -30,7 +30,10 @@ NLSP_COEF_CONST_TENSOR = 1
 
 class SetupParams(C.Structure):
     _fields_ = [("K", C.c_int), ("k", C.c_int), ("s1", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
-                ("omega", C.c_double), ("precision", C.c_int)]
+                ("omega", C.c_double), ("precision", C.c_int), ("seed", C.c_ulonglong)]
+
+
+NLSP_STREAM_S0 = 3
 
 
 class SolveParams(C.Structure):
@@ -73,7 +76,11 @@ SIGNATURES = {
     "nlsp_launch_count": (C.c_ulonglong, [vp]),
     "nlsp_apply_prec_noalloc": (ci, [vp, vp, ci, vp, i64, vp, i64]),
     "nlsp_prec_phase_times": (ci, [vp, vp, C.POINTER(C.c_double), ci]),
+    "nlsp_random_normal": (ci, [vp, C.c_ulonglong, C.c_ulonglong, C.c_ulonglong, i64, vp]),
     "nlsp_bench_kernel": (ci, [vp, vp, ci, ci]),
+    "nlsp_solve_batched": (ci, [vp, ci, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveParams), ci,
+                                C.POINTER(SolveInfo)]),
+    "nlsp_plan_teams": (ci, [ci, C.POINTER(i64), ci, ci, C.POINTER(ci), C.POINTER(ci), C.POINTER(cd)]),
 }
 
 _lib = None

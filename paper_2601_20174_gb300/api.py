@@ -137,16 +137,25 @@ class Preconditioner:
         self.r = r.value
 
     @staticmethod
-    def _params(k, K, s1, nu, omega, precision):
-        return L.SetupParams(K=K, k=k, s1=s1, nu1=nu, nu2=nu, omega=omega, precision=precision)
+    def _params(k, K, s1, nu, omega, precision, seed=0):
+        return L.SetupParams(K=K, k=k, s1=s1, nu1=nu, nu2=nu, omega=omega, precision=precision, seed=seed)
 
     @classmethod
-    def build(cls, op: Operator, S0: torch.Tensor, k: int, s1: int = 20, nu: int = 2, omega: float = 2.0 / 3.0,
-              precision: int = L.NLSP_FP64) -> "Preconditioner":
-        store, K = _colmajor(S0, op.n)
-        p = cls._params(k, K, s1, nu, omega, precision)
+    def build(cls, op: Operator, S0: torch.Tensor | None, k: int, s1: int = 20, nu: int = 2,
+              omega: float = 2.0 / 3.0, precision: int = L.NLSP_FP64, K: int | None = None,
+              seed: int = 0) -> "Preconditioner":
+        """S0: n x K random test vectors, or None to draw them on the device
+        (K columns, counter-based generator under `seed`)."""
+        if S0 is None:
+            if K is None:
+                raise ValueError("K is required when S0 is drawn on the device")
+            store, ptr = None, C.c_void_p(0)
+        else:
+            store, K = _colmajor(S0, op.n)
+            ptr = _ptr(store)
+        p = cls._params(k, K, s1, nu, omega, precision, seed)
         h = C.c_void_p()
-        L.check(op.ctx._lib.nlsp_build_prolongation(op.ctx.h, op.h, C.byref(p), _ptr(store), C.byref(h)),
+        L.check(op.ctx._lib.nlsp_build_prolongation(op.ctx.h, op.h, C.byref(p), ptr, C.byref(h)),
                 "nlsp_build_prolongation")
         return cls(op, h)
 
@@ -211,3 +220,44 @@ class Preconditioner:
             self.close()
         except Exception:
             pass
+
+
+def solve_batched(precs: list[Preconditioner], bs: list[torch.Tensor], tol: float = 1e-8, maxit: int = 2000,
+                  flexible: int = -1, tiles_per_cta: int = 0):
+    """Solves A_i x_i = b_i for every instance in one launch of the persistent
+    solver (nlsp_solve_batched).  precs: distinct preconditioners of one
+    context, one stencil kind and one precision; bs: float64 CUDA vectors of
+    length n_i.  Returns ([x_i], [SolveResult per instance])."""
+    count = len(precs)
+    if len(bs) != count:
+        raise ValueError("one right-hand side per preconditioner")
+    if count == 0:
+        return [], []
+    ctx = precs[0].ctx
+    bvec = [b.contiguous() for b in bs]
+    for M, b in zip(precs, bvec):
+        if b.dtype != torch.float64 or not b.is_cuda or b.dim() != 1 or b.shape[0] != M.n:
+            raise ValueError("each b_i must be a float64 CUDA vector of length n_i")
+    xs = [torch.empty_like(b) for b in bvec]
+    hp = (C.c_void_p * count)(*[M.h.value for M in precs])
+    hb = (C.c_void_p * count)(*[b.data_ptr() for b in bvec])
+    hx = (C.c_void_p * count)(*[x.data_ptr() for x in xs])
+    infos = (L.SolveInfo * count)()
+    prm = L.SolveParams(tol=tol, maxit=maxit, flexible=flexible, graph_mode=2)
+    st = ctx._lib.nlsp_solve_batched(ctx.h, count, hp, hb, hx, C.byref(prm), tiles_per_cta, infos)
+    L.check(st, "nlsp_solve_batched", allow=(L.NLSP_OK, L.NLSP_NOT_CONVERGED, L.NLSP_ERR_BREAKDOWN))
+    return xs, [SolveResult(i.iterations, i.status, i.relres, i.true_relres) for i in infos]
+
+
+def plan_teams(n: list[int], num_ctas: int, tiles_per_cta: int = 0):
+    """The batched solver's team plan for instances of n[i] nodes
+    (nlsp_plan_teams; host computation).  Returns (first_cta, team_size,
+    start) lists."""
+    lib = L.load()
+    count = len(n)
+    hn = (C.c_int64 * count)(*n)
+    first = (C.c_int * count)()
+    size = (C.c_int * count)()
+    start = (C.c_double * count)()
+    L.check(lib.nlsp_plan_teams(count, hn, num_ctas, tiles_per_cta, first, size, start), "nlsp_plan_teams")
+    return list(first), list(size), list(start)

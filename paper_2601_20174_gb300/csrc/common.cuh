@@ -77,7 +77,7 @@ struct StencilView {
 // temporaries are carved from them, so repeated calls allocate nothing once
 // the slots have grown to the working size.  Valid until the next call that
 // uses the same slot on this context.
-enum ScratchSlot { SLOT_SA = 0, SLOT_SB, SLOT_PART, SLOT_SMALL, SLOT_PNEW, SLOT_COUNT };
+enum ScratchSlot { SLOT_SA = 0, SLOT_SB, SLOT_PART, SLOT_SMALL, SLOT_PNEW, SLOT_BATCH, SLOT_COUNT };
 
 struct nlsp_ctx {
   int device;
@@ -194,3 +194,4 @@ __device__ __forceinline__ double block_sum_partials(const double* part, int cou
 template <typename T> __device__ __forceinline__ T ld_cg(const T* p) { return *p; }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }

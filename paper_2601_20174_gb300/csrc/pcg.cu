@@ -25,6 +25,7 @@
 // order by the last block to arrive.  The loop runs as a CUDA graph whose
 // while node is driven by the post kernel, so a solve needs no host round
 // trip until it finishes.
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -637,15 +638,15 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// Grid-wide barrier (all CTAs are co-resident: cooperative launch).  The
-// arrival counter grows monotonically, barrier number `gen` waits for
-// gen * gridDim.x arrivals.  A wait longer than 2 s, or one that sees the
+// Barrier over the `team` CTAs working on one instance (all CTAs of the
+// launch are co-resident: cooperative launch).  The arrival counter grows
+// monotonically, barrier number `gen` waits for gen * team arrivals.  A wait longer than 2 s, or one that sees the
 // abort flag, gives up and returns false in every thread of the CTA.
-__device__ __forceinline__ bool grid_sync(unsigned* ctr, int* abort, unsigned& gen, int* ok_s) {
+__device__ __forceinline__ bool grid_sync(unsigned* ctr, int* abort, unsigned& gen, int* ok_s, int team) {
   ++gen;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned target = gen * gridDim.x;
+    const unsigned target = gen * (unsigned)team;
     int ok = 1;
     __threadfence();
     atomicAdd(ctr, 1u);
@@ -671,10 +672,10 @@ __device__ __forceinline__ bool grid_sync(unsigned* ctr, int* abort, unsigned& g
 
 // Sum of the grid's partials of one dot product, in CTA order (same value in
 // every CTA).  Result valid in all threads.
-__device__ __forceinline__ double grid_total(const double* part, double* sm_d, double* bc) {
+__device__ __forceinline__ double grid_total(const double* part, double* sm_d, double* bc, int team) {
   double s = 0.0;
   if (threadIdx.x < 32) {
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += 32) s += __ldcg(part + c);
+    for (int c = threadIdx.x; c < team; c += 32) s += __ldcg(part + c);
     s = warp_sum(s);
     if (threadIdx.x == 0) *bc = s;
   }
@@ -684,9 +685,9 @@ __device__ __forceinline__ double grid_total(const double* part, double* sm_d, d
   return v;
 }
 
-__device__ __forceinline__ void put_partial(double s, double* part, double* sm_d) {
+__device__ __forceinline__ void put_partial(double s, double* part, double* sm_d, int rank) {
   s = block_sum_lean(s, sm_d);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (threadIdx.x == 0) part[rank] = s;
 }
 
 // Streams the CTA's P tiles through the ring: copy number j (running over the
@@ -709,9 +710,9 @@ __device__ __forceinline__ bool ring_wait(uint64_t* bar, int nstage, unsigned j)
 // n_sm in shared memory, both loaded once per solve; only the rest is
 // streamed through the TMA ring in every restriction and prolongation.
 template <int KIND, typename T, int CPG>
-__global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t mbar[8];
+__device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const int cta, const int G,
+                                               const unsigned tbase_all, uint64_t* mbar,
+                                               unsigned char* smem_raw) {
   __shared__ double sm_d[PT];
   __shared__ T red_t[PT];
   __shared__ T sacc[PT / 32][32];
@@ -720,11 +721,10 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
   __shared__ T zpart[2][4][NLSP_TILE];
   __shared__ double bc[2];
   __shared__ int ok_s, abort_s;
-  __shared__ unsigned tbase_s;
 
   constexpr bool FP32 = sizeof(T) == 4;
   constexpr int RPAD = 4 * CPG;
-  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int n = (int)a.AT.n, N = a.AT.N;
   const int ntiles = (n + NLSP_TILE - 1) / NLSP_TILE;
   const int t0 = (int)((int64_t)ntiles * cta / G);
@@ -744,17 +744,20 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
   bool ok = true;
   (void)N;
 
+  // the ring's barriers are re-initialised for every instance (all copies of
+  // the previous instance have been consumed)
+  __syncthreads();
   if (tid == 0) {
     abort_s = 0;
-    for (int s = 0; s < nstage; ++s) tma::mbar_init(&mbar[s], 1);
+    for (int s = 0; s < nstage; ++s) {
+      tma::mbar_inval(&mbar[s]);
+      tma::mbar_init(&mbar[s], 1);
+    }
     tma::fence_barrier_init();
   }
-  if (ntm > 0 && warp == 0) tmem::alloc(&tbase_s, 512);
-  tmem::fence_before_sync();
   __syncthreads();
-  tmem::fence_after_sync();
   const unsigned tlane = (unsigned)(32 * q) << 16;
-  const unsigned tbase = ntm > 0 ? tbase_s : 0u;
+  const unsigned tbase = ntm > 0 ? tbase_all : 0u;
   // one-time loads of the resident tiles
   for (int ti = 0; ti < ntm; ++ti) {
     float v[CPG];
@@ -777,7 +780,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
   auto sync = [&](int phase) -> bool {
     const bool timed = a.ptimes && cta == 0 && tid == 0;
     const unsigned long long t_arr = timed ? tma::now_ns() : 0ull;
-    ok = ok && grid_sync(a.ctr, a.abort, gen, &ok_s);
+    ok = ok && grid_sync(a.ctr, a.abort, gen, &ok_s, G);
     if (timed) {
       const unsigned long long t_rel = tma::now_ns();
       a.ptimes[2 * phase] += t_arr - t_last;
@@ -1004,8 +1007,8 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
       s_rz = fma(ri, zd, s_rz);
       if (flex) s_ro = fma(ri, zold64[i], s_ro);
     }
-    put_partial(s_rz, a.part + RED_RZ * G, sm_d);
-    if (flex) put_partial(s_ro, a.part + RED_RO * G, sm_d);
+    put_partial(s_rz, a.part + RED_RZ * G, sm_d, cta);
+    if (flex) put_partial(s_ro, a.part + RED_RO * G, sm_d, cta);
     return sync(PH_POST);
   };
 
@@ -1023,11 +1026,11 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
       a.p1[i] = 0.0;
       s = fma(bi, bi, s);
     }
-    put_partial(s, a.part + RED_BB * G, sm_d);
+    put_partial(s, a.part + RED_BB * G, sm_d, cta);
   }
   bool done = false;
   if (sync(PH_OTHER)) {
-    bb = grid_total(a.part + RED_BB * G, sm_d, bc);
+    bb = grid_total(a.part + RED_BB * G, sm_d, bc, G);
     tol2bn = a.tol * a.tol * bb;
     rr = bb;
     if (bb == 0.0) done = true;
@@ -1040,7 +1043,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
   // initial preconditioner application z_0 = B r_0
   if (!done) {
     if (apply(a.z0, a.z1, false)) {
-      rz = grid_total(a.part + RED_RZ * G, sm_d, bc);
+      rz = grid_total(a.part + RED_RZ * G, sm_d, bc, G);
       if (!(rz > 0.0) || !isfinite(rz)) { status = (int)NLSP_ERR_BREAKDOWN; done = true; }
     } else {
       done = true;
@@ -1063,10 +1066,10 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
         a.q[i] = qi;
         s = fma(pi, qi, s);
       }
-      put_partial(s, a.part + RED_PQ * G, sm_d);
+      put_partial(s, a.part + RED_PQ * G, sm_d, cta);
     }
     if (!sync(PH_SPMV)) break;
-    const double pq = grid_total(a.part + RED_PQ * G, sm_d, bc);
+    const double pq = grid_total(a.part + RED_PQ * G, sm_d, bc, G);
     iter = t + 1;
     if (!(pq > 0.0) || !isfinite(pq)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
     const double alpha = rz / pq;
@@ -1079,18 +1082,18 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
         if (FP32) a.rT[i] = (T)ri;
         s = fma(ri, ri, s);
       }
-      put_partial(s, a.part + RED_RR * G, sm_d);
+      put_partial(s, a.part + RED_RR * G, sm_d, cta);
     }
     if (!sync(PH_PRE)) break;
-    rr = grid_total(a.part + RED_RR * G, sm_d, bc);
+    rr = grid_total(a.part + RED_RR * G, sm_d, bc, G);
     if (!isfinite(rr)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
     if (rr <= tol2bn) break;  // converged
     double* zn = (iter & 1) ? a.z1 : a.z0;
     const double* zo = (iter & 1) ? a.z0 : a.z1;
     const bool flex = a.flexible != 0;
     if (!apply(zn, zo, flex)) break;
-    const double rzn = grid_total(a.part + RED_RZ * G, sm_d, bc);
-    const double ro = flex ? grid_total(a.part + RED_RO * G, sm_d, bc) : 0.0;
+    const double rzn = grid_total(a.part + RED_RZ * G, sm_d, bc, G);
+    const double ro = flex ? grid_total(a.part + RED_RO * G, sm_d, bc, G) : 0.0;
     if (!(rzn > 0.0) || !isfinite(rzn)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
     beta = (rzn - ro) / rz;
     rz = rzn;
@@ -1106,13 +1109,12 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
       const double ri = a.b[i] - stencil_apply<KIND>(a.A64, i, c, [&](int64_t m) { return __ldcg(a.x + m); });
       s = fma(ri, ri, s);
     }
-    put_partial(s, a.part + RED_TRUE * G, sm_d);
-    if (sync(PH_OTHER)) trr = grid_total(a.part + RED_TRUE * G, sm_d, bc);
+    put_partial(s, a.part + RED_TRUE * G, sm_d, cta);
+    if (sync(PH_OTHER)) trr = grid_total(a.part + RED_TRUE * G, sm_d, bc, G);
   }
   tmem::fence_before_sync();
   __syncthreads();
   tmem::fence_after_sync();
-  if (ntm > 0 && warp == 0) tmem::dealloc(tbase, 512);
   if (cta == 0 && tid == 0) {
     PcgState* st = a.st;
     st->bnorm2 = bb;
@@ -1126,6 +1128,56 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> a) {
     st->maxit = a.maxit;
     st->flexible = a.flexible;
   }
+  const bool ring_ok = abort_s == 0;
+  __syncthreads();
+  return ring_ok;
+}
+
+// One task of a CTA: instance `inst`, as CTA `rank` of a team of `size`.
+struct TeamTask {
+  int inst, rank, size, pad;
+};
+
+// The persistent solver kernel.  Without a task table (task_begin == null)
+// all CTAs of the launch solve instance `one` together.  Otherwise every CTA
+// works through its own list of tasks tasks[task_begin[cta] ..
+// task_begin[cta + 1]), which the host orders by planned start time (ties by
+// instance): the CTAs of one team meet their shared instances in the same
+// order, so no team waits on a CTA that waits on it.  A CTA whose copy ring
+// failed (a TMA wait that gave up) leaves its remaining tasks; their teams'
+// barrier waits then end at the time limit with a timeout status.  Tensor
+// memory is allocated once per CTA for the whole launch.
+template <int KIND, typename T, int CPG>
+__global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> one, const PersistArgs<T>* __restrict__ insts,
+                                                         const int* __restrict__ task_begin,
+                                                         const TeamTask* __restrict__ tasks, int use_tmem) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar[8];
+  __shared__ unsigned tbase_s;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0)
+    for (int s = 0; s < 8; ++s) tma::mbar_init(&mbar[s], 1);
+  if (use_tmem && warp == 0) tmem::alloc(&tbase_s, 512);
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  const unsigned tbase = use_tmem ? tbase_s : 0u;
+  // the instance's arguments are staged in shared memory (the single-
+  // instance launch passes them as a kernel parameter)
+  __shared__ __align__(16) PersistArgs<T> args_s;
+  const bool table = task_begin != nullptr;
+  const int tb = table ? task_begin[blockIdx.x] : 0, te = table ? task_begin[blockIdx.x + 1] : 1;
+  for (int t = tb; t < te; ++t) {
+    const TeamTask task = table ? tasks[t] : TeamTask{0, (int)blockIdx.x, (int)gridDim.x, 0};
+    __syncthreads();  // the previous instance is done with args_s
+    if (threadIdx.x == 0) args_s = table ? insts[task.inst] : one;
+    __syncthreads();
+    if (!solve_instance<KIND, T, CPG>(args_s, task.rank, task.size, tbase, mbar, smem_raw)) break;
+  }
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  if (use_tmem && warp == 0) tmem::dealloc(tbase, 512);
 }
 
 }  // namespace
@@ -1394,6 +1446,58 @@ nlsp_status enqueue_prec(const nlsp_prec* M, const PrecWork& pw, cudaStream_t s,
   return NLSP_OK;
 }
 
+// Team plan of a batched solve (host only).  Instance i of n[i] nodes gets a
+// team of size[i] consecutive CTAs starting at first[i]: ceil(tiles_i /
+// tiles_per_cta) CTAs, between 1 and min(num_ctas, tiles_i, cap[i]).  The
+// teams are placed greedily, largest estimated area (duration x size) first,
+// each in the window of CTAs that frees earliest (ties: least idle time, then
+// lowest CTA).  The duration model counts tile-iterations: sqrt(n_i)
+// iterations (PCG iteration counts grow with the grid side), each costing the
+// team's largest tile share plus 1.5 tiles of barrier time when the team has
+// more than one CTA.  start[i] is the planned start in those units; each
+// CTA later runs its tasks in (start, instance) order.
+nlsp_status nlsp_internal_plan_teams(int count, const int64_t* n, const int* cap, int G, int tiles_per_cta,
+                                     int* first, int* size, double* start) {
+  if (count < 0 || G < 1 || tiles_per_cta < 0 || (count > 0 && (!n || !first || !size || !start)))
+    return NLSP_ERR_INVALID;
+  if (tiles_per_cta == 0) tiles_per_cta = 16;
+  std::vector<double> dur(count);
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 1) return NLSP_ERR_INVALID;
+    const int64_t tiles = (n[i] + NLSP_TILE - 1) / NLSP_TILE;
+    int64_t hi = std::min<int64_t>(G, tiles);
+    if (cap) hi = std::min<int64_t>(hi, std::max(1, cap[i]));
+    const int s = (int)std::max<int64_t>(1, std::min<int64_t>(hi, (tiles + tiles_per_cta - 1) / tiles_per_cta));
+    size[i] = s;
+    const double share = (double)((tiles + s - 1) / s);
+    dur[i] = std::sqrt((double)n[i]) * (share + (s > 1 ? 1.5 : 0.0));
+  }
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return dur[a] * size[a] > dur[b] * size[b]; });
+  std::vector<double> freeat(G, 0.0);
+  for (int i : order) {
+    const int s = size[i];
+    int best_w = 0;
+    double best_st = 0.0, best_idle = 0.0;
+    for (int w = 0; w + s <= G; ++w) {
+      double st = 0.0, idle = 0.0;
+      for (int c = w; c < w + s; ++c) st = std::max(st, freeat[c]);
+      for (int c = w; c < w + s; ++c) idle += st - freeat[c];
+      if (w == 0 || st < best_st || (st == best_st && idle < best_idle)) {
+        best_w = w;
+        best_st = st;
+        best_idle = idle;
+      }
+    }
+    first[i] = best_w;
+    start[i] = best_st;
+    for (int c = best_w; c < best_w + s; ++c) freeat[c] = best_st + dur[i];
+  }
+  return NLSP_OK;
+}
+
 template <int KIND, typename T>
 struct Solver {
   static double* x(PcgWork* w) { return w->vec; }
@@ -1481,41 +1585,56 @@ struct Solver {
     return NLSP_OK;
   }
 
-  // The persistent cooperative solver (graph_mode 2): one launch per column.
-  static nlsp_status launch_persistent(nlsp_prec* M, const double* b, double* xout, const nlsp_solve_params* prm,
-                                       int flexible, PcgState* st_out) {
-    nlsp_ctx* ctx = M->ctx;
-    PcgWork* w = M->pcg;
-    cudaStream_t s = ctx->stream;
-    const int G = ctx->num_sms;
-    const int ntiles = (int)((M->n + NLSP_TILE - 1) / NLSP_TILE);
-    const int r = M->r;
-    const int cpg = r <= 32 ? 8 : (r <= 64 ? 16 : 32);
-    const void* fn = cpg == 8 ? (const void*)k_pcg_persistent<KIND, T, 8>
-                   : cpg == 16 ? (const void*)k_pcg_persistent<KIND, T, 16>
-                               : (const void*)k_pcg_persistent<KIND, T, 32>;
-    // residency plan: tensor memory (FP32), then shared memory, then the ring
+  static int cpg_for(int r) { return r <= 32 ? 8 : (r <= 64 ? 16 : 32); }
+  static const void* persistent_fn(int cpg) {
+    return cpg == 8 ? (const void*)k_pcg_persistent<KIND, T, 8>
+         : cpg == 16 ? (const void*)k_pcg_persistent<KIND, T, 16>
+                     : (const void*)k_pcg_persistent<KIND, T, 32>;
+  }
+
+  // Dynamic shared memory the persistent kernel may use beside its static
+  // shared memory (one CTA per SM).
+  static nlsp_status persistent_smem(int cpg, size_t* smem) {
     cudaFuncAttributes fa;
-    NLSP_CUDA(cudaFuncGetAttributes(&fa, fn));
+    NLSP_CUDA(cudaFuncGetAttributes(&fa, persistent_fn(cpg)));
     int dev = 0, optin = 0;
     NLSP_CUDA(cudaGetDevice(&dev));
     NLSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t tile = (size_t)r * NLSP_TILE * sizeof(T);
-    const int max_tiles = div_up(ntiles, G);
+    *smem = (size_t)std::max<int64_t>(0, (int64_t)optin - (int64_t)fa.sharedSizeBytes - 1024);
+    return NLSP_OK;
+  }
+
+  // Residency plan of one instance solved by `team` CTAs with `avail` bytes
+  // of dynamic shared memory: the first tiles of each CTA in tensor memory
+  // (FP32), the next ones resident in shared memory, the rest streamed
+  // through a TMA ring.  *need = the dynamic shared memory the plan uses.
+  static nlsp_status plan_instance(const nlsp_prec* M, int team, int cpg, bool tmem_ok, size_t avail,
+                                   StreamArgs* sa, size_t* need) {
+    const int ntiles = (int)((M->n + NLSP_TILE - 1) / NLSP_TILE);
+    const size_t tile = (size_t)M->r * NLSP_TILE * sizeof(T);
+    const int max_tiles = div_up(ntiles, team);
     const size_t rho = (size_t)max_tiles * NLSP_TILE * sizeof(T);
-    const int64_t avail = (int64_t)optin - (int64_t)fa.sharedSizeBytes - (int64_t)rho - 1024;
-    StreamArgs sa;
-    sa.max_nodes = max_tiles * NLSP_TILE;
-    sa.n_tm = sizeof(T) == 4 ? std::min(max_tiles, 512 / (4 * cpg)) : 0;
-    const int rem = max_tiles - sa.n_tm;
-    sa.nstage = rem > 0 ? 2 : 1;
-    if (avail < (int64_t)(sa.nstage * tile)) sa.nstage = 1;
-    if (avail < (int64_t)tile) {
+    const int64_t left = (int64_t)avail - (int64_t)rho;
+    sa->max_nodes = max_tiles * NLSP_TILE;
+    sa->n_tm = (sizeof(T) == 4 && tmem_ok) ? std::min(max_tiles, 512 / (4 * cpg)) : 0;
+    const int rem = max_tiles - sa->n_tm;
+    sa->nstage = rem > 0 ? 2 : 1;
+    if (left < (int64_t)(sa->nstage * tile)) sa->nstage = 1;
+    if (left < (int64_t)tile) {
       nlsp_record_message("persistent solver: one P tile does not fit in shared memory");
       return NLSP_ERR_INVALID;
     }
-    sa.n_sm = rem > 0 ? (int)std::min<int64_t>(rem, (avail - (int64_t)sa.nstage * tile) / (int64_t)tile) : 0;
-    const size_t smem = (size_t)(sa.nstage + sa.n_sm) * tile + rho;
+    sa->n_sm = rem > 0 ? (int)std::min<int64_t>(rem, (left - (int64_t)sa->nstage * tile) / (int64_t)tile) : 0;
+    *need = (size_t)(sa->nstage + sa->n_sm) * tile + rho;
+    return NLSP_OK;
+  }
+
+  // Kernel arguments of one instance: right-hand side b, iterate x (may be
+  // the caller's output: it is set to zero first), state st, barrier counter
+  // and abort flag ctr[0], ctr[1].
+  static PersistArgs<T> instance_args(nlsp_prec* M, const double* b, double* x_, const nlsp_solve_params* prm,
+                                      int flexible, PcgState* st_out, unsigned* ctr, const StreamArgs& sa) {
+    PcgWork* w = M->pcg;
     PersistArgs<T> a;
     a.A64 = M->A->v64;
     a.AT = view_T<T>(M->A);
@@ -1526,7 +1645,7 @@ struct Solver {
     a.maxit = prm->maxit;
     a.tol = prm->tol;
     a.b = b;
-    a.x = x(w);
+    a.x = x_;
     a.r = r_(w);
     a.q = q(w);
     Pair<double> P2 = Ppair(w), Z2 = Zpair(w);
@@ -1539,15 +1658,33 @@ struct Solver {
     a.zw2 = (T*)M->w1;
     a.P = (const T*)M->P;
     a.k = M->k;
-    a.rr_ = r;
+    a.rr_ = M->r;
     a.Ainv = (const T*)M->AinvT;
     a.part = w->part;
     a.cpart = (T*)M->cpart;
-    a.ctr = w->counter + 4;
-    a.abort = (int*)(w->counter + 5);
+    a.ctr = ctr;
+    a.abort = (int*)(ctr + 1);
     a.st = st_out;
     a.sa = sa;
     a.ptimes = w->ptimes;
+    return a;
+  }
+
+  // The persistent cooperative solver (graph_mode 2): one launch per column,
+  // all CTAs on the one instance.
+  static nlsp_status launch_persistent(nlsp_prec* M, const double* b, double* xout, const nlsp_solve_params* prm,
+                                       int flexible, PcgState* st_out) {
+    nlsp_ctx* ctx = M->ctx;
+    PcgWork* w = M->pcg;
+    cudaStream_t s = ctx->stream;
+    const int G = ctx->num_sms;
+    const int cpg = cpg_for(M->r);
+    const void* fn = persistent_fn(cpg);
+    size_t avail = 0, smem = 0;
+    NLSP_TRY(persistent_smem(cpg, &avail));
+    StreamArgs sa;
+    NLSP_TRY(plan_instance(M, G, cpg, true, avail, &sa, &smem));
+    PersistArgs<T> a = instance_args(M, b, x(w), prm, flexible, st_out, w->counter + 4, sa);
     int per_sm = 0;
     NLSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PT, smem));
     if (per_sm < 1) {
@@ -1556,7 +1693,11 @@ struct Solver {
     }
     if ((int64_t)RED_COUNT * G > 4 * (int64_t)w->max_blocks || G > M->rblocks) return NLSP_ERR_INVALID;
     NLSP_CUDA(cudaMemsetAsync(w->counter + 4, 0, sizeof(unsigned) * 2, s));
-    void* args[] = {&a};
+    const PersistArgs<T>* no_insts = nullptr;
+    const int* no_begin = nullptr;
+    const TeamTask* no_tasks = nullptr;
+    int use_tmem = sa.n_tm > 0 ? 1 : 0;
+    void* args[] = {&a, &no_insts, &no_begin, &no_tasks, &use_tmem};
     NLSP_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PT), args, smem, s));
     count_launches(ctx, 1);
     NLSP_CUDA(cudaMemcpyAsync(xout, x(w), sizeof(double) * M->n, cudaMemcpyDeviceToDevice, s));
@@ -1618,10 +1759,101 @@ struct Solver {
     return summarize(w, m, infos, 0);
   }
 
+  // Batched persistent solve: instance i solves A_i x_i = b_i with its own
+  // preconditioner Ms[i]; one cooperative launch runs every instance on a
+  // team of CTAs planned by nlsp_internal_plan_teams.
+  static nlsp_status solve_batched(nlsp_ctx* ctx, int count, nlsp_prec* const* Ms, const double* const* B,
+                                   double* const* X, const nlsp_solve_params* prm, int tiles_per_cta,
+                                   nlsp_solve_info* infos) {
+    cudaStream_t s = ctx->stream;
+    const int G = ctx->num_sms;
+    NLSP_TRY((prepare_stream_kernels<KIND, T>()));
+    int rmax = 1;
+    std::vector<int64_t> nn(count);
+    std::vector<int> cap(count);
+    for (int i = 0; i < count; ++i) {
+      NLSP_TRY(ensure_work(Ms[i], 1));
+      rmax = std::max(rmax, Ms[i]->r);
+      nn[i] = Ms[i]->n;
+      // a team may not exceed the partial arrays of the instance's work
+      cap[i] = (int)std::min<int64_t>(Ms[i]->rblocks, 4 * (int64_t)Ms[i]->pcg->max_blocks / RED_COUNT);
+    }
+    const int cpg = cpg_for(rmax);
+    const void* fn = persistent_fn(cpg);
+    size_t avail = 0;
+    NLSP_TRY(persistent_smem(cpg, &avail));
+    std::vector<int> first(count), size(count);
+    std::vector<double> start(count);
+    NLSP_TRY(nlsp_internal_plan_teams(count, nn.data(), cap.data(), G, tiles_per_cta, first.data(), size.data(),
+                                      start.data()));
+    // device table: instances, CTA task ranges, tasks, barrier words, states
+    std::vector<std::vector<TeamTask>> per(G);
+    std::vector<std::pair<double, int>> key(count);
+    for (int i = 0; i < count; ++i) key[i] = {start[i], i};
+    std::sort(key.begin(), key.end());
+    for (const auto& kv : key) {
+      const int i = kv.second;
+      for (int c = 0; c < size[i]; ++c) per[first[i] + c].push_back(TeamTask{i, c, size[i], 0});
+    }
+    int ntask = 0;
+    for (int c = 0; c < G; ++c) ntask += (int)per[c].size();
+    const size_t off_begin = align_up(sizeof(PersistArgs<T>) * count, 256);
+    const size_t off_tasks = off_begin + align_up(sizeof(int) * (G + 1), 256);
+    const size_t off_ctr = off_tasks + align_up(sizeof(TeamTask) * std::max(ntask, 1), 256);
+    const size_t off_st = off_ctr + align_up(sizeof(unsigned) * 2 * count, 256);
+    const size_t bytes = off_st + sizeof(PcgState) * count;
+    unsigned char* dev = (unsigned char*)ctx_slot(ctx, SLOT_BATCH, bytes);
+    if (!dev) return NLSP_ERR_OOM;
+    std::vector<unsigned char> host(bytes, 0);
+    size_t smem = 0;
+    for (int i = 0; i < count; ++i) {
+      StreamArgs sa;
+      size_t need = 0;
+      NLSP_TRY(plan_instance(Ms[i], size[i], cpg, true, avail, &sa, &need));
+      smem = std::max(smem, need);
+      PersistArgs<T> a = instance_args(Ms[i], B[i], X[i], prm,
+                                       prm->flexible < 0 ? (Ms[i]->precision != NLSP_FP64) : (prm->flexible != 0),
+                                       (PcgState*)(dev + off_st) + i, (unsigned*)(dev + off_ctr) + 2 * i, sa);
+      a.ptimes = nullptr;
+      memcpy(host.data() + sizeof(PersistArgs<T>) * i, &a, sizeof(a));
+    }
+    int* hb = (int*)(host.data() + off_begin);
+    TeamTask* ht = (TeamTask*)(host.data() + off_tasks);
+    for (int c = 0, t = 0; c < G; ++c) {
+      hb[c] = t;
+      for (const TeamTask& task : per[c]) ht[t++] = task;
+      hb[c + 1] = t;
+    }
+    int per_sm = 0;
+    NLSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PT, smem));
+    if (per_sm < 1) {
+      nlsp_record_message("batched solver: one CTA per SM does not fit (shared memory or registers)");
+      return NLSP_ERR_INVALID;
+    }
+    NLSP_CUDA(cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, s));
+    PersistArgs<T> one;
+    memset(&one, 0, sizeof(one));
+    const PersistArgs<T>* d_insts = (const PersistArgs<T>*)dev;
+    const int* d_begin = (const int*)(dev + off_begin);
+    const TeamTask* d_tasks = (const TeamTask*)(dev + off_tasks);
+    int use_tmem = sizeof(T) == 4 ? 1 : 0;
+    void* args[] = {&one, &d_insts, &d_begin, &d_tasks, &use_tmem};
+    NLSP_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PT), args, smem, s));
+    count_launches(ctx, 1);
+    std::vector<PcgState> hs(count);
+    NLSP_CUDA(cudaMemcpyAsync(hs.data(), dev + off_st, sizeof(PcgState) * count, cudaMemcpyDeviceToHost, s));
+    NLSP_CUDA(cudaStreamSynchronize(s));
+    return summarize_states(hs.data(), count, infos);
+  }
+
   static nlsp_status summarize(PcgWork* w, int m, nlsp_solve_info* infos, int) {
+    return summarize_states(w->h_st, m, infos);
+  }
+
+  static nlsp_status summarize_states(const PcgState* hs, int m, nlsp_solve_info* infos) {
     nlsp_status worst = NLSP_OK;
     for (int col = 0; col < m; ++col) {
-      const PcgState& h = w->h_st[col];
+      const PcgState& h = hs[col];
       int stc = h.status;
       if (stc == NLSP_OK && !h.done) stc = NLSP_NOT_CONVERGED;
       if (infos) {
@@ -1721,6 +1953,36 @@ extern "C" nlsp_status nlsp_solve(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_pr
   NLSP_CUDA(cudaSetDevice(ctx->device));
   nlsp_prec* M = const_cast<nlsp_prec*>(Mc);
   return dispatch(M, [&](auto S) { return decltype(S)::solve(M, m, dev_B, ldb, dev_X, ldx, params, infos); });
+}
+
+extern "C" nlsp_status nlsp_plan_teams(int count, const int64_t* n, int num_ctas, int tiles_per_cta, int* first_cta,
+                                       int* team_size, double* start) {
+  return nlsp_internal_plan_teams(count, n, nullptr, num_ctas, tiles_per_cta, first_cta, team_size, start);
+}
+
+extern "C" nlsp_status nlsp_solve_batched(nlsp_ctx* ctx, int count, nlsp_prec* const* M, const double* const* dev_b,
+                                          double* const* dev_x, const nlsp_solve_params* params, int tiles_per_cta,
+                                          nlsp_solve_info* infos) {
+  if (!ctx || !params || count < 0 || tiles_per_cta < 0) return NLSP_ERR_INVALID;
+  if (count == 0) return NLSP_OK;
+  if (!M || !dev_b || !dev_x || !(params->tol >= 0.0) || params->maxit < 1) return NLSP_ERR_INVALID;
+  std::vector<const nlsp_prec*> seen(M, M + count);
+  for (int i = 0; i < count; ++i) {
+    if (!M[i] || M[i]->ctx != ctx || !dev_b[i] || !dev_x[i] || dev_b[i] == dev_x[i]) return NLSP_ERR_INVALID;
+    if (M[i]->precision != M[0]->precision || M[i]->A->kind != M[0]->A->kind) {
+      nlsp_record_message("nlsp_solve_batched: every instance must share the stencil kind and the precision");
+      return NLSP_ERR_INVALID;
+    }
+  }
+  std::sort(seen.begin(), seen.end());
+  if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) {
+    nlsp_record_message("nlsp_solve_batched: a preconditioner appears twice (instances need their own workspace)");
+    return NLSP_ERR_INVALID;
+  }
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  return dispatch(M[0], [&](auto S) {
+    return decltype(S)::solve_batched(ctx, count, M, dev_b, dev_x, params, tiles_per_cta, infos);
+  });
 }
 
 extern "C" void nlsp_free_prec(nlsp_prec* M) {

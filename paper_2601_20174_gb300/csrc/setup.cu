@@ -49,6 +49,53 @@ __global__ void k_tiled_to_colmajor(const T* __restrict__ src, int64_t n, int nc
   }
 }
 
+// Random test vectors S0 ~ N(0, 1) drawn on the device, straight into the
+// tiled layout: SplitMix64 (Steele, Lea, Flood 2014) counter streams and the
+// Box-Muller transform, the same definition as the host-side input
+// generator: element (i, c) is normal number c * n + i of stream `stream`
+// under `seed`; normal 2j / 2j+1 use uniforms 2j, 2j+1 (top 53 bits) as
+// sqrt(-2 log(1 - u1)) * (cos, sin)(2 pi u2).
+__device__ __forceinline__ uint64_t splitmix_fin(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ inline uint64_t splitmix_stream_base(uint64_t seed, uint64_t stream) {
+  uint64_t v = seed ^ (stream * 0xD1B54A32D192ED03ull);
+  v += 0x9E3779B97F4A7C15ull;
+  v = (v ^ (v >> 30)) * 0xBF58476D1CE4E5B9ull;
+  v = (v ^ (v >> 27)) * 0x94D049BB133111EBull;
+  return v ^ (v >> 31);
+}
+
+__device__ __forceinline__ double normal_draw(uint64_t base, uint64_t idx) {
+  const uint64_t j = idx >> 1;
+  const uint64_t a = splitmix_fin(base + (2 * j + 1) * 0x9E3779B97F4A7C15ull);
+  const uint64_t b = splitmix_fin(base + (2 * j + 2) * 0x9E3779B97F4A7C15ull);
+  const double u1 = (double)(a >> 11) * 0x1.0p-53, u2 = (double)(b >> 11) * 0x1.0p-53;
+  const double rad = sqrt(-2.0 * log1p(-u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  return rad * ((idx & 1) ? s : c);
+}
+
+template <typename T>
+__global__ void k_random_samples_tiled(uint64_t base, int64_t n, int ncols, int64_t n_pad, T* __restrict__ dst) {
+  const int64_t total = n_pad * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / ((int64_t)ncols * NLSP_TILE);
+    const int c = (int)((e / NLSP_TILE) % ncols);
+    const int64_t i = t * NLSP_TILE + (e % NLSP_TILE);
+    dst[e] = i < n ? (T)normal_draw(base, (uint64_t)c * n + i) : T(0);
+  }
+}
+
+__global__ void k_random_normal(uint64_t base, uint64_t offset, int64_t count, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = normal_draw(base, offset + e);
+}
+
 // One weighted-Jacobi sweep on A S = 0 for all K columns of a tiled block:
 // S_out = S_in - w D^-1 A S_in.  Grid: x over the padded nodes, y over groups
 // of CPT columns (the index arithmetic and the coefficients of a node are
@@ -786,7 +833,11 @@ nlsp_status build_impl(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params*
   T* sa = slot_as<T>(ctx, SLOT_SA, (size_t)M->n_pad * K);
   T* sb = slot_as<T>(ctx, SLOT_SB, (size_t)M->n_pad * K);
   if (!sa || !sb) return fail(NLSP_ERR_OOM);
-  k_colmajor_to_tiled<T><<<grid_for(ctx, M->n_pad * K, 256, 8), 256, 0, s>>>(S0, A->n, A->n, K, M->n_pad, sa);
+  if (S0)
+    k_colmajor_to_tiled<T><<<grid_for(ctx, M->n_pad * K, 256, 8), 256, 0, s>>>(S0, A->n, A->n, K, M->n_pad, sa);
+  else
+    k_random_samples_tiled<T><<<grid_for(ctx, M->n_pad * K, 256, 8), 256, 0, s>>>(
+        splitmix_stream_base(p->seed, NLSP_STREAM_S0), A->n, K, M->n_pad, sa);
   if (cudaGetLastError() != cudaSuccess) return fail(NLSP_ERR_CUDA);
   count_launches(ctx, 1);
   T* S = nullptr;
@@ -879,9 +930,21 @@ extern "C" nlsp_status nlsp_smooth_samples(nlsp_ctx* ctx, const nlsp_op* A, int 
   return NLSP_OK;
 }
 
+extern "C" nlsp_status nlsp_random_normal(nlsp_ctx* ctx, unsigned long long seed, unsigned long long stream,
+                                          unsigned long long offset, int64_t count, double* dev_out) {
+  if (!ctx || count < 0 || (count > 0 && !dev_out)) return NLSP_ERR_INVALID;
+  if (count == 0) return NLSP_OK;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  k_random_normal<<<grid_for(ctx, count, 256, 8), 256, 0, ctx->stream>>>(splitmix_stream_base(seed, stream), offset,
+                                                                          count, dev_out);
+  NLSP_LAUNCH_CHECK();
+  count_launches(ctx, 1);
+  return NLSP_OK;
+}
+
 extern "C" nlsp_status nlsp_build_prolongation(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* params,
                                                const double* dev_S0, nlsp_prec** M_out) {
-  if (!ctx || !M_out || !dev_S0) return NLSP_ERR_INVALID;
+  if (!ctx || !M_out) return NLSP_ERR_INVALID;
   *M_out = nullptr;
   NLSP_TRY(check_setup_params(A, params, true));
   NLSP_CUDA(cudaSetDevice(ctx->device));
