@@ -185,6 +185,80 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+BATCH = dict(count=256, seed=0, tol=1e-8, tiles_per_cta=(2, 4, 8, 16, 32, 64))
+BATCH_DESC = ("256 2D diffusion 5-point instances, sides drawn from {64,128,192,256,384,512}, log-kappa i.i.d. "
+              "N(0,1) per cell, ranks k from {16,32,64}, K = 2k device-drawn samples (s1=20, omega=2/3), nu=2, "
+              "1 RHS U[-1,1] each, tol 1e-8, FP32 preconditioner / FP64 PCG")
+
+
+def run_batched(ctx, dev, timed, rank):
+    """The batched leg: builds every instance's operator and preconditioner,
+    then solves all of them in one launch of the persistent solver.  The team
+    size target (tiles per CTA) is tuned on the solve alone first."""
+    import statistics as st
+
+    import torch
+
+    from paper_2601_20174_gb300 import _lib as L, api, inputs as gen
+
+    probs = gen.batch_instances(BATCH["count"], seed=BATCH["seed"] + 7919 * rank, tol=BATCH["tol"],
+                                with_samples=False)
+    kap_h = [torch.as_tensor(p.coeffs.reshape(-1)) for p in probs]
+    f_h = [torch.as_tensor(p.f[:, 0].copy()) for p in probs]
+    kaps = [k.to(dev) for k in kap_h]
+    fs = [f.to(dev) for f in f_h]
+
+    def build_all():
+        ops = [api.Operator(ctx, 2, p.N, 5, kd, L.NLSP_COEF_CELL_KAPPA) for p, kd in zip(probs, kaps)]
+        precs = [api.Preconditioner.build(A, None, p.k, p.s1, p.nu, p.omega, L.NLSP_MIXED_FP32, K=p.K, seed=p.seed)
+                 for A, p in zip(ops, probs)]
+        return ops, precs
+
+    ops, precs = build_all()
+    tune = {}
+    for tpc in BATCH["tiles_per_cta"]:
+        api.solve_batched(precs, fs, tol=BATCH["tol"], tiles_per_cta=tpc)  # warm
+        ms, _ = timed(lambda: api.solve_batched(precs, fs, tol=BATCH["tol"], tiles_per_cta=tpc), 1)
+        tune[tpc] = ms[0]
+    best = min(tune, key=tune.get)
+    so_ms, (xs, res) = timed(lambda: api.solve_batched(precs, fs, tol=BATCH["tol"], tiles_per_cta=best), 3)
+    # one by one with the single-instance persistent solver, for comparison
+    def one_by_one():
+        return [M.solve(f, tol=BATCH["tol"], graph_mode=2)[1][0] for M, f in zip(precs, fs)]
+    seq_ms, seq_res = timed(one_by_one, 1)
+    for M in precs:
+        M.close()
+    for A in ops:
+        A.close()
+    del ops, precs
+
+    # the full step: setup of every instance + the batched solve
+    def full_step():
+        o, m = build_all()
+        x, r = api.solve_batched(m, fs, tol=BATCH["tol"], tiles_per_cta=best)
+        return o, m, r
+    full_ms, (o2, m2, res2) = timed(full_step, 2)
+    for M in m2:
+        M.close()
+    for A in o2:
+        A.close()
+    its = [r.iterations for r in res]
+    true_max = max(r.true_relres for r in res)
+    cnt = BATCH["count"]
+    return {"workload": BATCH_DESC, "instances": cnt,
+            "value": cnt / (st.median(full_ms) / 1000.0), "unit": "solves/s",
+            "ms_per_step": st.median(full_ms), "step": "assemble + setup (device-drawn samples) of all 256 instances, "
+                                                       "then one batched persistent solve",
+            "solve_only": {"value": cnt / (st.median(so_ms) / 1000.0), "unit": "solves/s", "ms": st.median(so_ms),
+                           "tiles_per_cta": best, "autotune_ms": {str(k): v for k, v in tune.items()}},
+            "one_by_one_solve_only": {"value": cnt / (seq_ms[0] / 1000.0), "unit": "solves/s", "ms": seq_ms[0],
+                                      "iterations_total": sum(r.iterations for r in seq_res)},
+            "iterations": {"min": min(its), "median": int(st.median(its)), "max": max(its), "total": sum(its)},
+            "all_converged": all(r.status == 0 for r in res) and all(r.status == 0 for r in res2),
+            "max_true_relres": true_max,
+            "l2": "not flushed: the batch's data (GBs) exceeds L2"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -314,6 +388,9 @@ def run_ours(args):
     e2e_val = world * len(e2e_ms) / (e2e_total / 1000.0)
     h2d = kap_h.numel() * 8 + S0_h.numel() * 8 + f_h.numel() * 8
 
+    # ---- batched: 256 uneven instances in one persistent launch ----------
+    batched = None if args.no_batched else run_batched(ctx, dev, timed, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cv, det = oracle_sample()
@@ -340,7 +417,7 @@ def run_ours(args):
                                "true_relres": res_d.true_relres},
                 "roofline": roof, "kernels": kern,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * 8},
-                "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu}
+                "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu, "batched": batched}
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
@@ -355,6 +432,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched leg")
     ap.add_argument("--graph-mode", type=int, default=2, choices=[0, 1, 2],
                     help="2: one persistent cooperative kernel per solve (default); 1: PCG loop as one graph "
                          "with a device-side while node; 0: one-iteration graph relaunched by the host "

@@ -298,8 +298,9 @@ NLSP_API nlsp_status nlsp_solve(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec
    output only (must not be b_i).  params: tol, maxit and flexible as in
    nlsp_solve (graph_mode is ignored).  tiles_per_cta: target number of
    128-node tiles per CTA of a team (0: 16).  infos: host array of `count`
-   entries (may be NULL).  Synchronises.  A team barrier that waits longer
-   than 2 s ends its instance with NLSP_ERR_TIMEOUT.  Returns as nlsp_solve
+   entries (may be NULL).  Synchronises.  A team barrier gives up after 2 s
+   without progress anywhere in the launch (no instance finished an
+   iteration), and its instance ends with NLSP_ERR_TIMEOUT.  Returns as nlsp_solve
    (the worst per-instance status), or NLSP_ERR_INVALID, NLSP_ERR_CUDA,
    NLSP_ERR_OOM. */
 NLSP_API nlsp_status nlsp_solve_batched(nlsp_ctx* ctx, int count, nlsp_prec* const* M, const double* const* dev_b,

@@ -625,6 +625,7 @@ struct PersistArgs {
   T* cpart;       // [grid][k]
   unsigned* ctr;  // grid barrier arrival counter (zero at launch)
   int* abort;     // set when a barrier wait gave up
+  unsigned* progress;  // launch-wide progress word (batched launches; null otherwise)
   PcgState* st;   // written by CTA 0 at the end
   StreamArgs sa;
   unsigned long long* ptimes;  // optional phase timers [PH_COUNT][2] (work, barrier wait) ns, CTA 0's view
@@ -640,9 +641,14 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 
 // Barrier over the `team` CTAs working on one instance (all CTAs of the
 // launch are co-resident: cooperative launch).  The arrival counter grows
-// monotonically, barrier number `gen` waits for gen * team arrivals.  A wait longer than 2 s, or one that sees the
-// abort flag, gives up and returns false in every thread of the CTA.
-__device__ __forceinline__ bool grid_sync(unsigned* ctr, int* abort, unsigned& gen, int* ok_s, int team) {
+// monotonically, barrier number `gen` waits for gen * team arrivals.  A wait
+// that sees the abort flag, or that lasts 2 s, gives up and returns false in
+// every thread of the CTA.  With a launch-wide progress word (batched
+// launches, where a team member may still be busy with earlier instances) the
+// 2 s count restarts whenever that word has changed: the wait gives up only
+// after 2 s without progress anywhere in the launch.
+__device__ __forceinline__ bool grid_sync(unsigned* ctr, int* abort, unsigned& gen, int* ok_s, int team,
+                                          const unsigned* progress) {
   ++gen;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -650,13 +656,23 @@ __device__ __forceinline__ bool grid_sync(unsigned* ctr, int* abort, unsigned& g
     int ok = 1;
     __threadfence();
     atomicAdd(ctr, 1u);
-    const unsigned long long t0 = tma::now_ns();
+    unsigned long long t0 = tma::now_ns();
+    unsigned seen = progress ? *((const volatile unsigned*)progress) : 0u;
     while (ld_acquire_u32(ctr) < target) {
       if (*((volatile int*)abort)) {
         ok = 0;
         break;
       }
-      if (tma::now_ns() - t0 > tma::WAIT_LIMIT_NS) {
+      const unsigned long long t = tma::now_ns();
+      if (t - t0 > tma::WAIT_LIMIT_NS) {
+        if (progress) {
+          const unsigned now_p = *((const volatile unsigned*)progress);
+          if (now_p != seen) {
+            seen = now_p;
+            t0 = t;
+            continue;
+          }
+        }
         atomicExch(abort, 1);
         ok = 0;
         break;
@@ -780,7 +796,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
   auto sync = [&](int phase) -> bool {
     const bool timed = a.ptimes && cta == 0 && tid == 0;
     const unsigned long long t_arr = timed ? tma::now_ns() : 0ull;
-    ok = ok && grid_sync(a.ctr, a.abort, gen, &ok_s, G);
+    ok = ok && grid_sync(a.ctr, a.abort, gen, &ok_s, G, a.progress);
     if (timed) {
       const unsigned long long t_rel = tma::now_ns();
       a.ptimes[2 * phase] += t_arr - t_last;
@@ -1052,6 +1068,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
   // ---- iterations --------------------------------------------------------
   while (!done && ok) {
     const int t = iter;
+    if (a.progress && cta == 0 && tid == 0) atomicAdd(a.progress, 1u);
     const double* zc = (t & 1) ? a.z1 : a.z0;
     const double* pin = (t & 1) ? a.p1 : a.p0;
     double* pout = (t & 1) ? a.p0 : a.p1;
@@ -1664,6 +1681,7 @@ struct Solver {
     a.cpart = (T*)M->cpart;
     a.ctr = ctr;
     a.abort = (int*)(ctr + 1);
+    a.progress = nullptr;
     a.st = st_out;
     a.sa = sa;
     a.ptimes = w->ptimes;
@@ -1800,7 +1818,7 @@ struct Solver {
     const size_t off_begin = align_up(sizeof(PersistArgs<T>) * count, 256);
     const size_t off_tasks = off_begin + align_up(sizeof(int) * (G + 1), 256);
     const size_t off_ctr = off_tasks + align_up(sizeof(TeamTask) * std::max(ntask, 1), 256);
-    const size_t off_st = off_ctr + align_up(sizeof(unsigned) * 2 * count, 256);
+    const size_t off_st = off_ctr + align_up(sizeof(unsigned) * (2 * count + 1), 256);
     const size_t bytes = off_st + sizeof(PcgState) * count;
     unsigned char* dev = (unsigned char*)ctx_slot(ctx, SLOT_BATCH, bytes);
     if (!dev) return NLSP_ERR_OOM;
@@ -1815,6 +1833,7 @@ struct Solver {
                                        prm->flexible < 0 ? (Ms[i]->precision != NLSP_FP64) : (prm->flexible != 0),
                                        (PcgState*)(dev + off_st) + i, (unsigned*)(dev + off_ctr) + 2 * i, sa);
       a.ptimes = nullptr;
+      a.progress = (unsigned*)(dev + off_ctr) + 2 * count;
       memcpy(host.data() + sizeof(PersistArgs<T>) * i, &a, sizeof(a));
     }
     int* hb = (int*)(host.data() + off_begin);
