@@ -340,7 +340,11 @@ NLSP_API nlsp_status nlsp_bench_kernel(nlsp_ctx* ctx, const nlsp_prec* M, int wh
    solves since the last call and then reset: out_ns[2 p] = time CTA 0 spent
    in phase p before its grid barrier, out_ns[2 p + 1] = its wait at that
    barrier, for p = spmv, pre, stored sweeps, restrict, prolong, post, other
-   (14 values).  Recording is enabled by the environment variable
+   (14 values); then 12 marks inside the phases (time since the previous
+   mark or barrier release): spmv totals, spmv nodes, pre totals, pre nodes,
+   restrict rho, restrict resident tiles, restrict streamed tiles, restrict
+   reduction, prolong coarse solve, prolong resident tiles, prolong streamed
+   tiles, post nodes (26 values in all).  Recording is enabled by the environment variable
    NLSP_PHASE_TIMERS=1 when the solver workspace is first created; otherwise
    zeros.  Synchronises. */
 NLSP_API nlsp_status nlsp_prec_phase_times(nlsp_ctx* ctx, const nlsp_prec* M, double* out_ns, int count);

@@ -598,8 +598,6 @@ namespace {
 
 constexpr int PT = 512;  // threads per CTA of the persistent solver
 
-enum { RED_BB = 0, RED_PQ, RED_RR, RED_RZ, RED_RO, RED_TRUE, RED_COUNT };
-
 template <typename T>
 struct PersistArgs {
   StencilView<double> A64;
@@ -621,10 +619,10 @@ struct PersistArgs {
   const T* P;
   int k, rr_;  // stored rank, active rank
   const T* Ainv;
-  double* part;   // [RED_COUNT][grid]
-  T* cpart;       // [grid][k]
-  unsigned* ctr;  // grid barrier arrival counter (zero at launch)
-  int* abort;     // set when a barrier wait gave up
+  unsigned long long* xw;  // team exchange area (16-byte aligned, zero at launch): arrival counter (two
+                           // words), partial slots [2][2][team rounded up to even] (FP64), rows c_rank of
+                           // the coarse right-hand side [team][k]
+  int* abort;              // set when a wait gave up
   unsigned* progress;  // launch-wide progress word (batched launches; null otherwise)
   PcgState* st;   // written by CTA 0 at the end
   StreamArgs sa;
@@ -632,78 +630,111 @@ struct PersistArgs {
 };
 
 enum { PH_SPMV = 0, PH_PRE, PH_SMOOTH, PH_RESTRICT, PH_PROLONG, PH_POST, PH_OTHER, PH_COUNT };
+// Marks inside phases (time since the previous mark or barrier release,
+// CTA 0 thread 0), stored after the phase timers.
+enum {
+  MK_SPMV_TOTALS = 0, MK_SPMV_NODES, MK_PRE_TOTALS, MK_PRE_NODES, MK_RES_RHO, MK_RES_RESIDENT, MK_RES_STREAM,
+  MK_RES_REDUCE, MK_PRO_COARSE, MK_PRO_RESIDENT, MK_PRO_STREAM, MK_POST_NODES, MK_COUNT
+};
+constexpr int PTIMES_LEN = 2 * PH_COUNT + MK_COUNT;
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+
+// ---- team barriers ------------------------------------------------------------
+// The CTAs of one instance (a team; all CTAs of the launch are co-resident)
+// meet at barriers: thread 0 of each CTA releases the CTA's global writes
+// (fence) and adds one to the team's arrival counter; barrier number gen is
+// passed when the counter reaches gen * team.  Sums over the team go through
+// per-rank partial slots written before a barrier and read after it; the slots
+// are double buffered by the parity of the barrier number (a CTA rewrites a
+// slot only after every rank has arrived at the next barrier, which each rank
+// does only after reading the slot).
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* ptr) {
   unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
   return v;
 }
 
-// Barrier over the `team` CTAs working on one instance (all CTAs of the
-// launch are co-resident: cooperative launch).  The arrival counter grows
-// monotonically, barrier number `gen` waits for gen * team arrivals.  A wait
-// that sees the abort flag, or that lasts 2 s, gives up and returns false in
-// every thread of the CTA.  With a launch-wide progress word (batched
-// launches, where a team member may still be busy with earlier instances) the
-// 2 s count restarts whenever that word has changed: the wait gives up only
-// after 2 s without progress anywhere in the launch.
-__device__ __forceinline__ bool grid_sync(unsigned* ctr, int* abort, unsigned& gen, int* ok_s, int team,
-                                          const unsigned* progress) {
-  ++gen;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned target = gen * (unsigned)team;
-    int ok = 1;
-    __threadfence();
-    atomicAdd(ctr, 1u);
-    unsigned long long t0 = tma::now_ns();
-    unsigned seen = progress ? *((const volatile unsigned*)progress) : 0u;
-    while (ld_acquire_u32(ctr) < target) {
-      if (*((volatile int*)abort)) {
-        ok = 0;
-        break;
-      }
-      const unsigned long long t = tma::now_ns();
-      if (t - t0 > tma::WAIT_LIMIT_NS) {
-        if (progress) {
-          const unsigned now_p = *((const volatile unsigned*)progress);
-          if (now_p != seen) {
-            seen = now_p;
-            t0 = t;
-            continue;
-          }
-        }
-        atomicExch(abort, 1);
-        ok = 0;
-        break;
+// Bounded wait bookkeeping of one polling thread: gives up after 2 s (the
+// count restarts while the launch-wide progress word moves: in batched
+// launches a team member may be busy with earlier instances) or when the
+// abort flag is set.  Returns false when the thread must stop waiting.
+struct PollClock {
+  unsigned long long t0;
+  unsigned seen;
+  bool started;
+  __device__ __forceinline__ PollClock() : t0(0), seen(0), started(false) {}
+  __device__ __forceinline__ bool keep_going(int* abort, const unsigned* progress) {
+    if (*((volatile int*)abort)) return false;
+    const unsigned long long t = tma::now_ns();
+    if (!started) {
+      started = true;
+      t0 = t;
+      seen = progress ? *((const volatile unsigned*)progress) : 0u;
+      return true;
+    }
+    if (t - t0 <= tma::WAIT_LIMIT_NS) return true;
+    if (progress) {
+      const unsigned now_p = *((const volatile unsigned*)progress);
+      if (now_p != seen) {
+        seen = now_p;
+        t0 = t;
+        return true;
       }
     }
+    atomicExch(abort, 1);
+    return false;
+  }
+};
+
+constexpr int XMAX_RANKS = 160;  // team size limit (the team sums read 5 ranks per lane)
+
+// Barrier number `gen` of the team; false in every thread when the wait gave
+// up (abort flag or time limit).
+__device__ __forceinline__ bool team_barrier(unsigned* ctr, int* abort, const unsigned* progress, unsigned gen,
+                                             int team, int* ok_s) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
     __threadfence();
-    if (ok && *((volatile int*)abort)) ok = 0;  // another CTA gave up earlier
+    atomicAdd(ctr, 1u);
+    int ok = 1;
+    PollClock clk;
+    const unsigned target = gen * (unsigned)team;
+    while (ld_acquire_u32(ctr) < target)
+      if (!clk.keep_going(abort, progress)) {
+        ok = 0;
+        break;
+      }
+    if (ok && *((volatile int*)abort)) ok = 0;
     *ok_s = ok;
   }
   __syncthreads();
   return *ok_s != 0;
 }
 
-// Sum of the grid's partials of one dot product, in CTA order (same value in
-// every CTA).  Result valid in all threads.
-__device__ __forceinline__ double grid_total(const double* part, double* sm_d, double* bc, int team) {
-  double s = 0.0;
-  if (threadIdx.x < 32) {
-    for (int c = threadIdx.x; c < team; c += 32) s += __ldcg(part + c);
-    s = warp_sum(s);
-    if (threadIdx.x == 0) *bc = s;
-  }
-  __syncthreads();
-  const double v = *bc;
-  __syncthreads();
-  return v;
+constexpr int XBAR = 7;  // mbarrier of the partial-slot copies (the P ring uses the first ones)
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-__device__ __forceinline__ void put_partial(double s, double* part, double* sm_d, int rank) {
-  s = block_sum_lean(s, sm_d);
-  if (threadIdx.x == 0) part[rank] = s;
+// Sums NV values over the CTA (warp sums first); result valid in thread 0.
+// Ends with a __syncthreads after every thread has contributed.
+template <int NV>
+__device__ __forceinline__ void cta_sums(const double (&val)[NV], double* sm_d, double (&out)[NV]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double w = warp_sum(val[v]);
+    if (lane == 0) sm_d[v * (PT / 32) + warp] = w;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double s = lane < PT / 32 ? sm_d[v * (PT / 32) + lane] : 0.0;
+      out[v] = warp_sum(s);
+    }
+  }
 }
 
 // Streams the CTA's P tiles through the ring: copy number j (running over the
@@ -713,6 +744,8 @@ __device__ __forceinline__ void ring_issue(uint64_t* bar, T* buf, const T* P, in
                                            int tile) {
   const unsigned bytes = (unsigned)r * NLSP_TILE * (unsigned)sizeof(T);
   const int s = (int)(j % (unsigned)nstage);
+  // the stage was last read (or used as scratch) through the generic proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tma::mbar_arrive_expect_tx(&bar[s], bytes);
   tma::bulk_g2s(buf + (size_t)s * r * NLSP_TILE, P + (size_t)tile * k * NLSP_TILE, bytes, &bar[s]);
 }
@@ -736,6 +769,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
   __shared__ T e_s[128];
   __shared__ T zpart[2][4][NLSP_TILE];
   __shared__ double bc[2];
+  __shared__ __align__(16) double tot_s[2][XMAX_RANKS];  // copies of the team's partial slots
   __shared__ int ok_s, abort_s;
 
   constexpr bool FP32 = sizeof(T) == 4;
@@ -756,9 +790,18 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
   T* rho_s = res + (size_t)a.sa.n_sm * r * NLSP_TILE;
   const T omega = a.omega;
   const int warp = tid >> 5, lane = tid & 31, q = warp & 3, g = warp >> 2, nd = 32 * q + lane;
+  // staged smoothing (2D stencils, FP32): node ranges one and two stencil
+  // hops (N + 1 nodes, diagonals included) around the own nodes, kept in the
+  // ring buffer when they fit
+  const int hop = N + 1;
+  const int e1lo = max(0, i0 - hop), e1hi = min(n, i1 + hop);
+  const int e2lo = max(0, i0 - 2 * hop), e2hi = min(n, i1 + 2 * hop);
+  const int ring_elems = nstage * r * NLSP_TILE;
+  const bool stage_pre = FP32 && KIND != ST_7PT && i1 > i0 && (e2hi - e2lo) + (e1hi - e1lo) <= ring_elems;
+  const bool stage_post = FP32 && KIND != ST_7PT && i1 > i0 && (e1hi - e1lo) <= ring_elems;
   unsigned gen = 0, jc = 0;
   bool ok = true;
-  (void)N;
+  double tol2bn = 0.0;
 
   // the ring's barriers are re-initialised for every instance (all copies of
   // the previous instance have been consumed)
@@ -769,6 +812,8 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       tma::mbar_inval(&mbar[s]);
       tma::mbar_init(&mbar[s], 1);
     }
+    tma::mbar_inval(&mbar[XBAR]);
+    tma::mbar_init(&mbar[XBAR], 1);
     tma::fence_barrier_init();
   }
   __syncthreads();
@@ -792,28 +837,137 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
   }
   __syncthreads();
 
-  unsigned long long t_last = (a.ptimes && cta == 0 && tid == 0) ? tma::now_ns() : 0ull;
-  auto sync = [&](int phase) -> bool {
-    const bool timed = a.ptimes && cta == 0 && tid == 0;
-    const unsigned long long t_arr = timed ? tma::now_ns() : 0ull;
-    ok = ok && grid_sync(a.ctr, a.abort, gen, &ok_s, G, a.progress);
-    if (timed) {
+  const bool timed0 = a.ptimes && cta == 0 && tid == 0;
+  unsigned long long t_last = timed0 ? tma::now_ns() : 0ull, t_mark = t_last;
+  // exchange area: arrival counter, partial slots [2][2][gs], c_rank rows
+  const int gs = (G + 1) & ~1;  // slot length: whole 16-byte units for the bulk copies
+  unsigned* const ctr = reinterpret_cast<unsigned*>(a.xw);
+  double* const slots = reinterpret_cast<double*>(a.xw + 2);
+  T* const cpart = reinterpret_cast<T*>(a.xw + 2 + (size_t)4 * gs);  // [team][k]
+  unsigned tpar = 0;  // copies of partial slots so far (mbarrier phase)
+  auto phase_time = [&](int phase, unsigned long long t_arr) {
+    if (timed0) {
       const unsigned long long t_rel = tma::now_ns();
       a.ptimes[2 * phase] += t_arr - t_last;
       a.ptimes[2 * phase + 1] += t_rel - t_arr;
-      t_last = t_rel;
+      t_last = t_mark = t_rel;
     }
+  };
+  // slot of sum v for barrier number g
+  auto slot_of = [&](unsigned g, int v) { return slots + ((size_t)(g & 1u) * 2 + v) * gs; };
+  // the CTA's partials of the sums carried by the next barrier
+  auto put = [&](int nv, double v0, double v1) {
+    const double in[2] = {v0, v1};
+    double s[2] = {0.0, 0.0};
+    cta_sums<2>(in, sm_d, s);
+    if (tid == 0) {
+      slot_of(gen + 1, 0)[cta] = s[0];
+      if (nv > 1) slot_of(gen + 1, 1)[cta] = s[1];
+    }
+  };
+  auto bar = [&](int phase) -> bool {
+    const unsigned long long t_arr = timed0 ? tma::now_ns() : 0ull;
+    ++gen;
+    ok = ok && team_barrier(ctr, a.abort, a.progress, gen, G, &ok_s);
+    phase_time(phase, t_arr);
     return ok;
+  };
+  // Totals of the nv sums carried by the last barrier: tot_issue starts bulk
+  // copies of the slots into shared memory (no registers held while other
+  // work runs), tot_finish adds them in rank order (the same value in every
+  // CTA).  False when the copy wait gave up.
+  auto tot_issue = [&](int nv) {
+    if (tid == 0) {
+      fence_proxy_async_global();  // the slots were acquired through the generic proxy
+      const unsigned bytes = (unsigned)(gs * sizeof(double));
+      tma::mbar_arrive_expect_tx(&mbar[XBAR], bytes * nv);
+      for (int v = 0; v < nv; ++v) tma::bulk_g2s(tot_s[v], slot_of(gen, v), bytes, &mbar[XBAR]);
+    }
+  };
+  auto tot_finish = [&](int nv, double* out) -> bool {
+    if (tid < 32) {
+      const bool got = tma::mbar_wait(&mbar[XBAR], tpar & 1u);
+      if (!got && tid == 0) {
+        atomicExch(a.abort, 1);
+        abort_s = 1;
+      }
+      for (int v = 0; v < nv; ++v) {
+        double s = 0.0;
+#pragma unroll
+        for (int u = 0; u < XMAX_RANKS / 32; ++u) {
+          const int c = tid + 32 * u;
+          if (c < G) s += tot_s[v][c];
+        }
+        s = warp_sum(s);
+        if (tid == 0) bc[v] = s;
+      }
+    }
+    ++tpar;
+    __syncthreads();
+    for (int v = 0; v < nv; ++v) out[v] = bc[v];
+    const bool good = abort_s == 0;
+    __syncthreads();
+    if (!good) ok = false;
+    return good;
+  };
+  auto total1 = [&]() -> double {
+    double o[1] = {0.0};
+    tot_issue(1);
+    tot_finish(1, o);
+    return o[0];
+  };
+  auto mark = [&](int id) {
+    if (timed0) {
+      const unsigned long long t = tma::now_ns();
+      a.ptimes[2 * PH_COUNT + id] += t - t_mark;
+      t_mark = t;
+    }
   };
 
   // ---- the two phases that read P ----------------------------------------
   // restrict: rho for the own nodes (z recomputed from rT when zm > 0), then
-  // c_cta = P^T rho over the own tiles -> a.cpart[cta].  Thread (g, q, lane)
+  // c_cta = P^T rho over the own tiles -> row cta of cpart.  Thread (g, q, lane)
   // accumulates columns [g CPG, g CPG + CPG) for node 32 q + lane of each tile.
   auto restrict_phase = [&](int zm, const T* zin) {
-    for (int s = 0; s < nstage && s < nst; ++s)
-      if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, tst + s);
-    for (int e = tid; e < nt * NLSP_TILE; e += PT) {
+    const bool staged = zm > 0 && stage_pre;
+    if (!staged)
+      for (int s = 0; s < nstage && s < nst; ++s)
+        if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, tst + s);
+    if (staged) {
+      // z1 = w D^-1 rT on the own nodes and two grid rows around them, then
+      // z2 = z1 + w D^-1 (rT - A z1) on one row around them, both in the ring
+      // buffer; rho = rT - A z2 on the own nodes.  Same arithmetic as
+      // presmooth_at, without recomputing z1 and z2 at every neighbour.
+      T* z1s = buf;
+      T* z2s = buf + (e2hi - e2lo);
+      for (int m = e2lo + tid; m < e2hi; m += PT) z1s[m - e2lo] = omega * stencil_dinv<KIND>(a.AT, m) * a.rT[m];
+      __syncthreads();
+      if (zm == 2) {
+        for (int m = e1lo + tid; m < e1hi; m += PT) {
+          const T az = stencil_apply<KIND>(a.AT, m, node_coord<KIND>(m, a.AT.N),
+                                           [&](int64_t mm) { return z1s[mm - e2lo]; });
+          z2s[m - e1lo] = z1s[m - e2lo] + omega * stencil_dinv<KIND>(a.AT, m) * (a.rT[m] - az);
+        }
+        __syncthreads();
+      }
+      const T* zs = zm == 2 ? z2s : z1s;
+      const int zlo = zm == 2 ? e1lo : e2lo;
+      for (int e = tid; e < nt * NLSP_TILE; e += PT) {
+        const int i = i0 + e;
+        T rho = T(0);
+        if (i < n) {
+          const T az = stencil_apply<KIND>(a.AT, i, node_coord<KIND>(i, a.AT.N),
+                                           [&](int64_t mm) { return zs[mm - zlo]; });
+          rho = a.rT[i] - az;
+          a.zw[i] = zs[i - zlo];
+        }
+        rho_s[e] = rho;
+      }
+      __syncthreads();  // the ring buffer is free again
+      for (int s = 0; s < nstage && s < nst; ++s)
+        if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, tst + s);
+    }
+    for (int e = tid; e < (staged ? 0 : nt * NLSP_TILE); e += PT) {
       const int i = i0 + e;
       T rho = T(0);
       if (i < n) {
@@ -842,6 +996,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       rho_s[e] = rho;
     }
     __syncthreads();
+    mark(MK_RES_RHO);
     T acc[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = T(0);
@@ -861,6 +1016,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         if (col < r) acc[j] += rho * tile[col * NLSP_TILE + nd];
       }
     }
+    mark(MK_RES_RESIDENT);
     for (int it = 0; it < nst; ++it) {
       if (!ring_wait(mbar, nstage, jc + it)) abort_s = 1;
       const T* tile = buf + (size_t)((jc + it) % (unsigned)nstage) * r * NLSP_TILE;
@@ -879,6 +1035,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       if (tid == 0 && it + nstage < nst) ring_issue(mbar, buf, a.P, k, r, nstage, jc + it + nstage, tst + it + nstage);
     }
     jc += nst;
+    mark(MK_RES_STREAM);
     sacc[warp][lane] = warp_reduce_scatter32(acc, lane);  // column g CPG + lane (lane < CPG)
     __syncthreads();
     for (int col = tid; col < r; col += PT) {
@@ -886,8 +1043,9 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       T s = T(0);
 #pragma unroll
       for (int qq = 0; qq < 4; ++qq) s += sacc[gg * 4 + qq][j];
-      a.cpart[(int64_t)cta * k + col] = s;
+      cpart[(size_t)cta * k + col] = s;
     }
+    mark(MK_RES_REDUCE);
   };
 
   // prolong: e_c = A_c^-1 (sum of the CTAs' c), z += P e_c on the own tiles.
@@ -898,11 +1056,14 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
     for (int s = 0; s < nstage && s < nst; ++s)
       if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, tst + s);
     {
+      // sum of the team's c_rank: thread (col, sl) adds ranks sl, sl + S, ...
+      // in order, eight loads in flight
       const int S = PT / r > 0 ? PT / r : 1;
       T part = T(0);
       if (tid < S * r) {
         const int col = tid % r, sl = tid / r;
-        for (int c = sl; c < G; c += S) part += __ldcg(a.cpart + (int64_t)c * k + col);
+#pragma unroll 8
+        for (int c = sl; c < G; c += S) part += __ldcg(cpart + (size_t)c * k + col);
       }
       red_t[tid] = part;
       __syncthreads();
@@ -912,13 +1073,25 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         cfull[col] = s;
       }
       __syncthreads();
-      for (int row = tid; row < RPAD; row += PT) {
+      {  // e_c = A_c^-1 c: PT / RPAD column groups per row, then a combine
+        constexpr int CG = PT / RPAD;
+        const int row = tid % RPAD, cg = tid / RPAD;
         T s = T(0);
-        if (row < r)
-          for (int col = 0; col < r; ++col) s += a.Ainv[(int64_t)col * r + row] * cfull[col];
-        e_s[row] = s;  // zero beyond r
+        if (row < r) {
+#pragma unroll 4
+          for (int col = cg; col < r; col += CG) s += a.Ainv[(int64_t)col * r + row] * cfull[col];
+        }
+        red_t[tid] = s;
+        __syncthreads();
+        if (tid < RPAD) {
+          T e = T(0);
+#pragma unroll
+          for (int gg = 0; gg < CG; ++gg) e += red_t[gg * RPAD + tid];
+          e_s[tid] = e;  // zero beyond r
+        }
       }
       __syncthreads();
+      mark(MK_PRO_COARSE);
     }
     for (int tl = g; tl < ntm + nsm; tl += 4) {
       T s = T(0);
@@ -937,6 +1110,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       const int i = (t0 + tl) * NLSP_TILE + nd;
       if (i < n) z[i] += s;
     }
+    mark(MK_PRO_RESIDENT);
     for (int it = 0; it < nst; ++it) {
       if (!ring_wait(mbar, nstage, jc + it)) abort_s = 1;
       const T* tile = buf + (size_t)((jc + it) % (unsigned)nstage) * r * NLSP_TILE;
@@ -961,6 +1135,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       }
     }
     jc += nst;
+    mark(MK_PRO_STREAM);
   };
 
   auto sweep_phase = [&](const T* zin, T* zout) {
@@ -973,7 +1148,14 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
 
   // The preconditioner on the current residual: z (FP64) -> zout64, with
   // r^T z and r^T zold64 accumulated into the RED_RZ / RED_RO partials.
-  auto apply = [&](double* zout64, const double* zold64, bool flex) -> bool {
+  // The preconditioner on the current residual: z (FP64) -> zout64, with the
+  // partials of r^T z (and r^T zold64) carried by its last barrier.  When
+  // rr_out is given, the team's r^T r from the barrier before is added up
+  // while the restriction runs; the application stops after the restriction
+  // (returns 2) when that shows convergence or a non-finite residual.
+  // Returns 0 when a wait gave up, 1 when done.
+  auto apply = [&](double* zout64, const double* zold64, bool flex, double* rr_out) -> int {
+    if (rr_out) tot_issue(1);
     T* cur = a.zw;
     T* oth = a.zw2;
     const bool fused_pre = FP32 && a.nu1 <= 2;
@@ -983,28 +1165,49 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         cur[i] = a.nu1 == 1 ? presmooth_at<KIND, T, 1>(a.AT, omega, a.rT, i, c)
                             : presmooth_at<KIND, T, 2>(a.AT, omega, a.rT, i, c);
       }
-      if (!sync(PH_SMOOTH)) return false;
+      if (!bar(PH_SMOOTH)) return 0;
       for (int sw = 2; sw < a.nu1; ++sw) {
         sweep_phase(cur, oth);
         T* tmp = cur; cur = oth; oth = tmp;
-        if (!sync(PH_SMOOTH)) return false;
+        if (!bar(PH_SMOOTH)) return 0;
       }
     }
     restrict_phase(fused_pre ? a.nu1 : 0, cur);
-    if (!sync(PH_RESTRICT)) return false;
+    if (rr_out) {
+      double o[1] = {0.0};
+      if (!tot_finish(1, o)) return 0;
+      *rr_out = o[0];
+      if (!isfinite(o[0]) || o[0] <= tol2bn) return 2;
+    }
+    if (!bar(PH_RESTRICT)) return 0;
     prolong_phase(cur);
-    if (!sync(PH_PROLONG)) return false;
+    if (!bar(PH_PROLONG)) return 0;
     const int nfinal = (FP32 && a.nu2 >= 2) ? 2 : 1;
     for (int sw = nfinal; sw < a.nu2; ++sw) {
       sweep_phase(cur, oth);
       T* tmp = cur; cur = oth; oth = tmp;
-      if (!sync(PH_SMOOTH)) return false;
+      if (!bar(PH_SMOOTH)) return 0;
     }
     double s_rz = 0.0, s_ro = 0.0;
+    const bool staged = nfinal == 2 && stage_post;
+    if (staged) {
+      // first post-sweep on the own nodes and one grid row around them into
+      // the (idle) ring buffer, the second one below reads it
+      T* z3s = buf;
+      for (int m = e1lo + tid; m < e1hi; m += PT) {
+        const T az = stencil_apply<KIND>(a.AT, m, node_coord<KIND>(m, a.AT.N), [&](int64_t mm) { return cur[mm]; });
+        z3s[m - e1lo] = cur[m] + omega * stencil_dinv<KIND>(a.AT, m) * (a.rT[m] - az);
+      }
+      __syncthreads();
+    }
     for (int i = i0 + tid; i < i1; i += PT) {
       const NodeCoord c = node_coord<KIND>(i, a.AT.N);
       T zf;
-      if (nfinal == 2) {
+      if (staged) {
+        const T* z3s = buf;
+        const T az4 = stencil_apply<KIND>(a.AT, i, c, [&](int64_t mm) { return z3s[mm - e1lo]; });
+        zf = z3s[i - e1lo] + omega * stencil_dinv<KIND>(a.AT, i) * (a.rT[i] - az4);
+      } else if (nfinal == 2) {
         auto z4at = [&](int64_t m, NodeCoord cm) -> T {
           const T az = stencil_apply<KIND>(a.AT, m, cm, [&](int64_t mm) { return cur[mm]; });
           return cur[m] + omega * stencil_dinv<KIND>(a.AT, m) * (a.rT[m] - az);
@@ -1023,14 +1226,14 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       s_rz = fma(ri, zd, s_rz);
       if (flex) s_ro = fma(ri, zold64[i], s_ro);
     }
-    put_partial(s_rz, a.part + RED_RZ * G, sm_d, cta);
-    if (flex) put_partial(s_ro, a.part + RED_RO * G, sm_d, cta);
-    return sync(PH_POST);
+    mark(MK_POST_NODES);
+    put(2, s_rz, s_ro);
+    return bar(PH_POST) ? 1 : 0;
   };
 
   // ---- start: r = b, x = 0, p = 0 ---------------------------------------
   int status = (int)NLSP_OK, iter = 0;
-  double bb, tol2bn, rz = 0.0, rr = 0.0, beta = 0.0;
+  double bb = 0.0, rz = 0.0, rr = 0.0, beta = 0.0;
   {
     double s = 0.0;
     for (int i = i0 + tid; i < i1; i += PT) {
@@ -1042,29 +1245,20 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       a.p1[i] = 0.0;
       s = fma(bi, bi, s);
     }
-    put_partial(s, a.part + RED_BB * G, sm_d, cta);
+    put(1, s, 0.0);
   }
   bool done = false;
-  if (sync(PH_OTHER)) {
-    bb = grid_total(a.part + RED_BB * G, sm_d, bc, G);
+  if (bar(PH_OTHER)) {
+    bb = total1();
     tol2bn = a.tol * a.tol * bb;
     rr = bb;
     if (bb == 0.0) done = true;
     else if (!isfinite(bb)) { status = (int)NLSP_ERR_BREAKDOWN; done = true; }
   } else {
-    bb = 0.0;
-    tol2bn = 0.0;
     done = true;
   }
   // initial preconditioner application z_0 = B r_0
-  if (!done) {
-    if (apply(a.z0, a.z1, false)) {
-      rz = grid_total(a.part + RED_RZ * G, sm_d, bc, G);
-      if (!(rz > 0.0) || !isfinite(rz)) { status = (int)NLSP_ERR_BREAKDOWN; done = true; }
-    } else {
-      done = true;
-    }
-  }
+  if (!done && apply(a.z0, a.z1, false, nullptr) != 1) done = true;
   // ---- iterations --------------------------------------------------------
   while (!done && ok) {
     const int t = iter;
@@ -1072,49 +1266,105 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
     const double* zc = (t & 1) ? a.z1 : a.z0;
     const double* pin = (t & 1) ? a.p1 : a.p0;
     double* pout = (t & 1) ? a.p0 : a.p1;
-    {  // spmv
+    {  // spmv: p = z + beta p_old on the own nodes first (their z and p_old
+       // are loaded while the team's r^T z is added up), then q = A p with p
+       // read back inside the own range and recomputed on halo nodes (the
+       // same expression, so the same value the owner stores)
+      tot_issue(2);
+      double zv[4], pv4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int iu = i0 + tid + u * PT;
+        zv[u] = iu < i1 ? __ldcg(zc + iu) : 0.0;
+        pv4[u] = iu < i1 ? __ldcg(pin + iu) : 0.0;
+      }
+      double tot[2] = {0.0, 0.0};
+      if (!tot_finish(2, tot)) break;
+      const double rzn = tot[0], ro = a.flexible ? tot[1] : 0.0;
+      if (!(rzn > 0.0) || !isfinite(rzn)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
+      if (t > 0) {
+        beta = (rzn - ro) / rz;
+        if (iter >= a.maxit) { status = (int)NLSP_NOT_CONVERGED; break; }
+      }
+      rz = rzn;
+      mark(MK_SPMV_TOTALS);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int iu = i0 + tid + u * PT;
+        if (iu < i1) pout[iu] = fma(beta, pv4[u], zv[u]);
+      }
+      for (int i = i0 + tid + 4 * PT; i < i1; i += PT) pout[i] = fma(beta, __ldcg(pin + i), __ldcg(zc + i));
+      __syncthreads();
       double s = 0.0;
-      for (int i = i0 + tid; i < i1; i += PT) {
-        const NodeCoord c = node_coord<KIND>(i, a.A64.N);
-        auto pv = [&](int64_t m) { return fma(beta, __ldcg(pin + m), __ldcg(zc + m)); };
-        const double pi = pv(i);
-        const double qi = stencil_apply<KIND>(a.A64, i, c, pv);
-        pout[i] = pi;
+      auto pv = [&](int64_t m) {
+        return (m >= i0 && m < i1) ? __ldcg(pout + m) : fma(beta, __ldcg(pin + m), __ldcg(zc + m));
+      };
+      for (int i = i0 + tid; i < i1; i += 2 * PT) {
+        const int i2 = i + PT;
+        const bool two = i2 < i1;
+        const double pi = __ldcg(pout + i);
+        const double qi = stencil_apply<KIND>(a.A64, i, node_coord<KIND>(i, a.A64.N), pv);
+        double pi2 = 0.0, qi2 = 0.0;
+        if (two) {
+          pi2 = __ldcg(pout + i2);
+          qi2 = stencil_apply<KIND>(a.A64, i2, node_coord<KIND>(i2, a.A64.N), pv);
+        }
         a.q[i] = qi;
         s = fma(pi, qi, s);
+        if (two) {
+          a.q[i2] = qi2;
+          s = fma(pi2, qi2, s);
+        }
       }
-      put_partial(s, a.part + RED_PQ * G, sm_d, cta);
+      mark(MK_SPMV_NODES);
+      put(1, s, 0.0);
+      if (!bar(PH_SPMV)) break;
     }
-    if (!sync(PH_SPMV)) break;
-    const double pq = grid_total(a.part + RED_PQ * G, sm_d, bc, G);
     iter = t + 1;
-    if (!(pq > 0.0) || !isfinite(pq)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
-    const double alpha = rz / pq;
-    {  // pre: x, r update
-      double s = 0.0;
-      for (int i = i0 + tid; i < i1; i += PT) {
-        a.x[i] = fma(alpha, pout[i], a.x[i]);
-        const double ri = fma(-alpha, a.q[i], a.r[i]);
-        a.r[i] = ri;
-        if (FP32) a.rT[i] = (T)ri;
-        s = fma(ri, ri, s);
+    {  // pre: x, r update; the own nodes' data is loaded while p^T q is added up
+      tot_issue(1);
+      double pv[4], xv[4], qv[4], rv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int iu = i0 + tid + u * PT;
+        const bool in = iu < i1;
+        pv[u] = in ? pout[iu] : 0.0;
+        xv[u] = in ? a.x[iu] : 0.0;
+        qv[u] = in ? a.q[iu] : 0.0;
+        rv[u] = in ? a.r[iu] : 0.0;
       }
-      put_partial(s, a.part + RED_RR * G, sm_d, cta);
+      double tot[1] = {0.0};
+      if (!tot_finish(1, tot)) break;
+      const double pq = tot[0];
+      if (!(pq > 0.0) || !isfinite(pq)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
+      const double alpha = rz / pq;
+      mark(MK_PRE_TOTALS);
+      double s = 0.0;
+      auto update = [&](int i, double pi, double xi, double qi, double ri) {
+        const double rn = fma(-alpha, qi, ri);
+        a.x[i] = fma(alpha, pi, xi);
+        a.r[i] = rn;
+        if (FP32) a.rT[i] = (T)rn;
+        s = fma(rn, rn, s);
+      };
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int iu = i0 + tid + u * PT;
+        if (iu < i1) update(iu, pv[u], xv[u], qv[u], rv[u]);
+      }
+      for (int i = i0 + tid + 4 * PT; i < i1; i += PT) update(i, pout[i], a.x[i], a.q[i], a.r[i]);
+      mark(MK_PRE_NODES);
+      put(1, s, 0.0);
+      if (!bar(PH_PRE)) break;
     }
-    if (!sync(PH_PRE)) break;
-    rr = grid_total(a.part + RED_RR * G, sm_d, bc, G);
-    if (!isfinite(rr)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
-    if (rr <= tol2bn) break;  // converged
     double* zn = (iter & 1) ? a.z1 : a.z0;
     const double* zo = (iter & 1) ? a.z0 : a.z1;
-    const bool flex = a.flexible != 0;
-    if (!apply(zn, zo, flex)) break;
-    const double rzn = grid_total(a.part + RED_RZ * G, sm_d, bc, G);
-    const double ro = flex ? grid_total(a.part + RED_RO * G, sm_d, bc, G) : 0.0;
-    if (!(rzn > 0.0) || !isfinite(rzn)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
-    beta = (rzn - ro) / rz;
-    rz = rzn;
-    if (iter >= a.maxit) { status = (int)NLSP_NOT_CONVERGED; break; }
+    const int st_apply = apply(zn, zo, a.flexible != 0, &rr);
+    if (st_apply == 0) break;
+    if (st_apply == 2) {
+      if (!isfinite(rr)) status = (int)NLSP_ERR_BREAKDOWN;
+      break;  // converged (or broke down)
+    }
   }
   if (!ok) status = (int)NLSP_ERR_TIMEOUT;
   // ---- true residual ------------------------------------------------------
@@ -1126,8 +1376,8 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       const double ri = a.b[i] - stencil_apply<KIND>(a.A64, i, c, [&](int64_t m) { return __ldcg(a.x + m); });
       s = fma(ri, ri, s);
     }
-    put_partial(s, a.part + RED_TRUE * G, sm_d, cta);
-    if (sync(PH_OTHER)) trr = grid_total(a.part + RED_TRUE * G, sm_d, bc, G);
+    put(1, s, 0.0);
+    if (bar(PH_OTHER)) trr = total1();
   }
   tmem::fence_before_sync();
   __syncthreads();
@@ -1221,6 +1471,8 @@ struct PcgWork {
   int built_r = -1;
   int body_launches = 0;  // kernels in one iteration body
   unsigned long long* ptimes = nullptr;  // phase timers of the persistent solver (NLSP_PHASE_TIMERS=1)
+  unsigned long long* xw = nullptr;      // exchange words of the persistent solver
+  size_t xw_cap = 0;
 };
 
 namespace {
@@ -1245,6 +1497,7 @@ void free_work(PcgWork* w) {
   if (w->part) cudaFree(w->part);
   if (w->counter) cudaFree(w->counter);
   if (w->ptimes) cudaFree(w->ptimes);
+  if (w->xw) cudaFree(w->xw);
   if (w->st_all) cudaFree(w->st_all);
   if (w->h_st) cudaFreeHost(w->h_st);
   if (w->cap) cudaStreamDestroy(w->cap);
@@ -1272,8 +1525,8 @@ nlsp_status ensure_work(nlsp_prec* M, int m) {
     NLSP_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
     const char* pt = getenv("NLSP_PHASE_TIMERS");
     if (pt && pt[0] == '1') {
-      NLSP_CUDA(cudaMalloc(&w->ptimes, sizeof(unsigned long long) * 2 * PH_COUNT));
-      NLSP_CUDA(cudaMemsetAsync(w->ptimes, 0, sizeof(unsigned long long) * 2 * PH_COUNT, ctx->stream));
+      NLSP_CUDA(cudaMalloc(&w->ptimes, sizeof(unsigned long long) * PTIMES_LEN));
+      NLSP_CUDA(cudaMemsetAsync(w->ptimes, 0, sizeof(unsigned long long) * PTIMES_LEN, ctx->stream));
     }
   }
   PcgWork* w = M->pcg;
@@ -1646,11 +1899,17 @@ struct Solver {
     return NLSP_OK;
   }
 
+  // Exchange words of one instance solved by `team` CTAs (zero at launch).
+  static size_t xw_words(const nlsp_prec* M, int team) {
+    return 2 + (size_t)4 * ((team + 1) & ~1) + ((size_t)team * M->k * sizeof(T) + 7) / 8;
+  }
+
   // Kernel arguments of one instance: right-hand side b, iterate x (may be
-  // the caller's output: it is set to zero first), state st, barrier counter
-  // and abort flag ctr[0], ctr[1].
+  // the caller's output: it is set to zero first), state st, exchange words
+  // xw and abort flag.
   static PersistArgs<T> instance_args(nlsp_prec* M, const double* b, double* x_, const nlsp_solve_params* prm,
-                                      int flexible, PcgState* st_out, unsigned* ctr, const StreamArgs& sa) {
+                                      int flexible, PcgState* st_out, unsigned long long* xw, int* abort_flag,
+                                      const StreamArgs& sa) {
     PcgWork* w = M->pcg;
     PersistArgs<T> a;
     a.A64 = M->A->v64;
@@ -1677,10 +1936,8 @@ struct Solver {
     a.k = M->k;
     a.rr_ = M->r;
     a.Ainv = (const T*)M->AinvT;
-    a.part = w->part;
-    a.cpart = (T*)M->cpart;
-    a.ctr = ctr;
-    a.abort = (int*)(ctr + 1);
+    a.xw = xw;
+    a.abort = abort_flag;
     a.progress = nullptr;
     a.st = st_out;
     a.sa = sa;
@@ -1695,21 +1952,29 @@ struct Solver {
     nlsp_ctx* ctx = M->ctx;
     PcgWork* w = M->pcg;
     cudaStream_t s = ctx->stream;
-    const int G = ctx->num_sms;
+    const int G = std::min(ctx->num_sms, XMAX_RANKS);
     const int cpg = cpg_for(M->r);
     const void* fn = persistent_fn(cpg);
     size_t avail = 0, smem = 0;
     NLSP_TRY(persistent_smem(cpg, &avail));
     StreamArgs sa;
     NLSP_TRY(plan_instance(M, G, cpg, true, avail, &sa, &smem));
-    PersistArgs<T> a = instance_args(M, b, x(w), prm, flexible, st_out, w->counter + 4, sa);
+    const size_t words = xw_words(M, G);
+    if (w->xw_cap < words) {
+      if (w->xw) cudaFree(w->xw);
+      w->xw = nullptr;
+      w->xw_cap = 0;
+      NLSP_CUDA(cudaMalloc(&w->xw, sizeof(unsigned long long) * words));
+      w->xw_cap = words;
+    }
+    PersistArgs<T> a = instance_args(M, b, x(w), prm, flexible, st_out, w->xw, (int*)(w->counter + 5), sa);
     int per_sm = 0;
     NLSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PT, smem));
     if (per_sm < 1) {
       nlsp_record_message("persistent solver: one CTA per SM does not fit (shared memory or registers)");
       return NLSP_ERR_INVALID;
     }
-    if ((int64_t)RED_COUNT * G > 4 * (int64_t)w->max_blocks || G > M->rblocks) return NLSP_ERR_INVALID;
+    NLSP_CUDA(cudaMemsetAsync(w->xw, 0, sizeof(unsigned long long) * words, s));
     NLSP_CUDA(cudaMemsetAsync(w->counter + 4, 0, sizeof(unsigned) * 2, s));
     const PersistArgs<T>* no_insts = nullptr;
     const int* no_begin = nullptr;
@@ -1784,17 +2049,15 @@ struct Solver {
                                    double* const* X, const nlsp_solve_params* prm, int tiles_per_cta,
                                    nlsp_solve_info* infos) {
     cudaStream_t s = ctx->stream;
-    const int G = ctx->num_sms;
+    const int G = std::min(ctx->num_sms, XMAX_RANKS);
     NLSP_TRY((prepare_stream_kernels<KIND, T>()));
     int rmax = 1;
     std::vector<int64_t> nn(count);
-    std::vector<int> cap(count);
+    std::vector<int> cap(count, G);
     for (int i = 0; i < count; ++i) {
       NLSP_TRY(ensure_work(Ms[i], 1));
       rmax = std::max(rmax, Ms[i]->r);
       nn[i] = Ms[i]->n;
-      // a team may not exceed the partial arrays of the instance's work
-      cap[i] = (int)std::min<int64_t>(Ms[i]->rblocks, 4 * (int64_t)Ms[i]->pcg->max_blocks / RED_COUNT);
     }
     const int cpg = cpg_for(rmax);
     const void* fn = persistent_fn(cpg);
@@ -1804,7 +2067,8 @@ struct Solver {
     std::vector<double> start(count);
     NLSP_TRY(nlsp_internal_plan_teams(count, nn.data(), cap.data(), G, tiles_per_cta, first.data(), size.data(),
                                       start.data()));
-    // device table: instances, CTA task ranges, tasks, barrier words, states
+    // device table: instances, CTA task ranges, tasks, abort flags and the
+    // progress word, states, exchange words
     std::vector<std::vector<TeamTask>> per(G);
     std::vector<std::pair<double, int>> key(count);
     for (int i = 0; i < count; ++i) key[i] = {start[i], i};
@@ -1818,11 +2082,18 @@ struct Solver {
     const size_t off_begin = align_up(sizeof(PersistArgs<T>) * count, 256);
     const size_t off_tasks = off_begin + align_up(sizeof(int) * (G + 1), 256);
     const size_t off_ctr = off_tasks + align_up(sizeof(TeamTask) * std::max(ntask, 1), 256);
-    const size_t off_st = off_ctr + align_up(sizeof(unsigned) * (2 * count + 1), 256);
-    const size_t bytes = off_st + sizeof(PcgState) * count;
+    const size_t off_st = off_ctr + align_up(sizeof(unsigned) * (count + 1), 256);
+    const size_t off_xw = off_st + align_up(sizeof(PcgState) * count, 256);
+    std::vector<size_t> xw_at(count);
+    size_t xw_total = 0;
+    for (int i = 0; i < count; ++i) {
+      xw_at[i] = xw_total;
+      xw_total += align_up(xw_words(Ms[i], size[i]), 32);
+    }
+    const size_t bytes = off_xw + sizeof(unsigned long long) * xw_total;
     unsigned char* dev = (unsigned char*)ctx_slot(ctx, SLOT_BATCH, bytes);
     if (!dev) return NLSP_ERR_OOM;
-    std::vector<unsigned char> host(bytes, 0);
+    std::vector<unsigned char> host(off_xw, 0);
     size_t smem = 0;
     for (int i = 0; i < count; ++i) {
       StreamArgs sa;
@@ -1831,9 +2102,10 @@ struct Solver {
       smem = std::max(smem, need);
       PersistArgs<T> a = instance_args(Ms[i], B[i], X[i], prm,
                                        prm->flexible < 0 ? (Ms[i]->precision != NLSP_FP64) : (prm->flexible != 0),
-                                       (PcgState*)(dev + off_st) + i, (unsigned*)(dev + off_ctr) + 2 * i, sa);
+                                       (PcgState*)(dev + off_st) + i,
+                                       (unsigned long long*)(dev + off_xw) + xw_at[i], (int*)(dev + off_ctr) + i, sa);
       a.ptimes = nullptr;
-      a.progress = (unsigned*)(dev + off_ctr) + 2 * count;
+      a.progress = (unsigned*)(dev + off_ctr) + count;
       memcpy(host.data() + sizeof(PersistArgs<T>) * i, &a, sizeof(a));
     }
     int* hb = (int*)(host.data() + off_begin);
@@ -1849,7 +2121,8 @@ struct Solver {
       nlsp_record_message("batched solver: one CTA per SM does not fit (shared memory or registers)");
       return NLSP_ERR_INVALID;
     }
-    NLSP_CUDA(cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, s));
+    NLSP_CUDA(cudaMemcpyAsync(dev, host.data(), off_xw, cudaMemcpyHostToDevice, s));
+    NLSP_CUDA(cudaMemsetAsync(dev + off_xw, 0, sizeof(unsigned long long) * xw_total, s));
     PersistArgs<T> one;
     memset(&one, 0, sizeof(one));
     const PersistArgs<T>* d_insts = (const PersistArgs<T>*)dev;
@@ -2017,10 +2290,10 @@ extern "C" nlsp_status nlsp_prec_phase_times(nlsp_ctx* ctx, const nlsp_prec* M, 
   if (!ctx || !M || !out_ns || count < 0) return NLSP_ERR_INVALID;
   for (int i = 0; i < count; ++i) out_ns[i] = 0.0;
   if (!M->pcg || !M->pcg->ptimes) return NLSP_OK;
-  unsigned long long h[2 * PH_COUNT];
+  unsigned long long h[PTIMES_LEN];
   NLSP_CUDA(cudaMemcpyAsync(h, M->pcg->ptimes, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   NLSP_CUDA(cudaStreamSynchronize(ctx->stream));
-  for (int i = 0; i < count && i < 2 * PH_COUNT; ++i) out_ns[i] = (double)h[i];
+  for (int i = 0; i < count && i < PTIMES_LEN; ++i) out_ns[i] = (double)h[i];
   NLSP_CUDA(cudaMemsetAsync(M->pcg->ptimes, 0, sizeof(h), ctx->stream));
   return NLSP_OK;
 }
