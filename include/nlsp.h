@@ -321,6 +321,41 @@ NLSP_API nlsp_status nlsp_plan_teams(int count, const int64_t* n, int num_ctas, 
                                      int* team_size, double* start);
 
 /* ---------------------------------------------------------------------------
+ * Differentiation (the objectives of Sec. 3 and the Appendix).
+ * ------------------------------------------------------------------------- */
+
+/* Subspace loss L = ||(I - Q Q^T) B||_F^2 with Q = qf(P_hat), the thin-Q
+   factor of P_hat (Sec. 3, "P = qf(P_hat)"; minimising this residual energy
+   maximises the subspace energy, Appendix on the optimality of smooth error
+   reduction), and optionally its gradient dL/dP_hat.  P_hat: n x k, B: n x K
+   (e.g. the smoothed samples), both FP64 column-major (ld = n), read during
+   the call.  precision: NLSP_FP64, or NLSP_MIXED_FP32 for FP32 arithmetic
+   with FP64 sums of the k x k / k x K products.  *loss is a host pointer;
+   dev_grad (n x k, FP64, ld = n) may be NULL.  k <= 128, K <= 256, P_hat of
+   full column rank.  Synchronises.  Errors: NLSP_ERR_INVALID,
+   NLSP_ERR_NOT_SPD (P_hat^T P_hat not positive definite), NLSP_ERR_CUDA,
+   NLSP_ERR_OOM. */
+NLSP_API nlsp_status nlsp_subspace_loss(nlsp_ctx* ctx, int64_t n, int k, int K, int precision,
+                                        const double* dev_Phat, const double* dev_B, double* loss, double* dev_grad);
+
+/* Unrolled-PCG loss L = ||r_T||_2 after exactly T PCG iterations (Sec. 4,
+   standard beta, x0 = 0) on A x = b with the two-level preconditioner of
+   Algorithm 1 built from the full-rank basis P (A_c = P^T A P, Cholesky;
+   nu pre- and post-sweeps of weighted Jacobi with weight omega), and
+   optionally dL/dP by reverse mode through the T iterations (the forward
+   states are kept as per-iteration checkpoints).  The paper trains with
+   subspace objectives only; this loss differentiates the solver itself.
+   P: n x k FP64 column-major (ld = n); b: FP64 length n; *loss host;
+   dev_grad (n x k, FP64, ld = n) may be NULL.  precision: NLSP_FP64, or
+   NLSP_MIXED_FP32 (FP32 preconditioner, FP64 recurrences).  k <= 128,
+   1 <= T <= 1000.  Synchronises.  Errors: NLSP_ERR_INVALID,
+   NLSP_ERR_NOT_SPD (A_c not positive definite), NLSP_ERR_CUDA,
+   NLSP_ERR_OOM. */
+NLSP_API nlsp_status nlsp_unrolled_pcg(nlsp_ctx* ctx, const nlsp_op* A, const double* dev_P, int k, int nu,
+                                       double omega, int precision, const double* dev_b, int T, double* loss,
+                                       double* dev_grad);
+
+/* ---------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper).
  * ------------------------------------------------------------------------- */
 
@@ -344,7 +379,8 @@ NLSP_API nlsp_status nlsp_bench_kernel(nlsp_ctx* ctx, const nlsp_prec* M, int wh
    mark or barrier release): spmv totals, spmv nodes, pre totals, pre nodes,
    restrict rho, restrict resident tiles, restrict streamed tiles, restrict
    reduction, prolong coarse solve, prolong resident tiles, prolong streamed
-   tiles, post nodes (26 values in all).  Recording is enabled by the environment variable
+   tiles, post nodes, spmv totals issued, spmv totals finished, restrict stage
+   A, restrict stage B, post stage (31 values in all).  Recording is enabled by the environment variable
    NLSP_PHASE_TIMERS=1 when the solver workspace is first created; otherwise
    zeros.  Synchronises. */
 NLSP_API nlsp_status nlsp_prec_phase_times(nlsp_ctx* ctx, const nlsp_prec* M, double* out_ns, int count);

@@ -261,3 +261,32 @@ def plan_teams(n: list[int], num_ctas: int, tiles_per_cta: int = 0):
     start = (C.c_double * count)()
     L.check(lib.nlsp_plan_teams(count, hn, num_ctas, tiles_per_cta, first, size, start), "nlsp_plan_teams")
     return list(first), list(size), list(start)
+
+
+def subspace_loss(ctx: Context, P_hat: torch.Tensor, B: torch.Tensor, precision: int = L.NLSP_FP64,
+                  grad: bool = True):
+    """L = ||(I - Q Q^T) B||_F^2 with Q = qf(P_hat) and dL/dP_hat
+    (nlsp_subspace_loss).  P_hat (n, k), B (n, K) float64 CUDA.  Returns
+    (loss as a Python float, gradient (n, k) or None)."""
+    n = P_hat.shape[0]
+    ps, k = _colmajor(P_hat, n)
+    bs, K = _colmajor(B, n)
+    g = torch.empty_like(ps) if grad else None
+    out = C.c_double()
+    L.check(ctx._lib.nlsp_subspace_loss(ctx.h, n, k, K, precision, _ptr(ps), _ptr(bs), C.byref(out),
+                                        _ptr(g) if grad else None), "nlsp_subspace_loss")
+    return out.value, (g.t() if grad else None)
+
+
+def unrolled_pcg(op: Operator, P: torch.Tensor, b: torch.Tensor, T: int = 10, nu: int = 2,
+                 omega: float = 2.0 / 3.0, precision: int = L.NLSP_FP64, grad: bool = True):
+    """||r_T|| after T PCG iterations with the two-level preconditioner
+    built from P, and its gradient dL/dP (nlsp_unrolled_pcg).  P (n, k),
+    b (n,) float64 CUDA.  Returns (loss, gradient (n, k) or None)."""
+    ps, k = _colmajor(P, op.n)
+    bs, _ = _colmajor(b, op.n)
+    g = torch.empty_like(ps) if grad else None
+    out = C.c_double()
+    L.check(op.ctx._lib.nlsp_unrolled_pcg(op.ctx.h, op.h, _ptr(ps), k, nu, omega, precision, _ptr(bs), T,
+                                          C.byref(out), _ptr(g) if grad else None), "nlsp_unrolled_pcg")
+    return out.value, (g.t() if grad else None)

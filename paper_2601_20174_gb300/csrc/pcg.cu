@@ -634,7 +634,8 @@ enum { PH_SPMV = 0, PH_PRE, PH_SMOOTH, PH_RESTRICT, PH_PROLONG, PH_POST, PH_OTHE
 // CTA 0 thread 0), stored after the phase timers.
 enum {
   MK_SPMV_TOTALS = 0, MK_SPMV_NODES, MK_PRE_TOTALS, MK_PRE_NODES, MK_RES_RHO, MK_RES_RESIDENT, MK_RES_STREAM,
-  MK_RES_REDUCE, MK_PRO_COARSE, MK_PRO_RESIDENT, MK_PRO_STREAM, MK_POST_NODES, MK_COUNT
+  MK_RES_REDUCE, MK_PRO_COARSE, MK_PRO_RESIDENT, MK_PRO_STREAM, MK_POST_NODES, MK_SPMV_ISSUE, MK_SPMV_FINISH,
+  MK_RES_STAGE_A, MK_RES_STAGE_B, MK_POST_STAGE, MK_COUNT
 };
 constexpr int PTIMES_LEN = 2 * PH_COUNT + MK_COUNT;
 
@@ -753,6 +754,38 @@ __device__ __forceinline__ void ring_issue(uint64_t* bar, T* buf, const T* P, in
 __device__ __forceinline__ bool ring_wait(uint64_t* bar, int nstage, unsigned j) {
   return tma::mbar_wait(&bar[j % (unsigned)nstage], (j / (unsigned)nstage) & 1u);
 }
+
+// Node loop over [lo, hi) with stride PT, U nodes per thread at a time:
+// f(m) (loads and arithmetic only) for all U nodes first, then store(m, v)
+// for each, so the loads of the U nodes are in flight together (a store
+// through a generic pointer would otherwise keep the next node's loads
+// behind it).  store() runs in node order.
+template <int U, typename F, typename S>
+__device__ __forceinline__ void node_batches(int lo, int hi, F f, S store) {
+  using V = decltype(f(lo));
+  for (int m0 = lo + (int)threadIdx.x; m0 < hi; m0 += U * PT) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int m = m0 + u * PT;
+      if (m < hi) v[u] = f(m);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int m = m0 + u * PT;
+      if (m < hi) store(m, v[u]);
+    }
+  }
+}
+
+template <typename T>
+struct RhoZ {
+  T rho, z;
+};
+
+struct PostVals {
+  double zd, ri, zo;
+};
 
 // CPG = columns of P per warp group (4 groups of 4 warps; r_pad = 4 CPG).
 // The CTA's first n_tm tiles of P live in tensor memory (FP32 path), the next
@@ -940,29 +973,37 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       // presmooth_at, without recomputing z1 and z2 at every neighbour.
       T* z1s = buf;
       T* z2s = buf + (e2hi - e2lo);
-      for (int m = e2lo + tid; m < e2hi; m += PT) z1s[m - e2lo] = omega * stencil_dinv<KIND>(a.AT, m) * a.rT[m];
+      node_batches<4>(
+          e2lo, e2hi, [&](int m) { return omega * stencil_dinv<KIND>(a.AT, m) * a.rT[m]; },
+          [&](int m, T v) { z1s[m - e2lo] = v; });
       __syncthreads();
+      mark(MK_RES_STAGE_A);
       if (zm == 2) {
-        for (int m = e1lo + tid; m < e1hi; m += PT) {
-          const T az = stencil_apply<KIND>(a.AT, m, node_coord<KIND>(m, a.AT.N),
-                                           [&](int64_t mm) { return z1s[mm - e2lo]; });
-          z2s[m - e1lo] = z1s[m - e2lo] + omega * stencil_dinv<KIND>(a.AT, m) * (a.rT[m] - az);
-        }
+        node_batches<1>(
+            e1lo, e1hi,
+            [&](int m) {
+              const T az = stencil_apply<KIND>(a.AT, m, node_coord<KIND>(m, a.AT.N),
+                                               [&](int64_t mm) { return z1s[mm - e2lo]; });
+              return z1s[m - e2lo] + omega * stencil_dinv<KIND>(a.AT, m) * (a.rT[m] - az);
+            },
+            [&](int m, T v) { z2s[m - e1lo] = v; });
         __syncthreads();
+        mark(MK_RES_STAGE_B);
       }
       const T* zs = zm == 2 ? z2s : z1s;
       const int zlo = zm == 2 ? e1lo : e2lo;
-      for (int e = tid; e < nt * NLSP_TILE; e += PT) {
-        const int i = i0 + e;
-        T rho = T(0);
-        if (i < n) {
-          const T az = stencil_apply<KIND>(a.AT, i, node_coord<KIND>(i, a.AT.N),
-                                           [&](int64_t mm) { return zs[mm - zlo]; });
-          rho = a.rT[i] - az;
-          a.zw[i] = zs[i - zlo];
-        }
-        rho_s[e] = rho;
-      }
+      node_batches<1>(
+          i0, i1,
+          [&](int i) {
+            const T az = stencil_apply<KIND>(a.AT, i, node_coord<KIND>(i, a.AT.N),
+                                             [&](int64_t mm) { return zs[mm - zlo]; });
+            return RhoZ<T>{a.rT[i] - az, zs[i - zlo]};
+          },
+          [&](int i, RhoZ<T> v) {
+            rho_s[i - i0] = v.rho;
+            a.zw[i] = v.z;
+          });
+      for (int e = (i1 - i0) + tid; e < nt * NLSP_TILE; e += PT) rho_s[e] = T(0);  // ragged last tile
       __syncthreads();  // the ring buffer is free again
       for (int s = 0; s < nstage && s < nst; ++s)
         if (tid == 0) ring_issue(mbar, buf, a.P, k, r, nstage, jc + s, tst + s);
@@ -1194,20 +1235,35 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       // first post-sweep on the own nodes and one grid row around them into
       // the (idle) ring buffer, the second one below reads it
       T* z3s = buf;
-      for (int m = e1lo + tid; m < e1hi; m += PT) {
-        const T az = stencil_apply<KIND>(a.AT, m, node_coord<KIND>(m, a.AT.N), [&](int64_t mm) { return cur[mm]; });
-        z3s[m - e1lo] = cur[m] + omega * stencil_dinv<KIND>(a.AT, m) * (a.rT[m] - az);
-      }
+      node_batches<1>(
+          e1lo, e1hi,
+          [&](int m) {
+            const T az =
+                stencil_apply<KIND>(a.AT, m, node_coord<KIND>(m, a.AT.N), [&](int64_t mm) { return cur[mm]; });
+            return cur[m] + omega * stencil_dinv<KIND>(a.AT, m) * (a.rT[m] - az);
+          },
+          [&](int m, T v) { z3s[m - e1lo] = v; });
       __syncthreads();
+      mark(MK_POST_STAGE);
+      const T* z3c = buf;
+      node_batches<1>(
+          i0, i1,
+          [&](int i) {
+            const T az4 = stencil_apply<KIND>(a.AT, i, node_coord<KIND>(i, a.AT.N),
+                                              [&](int64_t mm) { return z3c[mm - e1lo]; });
+            const T zf = z3c[i - e1lo] + omega * stencil_dinv<KIND>(a.AT, i) * (a.rT[i] - az4);
+            return PostVals{(double)zf, a.r[i], flex ? zold64[i] : 0.0};
+          },
+          [&](int i, PostVals v) {
+            zout64[i] = v.zd;
+            s_rz = fma(v.ri, v.zd, s_rz);
+            if (flex) s_ro = fma(v.ri, v.zo, s_ro);
+          });
     }
-    for (int i = i0 + tid; i < i1; i += PT) {
+    for (int i = i0 + tid; i < (staged ? 0 : i1); i += PT) {
       const NodeCoord c = node_coord<KIND>(i, a.AT.N);
       T zf;
-      if (staged) {
-        const T* z3s = buf;
-        const T az4 = stencil_apply<KIND>(a.AT, i, c, [&](int64_t mm) { return z3s[mm - e1lo]; });
-        zf = z3s[i - e1lo] + omega * stencil_dinv<KIND>(a.AT, i) * (a.rT[i] - az4);
-      } else if (nfinal == 2) {
+      if (nfinal == 2) {
         auto z4at = [&](int64_t m, NodeCoord cm) -> T {
           const T az = stencil_apply<KIND>(a.AT, m, cm, [&](int64_t mm) { return cur[mm]; });
           return cur[m] + omega * stencil_dinv<KIND>(a.AT, m) * (a.rT[m] - az);
@@ -1278,8 +1334,10 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         zv[u] = iu < i1 ? __ldcg(zc + iu) : 0.0;
         pv4[u] = iu < i1 ? __ldcg(pin + iu) : 0.0;
       }
+      mark(MK_SPMV_ISSUE);
       double tot[2] = {0.0, 0.0};
       if (!tot_finish(2, tot)) break;
+      mark(MK_SPMV_FINISH);
       const double rzn = tot[0], ro = a.flexible ? tot[1] : 0.0;
       if (!(rzn > 0.0) || !isfinite(rzn)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
       if (t > 0) {

@@ -40,12 +40,12 @@ def main() -> int:
     print(f"profile case: n={p.n} k={p.k} iterations={res[0].iterations} status={res[0].status}")
     if args.mode == 2:
         import ctypes as C
-        out = (C.c_double * 26)()
-        L.check(ctx._lib.nlsp_prec_phase_times(ctx.h, M.h, out, 26), "nlsp_prec_phase_times")
+        out = (C.c_double * 31)()
+        L.check(ctx._lib.nlsp_prec_phase_times(ctx.h, M.h, out, 31), "nlsp_prec_phase_times")
         names = ["spmv", "pre", "stored sweeps", "restrict", "prolong", "post", "other"]
         marks = ["spmv totals", "spmv nodes", "pre totals", "pre nodes", "restrict rho", "restrict resident",
                  "restrict streamed", "restrict reduce", "prolong coarse", "prolong resident", "prolong streamed",
-                 "post nodes"]
+                 "post nodes", "spmv issue", "spmv finish", "restrict stage A", "restrict stage B", "post stage"]
         it = max(1, res[0].iterations)
         for i, name in enumerate(names):
             print(f"  {name:18s} work {out[2 * i] / 1e3 / it:8.2f} us/it   barrier wait {out[2 * i + 1] / 1e3 / it:8.2f} us/it")
