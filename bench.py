@@ -40,9 +40,9 @@ FLUSH_BYTES = 256 << 20
 
 
 def _profiled_traffic(k: int, iterations: int):
-    """DRAM bytes (read + write) of one persistent-solver launch, scaled from the
-    per-iteration figure of the committed ncu summary -- only while the kernel
-    source is unchanged since that capture (else None)."""
+    """DRAM bytes (read + write) of one persistent-solver launch from the
+    committed two-point ncu fit (fixed + per-iteration bytes) -- only while
+    the kernel source is unchanged since that capture (else None)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "k_pcg_persistent_grf512_k64.json")) as f:
@@ -50,7 +50,7 @@ def _profiled_traffic(k: int, iterations: int):
         src = open(os.path.join(ROOT, "paper_2601_20174_gb300", "csrc", "pcg.cu"), "rb").read()
         if hashlib.sha256(src).hexdigest() != prof["pcg_cu_sha256"] or prof["k"] != k:
             return None
-        return prof["dram_bytes_per_iteration"] * iterations
+        return prof["dram_bytes_fixed"] + prof["dram_bytes_per_iteration"] * iterations
     except Exception:
         return None
 
@@ -189,6 +189,62 @@ BATCH = dict(count=256, seed=0, tol=1e-8, tiles_per_cta=(2, 4, 8, 16, 32, 64))
 BATCH_DESC = ("256 2D diffusion 5-point instances, sides drawn from {64,128,192,256,384,512}, log-kappa i.i.d. "
               "N(0,1) per cell, ranks k from {16,32,64}, K = 2k device-drawn samples (s1=20, omega=2/3), nu=2, "
               "1 RHS U[-1,1] each, tol 1e-8, FP32 preconditioner / FP64 PCG")
+
+
+DIFF = dict(N=64, k=64, K=128, s1=20, nu=2, omega=2.0 / 3.0, T=10, seed=0, noise=0.1)
+DIFF_DESC = ("3D diffusion 7-point 64^3 (n=262144), log-kappa i.i.d. N(0,1) per cell, k=64, K=128 smoothed "
+             "device-drawn samples; subspace loss ||(I-QQ^T)B||^2 at P_hat = SVD basis + N(0,0.1^2) noise, and "
+             "||r_T|| after T=10 unrolled PCG steps (nu=2, omega=2/3) at the SVD basis; FP32 arithmetic, "
+             "gradients by the library's reverse sweep")
+
+
+def run_differentiation(ctx, dev, timed):
+    """Loss + gradient of both objectives on the 64^3 problem (FP32), with
+    the FP64 results beside them for the error of the FP32 production path."""
+    import statistics as st
+    import ctypes as C
+
+    import torch
+
+    from paper_2601_20174_gb300 import _lib as L, api, inputs as gen
+
+    p = gen.iid_diffusion_3d(DIFF["N"], DIFF["k"], DIFF["K"], seed=DIFF["seed"], with_samples=False)
+    n, k, K = p.n, DIFF["k"], DIFF["K"]
+    A = api.Operator(ctx, 3, p.N, 7, torch.as_tensor(p.coeffs.reshape(-1)).to(dev), L.NLSP_COEF_CELL_KAPPA)
+    S0 = torch.empty(K, n, dtype=torch.float64, device=dev)
+    L.check(ctx._lib.nlsp_random_normal(ctx.h, p.seed, gen.STREAM_S0, 0, n * K, C.c_void_p(S0.data_ptr())),
+            "nlsp_random_normal")
+    B = torch.empty_like(S0)
+    L.check(ctx._lib.nlsp_smooth_samples(ctx.h, A.h, K, DIFF["s1"], DIFF["omega"], L.NLSP_FP64,
+                                         C.c_void_p(S0.data_ptr()), C.c_void_p(B.data_ptr())), "smooth")
+    M = api.Preconditioner.build(A, None, k, DIFF["s1"], DIFF["nu"], DIFF["omega"], L.NLSP_FP64, K=K, seed=p.seed)
+    U = M.basis().contiguous()
+    noise = torch.empty(k, n, dtype=torch.float64, device=dev)
+    L.check(ctx._lib.nlsp_random_normal(ctx.h, p.seed, gen.STREAM_NOISE, 0, n * k, C.c_void_p(noise.data_ptr())),
+            "nlsp_random_normal")
+    Ph = U + DIFF["noise"] * noise.t()
+    Bt = B.t()
+    b = torch.as_tensor(p.f[:, 0].copy()).to(dev)
+    out = {"workload": DIFF_DESC}
+    for name, fn in (("subspace", lambda prec: api.subspace_loss(ctx, Ph, Bt, prec)),
+                     ("unrolled_pcg", lambda prec: api.unrolled_pcg(A, U, b, DIFF["T"], DIFF["nu"], DIFF["omega"],
+                                                                     prec))):
+        fn(L.NLSP_MIXED_FP32)  # warm
+        ms, (l32, g32) = timed(lambda: fn(L.NLSP_MIXED_FP32), 3)
+        l64, g64 = fn(L.NLSP_FP64)
+        out[name] = {"ms_loss_and_grad": st.median(ms), "loss_fp32": l32, "loss_fp64": l64,
+                     "grad_rel_err_fp32_vs_fp64": float(torch.linalg.norm(g32 - g64) / torch.linalg.norm(g64)),
+                     "range_invariance": float(torch.linalg.norm(Ph.t() @ g64 if name == "subspace" else U.t() @ g64)
+                                               / torch.linalg.norm(g64))}
+    # algorithmic bytes of the subspace pass: FP64 inputs read, FP32 tiled
+    # copies written and read by the two products and the gradient pass,
+    # gradient written (FP64)
+    sub_bytes = n * (k + K) * 8 + n * (k + K) * 4 * 3 + n * k * 8
+    out["subspace"]["algorithmic_bytes"] = sub_bytes
+    out["subspace"]["achieved_gbs"] = sub_bytes / (out["subspace"]["ms_loss_and_grad"] / 1e3) / 1e9
+    M.close()
+    A.close()
+    return out
 
 
 def run_batched(ctx, dev, timed, rank):
@@ -351,6 +407,11 @@ def run_ours(args):
     traffic = _profiled_traffic(WL["k"], it_s)
     roof = {"kernel": "k_pcg_persistent", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
+            "traffic_note": "DRAM read+write bytes per launch from the committed two-point ncu fit "
+                            "(profiles/k_pcg_persistent_grf512_k64.json): a fixed ~83 MB (loading the resident P "
+                            "tiles and vectors) and ~0 per iteration, since the iteration runs out of tensor "
+                            "memory, shared memory and L2; the kernel is bound by on-chip latency and grid "
+                            "synchronisation rather than HBM",
             "peak_kind": f"{peak_kind} (copy, burst)",
             "algorithmic_bytes_per_iteration": alg_iter, "iterations": it_s,
             "timing": "solve-only launches (one persistent kernel per solve), CUDA events on the library stream, "
@@ -390,6 +451,7 @@ def run_ours(args):
 
     # ---- batched: 256 uneven instances in one persistent launch ----------
     batched = None if args.no_batched else run_batched(ctx, dev, timed, rank)
+    differentiation = None if args.no_differentiation else run_differentiation(ctx, dev, timed)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -417,7 +479,8 @@ def run_ours(args):
                                "true_relres": res_d.true_relres},
                 "roofline": roof, "kernels": kern,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * 8},
-                "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu, "batched": batched}
+                "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu, "batched": batched,
+                "differentiation": differentiation}
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
@@ -433,6 +496,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched leg")
+    ap.add_argument("--no-differentiation", action="store_true", help="skip the differentiation leg")
     ap.add_argument("--graph-mode", type=int, default=2, choices=[0, 1, 2],
                     help="2: one persistent cooperative kernel per solve (default); 1: PCG loop as one graph "
                          "with a device-side while node; 0: one-iteration graph relaunched by the host "
