@@ -286,6 +286,20 @@ NLSP_API nlsp_status nlsp_solve(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec
                        int64_t ldb, double* dev_X, int64_t ldx, const nlsp_solve_params* params,
                        nlsp_solve_info* infos);
 
+/* Block PCG: A X = B for m <= 32 right-hand sides advanced together, one
+   independent PCG recurrence per column (Sec. 4), so that each
+   preconditioner application (Algorithm 1) reads P once for all columns: the
+   restriction is the dense product P_r^T rho (r x m) and the prolongation
+   P_r E (n x m).  Same arguments, stopping rule and per-column results as
+   nlsp_solve (params->graph_mode is ignored); x0 = 0.  Uses the active rank
+   r <= 128 of M.  Allocates its block workspace (about 80 m n bytes) for the
+   duration of the call.  Synchronises.  Errors: NLSP_ERR_INVALID,
+   NLSP_ERR_CUDA, NLSP_ERR_OOM; per-column NLSP_NOT_CONVERGED /
+   NLSP_ERR_BREAKDOWN as nlsp_solve. */
+NLSP_API nlsp_status nlsp_solve_block(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec* M, int m,
+                                      const double* dev_B, int64_t ldb, double* dev_X, int64_t ldx,
+                                      const nlsp_solve_params* params, nlsp_solve_info* infos);
+
 /* Batched solve: instance i solves A_i x_i = b_i by PCG with its own
    preconditioner M[i] (Sec. 4 per instance; the paper solves its instances
    one after another and has no batched counterpart).  One cooperative launch

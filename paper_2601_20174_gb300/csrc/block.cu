@@ -1,0 +1,574 @@
+// Block PCG: m <= 32 right-hand sides advance together (independent
+// recurrences, one per column; Sec. 4 PCG with the two-level preconditioner
+// of Algorithm 1), so each preconditioner application reads P once for all
+// columns: the restriction is the dense product P^T rho (k x m) and the
+// prolongation P E (n x m).
+//
+// Layout: block vectors are node-major with a row of 32 columns per node
+// (element (i, c) at i * 32 + c), so a warp holds one node's row (lane =
+// column) and every stencil neighbour is one coalesced row.  Columns beyond m
+// are zero and never iterate.  The PCG recurrences and their dot products are
+// FP64; the preconditioner runs in its own precision T (FP32 or FP64).
+// Per-column scalars (alpha, beta, r^T z, convergence, iteration counts)
+// stay on the device; the host relaunches a captured iteration graph in
+// chunks and reads one "all columns done" word between chunks.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "stencil.cuh"
+
+namespace {
+
+constexpr int MB = 32;        // columns per node row
+constexpr int BT = 256;       // threads per block (8 warps)
+constexpr int BW = BT / 32;   // warps per block
+
+// Per-column state of the block recurrences (device).
+struct BlockState {
+  double bb[MB], tol2bn[MB], rz[MB], rr[MB], alpha[MB], beta[MB], true_rr[MB];
+  int iter[MB], done[MB], status[MB];
+  int all_done, maxit, flexible, m;
+  int t;  // iterations started (A p products formed)
+};
+
+// Sum of the warps' per-column partials of a block, written to part[block][c].
+__device__ __forceinline__ void block_col_partial(double v, double (*sm)[MB], double* part) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  sm[w][lane] = v;
+  __syncthreads();
+  if (w == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < BW; ++q) s += sm[q][lane];
+    part[(int64_t)blockIdx.x * MB + lane] = s;
+  }
+}
+
+// p = z + beta p (beta = 0 before the first iteration, p = 0 initially)
+__global__ void __launch_bounds__(BT) k_b_dir(const double* __restrict__ z, double* __restrict__ p, int64_t n,
+                                             const BlockState* st) {
+  const int lane = threadIdx.x & 31;
+  const double beta = st->beta[lane];
+  for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < n * MB; e += (int64_t)gridDim.x * BT)
+    p[e] = fma(beta, p[e], z[e]);
+}
+
+// q = A p, per-column partials of p^T q
+template <int KIND>
+__global__ void __launch_bounds__(BT) k_b_spmv(StencilView<double> A, const double* __restrict__ p,
+                                              double* __restrict__ q, double* __restrict__ part) {
+  __shared__ double sm[BW][MB];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * BW + (threadIdx.x >> 5), ws = (int64_t)gridDim.x * BW;
+  double s = 0.0;
+  for (int64_t i = w0; i < A.n; i += ws) {
+    const double qi = stencil_apply<KIND>(A, i, node_coord<KIND>(i, A.N), [&](int64_t m) { return p[m * MB + lane]; });
+    q[i * MB + lane] = qi;
+    s = fma(p[i * MB + lane], qi, s);
+  }
+  block_col_partial(s, sm, part);
+}
+
+// x += alpha p, r -= alpha q, rT = r (precision T), z1 = w D^-1 rT (first
+// pre-sweep from zero), per-column partials of r^T r
+template <int KIND, typename T>
+__global__ void __launch_bounds__(BT) k_b_update(StencilView<T> A, T omega, double* __restrict__ x,
+                                                double* __restrict__ r, const double* __restrict__ p,
+                                                const double* __restrict__ q, T* __restrict__ rT,
+                                                T* __restrict__ z1, const BlockState* st,
+                                                double* __restrict__ part) {
+  __shared__ double sm[BW][MB];
+  const int lane = threadIdx.x & 31;
+  const double alpha = st->alpha[lane];
+  const int64_t w0 = (int64_t)blockIdx.x * BW + (threadIdx.x >> 5), ws = (int64_t)gridDim.x * BW;
+  double s = 0.0;
+  for (int64_t i = w0; i < A.n; i += ws) {
+    const int64_t e = i * MB + lane;
+    x[e] = fma(alpha, p[e], x[e]);
+    const double rn = fma(-alpha, q[e], r[e]);
+    r[e] = rn;
+    const T rt = (T)rn;
+    rT[e] = rt;
+    z1[e] = omega * stencil_dinv<KIND>(A, i) * rt;
+    s = fma(rn, rn, s);
+  }
+  block_col_partial(s, sm, part);
+}
+
+// zout = zin + w D^-1 (rT - A zin)  (pre-sweeps 2..nu and post-sweeps)
+template <int KIND, typename T>
+__global__ void __launch_bounds__(BT) k_b_sweep(StencilView<T> A, T omega, const T* __restrict__ rT,
+                                               const T* __restrict__ zin, T* __restrict__ zout) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * BW + (threadIdx.x >> 5), ws = (int64_t)gridDim.x * BW;
+  for (int64_t i = w0; i < A.n; i += ws) {
+    const T az = stencil_apply<KIND>(A, i, node_coord<KIND>(i, A.N), [&](int64_t m) { return zin[m * MB + lane]; });
+    const int64_t e = i * MB + lane;
+    zout[e] = zin[e] + omega * stencil_dinv<KIND>(A, i) * (rT[e] - az);
+  }
+}
+
+// Restriction of the residual after the pre-sweeps: per block, over its node
+// tiles, C_b = P_t^T rho_t (k x 32) with rho = rT - A z.  The tile's rho
+// (128 x 32) and its P rows, transposed to [node][k + 1], are staged in
+// shared memory; thread (jb, cb) owns a 4 x 4 register tile of C.
+template <int KIND, typename T>
+__global__ void __launch_bounds__(BT) k_b_restrict(StencilView<T> A, const T* __restrict__ rT,
+                                                  const T* __restrict__ z, const T* __restrict__ P, int kst,
+                                                  int k, int64_t ntiles, T* __restrict__ cpart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int kp = k + 1;
+  T* ps = reinterpret_cast<T*>(smem_raw);         // [128][k + 1]
+  T* rs = ps + (size_t)NLSP_TILE * kp;            // [128][33]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int jb = threadIdx.x >> 3, cb = threadIdx.x & 7;  // j = 4 jb .. (k <= 128), c = 4 cb ..
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    __syncthreads();
+    // rho rows of the tile's nodes (warp per node, lane = column)
+    for (int wn = w; wn < NLSP_TILE; wn += BW) {
+      const int64_t i = t * NLSP_TILE + wn;
+      T rho = T(0);
+      if (i < A.n) {
+        const T az =
+            stencil_apply<KIND>(A, i, node_coord<KIND>(i, A.N), [&](int64_t m) { return z[m * MB + lane]; });
+        rho = rT[i * MB + lane] - az;
+      }
+      rs[wn * 33 + lane] = rho;
+    }
+    // P tile transposed: ps[node][j]
+    const T* src = P + t * kst * NLSP_TILE;  // the first k of the tile's kst columns
+    for (int e = threadIdx.x; e < k * NLSP_TILE; e += BT) {
+      const int j = e / NLSP_TILE, wn = e % NLSP_TILE;
+      ps[wn * kp + j] = src[e];
+    }
+    __syncthreads();
+    if (4 * jb < k) {
+      for (int wn = 0; wn < NLSP_TILE; ++wn) {
+        T pa[4], rb[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) pa[a] = 4 * jb + a < k ? ps[wn * kp + 4 * jb + a] : T(0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rb[b] = rs[wn * 33 + 4 * cb + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += pa[a] * rb[b];
+      }
+    }
+  }
+  if (4 * jb < k) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (4 * jb + a < k) cpart[((int64_t)blockIdx.x * k + 4 * jb + a) * MB + 4 * cb + b] = acc[a][b];
+  }
+}
+
+// C = sum of the block partials (block order), E = A_c^-1 C  (k x 32, in T).
+template <typename T>
+__global__ void k_b_coarse(const T* __restrict__ cpart, int nb, int k, const double* __restrict__ Ainv,
+                           T* __restrict__ E) {
+  extern __shared__ double cs[];  // [k][32]
+  for (int e = threadIdx.x; e < k * MB; e += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += (double)cpart[(int64_t)b * k * MB + e];
+    cs[e] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * MB; e += blockDim.x) {
+    const int i = e / MB, c = e % MB;
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s = fma(Ainv[(int64_t)j * k + i], cs[j * MB + c], s);
+    E[e] = (T)s;
+  }
+}
+
+// z += P E (warp per node, lane = column; the node's P row is a broadcast)
+template <typename T>
+__global__ void __launch_bounds__(BT) k_b_prolong(const T* __restrict__ P, int kst, int k, int64_t n,
+                                                 const T* __restrict__ E, T* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* es = reinterpret_cast<T*>(smem_raw);  // [k][32]
+  for (int e = threadIdx.x; e < k * MB; e += BT) es[e] = E[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * BW + (threadIdx.x >> 5), ws = (int64_t)gridDim.x * BW;
+  for (int64_t i = w0; i < n; i += ws) {
+    const T* prow = P + ((i >> 7) * kst) * NLSP_TILE + (i & 127);
+    T s = T(0);
+    for (int j = 0; j < k; ++j) s += prow[(int64_t)j * NLSP_TILE] * es[j * MB + lane];
+    z[i * MB + lane] += s;
+  }
+}
+
+// Last post-sweep: z = zin + w D^-1 (rT - A zin) stored in FP64, with the
+// per-column partials of r^T z and r^T z_old (flexible beta).
+template <int KIND, typename T>
+__global__ void __launch_bounds__(BT) k_b_post(StencilView<T> A, T omega, const T* __restrict__ rT,
+                                              const T* __restrict__ zin, const double* __restrict__ r,
+                                              double* __restrict__ zout, double* __restrict__ part) {
+  __shared__ double sm[BW][MB];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * BW + (threadIdx.x >> 5), ws = (int64_t)gridDim.x * BW;
+  double s_rz = 0.0, s_ro = 0.0;
+  for (int64_t i = w0; i < A.n; i += ws) {
+    const T az = stencil_apply<KIND>(A, i, node_coord<KIND>(i, A.N), [&](int64_t m) { return zin[m * MB + lane]; });
+    const int64_t e = i * MB + lane;
+    const double zd = (double)(zin[e] + omega * stencil_dinv<KIND>(A, i) * (rT[e] - az));
+    const double ri = r[e];
+    s_ro = fma(ri, zout[e], s_ro);  // the previous z
+    zout[e] = zd;
+    s_rz = fma(ri, zd, s_rz);
+  }
+  block_col_partial(s_rz, sm, part);
+  __syncthreads();
+  block_col_partial(s_ro, sm, part + (int64_t)gridDim.x * MB);
+}
+
+enum BlockStage { BS_INIT = 0, BS_PQ, BS_RR, BS_RZ };
+
+// Per-column scalar step from the block partials (one warp, lane = column).
+__global__ void k_b_scalars(const double* __restrict__ part, int nb, BlockState* st, int stage) {
+  const int c = threadIdx.x;
+  const int t = st->t;  // read before any lane may advance it
+  __syncwarp();
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = 0; b < nb; ++b) s0 += part[(int64_t)b * MB + c];
+  if (stage == BS_RZ && st->flexible)
+    for (int b = 0; b < nb; ++b) s1 += part[(int64_t)(nb + b) * MB + c];
+  const bool active = c < st->m && !st->done[c];
+  switch (stage) {
+    case BS_INIT:  // s0 = b^T b
+      st->bb[c] = s0;
+      st->rr[c] = s0;
+      st->tol2bn[c] = 0.0;
+      st->iter[c] = 0;
+      st->status[c] = (int)NLSP_OK;
+      st->alpha[c] = 0.0;
+      st->beta[c] = 0.0;
+      st->done[c] = c >= st->m ? 1 : 0;
+      if (c < st->m) {
+        if (s0 == 0.0) st->done[c] = 1;
+        else if (!isfinite(s0)) { st->status[c] = (int)NLSP_ERR_BREAKDOWN; st->done[c] = 1; }
+      }
+      break;
+    case BS_PQ:  // s0 = p^T q; starts iteration t + 1
+      if (c == 0) st->t = t + 1;
+      if (active) {
+        st->iter[c] = t + 1;
+        if (!(s0 > 0.0) || !isfinite(s0)) {
+          st->status[c] = (int)NLSP_ERR_BREAKDOWN;
+          st->done[c] = 1;
+          st->alpha[c] = 0.0;
+        } else {
+          st->alpha[c] = st->rz[c] / s0;
+        }
+      } else {
+        st->alpha[c] = 0.0;
+      }
+      break;
+    case BS_RR:  // s0 = r^T r after the update
+      if (active) {
+        st->rr[c] = s0;
+        if (!isfinite(s0)) { st->status[c] = (int)NLSP_ERR_BREAKDOWN; st->done[c] = 1; }
+        else if (s0 <= st->tol2bn[c]) st->done[c] = 1;
+        else if (t >= st->maxit) { st->status[c] = (int)NLSP_NOT_CONVERGED; st->done[c] = 1; }
+      }
+      break;
+    case BS_RZ:  // s0 = r^T z, s1 = r^T z_old
+      if (active) {
+        if (!(s0 > 0.0) || !isfinite(s0)) {
+          st->status[c] = (int)NLSP_ERR_BREAKDOWN;
+          st->done[c] = 1;
+        } else {
+          st->beta[c] = t == 0 ? 0.0 : (s0 - (st->flexible ? s1 : 0.0)) / st->rz[c];
+          st->rz[c] = s0;
+        }
+      }
+      if (!active) st->beta[c] = 0.0;
+      break;
+    default:
+      break;
+  }
+  __syncwarp();
+  const unsigned pend = __ballot_sync(0xffffffffu, c < st->m && !st->done[c]);
+  if (c == 0) st->all_done = pend == 0u;
+}
+
+__global__ void k_b_set_tol(BlockState* st, double tol) {
+  const int c = threadIdx.x;
+  st->tol2bn[c] = tol * tol * st->bb[c];
+}
+
+// column-major (ld) <-> node rows of 32
+__global__ void k_b_gather(const double* __restrict__ src, int64_t ld, int m, int64_t n, double* __restrict__ dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * MB; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / MB;
+    const int c = (int)(e % MB);
+    dst[e] = c < m ? src[(int64_t)c * ld + i] : 0.0;
+  }
+}
+
+__global__ void k_b_scatter(const double* __restrict__ src, int m, int64_t n, double* __restrict__ dst, int64_t ld) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / n);
+    const int64_t i = e % n;
+    dst[(int64_t)c * ld + i] = src[i * MB + c];
+  }
+}
+
+// true residual partials: ||b - A x||^2 per column
+template <int KIND>
+__global__ void __launch_bounds__(BT) k_b_true(StencilView<double> A, const double* __restrict__ b,
+                                              const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double sm[BW][MB];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * BW + (threadIdx.x >> 5), ws = (int64_t)gridDim.x * BW;
+  double s = 0.0;
+  for (int64_t i = w0; i < A.n; i += ws) {
+    const double ri =
+        b[i * MB + lane] - stencil_apply<KIND>(A, i, node_coord<KIND>(i, A.N), [&](int64_t m) { return x[m * MB + lane]; });
+    s = fma(ri, ri, s);
+  }
+  block_col_partial(s, sm, part);
+}
+
+__global__ void k_b_true_fin(const double* __restrict__ part, int nb, BlockState* st) {
+  const int c = threadIdx.x;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(int64_t)b * MB + c];
+  st->true_rr[c] = s;
+}
+
+__global__ void k_b_dot_init(const double* __restrict__ b, int64_t n, double* __restrict__ part) {
+  __shared__ double sm[BW][MB];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * BW + (threadIdx.x >> 5), ws = (int64_t)gridDim.x * BW;
+  double s = 0.0;
+  for (int64_t i = w0; i < n; i += ws) s = fma(b[i * MB + lane], b[i * MB + lane], s);
+  block_col_partial(s, sm, part);
+}
+
+}  // namespace
+
+// ============================================================================
+// Host side
+// ============================================================================
+namespace {
+
+template <typename T>
+const StencilView<T>& bview(const nlsp_op* A) {
+  return *reinterpret_cast<const StencilView<T>*>(sizeof(T) == 8 ? (const void*)&A->v64 : (const void*)&A->v32);
+}
+
+template <int KIND, typename T>
+struct BlockSolver {
+  static nlsp_status run(nlsp_ctx* ctx, const nlsp_prec* M, int m, const double* B, int64_t ldb, double* X,
+                         int64_t ldx, const nlsp_solve_params* prm, nlsp_solve_info* infos) {
+    cudaStream_t s = ctx->stream;
+    const nlsp_op* A = M->A;
+    const int64_t n = A->n, n_pad = M->n_pad;
+    const int k = M->r;  // active rank
+    const int nu = M->nu1;
+    const T omega = (T)M->omega;
+    const StencilView<T>& AT = bview<T>(A);
+    const int nb = std::max(1, std::min<int>(ctx->num_sms * 8, (int)((n + BW - 1) / BW)));
+    const int64_t ntiles = n_pad / NLSP_TILE;
+    const int nbr = (int)std::max<int64_t>(1, std::min<int64_t>(2 * ctx->num_sms, ntiles));
+    const int flexible = prm->flexible < 0 ? (M->precision != NLSP_FP64) : (prm->flexible != 0);
+    // workspace
+    const size_t nv = (size_t)n * MB;
+    const size_t bytes = sizeof(double) * nv * 6 + sizeof(T) * nv * 4 + sizeof(double) * (size_t)2 * nb * MB +
+                         sizeof(T) * (size_t)nbr * k * MB + sizeof(T) * (size_t)k * MB + sizeof(BlockState) + 4096;
+    DevBuf buf;
+    NLSP_TRY(buf.alloc(bytes));
+    unsigned char* base = buf.as<unsigned char>();
+    size_t off = 0;
+    auto take = [&](size_t b) {
+      unsigned char* q = base + off;
+      off = align_up(off + b, 256);
+      return q;
+    };
+    double* b = (double*)take(sizeof(double) * nv);
+    double* x = (double*)take(sizeof(double) * nv);
+    double* r = (double*)take(sizeof(double) * nv);
+    double* p = (double*)take(sizeof(double) * nv);
+    double* q = (double*)take(sizeof(double) * nv);
+    double* z = (double*)take(sizeof(double) * nv);
+    T* rT = (T*)take(sizeof(T) * nv);
+    T* za = (T*)take(sizeof(T) * nv);
+    T* zb = (T*)take(sizeof(T) * nv);
+    T* E = (T*)take(sizeof(T) * (size_t)k * MB);
+    double* part = (double*)take(sizeof(double) * (size_t)2 * nb * MB);
+    T* cpart = (T*)take(sizeof(T) * (size_t)nbr * k * MB);
+    BlockState* st = (BlockState*)take(sizeof(BlockState));
+    (void)zb;
+    // restriction / prolongation shared memory
+    const size_t sm_r = sizeof(T) * ((size_t)NLSP_TILE * (k + 1) + (size_t)NLSP_TILE * 33);
+    const size_t sm_p = sizeof(T) * (size_t)k * MB;
+    const size_t sm_c = sizeof(double) * (size_t)k * MB;
+    auto fr = k_b_restrict<KIND, T>;
+    auto fp = k_b_prolong<T>;
+    if (sm_r > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_r));
+    if (sm_p > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_p));
+    if (sm_c > 48 * 1024)
+      NLSP_CUDA(cudaFuncSetAttribute(k_b_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
+    // state
+    BlockState h;
+    memset(&h, 0, sizeof(h));
+    h.maxit = prm->maxit;
+    h.flexible = flexible;
+    h.m = m;
+    NLSP_CUDA(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    const int ge = grid_for(ctx, (int64_t)nv, BT, 8);
+    k_b_gather<<<ge, BT, 0, s>>>(B, ldb, m, n, b);
+    NLSP_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+    NLSP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, s));
+    NLSP_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * nv, s));
+    k_b_dot_init<<<nb, BT, 0, s>>>(b, n, part);
+    k_b_scalars<<<1, 32, 0, s>>>(part, nb, st, BS_INIT);
+    k_b_set_tol<<<1, 32, 0, s>>>(st, prm->tol);
+    NLSP_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * nv, s));
+    NLSP_CUDA(cudaMemsetAsync(q, 0, sizeof(double) * nv, s));
+    NLSP_LAUNCH_CHECK();
+    int launches = 6;
+    // z = B r.  In the iteration the update kernel forms x, r with alpha and
+    // then rT and the first pre-sweep; for the initial application alpha = 0
+    // leaves x and r as they are.
+    auto apply = [&](cudaStream_t ss, bool with_rr) -> int {
+      int nl = 0;
+      k_b_update<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, x, r, p, q, rT, za, st, part);
+      ++nl;
+      if (with_rr) {  // r^T r of the updated residual: convergence, maxit
+        k_b_scalars<<<1, 32, 0, ss>>>(part, nb, st, BS_RR);
+        ++nl;
+      }
+      T* cur = za;
+      T* oth = zb;
+      for (int sw = 1; sw < nu; ++sw, ++nl) {
+        k_b_sweep<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, oth);
+        std::swap(cur, oth);
+      }
+      fr<<<nbr, BT, sm_r, ss>>>(AT, rT, cur, (const T*)M->P, M->k, k, ntiles, cpart);
+      k_b_coarse<T><<<1, 256, sm_c, ss>>>(cpart, nbr, k, M->Ainv, E);
+      fp<<<nb, BT, sm_p, ss>>>((const T*)M->P, M->k, k, n, E, cur);
+      nl += 3;
+      for (int sw = 1; sw < nu; ++sw, ++nl) {
+        k_b_sweep<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, oth);
+        std::swap(cur, oth);
+      }
+      k_b_post<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, r, z, part);
+      k_b_scalars<<<1, 32, 0, ss>>>(part, nb, st, BS_RZ);
+      nl += 2;
+      return nl;
+    };
+    launches += apply(s, false);
+    NLSP_LAUNCH_CHECK();
+    // one iteration: p = z + beta p, q = A p, alpha, update, z = B r, beta
+    auto body = [&](cudaStream_t ss) -> int {
+      k_b_dir<<<ge, BT, 0, ss>>>(z, p, n, st);
+      k_b_spmv<KIND><<<nb, BT, 0, ss>>>(A->v64, p, q, part);
+      k_b_scalars<<<1, 32, 0, ss>>>(part, nb, st, BS_PQ);
+      return 3 + apply(ss, true);
+    };
+    cudaStream_t cap;
+    NLSP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&]() {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cap);
+    };
+    cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int nbody = 0;
+    if (ce == cudaSuccess) {
+      nbody = body(cap);
+      ce = cudaStreamEndCapture(cap, &graph);
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+      cleanup();
+      NLSP_CUDA(ce);
+    }
+    // relaunch in chunks of 8 iterations; iterations past a column's stop
+    // leave it untouched (alpha = 0), so a chunk may overrun safely
+    int hdone = 0, iters = 0;
+    while (iters < prm->maxit) {
+      const int chunk = std::min(8, prm->maxit - iters);
+      for (int c = 0; c < chunk; ++c) {
+        ce = cudaGraphLaunch(exec, s);
+        if (ce != cudaSuccess) {
+          cleanup();
+          NLSP_CUDA(ce);
+        }
+      }
+      launches += chunk * nbody;
+      iters += chunk;
+      ce = cudaMemcpyAsync(&hdone, &st->all_done, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) {
+        cleanup();
+        NLSP_CUDA(ce);
+      }
+      if (hdone) break;
+    }
+    cleanup();
+    k_b_true<KIND><<<nb, BT, 0, s>>>(A->v64, b, x, part);
+    k_b_true_fin<<<1, 32, 0, s>>>(part, nb, st);
+    k_b_scatter<<<ge, BT, 0, s>>>(x, m, n, X, ldx);
+    NLSP_LAUNCH_CHECK();
+    launches += 3;
+    NLSP_CUDA(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    NLSP_CUDA(cudaStreamSynchronize(s));
+    count_launches(ctx, (unsigned long long)launches);
+    nlsp_status worst = NLSP_OK;
+    for (int c = 0; c < m; ++c) {
+      int stc = h.status[c];
+      if (stc == NLSP_OK && !h.done[c]) stc = NLSP_NOT_CONVERGED;
+      if (infos) {
+        infos[c].iterations = h.iter[c];
+        infos[c].status = stc;
+        infos[c].relres = h.bb[c] > 0 ? sqrt(h.rr[c] / h.bb[c]) : 0.0;
+        infos[c].true_relres = h.bb[c] > 0 ? sqrt(h.true_rr[c] / h.bb[c]) : 0.0;
+      }
+      if (stc == NLSP_ERR_BREAKDOWN) worst = NLSP_ERR_BREAKDOWN;
+      else if (stc == NLSP_NOT_CONVERGED && worst == NLSP_OK) worst = NLSP_NOT_CONVERGED;
+    }
+    return worst;
+  }
+};
+
+}  // namespace
+
+extern "C" nlsp_status nlsp_solve_block(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec* M, int m,
+                                        const double* dev_B, int64_t ldb, double* dev_X, int64_t ldx,
+                                        const nlsp_solve_params* params, nlsp_solve_info* infos) {
+  if (!ctx || !A || !M || !params || M->A != A || m < 0 || m > MB || ldb < A->n || ldx < A->n) return NLSP_ERR_INVALID;
+  if (m > 0 && (!dev_B || !dev_X)) return NLSP_ERR_INVALID;
+  if (!(params->tol >= 0.0) || params->maxit < 1 || M->r > 128) return NLSP_ERR_INVALID;
+  if (m == 0) return NLSP_OK;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  if (M->precision == NLSP_FP64) {
+    switch (A->kind) {
+      case ST_5PT: return BlockSolver<ST_5PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
+      case ST_9PT: return BlockSolver<ST_9PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
+      default: return BlockSolver<ST_7PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
+    }
+  }
+  switch (A->kind) {
+    case ST_5PT: return BlockSolver<ST_5PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
+    case ST_9PT: return BlockSolver<ST_9PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
+    default: return BlockSolver<ST_7PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
+  }
+}

@@ -1,0 +1,121 @@
+"""GPU tests of the block PCG (nlsp_solve_block): m <= 32 right-hand sides
+advanced together with one preconditioner application per iteration for all
+columns.
+
+Each column runs its own PCG recurrence, so it must reproduce what a
+single-column solve gives: for the FP64 path the oracle's iterations (+-1,
+the block sums are added in another order) and its solution (1e-8); for
+both paths the FP64 true relative residual (oracle operator) below the
+tolerance and the iteration count of the library's single-column solve
+(+-1 FP64, +-2 mixed).  Edge cases: a zero column, a scaled column, maxit,
+more than 32 columns rejected."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import rel, to_dev, to_np
+from oracle import operator as op, pcg as opcg
+from paper_2601_20174_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED = 0, 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_20174_gb300 import api
+    return api.Context(0)
+
+
+def _api():
+    from paper_2601_20174_gb300 import api
+    return api
+
+
+CASES = {
+    "poisson5": lambda: gen.poisson_2d(37, 8, 24, seed=1),
+    "grf5": lambda: gen.grf_diffusion_2d(N=45, k=12, K=32, seed=2),
+    "aniso9": lambda: gen.aniso_9pt_2d(N=29, k=10, K=24, m=1, seed=3),
+    "iid3d": lambda: gen.iid_diffusion_3d(N=11, k=10, K=24, seed=4),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_block_matches_oracle_and_single_column(ctx, name):
+    api = _api()
+    p = CASES[name]()
+    p.tol = 1e-8
+    A = op.assemble(p)
+    B = gen.rhs_uniform(p.n, 5, seed=11)
+    Aop = api.Operator.from_problem(ctx, p)
+    for precision in (FP64, MIXED):
+        M = api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, precision)
+        X, res = M.solve_block(to_dev(B), tol=p.tol)
+        X = to_np(X)
+        X1, res1 = M.solve(to_dev(B), tol=p.tol, graph_mode=1)
+        X1 = to_np(X1)
+        for c in range(B.shape[1]):
+            true = np.linalg.norm(B[:, c] - A @ X[:, c]) / np.linalg.norm(B[:, c])
+            assert res[c].status == 0 and true <= p.tol * 1.01, (precision, c, res[c], true)
+            assert abs(res[c].true_relres - true) <= 1e-3 * true
+            assert abs(res[c].iterations - res1[c].iterations) <= (1 if precision == FP64 else 2)
+            assert rel(X[:, c], X1[:, c]) <= 1e-6
+        if precision == FP64:
+            P = to_np(M.basis())
+            import scipy.linalg as sla
+            Lc = sla.cholesky(P.T @ (A @ P), lower=True)
+            apply_B = opcg.two_level_solver(A, P, Lc, p.omega, p.nu, p.nu)
+            for c in range(B.shape[1]):
+                o = opcg.pcg(A, apply_B, B[:, c], p.tol)
+                assert abs(res[c].iterations - o["iters"]) <= 1
+                assert rel(X[:, c], o["x"]) <= 1e-8
+
+
+def test_block_32_columns_zero_and_scaled(ctx):
+    api = _api()
+    p = CASES["grf5"]()
+    A = op.assemble(p)
+    B = gen.rhs_uniform(p.n, 32, seed=12)
+    B[:, 3] = 0.0
+    B[:, 7] = 4.0 * B[:, 5]
+    Aop = api.Operator.from_problem(ctx, p)
+    M = api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, FP64)
+    X, res = M.solve_block(to_dev(B), tol=1e-9)
+    X = to_np(X)
+    assert res[3].iterations == 0 and res[3].status == 0 and np.all(X[:, 3] == 0)
+    assert res[7].iterations == res[5].iterations
+    assert rel(X[:, 7], 4.0 * X[:, 5]) <= 1e-10
+    for c in range(32):
+        if c == 3:
+            continue
+        true = np.linalg.norm(B[:, c] - A @ X[:, c]) / np.linalg.norm(B[:, c])
+        assert res[c].status == 0 and true <= 1e-9 * 1.01
+
+
+def test_block_maxit_and_too_many_columns(ctx):
+    api = _api()
+    p = CASES["grf5"]()
+    Aop = api.Operator.from_problem(ctx, p)
+    M = api.Preconditioner.build(Aop, to_dev(p.S0), 2, p.s1, p.nu, p.omega, FP64)
+    B = gen.rhs_uniform(p.n, 3, seed=13)
+    X, res = M.solve_block(to_dev(B), tol=1e-14, maxit=3)
+    assert all(r.status == 1 and r.iterations == 3 for r in res)
+    with pytest.raises(api.L.NlspError):
+        M.solve_block(to_dev(gen.rhs_uniform(p.n, 33, seed=14)))
+
+
+def test_block_anisotropic_256_mixed(ctx):
+    # 9-point rotated anisotropy (eps = 1e-3), k = 64, 32 right-hand sides
+    api = _api()
+    p = gen.aniso_9pt_2d(N=256, k=64, K=128, m=32, seed=5, tol=1e-8)
+    A = op.assemble(p)
+    Aop = api.Operator.from_problem(ctx, p)
+    M = api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, MIXED)
+    X, res = M.solve_block(to_dev(p.f), tol=p.tol, maxit=5000)
+    X = to_np(X)
+    for c in range(p.f.shape[1]):
+        true = np.linalg.norm(p.f[:, c] - A @ X[:, c]) / np.linalg.norm(p.f[:, c])
+        assert res[c].status == 0 and true <= 1e-8 * 1.01, (c, res[c], true)
