@@ -247,6 +247,45 @@ def run_differentiation(ctx, dev, timed):
     return out
 
 
+BLOCK = dict(N=1024, k=128, K=128, m=32, s1=20, nu=2, omega=2.0 / 3.0, tol=1e-8, seed=0, seq_cols=4)
+BLOCK_DESC = ("2D rotated anisotropic diffusion, 9-point, 1024^2 (n=1046529), theta ~ U[0,pi), eps=1e-3, k=128 "
+              "from K=128 device-drawn smoothed samples (s1=20, omega=2/3), nu=2; 32 RHS U[-1,1] by block PCG "
+              "(FP32 preconditioner, FP64 recurrences), tol 1e-8")
+
+
+def run_block(ctx, dev, timed):
+    """32 right-hand sides advanced together (nlsp_solve_block) against the
+    same columns solved one at a time by the persistent single-column solver
+    (a bounded sample of seq_cols columns, scaled to 32)."""
+    import statistics as st
+
+    import torch
+
+    from paper_2601_20174_gb300 import _lib as L, api, inputs as gen
+
+    p = gen.aniso_9pt_2d(BLOCK["N"], BLOCK["k"], BLOCK["K"], m=BLOCK["m"], seed=BLOCK["seed"], tol=BLOCK["tol"],
+                         with_samples=False)
+    A = api.Operator.from_problem(ctx, p)
+    M = api.Preconditioner.build(A, None, BLOCK["k"], BLOCK["s1"], BLOCK["nu"], BLOCK["omega"], L.NLSP_MIXED_FP32,
+                                 K=BLOCK["K"], seed=p.seed)
+    F = torch.as_tensor(p.f).to(dev)
+    M.solve_block(F, tol=BLOCK["tol"], maxit=20000)  # warm
+    ms, (X, res) = timed(lambda: M.solve_block(F, tol=BLOCK["tol"], maxit=20000), 1)
+    cols = BLOCK["seq_cols"]
+    ms1, (X1, res1) = timed(lambda: M.solve(F[:, :cols], tol=BLOCK["tol"], maxit=20000, graph_mode=2), 1)
+    its = [r.iterations for r in res]
+    out = {"workload": BLOCK_DESC, "rhs": BLOCK["m"], "ms": ms[0], "value": BLOCK["m"] / (ms[0] / 1e3),
+           "unit": "solves/s", "iterations": {"min": min(its), "max": max(its)},
+           "all_converged": all(r.status == 0 for r in res),
+           "max_true_relres": max(r.true_relres for r in res),
+           "ms_per_iteration": ms[0] / max(its),
+           "single_column_solver": {"columns_timed": cols, "ms": ms1[0], "value": cols / (ms1[0] / 1e3),
+                                    "unit": "solves/s", "iterations": [r.iterations for r in res1]}}
+    M.close()
+    A.close()
+    return out
+
+
 def run_batched(ctx, dev, timed, rank):
     """The batched leg: builds every instance's operator and preconditioner,
     then solves all of them in one launch of the persistent solver.  The team
@@ -452,6 +491,7 @@ def run_ours(args):
     # ---- batched: 256 uneven instances in one persistent launch ----------
     batched = None if args.no_batched else run_batched(ctx, dev, timed, rank)
     differentiation = None if args.no_differentiation else run_differentiation(ctx, dev, timed)
+    block = None if args.no_block else run_block(ctx, dev, timed)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -480,7 +520,7 @@ def run_ours(args):
                 "roofline": roof, "kernels": kern,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * 8},
                 "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu, "batched": batched,
-                "differentiation": differentiation}
+                "differentiation": differentiation, "block": block}
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
@@ -497,6 +537,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched leg")
     ap.add_argument("--no-differentiation", action="store_true", help="skip the differentiation leg")
+    ap.add_argument("--no-block", action="store_true", help="skip the 32-RHS block PCG leg")
     ap.add_argument("--graph-mode", type=int, default=2, choices=[0, 1, 2],
                     help="2: one persistent cooperative kernel per solve (default); 1: PCG loop as one graph "
                          "with a device-side while node; 0: one-iteration graph relaunched by the host "

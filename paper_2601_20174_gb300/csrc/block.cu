@@ -99,6 +99,168 @@ __global__ void __launch_bounds__(BT) k_b_update(StencilView<T> A, T omega, doub
   block_col_partial(s, sm, part);
 }
 
+// ---- four columns per thread: 8 threads per node row, vector loads -------
+template <typename T>
+struct V4 {
+  T v[4];
+};
+
+template <typename T>
+__device__ __forceinline__ V4<T> ld4(const T* p) {
+  V4<T> r;
+  if (sizeof(T) == 4) {
+    const float4 f = *reinterpret_cast<const float4*>(p);
+    r.v[0] = (T)f.x; r.v[1] = (T)f.y; r.v[2] = (T)f.z; r.v[3] = (T)f.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    r.v[0] = (T)a.x; r.v[1] = (T)a.y; r.v[2] = (T)b.x; r.v[3] = (T)b.y;
+  }
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const V4<T>& r) {
+  if (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4((float)r.v[0], (float)r.v[1], (float)r.v[2], (float)r.v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2((double)r.v[0], (double)r.v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2((double)r.v[2], (double)r.v[3]);
+  }
+}
+
+// (A x)_idx for four columns at once (same arithmetic as stencil_apply, per column)
+template <int KIND, typename T, typename Get>
+__device__ __forceinline__ V4<T> stencil_apply4(const StencilView<T>& A, int64_t idx, NodeCoord c, Get get) {
+  const int N = A.N;
+  V4<T> s;
+  if (KIND == ST_9PT) {
+    const bool w = c.i > 0, e = c.i < N - 1, so = c.j > 0, no = c.j < N - 1;
+    const V4<T> x0 = get(idx);
+    V4<T> ew, ns, d1, d2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ew.v[q] = ns.v[q] = d1.v[q] = d2.v[q] = T(0);
+    auto add = [&](V4<T>& acc, int64_t m) {
+      const V4<T> x = get(m);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc.v[q] += x.v[q];
+    };
+    if (w) add(ew, idx - 1);
+    if (e) add(ew, idx + 1);
+    if (so) add(ns, idx - N);
+    if (no) add(ns, idx + N);
+    if (e && no) add(d1, idx + N + 1);
+    if (w && so) add(d1, idx - N - 1);
+    if (w && no) add(d2, idx + N - 1);
+    if (e && so) add(d2, idx - N + 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      s.v[q] = A.c[0] * x0.v[q] + A.c[1] * ew.v[q] + A.c[2] * ns.v[q] + A.c[3] * d1.v[q] + A.c[4] * d2.v[q];
+  } else {
+    const V4<T> x0 = get(idx);
+    const T d = A.diag[idx];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s.v[q] = d * x0.v[q];
+    auto sub = [&](T wgt, int64_t m) {
+      const V4<T> x = get(m);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s.v[q] -= wgt * x.v[q];
+    };
+    if (c.i > 0) sub(A.cx[idx - 1], idx - 1);
+    if (c.i < N - 1) sub(A.cx[idx], idx + 1);
+    if (c.j > 0) sub(A.cy[idx - N], idx - N);
+    if (c.j < N - 1) sub(A.cy[idx], idx + N);
+    if (KIND == ST_7PT) {
+      const int64_t nn = (int64_t)N * N;
+      if (c.l > 0) sub(A.cz[idx - nn], idx - nn);
+      if (c.l < N - 1) sub(A.cz[idx], idx + nn);
+    }
+  }
+  return s;
+}
+
+// Per-column block partials from four-column threads: thread (slot g, quad
+// q) holds columns 4q .. 4q + 3 of its nodes.
+__device__ __forceinline__ void block_col_partial4(const double (&v)[4], double (*sm)[MB], double* part) {
+  const int g = threadIdx.x >> 3, q = threadIdx.x & 7;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sm[g][4 * q + j] = v[j];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int gg = 0; gg < BT / 8; ++gg) s += sm[gg][threadIdx.x];
+    part[(int64_t)blockIdx.x * MB + threadIdx.x] = s;
+  }
+}
+
+constexpr int NPB = BT / 8;  // node rows per block step (8 threads per row)
+
+// q = A p (FP64), four columns per thread, partials of p^T q
+template <int KIND>
+__global__ void __launch_bounds__(BT) k_b_spmv4(StencilView<double> A, const double* __restrict__ p,
+                                               double* __restrict__ q, double* __restrict__ part) {
+  __shared__ double sm[NPB][MB];
+  const int qd = threadIdx.x & 7;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * NPB + (threadIdx.x >> 3); i < A.n; i += (int64_t)gridDim.x * NPB) {
+    const V4<double> qi = stencil_apply4<KIND>(A, i, node_coord<KIND>(i, A.N),
+                                               [&](int64_t m) { return ld4(p + m * MB + 4 * qd); });
+    const int64_t e = i * MB + 4 * qd;
+    const V4<double> pi = ld4(p + e);
+    st4(q + e, qi);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = fma(pi.v[j], qi.v[j], s[j]);
+  }
+  block_col_partial4(s, sm, part);
+}
+
+// zout = zin + w D^-1 (rT - A zin), four columns per thread
+template <int KIND, typename T>
+__global__ void __launch_bounds__(BT) k_b_sweep4(StencilView<T> A, T omega, const T* __restrict__ rT,
+                                                const T* __restrict__ zin, T* __restrict__ zout) {
+  const int q = threadIdx.x & 7;
+  for (int64_t i = (int64_t)blockIdx.x * NPB + (threadIdx.x >> 3); i < A.n; i += (int64_t)gridDim.x * NPB) {
+    const V4<T> az = stencil_apply4<KIND>(A, i, node_coord<KIND>(i, A.N),
+                                          [&](int64_t m) { return ld4(zin + m * MB + 4 * q); });
+    const int64_t e = i * MB + 4 * q;
+    const V4<T> z0 = ld4(zin + e), r0 = ld4(rT + e);
+    const T di = omega * stencil_dinv<KIND>(A, i);
+    V4<T> o;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o.v[j] = z0.v[j] + di * (r0.v[j] - az.v[j]);
+    st4(zout + e, o);
+  }
+}
+
+// Last post-sweep, four columns per thread: z (FP64) and the partials of
+// r^T z and r^T z_old.
+template <int KIND, typename T>
+__global__ void __launch_bounds__(BT) k_b_post4(StencilView<T> A, T omega, const T* __restrict__ rT,
+                                               const T* __restrict__ zin, const double* __restrict__ r,
+                                               double* __restrict__ zout, double* __restrict__ part) {
+  __shared__ double sm[NPB][MB];
+  const int q = threadIdx.x & 7;
+  double s_rz[4] = {0.0, 0.0, 0.0, 0.0}, s_ro[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * NPB + (threadIdx.x >> 3); i < A.n; i += (int64_t)gridDim.x * NPB) {
+    const V4<T> az = stencil_apply4<KIND>(A, i, node_coord<KIND>(i, A.N),
+                                          [&](int64_t m) { return ld4(zin + m * MB + 4 * q); });
+    const int64_t e = i * MB + 4 * q;
+    const V4<T> z0 = ld4(zin + e), r0 = ld4(rT + e);
+    const V4<double> ri = ld4(r + e), zo = ld4(zout + e);
+    const T di = omega * stencil_dinv<KIND>(A, i);
+    V4<double> zd;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      zd.v[j] = (double)(z0.v[j] + di * (r0.v[j] - az.v[j]));
+      s_ro[j] = fma(ri.v[j], zo.v[j], s_ro[j]);
+      s_rz[j] = fma(ri.v[j], zd.v[j], s_rz[j]);
+    }
+    st4(zout + e, zd);
+  }
+  block_col_partial4(s_rz, sm, part);
+  __syncthreads();
+  block_col_partial4(s_ro, sm, part + (int64_t)gridDim.x * MB);
+}
+
 // zout = zin + w D^-1 (rT - A zin)  (pre-sweeps 2..nu and post-sweeps)
 template <int KIND, typename T>
 __global__ void __launch_bounds__(BT) k_b_sweep(StencilView<T> A, T omega, const T* __restrict__ rT,
@@ -121,10 +283,9 @@ __global__ void __launch_bounds__(BT) k_b_restrict(StencilView<T> A, const T* __
                                                   const T* __restrict__ z, const T* __restrict__ P, int kst,
                                                   int k, int64_t ntiles, T* __restrict__ cpart) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int kp = k + 1;
-  T* ps = reinterpret_cast<T*>(smem_raw);         // [128][k + 1]
-  T* rs = ps + (size_t)NLSP_TILE * kp;            // [128][33]
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int kp = (k + 3) / 4 * 4 + 4;             // rows of whole 16-byte units, zero-padded
+  T* ps = reinterpret_cast<T*>(smem_raw);         // [128][k + 4]
+  T* rs = ps + (size_t)NLSP_TILE * kp;            // [128][36]
   const int jb = threadIdx.x >> 3, cb = threadIdx.x & 7;  // j = 4 jb .. (k <= 128), c = 4 cb ..
   T acc[4][4];
 #pragma unroll
@@ -133,35 +294,37 @@ __global__ void __launch_bounds__(BT) k_b_restrict(StencilView<T> A, const T* __
     for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     __syncthreads();
-    // rho rows of the tile's nodes (warp per node, lane = column)
-    for (int wn = w; wn < NLSP_TILE; wn += BW) {
+    // rho rows of the tile's nodes (8 threads per node, four columns each)
+    for (int wn = threadIdx.x >> 3; wn < NLSP_TILE; wn += BT / 8) {
+      const int qd = threadIdx.x & 7;
       const int64_t i = t * NLSP_TILE + wn;
-      T rho = T(0);
+      V4<T> rho;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rho.v[j] = T(0);
       if (i < A.n) {
-        const T az =
-            stencil_apply<KIND>(A, i, node_coord<KIND>(i, A.N), [&](int64_t m) { return z[m * MB + lane]; });
-        rho = rT[i * MB + lane] - az;
+        const V4<T> az = stencil_apply4<KIND>(A, i, node_coord<KIND>(i, A.N),
+                                              [&](int64_t m) { return ld4(z + m * MB + 4 * qd); });
+        const V4<T> r0 = ld4(rT + i * MB + 4 * qd);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) rho.v[j] = r0.v[j] - az.v[j];
       }
-      rs[wn * 33 + lane] = rho;
+      st4(rs + wn * 36 + 4 * qd, rho);
     }
-    // P tile transposed: ps[node][j]
+    // P tile transposed: ps[node][j], columns k .. kp - 1 zero
     const T* src = P + t * kst * NLSP_TILE;  // the first k of the tile's kst columns
-    for (int e = threadIdx.x; e < k * NLSP_TILE; e += BT) {
+    for (int e = threadIdx.x; e < kp * NLSP_TILE; e += BT) {
       const int j = e / NLSP_TILE, wn = e % NLSP_TILE;
-      ps[wn * kp + j] = src[e];
+      ps[wn * kp + j] = j < k ? src[e] : T(0);
     }
     __syncthreads();
     if (4 * jb < k) {
       for (int wn = 0; wn < NLSP_TILE; ++wn) {
-        T pa[4], rb[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) pa[a] = 4 * jb + a < k ? ps[wn * kp + 4 * jb + a] : T(0);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) rb[b] = rs[wn * 33 + 4 * cb + b];
+        // k is a multiple of 4 here or the tail columns of ps are zero
+        const V4<T> pa = ld4(ps + wn * kp + 4 * jb), rb = ld4(rs + wn * 36 + 4 * cb);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] += pa[a] * rb[b];
+          for (int b = 0; b < 4; ++b) acc[a][b] += pa.v[a] * rb.v[b];
       }
     }
   }
@@ -174,26 +337,32 @@ __global__ void __launch_bounds__(BT) k_b_restrict(StencilView<T> A, const T* __
   }
 }
 
-// C = sum of the block partials (block order), E = A_c^-1 C  (k x 32, in T).
+// C = sum of the restriction partials in block order (one thread per entry
+// of the k x 32 block), FP64.
 template <typename T>
-__global__ void k_b_coarse(const T* __restrict__ cpart, int nb, int k, const double* __restrict__ Ainv,
-                           T* __restrict__ E) {
-  extern __shared__ double cs[];  // [k][32]
-  for (int e = threadIdx.x; e < k * MB; e += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += (double)cpart[(int64_t)b * k * MB + e];
-    cs[e] = s;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < k * MB; e += blockDim.x) {
-    const int i = e / MB, c = e % MB;
-    double s = 0.0;
-    for (int j = 0; j < k; ++j) s = fma(Ainv[(int64_t)j * k + i], cs[j * MB + c], s);
-    E[e] = (T)s;
-  }
+__global__ void k_b_csum(const T* __restrict__ cpart, int nb, int k, double* __restrict__ C) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * MB) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += (double)cpart[(int64_t)b * k * MB + e];
+  C[e] = s;
 }
 
-// z += P E (warp per node, lane = column; the node's P row is a broadcast)
+// E = A_c^-1 C (k x 32), one thread per entry.
+template <typename T>
+__global__ void k_b_coarse(const double* __restrict__ C, int k, const double* __restrict__ Ainv, T* __restrict__ E) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * MB) return;
+  const int i = e / MB, c = e % MB;
+  double s = 0.0;
+  for (int j = 0; j < k; ++j) s = fma(Ainv[(int64_t)j * k + i], C[j * MB + c], s);
+  E[e] = (T)s;
+}
+
+// z += P E: the block's two halves take one node tile each; a thread owns
+// its node's whole row (32 columns).  P's tile rows are read once, coalesced
+// along the nodes, sixteen loads in flight; E is read from shared memory as
+// 16-byte vectors.
 template <typename T>
 __global__ void __launch_bounds__(BT) k_b_prolong(const T* __restrict__ P, int kst, int k, int64_t n,
                                                  const T* __restrict__ E, T* __restrict__ z) {
@@ -201,13 +370,35 @@ __global__ void __launch_bounds__(BT) k_b_prolong(const T* __restrict__ P, int k
   T* es = reinterpret_cast<T*>(smem_raw);  // [k][32]
   for (int e = threadIdx.x; e < k * MB; e += BT) es[e] = E[e];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = (int64_t)blockIdx.x * BW + (threadIdx.x >> 5), ws = (int64_t)gridDim.x * BW;
-  for (int64_t i = w0; i < n; i += ws) {
-    const T* prow = P + ((i >> 7) * kst) * NLSP_TILE + (i & 127);
-    T s = T(0);
-    for (int j = 0; j < k; ++j) s += prow[(int64_t)j * NLSP_TILE] * es[j * MB + lane];
-    z[i * MB + lane] += s;
+  const int node = threadIdx.x & (NLSP_TILE - 1), half = threadIdx.x >> 7;
+  const int64_t ntiles = (n + NLSP_TILE - 1) / NLSP_TILE;
+  for (int64_t t = 2 * (int64_t)blockIdx.x + half; t < ntiles; t += 2 * (int64_t)gridDim.x) {
+    const int64_t i = t * NLSP_TILE + node;
+    const T* pc = P + t * kst * NLSP_TILE + node;
+    T acc[MB];
+#pragma unroll
+    for (int c = 0; c < MB; ++c) acc[c] = T(0);
+#pragma unroll 16
+    for (int j = 0; j < k; ++j) {
+      const T pv = pc[(int64_t)j * NLSP_TILE];
+      const T* ej = es + j * MB;
+#pragma unroll
+      for (int c4 = 0; c4 < MB / 4; ++c4) {
+        const V4<T> e4 = ld4(ej + 4 * c4);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[4 * c4 + c] += pv * e4.v[c];
+      }
+    }
+    if (i < n) {
+      T* zr = z + i * MB;
+#pragma unroll
+      for (int c4 = 0; c4 < MB / 4; ++c4) {
+        V4<T> zv = ld4(zr + 4 * c4);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) zv.v[c] += acc[4 * c4 + c];
+        st4(zr + 4 * c4, zv);
+      }
+    }
   }
 }
 
@@ -238,14 +429,29 @@ __global__ void __launch_bounds__(BT) k_b_post(StencilView<T> A, T omega, const 
 enum BlockStage { BS_INIT = 0, BS_PQ, BS_RR, BS_RZ };
 
 // Per-column scalar step from the block partials (one warp, lane = column).
-__global__ void k_b_scalars(const double* __restrict__ part, int nb, BlockState* st, int stage) {
-  const int c = threadIdx.x;
+// 32 x 32 threads: group g adds blocks g, g + 32, ... of column c, then warp
+// 0 adds the 32 group sums in order (deterministic).
+__global__ void __launch_bounds__(1024) k_b_scalars(const double* __restrict__ part, int nb, BlockState* st,
+                                                    int stage) {
+  __shared__ double gs[2][32][MB];
+  const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const bool two = stage == BS_RZ && st->flexible;
+  double a0 = 0.0, a1 = 0.0;
+  for (int b = g; b < nb; b += 32) {
+    a0 += part[(int64_t)b * MB + c];
+    if (two) a1 += part[(int64_t)(nb + b) * MB + c];
+  }
+  gs[0][g][c] = a0;
+  gs[1][g][c] = a1;
+  __syncthreads();
+  if (g != 0) return;
   const int t = st->t;  // read before any lane may advance it
   __syncwarp();
   double s0 = 0.0, s1 = 0.0;
-  for (int b = 0; b < nb; ++b) s0 += part[(int64_t)b * MB + c];
-  if (stage == BS_RZ && st->flexible)
-    for (int b = 0; b < nb; ++b) s1 += part[(int64_t)(nb + b) * MB + c];
+  for (int q = 0; q < 32; ++q) {
+    s0 += gs[0][q][c];
+    s1 += gs[1][q][c];
+  }
   const bool active = c < st->m && !st->done[c];
   switch (stage) {
     case BS_INIT:  // s0 = b^T b
@@ -389,7 +595,8 @@ struct BlockSolver {
     // workspace
     const size_t nv = (size_t)n * MB;
     const size_t bytes = sizeof(double) * nv * 6 + sizeof(T) * nv * 4 + sizeof(double) * (size_t)2 * nb * MB +
-                         sizeof(T) * (size_t)nbr * k * MB + sizeof(T) * (size_t)k * MB + sizeof(BlockState) + 4096;
+                         sizeof(T) * (size_t)nbr * k * MB + (sizeof(T) + sizeof(double)) * (size_t)k * MB +
+                         sizeof(BlockState) + 8192;
     DevBuf buf;
     NLSP_TRY(buf.alloc(bytes));
     unsigned char* base = buf.as<unsigned char>();
@@ -409,20 +616,18 @@ struct BlockSolver {
     T* za = (T*)take(sizeof(T) * nv);
     T* zb = (T*)take(sizeof(T) * nv);
     T* E = (T*)take(sizeof(T) * (size_t)k * MB);
+    double* Csum = (double*)take(sizeof(double) * (size_t)k * MB);
     double* part = (double*)take(sizeof(double) * (size_t)2 * nb * MB);
     T* cpart = (T*)take(sizeof(T) * (size_t)nbr * k * MB);
     BlockState* st = (BlockState*)take(sizeof(BlockState));
     (void)zb;
     // restriction / prolongation shared memory
-    const size_t sm_r = sizeof(T) * ((size_t)NLSP_TILE * (k + 1) + (size_t)NLSP_TILE * 33);
+    const size_t sm_r = sizeof(T) * ((size_t)NLSP_TILE * ((k + 3) / 4 * 4 + 4) + (size_t)NLSP_TILE * 36);
     const size_t sm_p = sizeof(T) * (size_t)k * MB;
-    const size_t sm_c = sizeof(double) * (size_t)k * MB;
     auto fr = k_b_restrict<KIND, T>;
     auto fp = k_b_prolong<T>;
     if (sm_r > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_r));
     if (sm_p > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_p));
-    if (sm_c > 48 * 1024)
-      NLSP_CUDA(cudaFuncSetAttribute(k_b_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
     // state
     BlockState h;
     memset(&h, 0, sizeof(h));
@@ -436,7 +641,7 @@ struct BlockSolver {
     NLSP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, s));
     NLSP_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * nv, s));
     k_b_dot_init<<<nb, BT, 0, s>>>(b, n, part);
-    k_b_scalars<<<1, 32, 0, s>>>(part, nb, st, BS_INIT);
+    k_b_scalars<<<1, 1024, 0, s>>>(part, nb, st, BS_INIT);
     k_b_set_tol<<<1, 32, 0, s>>>(st, prm->tol);
     NLSP_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * nv, s));
     NLSP_CUDA(cudaMemsetAsync(q, 0, sizeof(double) * nv, s));
@@ -450,25 +655,26 @@ struct BlockSolver {
       k_b_update<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, x, r, p, q, rT, za, st, part);
       ++nl;
       if (with_rr) {  // r^T r of the updated residual: convergence, maxit
-        k_b_scalars<<<1, 32, 0, ss>>>(part, nb, st, BS_RR);
+        k_b_scalars<<<1, 1024, 0, ss>>>(part, nb, st, BS_RR);
         ++nl;
       }
       T* cur = za;
       T* oth = zb;
       for (int sw = 1; sw < nu; ++sw, ++nl) {
-        k_b_sweep<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, oth);
+        k_b_sweep4<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, oth);
         std::swap(cur, oth);
       }
       fr<<<nbr, BT, sm_r, ss>>>(AT, rT, cur, (const T*)M->P, M->k, k, ntiles, cpart);
-      k_b_coarse<T><<<1, 256, sm_c, ss>>>(cpart, nbr, k, M->Ainv, E);
+      k_b_csum<T><<<div_up((int64_t)k * MB, 128), 128, 0, ss>>>(cpart, nbr, k, Csum);
+      k_b_coarse<T><<<div_up((int64_t)k * MB, 128), 128, 0, ss>>>(Csum, k, M->Ainv, E);
       fp<<<nb, BT, sm_p, ss>>>((const T*)M->P, M->k, k, n, E, cur);
-      nl += 3;
+      nl += 4;
       for (int sw = 1; sw < nu; ++sw, ++nl) {
-        k_b_sweep<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, oth);
+        k_b_sweep4<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, oth);
         std::swap(cur, oth);
       }
-      k_b_post<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, r, z, part);
-      k_b_scalars<<<1, 32, 0, ss>>>(part, nb, st, BS_RZ);
+      k_b_post4<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, r, z, part);
+      k_b_scalars<<<1, 1024, 0, ss>>>(part, nb, st, BS_RZ);
       nl += 2;
       return nl;
     };
@@ -477,8 +683,8 @@ struct BlockSolver {
     // one iteration: p = z + beta p, q = A p, alpha, update, z = B r, beta
     auto body = [&](cudaStream_t ss) -> int {
       k_b_dir<<<ge, BT, 0, ss>>>(z, p, n, st);
-      k_b_spmv<KIND><<<nb, BT, 0, ss>>>(A->v64, p, q, part);
-      k_b_scalars<<<1, 32, 0, ss>>>(part, nb, st, BS_PQ);
+      k_b_spmv4<KIND><<<nb, BT, 0, ss>>>(A->v64, p, q, part);
+      k_b_scalars<<<1, 1024, 0, ss>>>(part, nb, st, BS_PQ);
       return 3 + apply(ss, true);
     };
     cudaStream_t cap;
