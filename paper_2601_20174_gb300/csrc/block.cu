@@ -13,6 +13,7 @@
 // stay on the device; the host relaunches a captured iteration graph in
 // chunks and reads one "all columns done" word between chunks.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -20,6 +21,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace {
 
@@ -32,7 +34,8 @@ struct BlockState {
   double bb[MB], tol2bn[MB], rz[MB], rr[MB], alpha[MB], beta[MB], true_rr[MB];
   int iter[MB], done[MB], status[MB];
   int all_done, maxit, flexible, m;
-  int t;  // iterations started (A p products formed)
+  int t;    // iterations started (A p products formed)
+  int err;  // a tensor-core completion wait gave up
 };
 
 // Sum of the warps' per-column partials of a block, written to part[block][c].
@@ -402,6 +405,255 @@ __global__ void __launch_bounds__(BT) k_b_prolong(const T* __restrict__ P, int k
   }
 }
 
+// ---- tensor-core (tcgen05, kind::tf32) restriction and prolongation ------
+// Operands live in shared memory in the canonical K-major layout without
+// swizzle: 8-row x 16-byte core matrices, (row / 8, k / 4) -> ((row / 8) *
+// (kcols / 4) + k / 4) * 128 bytes, row r of a core matrix at r * 16.  One
+// instruction is M = 128, N = 32, K = 8 (two core matrices along K); the
+// accumulator is 32 TMEM columns over the 128 lanes.
+namespace tc {
+
+__host__ __device__ inline unsigned core_off(int row, int kk, int kcols) {
+  return (unsigned)(((row >> 3) * (kcols >> 2) + (kk >> 2)) * 128 + (row & 7) * 16 + (kk & 3) * 4);
+}
+
+__device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr & 0x3FFFF) >> 4) | ((unsigned long long)(lbo >> 4) << 16) |
+         ((unsigned long long)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void ld16(unsigned ta, float (&v)[16]) { tmem::Io<16>::ld(ta, v); }
+
+// x = hi + lo with hi rounded to TF32 (round to nearest, ties away) and lo
+// the remainder: the three-product split of Ootomo & Yokota (2022,
+// "Recovering single precision accuracy from Tensor Cores while surpassing
+// the FP32 theoretical peak performance") keeps FP32-level accuracy.
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  unsigned h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
+  lo = x - hi;
+}
+
+__device__ __forceinline__ void split4(const float4 v, float4& hi, float4& lo) {
+  split_tf32(v.x, hi.x, lo.x);
+  split_tf32(v.y, hi.y, lo.y);
+  split_tf32(v.z, hi.z, lo.z);
+  split_tf32(v.w, hi.w, lo.w);
+}
+
+// D [+]= A_hi B_hi + A_hi B_lo + A_lo B_hi, `ksteps` MMA steps of K = 8 from
+// the operand start addresses (A: 128 rows, B: 32 rows, canonical K-major
+// layouts with M/N-group strides a_sbo / b_sbo); one commit for all.
+__device__ __forceinline__ void mma3_128x32(unsigned tmem_d, unsigned ah, unsigned al, unsigned a_sbo, unsigned bh,
+                                            unsigned bl, unsigned b_sbo, int ksteps, bool accumulate,
+                                            uint64_t* bar) {
+  constexpr unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(MB >> 3) << 17) | ((128u >> 4) << 24);
+  const unsigned as[3] = {al, ah, ah}, bs[3] = {bh, bl, bh};  // small terms first
+  for (int pr = 0; pr < 3; ++pr)
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const unsigned long long ad = sdesc(as[pr] + ks * 256, 128, a_sbo);
+      const unsigned long long bd = sdesc(bs[pr] + ks * 256, 128, b_sbo);
+      const unsigned acc = (accumulate || pr > 0 || ks > 0) ? 1u : 0u;
+      asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                   "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                   "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                   : "memory");
+    }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   tma::smem_addr(bar))
+               : "memory");
+}
+
+}  // namespace tc
+
+constexpr int TCK = 64;  // K chunk of the tensor-core contractions (2 CTAs per SM fit)
+
+// Restriction on tensor cores (FP32 preconditioner): per block, over its
+// tiles, D[j][c] += sum over the tile's nodes of P[node][j] rho[node][c],
+// accumulated in TMEM across tiles; A = P_t^T (rows j, zero beyond k), B =
+// rho_t^T (rows c), K = the tile's nodes in two chunks of 64.  Each operand
+// is split into TF32 hi + lo parts (three products).
+template <int KIND>
+__global__ void __launch_bounds__(BT, 2) k_b_restrict_tc(StencilView<float> A, const float* __restrict__ rT,
+                                                        const float* __restrict__ z, const float* __restrict__ P,
+                                                        int kst, int k, int64_t ntiles, float* __restrict__ cpart,
+                                                        BlockState* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* sa = smem_raw;               // A_hi: 128 x 64 tf32 (32 KB)
+  unsigned char* sal = sa + 128 * TCK * 4;    // A_lo
+  unsigned char* sb = sal + 128 * TCK * 4;    // B_hi: 32 x 64 (8 KB)
+  unsigned char* sbl = sb + 32 * TCK * 4;     // B_lo
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ unsigned tbase_s;
+  __shared__ int bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    tma::mbar_init(&bar, 1);
+    tma::fence_barrier_init();
+    bad = 0;
+  }
+  if (warp == 0) tmem::alloc(&tbase_s, 32);
+  for (int e = tid; e < 128 * TCK; e += BT) {  // rows j >= k of A stay zero
+    const int j = e / TCK, nd = e % TCK;
+    if (j >= k) {
+      *reinterpret_cast<float*>(sa + tc::core_off(j, nd, TCK)) = 0.0f;
+      *reinterpret_cast<float*>(sal + tc::core_off(j, nd, TCK)) = 0.0f;
+    }
+  }
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  const unsigned td = tbase_s;
+  const unsigned sbo = (TCK / 4) * 128;
+  unsigned phase = 0;
+  bool first = true;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int h = 0; h < NLSP_TILE / TCK; ++h) {
+      // rho of the chunk's 64 nodes -> B (8 threads per node, four columns each)
+      for (int wn = tid >> 3; wn < TCK; wn += BT / 8) {
+        const int qd = tid & 7;
+        const int64_t i = t * NLSP_TILE + h * TCK + wn;
+        V4<float> rho;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) rho.v[j] = 0.0f;
+        if (i < A.n) {
+          const V4<float> az = stencil_apply4<KIND>(A, i, node_coord<KIND>(i, A.N),
+                                                    [&](int64_t m) { return ld4(z + m * MB + 4 * qd); });
+          const V4<float> r0 = ld4(rT + i * MB + 4 * qd);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) rho.v[j] = r0.v[j] - az.v[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float hi, lo;
+          tc::split_tf32(rho.v[j], hi, lo);
+          *reinterpret_cast<float*>(sb + tc::core_off(4 * qd + j, wn, TCK)) = hi;
+          *reinterpret_cast<float*>(sbl + tc::core_off(4 * qd + j, wn, TCK)) = lo;
+        }
+      }
+      // the chunk's P rows -> A (row j, K = node); 16-byte chunks of four nodes
+      const float* src = P + t * kst * NLSP_TILE + h * TCK;
+      for (int e = tid; e < k * (TCK / 4); e += BT) {
+        const int j = e % k, q = e / k;  // j fastest across the threads (fewer bank conflicts)
+        const float4 v = *reinterpret_cast<const float4*>(src + (int64_t)j * NLSP_TILE + 4 * q);
+        float4 hi, lo;
+        tc::split4(v, hi, lo);
+        *reinterpret_cast<float4*>(sa + tc::core_off(j, 4 * q, TCK)) = hi;
+        *reinterpret_cast<float4*>(sal + tc::core_off(j, 4 * q, TCK)) = lo;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0)
+        tc::mma3_128x32(td, tma::smem_addr(sa), tma::smem_addr(sal), sbo, tma::smem_addr(sb), tma::smem_addr(sbl),
+                        sbo, TCK / 8, !first, &bar);
+      if (!tma::mbar_wait(&bar, phase)) bad = 1;  // the operands are reused by the next chunk
+      phase ^= 1u;
+      first = false;
+      tmem::fence_after_sync();
+      __syncthreads();
+    }
+  }
+  // D -> partials (warps 0-3: columns 0-15, warps 4-7: columns 16-31)
+  if (!first) {
+    float v[16];
+    tc::ld16(td + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(16 * (warp >> 2)), v);
+    const int j = 32 * (warp & 3) + lane;
+    if (j < k) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) cpart[((int64_t)blockIdx.x * k + j) * MB + 16 * (warp >> 2) + c] = v[c];
+    }
+  } else {
+    for (int e = tid; e < k * MB; e += BT) cpart[(int64_t)blockIdx.x * k * MB + e] = 0.0f;
+  }
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  if (warp == 0) tmem::dealloc(td, 32);
+  if (tid == 0 && bad) atomicExch(&st->err, 1);
+}
+
+// Prolongation on tensor cores (FP32): per tile, D[node][c] = sum_j
+// P[node][j] E[j][c] with A = the P tile (rows = nodes, K = j, in chunks of
+// 64) and B = E^T (rows c, all of K resident), then z += D.  Operands split
+// into TF32 hi + lo parts (three products).
+__global__ void __launch_bounds__(BT, 2) k_b_prolong_tc(const float* __restrict__ P, int kst, int k, int64_t n,
+                                                       const float* __restrict__ E, float* __restrict__ z,
+                                                       BlockState* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int kp = (k + 7) / 8 * 8;              // K padded to whole MMA steps
+  const int kc = kp < TCK ? kp : TCK;          // chunk width
+  unsigned char* sa = smem_raw;                // A_hi: 128 x kc
+  unsigned char* sal = sa + 128 * kc * 4;      // A_lo
+  unsigned char* sb = sal + 128 * kc * 4;      // B_hi: 32 x kp
+  unsigned char* sbl = sb + 32 * kp * 4;       // B_lo
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ unsigned tbase_s;
+  __shared__ int bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    tma::mbar_init(&bar, 1);
+    tma::fence_barrier_init();
+    bad = 0;
+  }
+  if (warp == 0) tmem::alloc(&tbase_s, 32);
+  for (int e = tid; e < MB * kp; e += BT) {  // B = E^T, zero beyond k
+    const int c = e % MB, j = e / MB;
+    float hi = 0.0f, lo = 0.0f;
+    if (j < k) tc::split_tf32(E[j * MB + c], hi, lo);
+    *reinterpret_cast<float*>(sb + tc::core_off(c, j, kp)) = hi;
+    *reinterpret_cast<float*>(sbl + tc::core_off(c, j, kp)) = lo;
+  }
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  const unsigned td = tbase_s;
+  const unsigned a_sbo = (unsigned)(kc / 4) * 128, b_sbo = (unsigned)(kp / 4) * 128;
+  unsigned phase = 0;
+  const int64_t ntiles = (n + NLSP_TILE - 1) / NLSP_TILE;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const float* src = P + t * kst * NLSP_TILE;
+    for (int j0 = 0; j0 < kp; j0 += kc) {
+      for (int e = tid; e < kc * NLSP_TILE; e += BT) {  // coalesced along the nodes
+        const int jj = e / NLSP_TILE, nd = e % NLSP_TILE, j = j0 + jj;
+        float hi = 0.0f, lo = 0.0f;
+        if (j < k) tc::split_tf32(src[(int64_t)j * NLSP_TILE + nd], hi, lo);
+        *reinterpret_cast<float*>(sa + tc::core_off(nd, jj, kc)) = hi;
+        *reinterpret_cast<float*>(sal + tc::core_off(nd, jj, kc)) = lo;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        const unsigned boff = (unsigned)(j0 / 4) * 128;  // K offset of the chunk in B
+        tc::mma3_128x32(td, tma::smem_addr(sa), tma::smem_addr(sal), a_sbo, tma::smem_addr(sb) + boff,
+                        tma::smem_addr(sbl) + boff, b_sbo, kc / 8, j0 > 0, &bar);
+      }
+      if (!tma::mbar_wait(&bar, phase)) bad = 1;
+      phase ^= 1u;
+      tmem::fence_after_sync();
+      __syncthreads();  // A is restaged by the next chunk
+    }
+    float v[16];
+    tc::ld16(td + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(16 * (warp >> 2)), v);
+    const int64_t i = t * NLSP_TILE + 32 * (warp & 3) + lane;
+    if (i < n) {
+      float* zr = z + i * MB + 16 * (warp >> 2);
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        V4<float> zv = ld4(zr + 4 * c4);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) zv.v[c] += v[4 * c4 + c];
+        st4(zr + 4 * c4, zv);
+      }
+    }
+    tmem::fence_before_sync();
+    __syncthreads();  // D is overwritten by the next tile
+    tmem::fence_after_sync();
+  }
+  if (warp == 0) tmem::dealloc(td, 32);
+  if (tid == 0 && bad) atomicExch(&st->err, 1);
+}
+
 // Last post-sweep: z = zin + w D^-1 (rT - A zin) stored in FP64, with the
 // per-column partials of r^T z and r^T z_old (flexible beta).
 template <int KIND, typename T>
@@ -628,6 +880,21 @@ struct BlockSolver {
     auto fp = k_b_prolong<T>;
     if (sm_r > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_r));
     if (sm_p > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_p));
+    // FP32 preconditioner: the restriction on tensor cores (split TF32
+    // inputs, FP32 accumulation); the prolongation too with NLSP_BLOCK_TC=2
+    // (slower on GB300: its operand staging costs more than the CUDA-core
+    // product), neither with NLSP_BLOCK_TC=0.
+    const char* tc_env = getenv("NLSP_BLOCK_TC");
+    const int tc_mode = tc_env ? (tc_env[0] - '0') : 1;
+    const bool use_tc = sizeof(T) == 4 && tc_mode >= 1;
+    const bool use_tc_prolong = sizeof(T) == 4 && tc_mode >= 2;
+    const int kp8 = (k + 7) / 8 * 8;
+    const size_t sm_rtc = (size_t)2 * (128 * TCK + 32 * TCK) * 4;
+    const size_t sm_ptc = (size_t)2 * (128 * std::min(kp8, TCK) + 32 * kp8) * 4;
+    if (use_tc) {
+      NLSP_CUDA(cudaFuncSetAttribute(k_b_restrict_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rtc));
+      NLSP_CUDA(cudaFuncSetAttribute(k_b_prolong_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ptc));
+    }
     // state
     BlockState h;
     memset(&h, 0, sizeof(h));
@@ -664,10 +931,18 @@ struct BlockSolver {
         k_b_sweep4<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, oth);
         std::swap(cur, oth);
       }
-      fr<<<nbr, BT, sm_r, ss>>>(AT, rT, cur, (const T*)M->P, M->k, k, ntiles, cpart);
+      if (use_tc)
+        k_b_restrict_tc<KIND><<<nbr, BT, sm_rtc, ss>>>(*reinterpret_cast<const StencilView<float>*>(&AT),
+                                                       (const float*)rT, (const float*)cur, (const float*)M->P,
+                                                       M->k, k, ntiles, (float*)cpart, st);
+      else
+        fr<<<nbr, BT, sm_r, ss>>>(AT, rT, cur, (const T*)M->P, M->k, k, ntiles, cpart);
       k_b_csum<T><<<div_up((int64_t)k * MB, 128), 128, 0, ss>>>(cpart, nbr, k, Csum);
       k_b_coarse<T><<<div_up((int64_t)k * MB, 128), 128, 0, ss>>>(Csum, k, M->Ainv, E);
-      fp<<<nb, BT, sm_p, ss>>>((const T*)M->P, M->k, k, n, E, cur);
+      if (use_tc_prolong)
+        k_b_prolong_tc<<<nbr, BT, sm_ptc, ss>>>((const float*)M->P, M->k, k, n, (const float*)E, (float*)cur, st);
+      else
+        fp<<<nb, BT, sm_p, ss>>>((const T*)M->P, M->k, k, n, E, cur);
       nl += 4;
       for (int sw = 1; sw < nu; ++sw, ++nl) {
         k_b_sweep4<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, oth);
@@ -738,6 +1013,10 @@ struct BlockSolver {
     NLSP_CUDA(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
     NLSP_CUDA(cudaStreamSynchronize(s));
     count_launches(ctx, (unsigned long long)launches);
+    if (h.err) {
+      nlsp_record_message("block solve: a tensor-core completion wait gave up");
+      return NLSP_ERR_TIMEOUT;
+    }
     nlsp_status worst = NLSP_OK;
     for (int c = 0; c < m; ++c) {
       int stc = h.status[c];

@@ -107,6 +107,25 @@ def test_block_maxit_and_too_many_columns(ctx):
         M.solve_block(to_dev(gen.rhs_uniform(p.n, 33, seed=14)))
 
 
+@pytest.mark.parametrize("tc_mode", ["0", "2"])
+def test_block_tensor_core_modes_agree(ctx, tc_mode, monkeypatch):
+    # CUDA-core contractions (0) and both contractions on tensor cores (2)
+    # against the default (tensor-core restriction): same iterations to +-1
+    api = _api()
+    p = CASES["aniso9"]()
+    A = op.assemble(p)
+    B = gen.rhs_uniform(p.n, 8, seed=21)
+    Aop = api.Operator.from_problem(ctx, p)
+    M = api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, MIXED)
+    X0, r0 = M.solve_block(to_dev(B), tol=1e-8)
+    monkeypatch.setenv("NLSP_BLOCK_TC", tc_mode)
+    X1, r1 = M.solve_block(to_dev(B), tol=1e-8)
+    for c in range(B.shape[1]):
+        true = np.linalg.norm(B[:, c] - A @ to_np(X1)[:, c]) / np.linalg.norm(B[:, c])
+        assert r1[c].status == 0 and true <= 1e-8 * 1.01
+        assert abs(r1[c].iterations - r0[c].iterations) <= 1
+
+
 def test_block_anisotropic_256_mixed(ctx):
     # 9-point rotated anisotropy (eps = 1e-3), k = 64, 32 right-hand sides
     api = _api()
