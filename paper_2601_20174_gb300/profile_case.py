@@ -8,6 +8,10 @@ with --mode 2 and NLSP_PHASE_TIMERS=1 in the environment the persistent
 solver's per-phase times are printed (microseconds per iteration).
 
     python -m paper_2601_20174_gb300.profile_case [--precision mixed|fp64] [--iters 4] [--N 512] [--mode 0|1|2]
+
+With --block the 2D rotated anisotropic 9-point workload (N^2 nodes, k from K
+device-drawn samples, 32 right-hand sides) runs --iters iterations of the
+block PCG instead.
 """
 from __future__ import annotations
 
@@ -27,7 +31,22 @@ def main() -> int:
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--K", type=int, default=128)
     ap.add_argument("--mode", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--block", action="store_true", help="block PCG on the anisotropic 9-point workload")
     args = ap.parse_args()
+    if args.block:
+        p = gen.aniso_9pt_2d(args.N, args.k, args.K, m=32, seed=0, tol=1e-8, with_samples=False)
+        ctx = api.Context(0)
+        A = api.Operator.from_problem(ctx, p)
+        prec = L.NLSP_MIXED_FP32 if args.precision == "mixed" else L.NLSP_FP64
+        M = api.Preconditioner.build(A, None, args.k, p.s1, p.nu, p.omega, prec, K=args.K, seed=p.seed)
+        F = torch.as_tensor(p.f).cuda()
+        _, res = M.solve_block(F, tol=1e-8, maxit=args.iters)
+        torch.cuda.synchronize()
+        print(f"profile case (block): n={p.n} k={args.k} rhs=32 iterations={res[0].iterations} status={res[0].status}")
+        M.close()
+        A.close()
+        ctx.close()
+        return 0
     p = gen.grf_diffusion_2d(args.N, args.k, args.K, seed=0)
     ctx = api.Context(0)
     A = api.Operator.from_problem(ctx, p)
