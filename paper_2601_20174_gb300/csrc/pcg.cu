@@ -1299,6 +1299,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       a.x[i] = 0.0;
       a.p0[i] = 0.0;
       a.p1[i] = 0.0;
+      a.q[i] = 0.0;  // q = A z + beta q_old starts from q_old = 0
       s = fma(bi, bi, s);
     }
     put(1, s, 0.0);
@@ -1322,17 +1323,17 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
     const double* zc = (t & 1) ? a.z1 : a.z0;
     const double* pin = (t & 1) ? a.p1 : a.p0;
     double* pout = (t & 1) ? a.p0 : a.p1;
-    {  // spmv: p = z + beta p_old on the own nodes first (their z and p_old
-       // are loaded while the team's r^T z is added up), then q = A p with p
-       // read back inside the own range and recomputed on halo nodes (the
-       // same expression, so the same value the owner stores)
+    {  // spmv in the form q = A z + beta q_old (= A p for p = z + beta p_old):
+       // A z on the own nodes needs no beta, so it is computed while the
+       // team's r^T z (and r^T z_old) are added up; then p, q and p^T q.
       tot_issue(2);
-      double zv[4], pv4[4];
+      double az[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int iu = i0 + tid + u * PT;
-        zv[u] = iu < i1 ? __ldcg(zc + iu) : 0.0;
-        pv4[u] = iu < i1 ? __ldcg(pin + iu) : 0.0;
+        az[u] = iu < i1 ? stencil_apply<KIND>(a.A64, iu, node_coord<KIND>(iu, a.A64.N),
+                                              [&](int64_t m) { return __ldcg(zc + m); })
+                        : 0.0;
       }
       mark(MK_SPMV_ISSUE);
       double tot[2] = {0.0, 0.0};
@@ -1346,34 +1347,21 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       }
       rz = rzn;
       mark(MK_SPMV_TOTALS);
+      double s = 0.0;
+      auto update = [&](int i, double azi) {
+        const double pi = fma(beta, __ldcg(pin + i), __ldcg(zc + i));
+        const double qi = fma(beta, a.q[i], azi);
+        pout[i] = pi;
+        a.q[i] = qi;
+        s = fma(pi, qi, s);
+      };
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int iu = i0 + tid + u * PT;
-        if (iu < i1) pout[iu] = fma(beta, pv4[u], zv[u]);
+        if (iu < i1) update(iu, az[u]);
       }
-      for (int i = i0 + tid + 4 * PT; i < i1; i += PT) pout[i] = fma(beta, __ldcg(pin + i), __ldcg(zc + i));
-      __syncthreads();
-      double s = 0.0;
-      auto pv = [&](int64_t m) {
-        return (m >= i0 && m < i1) ? __ldcg(pout + m) : fma(beta, __ldcg(pin + m), __ldcg(zc + m));
-      };
-      for (int i = i0 + tid; i < i1; i += 2 * PT) {
-        const int i2 = i + PT;
-        const bool two = i2 < i1;
-        const double pi = __ldcg(pout + i);
-        const double qi = stencil_apply<KIND>(a.A64, i, node_coord<KIND>(i, a.A64.N), pv);
-        double pi2 = 0.0, qi2 = 0.0;
-        if (two) {
-          pi2 = __ldcg(pout + i2);
-          qi2 = stencil_apply<KIND>(a.A64, i2, node_coord<KIND>(i2, a.A64.N), pv);
-        }
-        a.q[i] = qi;
-        s = fma(pi, qi, s);
-        if (two) {
-          a.q[i2] = qi2;
-          s = fma(pi2, qi2, s);
-        }
-      }
+      for (int i = i0 + tid + 4 * PT; i < i1; i += PT)
+        update(i, stencil_apply<KIND>(a.A64, i, node_coord<KIND>(i, a.A64.N), [&](int64_t m) { return __ldcg(zc + m); }));
       mark(MK_SPMV_NODES);
       put(1, s, 0.0);
       if (!bar(PH_SPMV)) break;
