@@ -613,6 +613,8 @@ struct PersistArgs {
   double* p1;
   double* z0;
   double* z1;
+  double* r1;  // second residual buffer (merged CG update + restriction)
+  int merge;   // 1: the CG update runs inside the restriction phase (staged 2D, FP32)
   T* rT;    // residual in the preconditioner precision (== r for FP64)
   T* zw;    // preconditioner work vectors
   T* zw2;
@@ -754,6 +756,18 @@ __device__ __forceinline__ void ring_issue(uint64_t* bar, T* buf, const T* P, in
 __device__ __forceinline__ bool ring_wait(uint64_t* bar, int nstage, unsigned j) {
   return tma::mbar_wait(&bar[j % (unsigned)nstage], (j / (unsigned)nstage) & 1u);
 }
+
+// Arguments of the restriction when it also performs the CG update
+// (x += alpha p, r_next = r_cur - alpha q): its own nodes' results go to
+// global memory, the updated residual of the own nodes and two stencil hops
+// around them to shared memory for the pre-sweeps.
+struct MergeArgs {
+  double alpha;
+  const double* rc;   // r_cur (read on own and halo nodes)
+  double* rn;         // r_next (own nodes)
+  const double* pd;   // p (own nodes)
+  double s_rr;        // this thread's part of r_next^T r_next
+};
 
 // Node loop over [lo, hi) with stride PT, U nodes per thread at a time:
 // f(m) (loads and arithmetic only) for all U nodes first, then store(m, v)
@@ -961,7 +975,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
   // restrict: rho for the own nodes (z recomputed from rT when zm > 0), then
   // c_cta = P^T rho over the own tiles -> row cta of cpart.  Thread (g, q, lane)
   // accumulates columns [g CPG, g CPG + CPG) for node 32 q + lane of each tile.
-  auto restrict_phase = [&](int zm, const T* zin) {
+  auto restrict_phase = [&](int zm, const T* zin, MergeArgs* mg) {
     const bool staged = zm > 0 && stage_pre;
     if (!staged)
       for (int s = 0; s < nstage && s < nst; ++s)
@@ -971,10 +985,26 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       // z2 = z1 + w D^-1 (rT - A z1) on one row around them, both in the ring
       // buffer; rho = rT - A z2 on the own nodes.  Same arithmetic as
       // presmooth_at, without recomputing z1 and z2 at every neighbour.
-      T* z1s = buf;
-      T* z2s = buf + (e2hi - e2lo);
+      T* rts = buf;                                   // merged: updated residual (E2)
+      T* z1s = buf + (mg ? (e2hi - e2lo) : 0);
+      T* z2s = z1s + (e2hi - e2lo);
+      if (mg) {
+        node_batches<4>(
+            e2lo, e2hi, [&](int m) { return fma(-mg->alpha, __ldcg(a.q + m), __ldcg(mg->rc + m)); },
+            [&](int m, double v) {
+              rts[m - e2lo] = (T)v;
+              if (m >= i0 && m < i1) {
+                mg->rn[m] = v;
+                a.rT[m] = (T)v;
+                a.x[m] = fma(mg->alpha, mg->pd[m], a.x[m]);
+                mg->s_rr = fma(v, v, mg->s_rr);
+              }
+            });
+        __syncthreads();
+      }
+      auto rt = [&](int m) -> T { return mg ? rts[m - e2lo] : a.rT[m]; };
       node_batches<4>(
-          e2lo, e2hi, [&](int m) { return omega * stencil_dinv<KIND>(a.AT, m) * a.rT[m]; },
+          e2lo, e2hi, [&](int m) { return omega * stencil_dinv<KIND>(a.AT, m) * rt(m); },
           [&](int m, T v) { z1s[m - e2lo] = v; });
       __syncthreads();
       mark(MK_RES_STAGE_A);
@@ -984,7 +1014,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
             [&](int m) {
               const T az = stencil_apply<KIND>(a.AT, m, node_coord<KIND>(m, a.AT.N),
                                                [&](int64_t mm) { return z1s[mm - e2lo]; });
-              return z1s[m - e2lo] + omega * stencil_dinv<KIND>(a.AT, m) * (a.rT[m] - az);
+              return z1s[m - e2lo] + omega * stencil_dinv<KIND>(a.AT, m) * (rt(m) - az);
             },
             [&](int m, T v) { z2s[m - e1lo] = v; });
         __syncthreads();
@@ -997,7 +1027,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
           [&](int i) {
             const T az = stencil_apply<KIND>(a.AT, i, node_coord<KIND>(i, a.AT.N),
                                              [&](int64_t mm) { return zs[mm - zlo]; });
-            return RhoZ<T>{a.rT[i] - az, zs[i - zlo]};
+            return RhoZ<T>{rt(i) - az, zs[i - zlo]};
           },
           [&](int i, RhoZ<T> v) {
             rho_s[i - i0] = v.rho;
@@ -1195,8 +1225,11 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
   // while the restriction runs; the application stops after the restriction
   // (returns 2) when that shows convergence or a non-finite residual.
   // Returns 0 when a wait gave up, 1 when done.
-  auto apply = [&](double* zout64, const double* zold64, bool flex, double* rr_out) -> int {
-    if (rr_out) tot_issue(1);
+  const double* rpost = a.r;  // the residual the post-smoothing's r^T z uses
+  // With mg (merged path) the restriction also performs the CG update and
+  // its barrier carries r^T r, added up during the prolongation.
+  auto apply = [&](double* zout64, const double* zold64, bool flex, double* rr_out, MergeArgs* mg) -> int {
+    if (rr_out && !mg) tot_issue(1);
     T* cur = a.zw;
     T* oth = a.zw2;
     const bool fused_pre = FP32 && a.nu1 <= 2;
@@ -1213,15 +1246,23 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         if (!bar(PH_SMOOTH)) return 0;
       }
     }
-    restrict_phase(fused_pre ? a.nu1 : 0, cur);
-    if (rr_out) {
+    restrict_phase(fused_pre ? a.nu1 : 0, cur, mg);
+    if (rr_out && !mg) {
       double o[1] = {0.0};
       if (!tot_finish(1, o)) return 0;
       *rr_out = o[0];
       if (!isfinite(o[0]) || o[0] <= tol2bn) return 2;
     }
+    if (mg) put(1, mg->s_rr, 0.0);
     if (!bar(PH_RESTRICT)) return 0;
+    if (mg) tot_issue(1);
     prolong_phase(cur);
+    if (mg) {
+      double o[1] = {0.0};
+      if (!tot_finish(1, o)) return 0;
+      *rr_out = o[0];
+      if (!isfinite(o[0]) || o[0] <= tol2bn) return 2;
+    }
     if (!bar(PH_PROLONG)) return 0;
     const int nfinal = (FP32 && a.nu2 >= 2) ? 2 : 1;
     for (int sw = nfinal; sw < a.nu2; ++sw) {
@@ -1252,7 +1293,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
             const T az4 = stencil_apply<KIND>(a.AT, i, node_coord<KIND>(i, a.AT.N),
                                               [&](int64_t mm) { return z3c[mm - e1lo]; });
             const T zf = z3c[i - e1lo] + omega * stencil_dinv<KIND>(a.AT, i) * (a.rT[i] - az4);
-            return PostVals{(double)zf, a.r[i], flex ? zold64[i] : 0.0};
+            return PostVals{(double)zf, rpost[i], flex ? zold64[i] : 0.0};
           },
           [&](int i, PostVals v) {
             zout64[i] = v.zd;
@@ -1277,7 +1318,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         zf = cur[i] + omega * stencil_dinv<KIND>(a.AT, i) * (a.rT[i] - az);
       }
       const double zd = (double)zf;
-      const double ri = a.r[i];
+      const double ri = rpost[i];
       zout64[i] = zd;
       s_rz = fma(ri, zd, s_rz);
       if (flex) s_ro = fma(ri, zold64[i], s_ro);
@@ -1315,7 +1356,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
     done = true;
   }
   // initial preconditioner application z_0 = B r_0
-  if (!done && apply(a.z0, a.z1, false, nullptr) != 1) done = true;
+  if (!done && apply(a.z0, a.z1, false, nullptr, nullptr) != 1) done = true;
   // ---- iterations --------------------------------------------------------
   while (!done && ok) {
     const int t = iter;
@@ -1367,6 +1408,32 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       if (!bar(PH_SPMV)) break;
     }
     iter = t + 1;
+    if (a.merge) {
+      // the CG update runs inside the restriction; r alternates between
+      // two buffers so that halo nodes read the previous residual
+      tot_issue(1);
+      double tot[1] = {0.0};
+      if (!tot_finish(1, tot)) break;
+      const double pq = tot[0];
+      if (!(pq > 0.0) || !isfinite(pq)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
+      MergeArgs mg;
+      mg.alpha = rz / pq;
+      mg.rc = (t & 1) ? a.r1 : a.r;
+      mg.rn = (t & 1) ? a.r : a.r1;
+      mg.pd = pout;
+      mg.s_rr = 0.0;
+      mark(MK_PRE_TOTALS);
+      rpost = mg.rn;
+      double* zn = (iter & 1) ? a.z1 : a.z0;
+      const double* zo = (iter & 1) ? a.z0 : a.z1;
+      const int st_apply = apply(zn, zo, a.flexible != 0, &rr, &mg);
+      if (st_apply == 0) break;
+      if (st_apply == 2) {
+        if (!isfinite(rr)) status = (int)NLSP_ERR_BREAKDOWN;
+        break;
+      }
+      continue;
+    }
     {  // pre: x, r update; the own nodes' data is loaded while p^T q is added up
       tot_issue(1);
       double pv[4], xv[4], qv[4], rv[4];
@@ -1405,7 +1472,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
     }
     double* zn = (iter & 1) ? a.z1 : a.z0;
     const double* zo = (iter & 1) ? a.z0 : a.z1;
-    const int st_apply = apply(zn, zo, a.flexible != 0, &rr);
+    const int st_apply = apply(zn, zo, a.flexible != 0, &rr, nullptr);
     if (st_apply == 0) break;
     if (st_apply == 2) {
       if (!isfinite(rr)) status = (int)NLSP_ERR_BREAKDOWN;
@@ -1560,8 +1627,8 @@ nlsp_status ensure_work(nlsp_prec* M, int m) {
     w->tsize = M->precision == NLSP_FP64 ? 8 : 4;
     w->max_blocks = ctx->num_sms * NODE_BPS;
     M->pcg = w;
-    NLSP_CUDA(cudaMalloc(&w->vec, sizeof(double) * M->n * 7));
-    NLSP_CUDA(cudaMemsetAsync(w->vec, 0, sizeof(double) * M->n * 7, ctx->stream));
+    NLSP_CUDA(cudaMalloc(&w->vec, sizeof(double) * M->n * 8));  // x r q p0 p1 z0 z1 r1
+    NLSP_CUDA(cudaMemsetAsync(w->vec, 0, sizeof(double) * M->n * 8, ctx->stream));
     NLSP_CUDA(cudaMalloc(&w->rT, (size_t)w->tsize * M->n));
     NLSP_CUDA(cudaMalloc(&w->part, sizeof(double) * 4 * w->max_blocks));
     // [0..3]: last-block arrival counters of the graph kernels;
@@ -1945,6 +2012,21 @@ struct Solver {
     return NLSP_OK;
   }
 
+  // Whether the CG update can run inside the staged restriction: FP32, a 2D
+  // stencil, fused pre-smoothing (nu <= 2) and, for the largest CTA share,
+  // room in the ring buffer for the updated residual and both pre-sweeps
+  // over the own nodes plus two stencil hops (N + 1 nodes each).  Off with
+  // NLSP_MERGE_PRE=0.
+  static int merge_ok(const nlsp_prec* M, const StreamArgs& sa) {
+    static const char* env = getenv("NLSP_MERGE_PRE");
+    if (env && env[0] == '0') return 0;
+    if (sizeof(T) != 4 || KIND == ST_7PT || M->nu1 > 2) return 0;
+    const int64_t hop = (int64_t)M->A->N + 1;
+    const int64_t nodes = sa.max_nodes;
+    const int64_t need = 2 * (nodes + 4 * hop) + (nodes + 2 * hop);
+    return need <= (int64_t)sa.nstage * M->r * NLSP_TILE ? 1 : 0;
+  }
+
   // Exchange words of one instance solved by `team` CTAs (zero at launch).
   static size_t xw_words(const nlsp_prec* M, int team) {
     return 2 + (size_t)4 * ((team + 1) & ~1) + ((size_t)team * M->k * sizeof(T) + 7) / 8;
@@ -1975,6 +2057,8 @@ struct Solver {
     a.p1 = P2.v[1];
     a.z0 = Z2.v[0];
     a.z1 = Z2.v[1];
+    a.r1 = w->vec + 7 * w->n;
+    a.merge = merge_ok(M, sa);
     a.rT = rT(w);
     a.zw = (T*)M->w0;
     a.zw2 = (T*)M->w1;
