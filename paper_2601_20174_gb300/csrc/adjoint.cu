@@ -217,22 +217,34 @@ __global__ void __launch_bounds__(RV_THREADS) k_restrict_vec(const T* __restrict
   }
 }
 
-// c = sum of the block partials (block order); e = A_c^-1 c (FP64).  Both
-// may be stored (c_out / e_out nullable).  One block of 128 threads.
-__global__ void k_coarse_apply(const double* __restrict__ part, int nb, int k, const double* __restrict__ Ainv,
-                               double* __restrict__ c_out, double* __restrict__ e_out) {
+// c = sum of the block partials; e = A_c^-1 c (FP64).  Both may be stored
+// (c_out / e_out nullable).  One block of 256 threads: 256 / k groups add
+// interleaved blocks of the partials, then the groups are added in order.
+constexpr int CA_THREADS = 256;
+
+__global__ void __launch_bounds__(CA_THREADS) k_coarse_apply(const double* __restrict__ part, int nb, int k,
+                                                            const double* __restrict__ Ainv,
+                                                            double* __restrict__ c_out, double* __restrict__ e_out) {
+  __shared__ double gsum[CA_THREADS];
   __shared__ double c[128];
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * k + j];
-    c[j] = s;
-    if (c_out) c_out[j] = s;
+  const int groups = CA_THREADS / k;  // k <= 128: at least 2
+  const int j = threadIdx.x % k, g = threadIdx.x / k;
+  double s = 0.0;
+  if (g < groups)
+    for (int b = g; b < nb; b += groups) s += part[(int64_t)b * k + j];
+  gsum[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double t = 0.0;
+    for (int q = 0; q < groups; ++q) t += gsum[q * k + threadIdx.x];
+    c[threadIdx.x] = t;
+    if (c_out) c_out[threadIdx.x] = t;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < k; ++j) s = fma(Ainv[(int64_t)j * k + i], c[j], s);
-    if (e_out) e_out[i] = s;
+  for (int i = threadIdx.x; i < k; i += CA_THREADS) {
+    double t = 0.0;
+    for (int jj = 0; jj < k; ++jj) t = fma(Ainv[(int64_t)jj * k + i], c[jj], t);
+    if (e_out) e_out[i] = t;
   }
 }
 
@@ -668,7 +680,7 @@ struct Unrolled {
     k_resid<KIND, TP><<<g, VB, 0, s>>>(AT, v, cur, rho);
     k_restrict_vec<TP><<<nb, RV_THREADS, 0, s>>>((const TP*)M->P, k, n_pad, rho, part);
     double* e = j >= 0 ? E + (size_t)j * k : vtmp + n;  // vtmp holds n + k doubles
-    k_coarse_apply<<<1, 128, 0, s>>>(part, nb, k, M->Ainv, nullptr, e);
+    k_coarse_apply<<<1, CA_THREADS, 0, s>>>(part, nb, k, M->Ainv, nullptr, e);
     k_prolong_vec<TP><<<nb, NLSP_TILE, 0, s>>>((const TP*)M->P, k, n, e, cur);
     for (int sw = 0; sw < nu; ++sw) {
       k_jsweep<KIND, TP><<<g, VB, 0, s>>>(AT, omega, v, cur, oth);
@@ -693,7 +705,7 @@ struct Unrolled {
     TP* yb = YB + (size_t)j * n_pad;
     cudaMemcpyAsync(yb, cur, sizeof(TP) * n_pad, cudaMemcpyDeviceToDevice, s);
     k_restrict_vec<TP><<<nb, RV_THREADS, 0, s>>>((const TP*)M->P, k, n_pad, yb, part);
-    k_coarse_apply<<<1, 128, 0, s>>>(part, nb, k, M->Ainv, nullptr, CB + (size_t)j * k);
+    k_coarse_apply<<<1, CA_THREADS, 0, s>>>(part, nb, k, M->Ainv, nullptr, CB + (size_t)j * k);
     launches += nu + 3;
   }
 

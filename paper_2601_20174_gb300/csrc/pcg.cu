@@ -2018,7 +2018,7 @@ struct Solver {
   // over the own nodes plus two stencil hops (N + 1 nodes each).  Off with
   // NLSP_MERGE_PRE=0.
   static int merge_ok(const nlsp_prec* M, const StreamArgs& sa) {
-    static const char* env = getenv("NLSP_MERGE_PRE");
+    const char* env = getenv("NLSP_MERGE_PRE");
     if (env && env[0] == '0') return 0;
     if (sizeof(T) != 4 || KIND == ST_7PT || M->nu1 > 2) return 0;
     const int64_t hop = (int64_t)M->A->N + 1;

@@ -32,7 +32,32 @@ def main() -> int:
     ap.add_argument("--K", type=int, default=128)
     ap.add_argument("--mode", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--block", action="store_true", help="block PCG on the anisotropic 9-point workload")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="subspace loss and T=10 unrolled-PCG loss with gradients on the 3D 7-point N^3 workload")
     args = ap.parse_args()
+    if args.adjoint:
+        import ctypes as C
+        p = gen.iid_diffusion_3d(args.N, args.k, args.K, seed=0, with_samples=False)
+        ctx = api.Context(0)
+        A = api.Operator.from_problem(ctx, p)
+        prec = L.NLSP_MIXED_FP32 if args.precision == "mixed" else L.NLSP_FP64
+        M = api.Preconditioner.build(A, None, args.k, p.s1, p.nu, p.omega, L.NLSP_FP64, K=args.K, seed=p.seed)
+        U = M.basis().contiguous()
+        S0 = torch.empty(args.K, p.n, dtype=torch.float64, device="cuda")
+        L.check(ctx._lib.nlsp_random_normal(ctx.h, p.seed, gen.STREAM_S0, 0, p.n * args.K,
+                                            C.c_void_p(S0.data_ptr())), "nlsp_random_normal")
+        B = torch.empty_like(S0)
+        L.check(ctx._lib.nlsp_smooth_samples(ctx.h, A.h, args.K, p.s1, p.omega, L.NLSP_FP64,
+                                             C.c_void_p(S0.data_ptr()), C.c_void_p(B.data_ptr())), "smooth")
+        b = torch.as_tensor(p.f[:, 0].copy()).cuda()
+        l1, _ = api.subspace_loss(ctx, U, B.t(), prec)
+        l2, _ = api.unrolled_pcg(A, U, b, 10, p.nu, p.omega, prec)
+        torch.cuda.synchronize()
+        print(f"profile case (adjoint): n={p.n} k={args.k} K={args.K} subspace loss={l1:.6e} unrolled loss={l2:.6e}")
+        M.close()
+        A.close()
+        ctx.close()
+        return 0
     if args.block:
         p = gen.aniso_9pt_2d(args.N, args.k, args.K, m=32, seed=0, tol=1e-8, with_samples=False)
         ctx = api.Context(0)

@@ -230,3 +230,22 @@ def test_persistent_solver_large_grids(ctx, case):
         golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "bench_workloads.json")))
         it_oracle = golden["grf_diffusion2d_N512_k64_K128_seed0"]["iters"]
         assert abs(r2[0].iterations - it_oracle) <= 8
+
+
+@pytest.mark.parametrize("name", ["poisson5", "grf5", "aniso9"])
+def test_persistent_merged_update_matches_separate_phase(ctx, name, monkeypatch):
+    # the CG update inside the staged restriction (default on 2D FP32) and
+    # the separate update phase (NLSP_MERGE_PRE=0) take the same iterations
+    # (+-1) and both reach the FP64 true residual
+    p = PROBLEMS[name]()
+    A = op.assemble(p)
+    Aop = _api().Operator.from_problem(ctx, p)
+    M = _api().Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, MIXED)
+    b = p.f[:, 0]
+    x_m, r_m = M.solve(to_dev(b), tol=1e-8, graph_mode=2)
+    monkeypatch.setenv("NLSP_MERGE_PRE", "0")
+    x_s, r_s = M.solve(to_dev(b), tol=1e-8, graph_mode=2)
+    for x, r in ((x_m, r_m), (x_s, r_s)):
+        true = np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b)
+        assert r[0].status == 0 and true <= 1e-8 * 1.01
+    assert abs(r_m[0].iterations - r_s[0].iterations) <= 1
