@@ -183,6 +183,31 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+# replicas (N > 1): each rank solves its own seeded instance; the only
+# collective is the max of the ranks' timed totals
+# ----------------------------------------------------------------------------
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Instance seed of a rank: independent problems, no data-path exchange."""
+    return base_seed + rank
+
+
+def max_over_ranks(total_ms: float, world: int, device) -> float:
+    """The slowest rank's timed total (all-reduce MAX; identity for one rank)."""
+    if world <= 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, total_ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * steps / (total_ms / 1000.0)
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 BATCH = dict(count=256, seed=0, tol=1e-8, tiles_per_cta=(2, 4, 8, 16, 32, 64))
@@ -368,7 +393,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    p = gen.grf_diffusion_2d(WL["N"], WL["k"], WL["K"], seed=WL["seed"] + rank, tol=WL["tol"])
+    p = gen.grf_diffusion_2d(WL["N"], WL["k"], WL["K"], seed=replica_seed(WL["seed"], rank), tol=WL["tol"])
     n = p.n
     kap_h = torch.as_tensor(p.coeffs.reshape(-1)).pin_memory()
     S0_h = torch.as_tensor(np.ascontiguousarray(p.S0.T)).pin_memory()  # (K, n): column-major n x K
@@ -420,13 +445,10 @@ def run_ours(args):
     ms, (A_m, M_m, x_m, res_m) = timed(lambda: step(mixed, kap, S0s, f), args.steps)
     launches = int(ctx._lib.nlsp_launch_count(ctx.h) - l0)
     clocks = sampler.stop()
-    total_ms = sum(ms)
+    total_ms = max_over_ranks(sum(ms), world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    value = world * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(world, args.steps, total_ms)
     true_m = float(torch.linalg.norm(f - A_m.apply(x_m)) / torch.linalg.norm(f))
 
     # ---- solve only (preconditioner prebuilt) ---------------------------
@@ -480,12 +502,8 @@ def run_ours(args):
         return A, M, x_h
 
     e2e_ms, _ = timed(e2e_step, max(2, args.steps))
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_val = world * len(e2e_ms) / (e2e_total / 1000.0)
+    e2e_total = max_over_ranks(sum(e2e_ms), world, dev)
+    e2e_val = whole_job_rate(world, len(e2e_ms), e2e_total)
     h2d = kap_h.numel() * 8 + S0_h.numel() * 8 + f_h.numel() * 8
 
     # ---- batched: 256 uneven instances in one persistent launch ----------
