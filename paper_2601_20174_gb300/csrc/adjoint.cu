@@ -199,15 +199,19 @@ __global__ void __launch_bounds__(RV_THREADS) k_restrict_vec(const T* __restrict
     T xv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) xv[u] = x[t * NLSP_TILE + lane + 32 * u];
+    // all of the warp's column loads of the tile first, then the products
+    T pv[RV_MAXC][4];
 #pragma unroll
     for (int j = 0; j < RV_MAXC; ++j) {
       const int col = warp + 8 * j;
-      if (col < k) {
-        const T* src = P + (t * k + col) * NLSP_TILE;
+      const T* src = P + (t * k + (col < k ? col : 0)) * NLSP_TILE;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[j] += src[lane + 32 * u] * xv[u];
-      }
+      for (int u = 0; u < 4; ++u) pv[j][u] = col < k ? src[lane + 32 * u] : T(0);
     }
+#pragma unroll
+    for (int j = 0; j < RV_MAXC; ++j)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[j] += pv[j][u] * xv[u];
   }
 #pragma unroll
   for (int j = 0; j < RV_MAXC; ++j) {
@@ -220,14 +224,14 @@ __global__ void __launch_bounds__(RV_THREADS) k_restrict_vec(const T* __restrict
 // c = sum of the block partials; e = A_c^-1 c (FP64).  Both may be stored
 // (c_out / e_out nullable).  One block of 256 threads: 256 / k groups add
 // interleaved blocks of the partials, then the groups are added in order.
-constexpr int CA_THREADS = 256;
+constexpr int CA_THREADS = 1024;
 
 __global__ void __launch_bounds__(CA_THREADS) k_coarse_apply(const double* __restrict__ part, int nb, int k,
                                                             const double* __restrict__ Ainv,
                                                             double* __restrict__ c_out, double* __restrict__ e_out) {
   __shared__ double gsum[CA_THREADS];
   __shared__ double c[128];
-  const int groups = CA_THREADS / k;  // k <= 128: at least 2
+  const int groups = CA_THREADS / k;  // k <= 128: at least 8
   const int j = threadIdx.x % k, g = threadIdx.x / k;
   double s = 0.0;
   if (g < groups)
@@ -241,10 +245,16 @@ __global__ void __launch_bounds__(CA_THREADS) k_coarse_apply(const double* __res
     if (c_out) c_out[threadIdx.x] = t;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < k; i += CA_THREADS) {
-    double t = 0.0;
-    for (int jj = 0; jj < k; ++jj) t = fma(Ainv[(int64_t)jj * k + i], c[jj], t);
-    if (e_out) e_out[i] = t;
+  // e = A_c^-1 c: group g adds columns jj = g, g + groups, ... of row i
+  double t = 0.0;
+  if (g < groups)
+    for (int jj = g; jj < k; jj += groups) t = fma(Ainv[(int64_t)jj * k + j], c[jj], t);
+  gsum[threadIdx.x] = t;
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double e = 0.0;
+    for (int q = 0; q < groups; ++q) e += gsum[q * k + threadIdx.x];
+    if (e_out) e_out[threadIdx.x] = e;
   }
 }
 
@@ -258,10 +268,16 @@ __global__ void __launch_bounds__(NLSP_TILE) k_prolong_vec(const T* __restrict__
   const int64_t ntiles = (n + NLSP_TILE - 1) / NLSP_TILE;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t i = t * NLSP_TILE + threadIdx.x;
-    T s = T(0);
+    T s0 = T(0), s1 = T(0);
     const T* src = P + t * k * NLSP_TILE + threadIdx.x;
-    for (int j = 0; j < k; ++j) s += src[(int64_t)j * NLSP_TILE] * es[j];
-    if (i < n) z[i] += s;
+    int j = 0;
+#pragma unroll 8
+    for (; j + 1 < k; j += 2) {  // sixteen loads in flight, two partial sums
+      s0 += src[(int64_t)j * NLSP_TILE] * es[j];
+      s1 += src[(int64_t)(j + 1) * NLSP_TILE] * es[j + 1];
+    }
+    if (j < k) s0 += src[(int64_t)j * NLSP_TILE] * es[j];
+    if (i < n) z[i] += s0 + s1;
   }
 }
 
@@ -612,7 +628,7 @@ struct Unrolled {
   nlsp_ctx* ctx;
   const nlsp_op* A;
   nlsp_prec* M;
-  int T, nu, k, nb;
+  int T, nu, k, nb, ntb;  // nb: partial-sum grids; ntb: tile-per-block grids
   int64_t n, n_pad;
   TP omega;
   ScalarIndex ix;
@@ -681,7 +697,7 @@ struct Unrolled {
     k_restrict_vec<TP><<<nb, RV_THREADS, 0, s>>>((const TP*)M->P, k, n_pad, rho, part);
     double* e = j >= 0 ? E + (size_t)j * k : vtmp + n;  // vtmp holds n + k doubles
     k_coarse_apply<<<1, CA_THREADS, 0, s>>>(part, nb, k, M->Ainv, nullptr, e);
-    k_prolong_vec<TP><<<nb, NLSP_TILE, 0, s>>>((const TP*)M->P, k, n, e, cur);
+    k_prolong_vec<TP><<<ntb, NLSP_TILE, 0, s>>>((const TP*)M->P, k, n, e, cur);
     for (int sw = 0; sw < nu; ++sw) {
       k_jsweep<KIND, TP><<<g, VB, 0, s>>>(AT, omega, v, cur, oth);
       std::swap(cur, oth);
@@ -780,7 +796,7 @@ struct Unrolled {
     const size_t sm = sizeof(TP) * ((size_t)k * k + 2 * (size_t)T * k);
     auto fn = k_pbar<TP>;
     if (sm > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    fn<<<nb, NLSP_TILE, sm, s>>>(YB, RHO, E, CB, T, AP, W, k, n, n_pad, grad, n);
+    fn<<<ntb, NLSP_TILE, sm, s>>>(YB, RHO, E, CB, T, AP, W, k, n, n_pad, grad, n);
     launches += 3;
     NLSP_LAUNCH_CHECK();
     return NLSP_OK;
@@ -801,6 +817,7 @@ struct Unrolled {
     u.ix.T = T;
     u.s = ctx->stream;
     u.nb = std::max(1, std::min<int>(2 * ctx->num_sms, (int)(u.n_pad / NLSP_TILE)));
+    u.ntb = (int)std::max<int64_t>(1, std::min<int64_t>(u.n_pad / NLSP_TILE, (int64_t)16 * ctx->num_sms));
     const int64_t n = u.n, n_pad = u.n_pad, k = u.k;
     Arena ar;
     const std::vector<size_t> parts = {
@@ -974,7 +991,8 @@ nlsp_status subspace_impl(nlsp_ctx* ctx, int64_t n, int k, int K, const double* 
     const size_t sm = sizeof(TP) * (size_t)(K + k) * k;
     auto fn = k_tile_gemm2<TP>;
     if (sm > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    fn<<<nb, NLSP_TILE, sm, s>>>(Bt, K, X, Pt, k, Z, k, n, n_pad, grad, n);
+    const int ntb = (int)std::min<int64_t>(n_pad / NLSP_TILE, (int64_t)16 * ctx->num_sms);
+    fn<<<ntb, NLSP_TILE, sm, s>>>(Bt, K, X, Pt, k, Z, k, n, n_pad, grad, n);
     NLSP_LAUNCH_CHECK();
     launches += 5;
   }
