@@ -459,24 +459,61 @@ __global__ void k_sum_blocks(const double* __restrict__ part, int nb, int count,
   }
 }
 
+// acc[0..KC) += sum over the nc input columns c of x[c] * m[c][j0 + j] for
+// one node: x points at the node's entry of column 0 of a tile (columns
+// NLSP_TILE apart), m is row-major with rows padded to ldm (a multiple of the
+// 16-byte vector width, zeros past the last column).  Input loads are issued
+// CU at a time ahead of their products; m is read as 16-byte broadcasts.
+template <typename T, int KC, int CU>
+__device__ __forceinline__ void tile_rows_times(const T* __restrict__ x, int nc, const T* m, int ldm, int j0,
+                                                T (&acc)[KC]) {
+  using V = typename Vec16<T>::type;
+  constexpr int VN = Vec16<T>::N;
+  for (int c0 = 0; c0 < nc; c0 += CU) {
+    T sv[CU];
+#pragma unroll
+    for (int u = 0; u < CU; ++u) sv[u] = c0 + u < nc ? x[(int64_t)(c0 + u) * NLSP_TILE] : T(0);
+#pragma unroll
+    for (int u = 0; u < CU; ++u) {
+      if (c0 + u >= nc) break;
+      const T* mrow = m + (c0 + u) * ldm + j0;
+#pragma unroll
+      for (int j = 0; j < KC; j += VN) {
+        if (j0 + j >= ldm) break;
+        T mv[VN];
+        *reinterpret_cast<V*>(mv) = *reinterpret_cast<const V*>(mrow + j);
+#pragma unroll
+        for (int q = 0; q < VN; ++q) acc[j + q] += sv[u] * mv[q];
+      }
+    }
+  }
+}
+
+constexpr int TG_KC = 32;  // output columns per register pass of k_tile_gemm2
+constexpr int TG_CU = 8;   // input loads in flight
+
+__host__ __device__ constexpr int tg_ldm(int k) { return (k + 3) / 4 * 4; }
+
 // Out (column-major FP64 n x k, ld) = In1 M1 + In2 M2 with In1 (nc1 columns)
 // and In2 (nc2 columns) node-tiled, M1 (nc1 x k) and M2 (nc2 x k)
-// column-major FP64.  One 128-thread block per tile at a time.
+// column-major FP64.  One 128-thread block per tile at a time; M1 and M2 sit
+// in shared memory as T, rows padded to tg_ldm(k).
 template <typename T>
 __global__ void __launch_bounds__(NLSP_TILE) k_tile_gemm2(const T* __restrict__ In1, int nc1,
                                                          const double* __restrict__ M1, const T* __restrict__ In2,
                                                          int nc2, const double* __restrict__ M2, int k, int64_t n,
                                                          int64_t n_pad, double* __restrict__ out, int64_t ld) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* m1 = reinterpret_cast<T*>(smem_raw);  // [nc1][k] row-major (row = input column)
-  T* m2 = m1 + (size_t)nc1 * k;
-  for (int e = threadIdx.x; e < nc1 * k; e += NLSP_TILE) {
-    const int c = e / k, j = e % k;
-    m1[e] = (T)M1[(int64_t)j * nc1 + c];
+  const int ldm = tg_ldm(k);
+  T* m1 = reinterpret_cast<T*>(smem_raw);  // [nc1][ldm] (row = input column)
+  T* m2 = m1 + (size_t)nc1 * ldm;
+  for (int e = threadIdx.x; e < nc1 * ldm; e += NLSP_TILE) {
+    const int c = e / ldm, j = e % ldm;
+    m1[e] = j < k ? (T)M1[(int64_t)j * nc1 + c] : T(0);
   }
-  for (int e = threadIdx.x; e < nc2 * k; e += NLSP_TILE) {
-    const int c = e / k, j = e % k;
-    m2[e] = (T)M2[(int64_t)j * nc2 + c];
+  for (int e = threadIdx.x; e < nc2 * ldm; e += NLSP_TILE) {
+    const int c = e / ldm, j = e % ldm;
+    m2[e] = j < k ? (T)M2[(int64_t)j * nc2 + c] : T(0);
   }
   __syncthreads();
   const int64_t ntiles = n_pad / NLSP_TILE;
@@ -484,25 +521,15 @@ __global__ void __launch_bounds__(NLSP_TILE) k_tile_gemm2(const T* __restrict__ 
     const int64_t i = t * NLSP_TILE + threadIdx.x;
     const T* x1 = In1 + t * nc1 * NLSP_TILE + threadIdx.x;
     const T* x2 = In2 + t * nc2 * NLSP_TILE + threadIdx.x;
-    for (int c0 = 0; c0 < k; c0 += PB_CH) {
-      T acc[PB_CH];
+    for (int c0 = 0; c0 < k; c0 += TG_KC) {
+      T acc[TG_KC];
 #pragma unroll
-      for (int jj = 0; jj < PB_CH; ++jj) acc[jj] = T(0);
-      for (int c = 0; c < nc1; ++c) {
-        const T v = x1[(int64_t)c * NLSP_TILE];
-#pragma unroll
-        for (int jj = 0; jj < PB_CH; ++jj)
-          if (c0 + jj < k) acc[jj] += v * m1[c * k + c0 + jj];
-      }
-      for (int c = 0; c < nc2; ++c) {
-        const T v = x2[(int64_t)c * NLSP_TILE];
-#pragma unroll
-        for (int jj = 0; jj < PB_CH; ++jj)
-          if (c0 + jj < k) acc[jj] += v * m2[c * k + c0 + jj];
-      }
+      for (int jj = 0; jj < TG_KC; ++jj) acc[jj] = T(0);
+      tile_rows_times<T, TG_KC, TG_CU>(x1, nc1, m1, ldm, c0, acc);
+      tile_rows_times<T, TG_KC, TG_CU>(x2, nc2, m2, ldm, c0, acc);
       if (i < n) {
 #pragma unroll
-        for (int jj = 0; jj < PB_CH; ++jj)
+        for (int jj = 0; jj < TG_KC; ++jj)
           if (c0 + jj < k) out[(int64_t)(c0 + jj) * ld + i] = (double)acc[jj];
       }
     }
@@ -988,7 +1015,7 @@ nlsp_status subspace_impl(nlsp_ctx* ctx, int64_t n, int k, int K, const double* 
     k_small_mm<<<div_up((int64_t)k * k, 128), 128, 0, s>>>(C, 0, C, 1, CC, k, k, K, 1.0);   // C C^T
     k_small_mm<<<div_up((int64_t)k * k, 128), 128, 0, s>>>(CC, 0, Li, 0, Zt, k, k, k, 1.0);  // C C^T L^-1
     k_small_mm<<<div_up((int64_t)k * k, 128), 128, 0, s>>>(Li, 1, Zt, 0, Z, k, k, k, 2.0);  // 2 L^-T C C^T L^-1
-    const size_t sm = sizeof(TP) * (size_t)(K + k) * k;
+    const size_t sm = sizeof(TP) * (size_t)(K + k) * tg_ldm(k);
     auto fn = k_tile_gemm2<TP>;
     if (sm > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int ntb = (int)std::min<int64_t>(n_pad / NLSP_TILE, (int64_t)16 * ctx->num_sms);

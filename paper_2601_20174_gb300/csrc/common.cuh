@@ -31,6 +31,21 @@
 void nlsp_record_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 void nlsp_record_message(const char* msg);
 
+// 16-byte vector of T (float4 / double2), for broadcast reads of small
+// matrices held in shared memory.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int N = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int N = 2;
+};
+
 // ----------------------------------------------------------------------------
 // Geometry and layouts
 // ----------------------------------------------------------------------------

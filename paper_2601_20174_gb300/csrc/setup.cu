@@ -80,6 +80,22 @@ __device__ __forceinline__ double normal_draw(uint64_t base, uint64_t idx) {
   return rad * ((idx & 1) ? s : c);
 }
 
+// The same draw evaluated in FP32 (for FP32 sample blocks): 1 - u1 is formed
+// exactly as an integer and rounded once, u2 keeps its top 24 bits, and the
+// transform uses FP32 log / sincospi.  Agrees with normal_draw to a few FP32
+// ulps of the radius plus 2^-24 of the angle.
+__device__ __forceinline__ float normal_draw_f32(uint64_t base, uint64_t idx) {
+  const uint64_t j = idx >> 1;
+  const uint64_t a = splitmix_fin(base + (2 * j + 1) * 0x9E3779B97F4A7C15ull);
+  const uint64_t b = splitmix_fin(base + (2 * j + 2) * 0x9E3779B97F4A7C15ull);
+  const float om = __ull2float_rn((1ull << 53) - (a >> 11)) * 0x1.0p-53f;  // 1 - u1, in (0, 1]
+  const float u2 = __uint2float_rn((unsigned)(b >> 40)) * 0x1.0p-24f;
+  const float rad = sqrtf(-2.0f * logf(om));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return rad * ((idx & 1) ? s : c);
+}
+
 template <typename T>
 __global__ void k_random_samples_tiled(uint64_t base, int64_t n, int ncols, int64_t n_pad, T* __restrict__ dst) {
   const int64_t total = n_pad * ncols;
@@ -87,7 +103,14 @@ __global__ void k_random_samples_tiled(uint64_t base, int64_t n, int ncols, int6
     const int64_t t = e / ((int64_t)ncols * NLSP_TILE);
     const int c = (int)((e / NLSP_TILE) % ncols);
     const int64_t i = t * NLSP_TILE + (e % NLSP_TILE);
-    dst[e] = i < n ? (T)normal_draw(base, (uint64_t)c * n + i) : T(0);
+    T v = T(0);
+    if (i < n) {
+      if constexpr (sizeof(T) == 4)
+        v = normal_draw_f32(base, (uint64_t)c * n + i);
+      else
+        v = (T)normal_draw(base, (uint64_t)c * n + i);
+    }
+    dst[e] = v;
   }
 }
 
@@ -157,37 +180,73 @@ __global__ void __launch_bounds__(TD* TD) k_tsgemm(StencilView<T> A, const T* __
     for (int b = 0; b < RB; ++b) acc[a][b] = T(0);
 
   const int64_t ntiles = n_pad / NLSP_TILE;
-  const int nthreads = TD * TD;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    for (int w0 = 0; w0 < NLSP_TILE; w0 += GRAM_CW) {
-      __syncthreads();
-      // stage X chunk (and A X chunk) transposed: element (w, c)
-      for (int e = threadIdx.x; e < GRAM_CW * KP; e += nthreads) {
+  constexpr int nthreads = TD * TD;
+  auto products = [&]() {
+#pragma unroll 1
+    for (int w = 0; w < GRAM_CW; ++w) {
+      T xa[RB], yb[RB];
+#pragma unroll
+      for (int a = 0; a < RB; ++a) xa[a] = xs[w * LDS + ty * RB + a];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) yb[b] = ys[w * LDS + tx * RB + b];
+#pragma unroll
+      for (int a = 0; a < RB; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) acc[a][b] += xa[a] * yb[b];
+    }
+  };
+  if constexpr (!WITH_A) {
+    // Software pipeline over the block's chunks (CW nodes of one tile each):
+    // the loads of chunk q + 1 are in flight while chunk q is multiplied.
+    constexpr int PER = GRAM_CW * KP / nthreads;
+    static_assert(PER * nthreads == GRAM_CW * KP, "chunk must split evenly over the block");
+    constexpr int CPT = NLSP_TILE / GRAM_CW;  // chunks per tile
+    const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t nchunks = my_tiles * CPT;
+    T pre[PER];
+    auto load = [&](int64_t q) {
+      const int64_t t = blockIdx.x + (q / CPT) * gridDim.x;
+      const int w0 = (int)(q % CPT) * GRAM_CW;
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * nthreads;
         const int c = e / GRAM_CW, w = e % GRAM_CW;
-        T xv = T(0), yv = T(0);
-        const int64_t i = t * NLSP_TILE + w0 + w;
-        if (c < ncx) {
-          xv = X[(t * ncols + c) * NLSP_TILE + w0 + w];
-          if (WITH_A && i < A.n) {
-            const NodeCoord nc = node_coord<KIND>(i, A.N);
-            yv = stencil_apply<KIND>(A, i, nc, [&](int64_t m) { return X[tiled_index(m, c, ncols)]; });
-          }
-        }
-        xs[w * LDS + c] = xv;
-        if (WITH_A) ys[w * LDS + c] = yv;
+        pre[u] = c < ncx ? X[(t * ncols + c) * NLSP_TILE + w0 + w] : T(0);
+      }
+    };
+    if (nchunks > 0) load(0);
+    for (int64_t q = 0; q < nchunks; ++q) {
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * nthreads;
+        xs[(e % GRAM_CW) * LDS + e / GRAM_CW] = pre[u];
       }
       __syncthreads();
-#pragma unroll 4
-      for (int w = 0; w < GRAM_CW; ++w) {
-        T xa[RB], yb[RB];
-#pragma unroll
-        for (int a = 0; a < RB; ++a) xa[a] = xs[w * LDS + ty * RB + a];
-#pragma unroll
-        for (int b = 0; b < RB; ++b) yb[b] = ys[w * LDS + tx * RB + b];
-#pragma unroll
-        for (int a = 0; a < RB; ++a)
-#pragma unroll
-          for (int b = 0; b < RB; ++b) acc[a][b] += xa[a] * yb[b];
+      if (q + 1 < nchunks) load(q + 1);
+      products();
+    }
+  } else {
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      for (int w0 = 0; w0 < NLSP_TILE; w0 += GRAM_CW) {
+        __syncthreads();
+        // stage the X chunk and the A X chunk transposed: element (w, c)
+        for (int e = threadIdx.x; e < GRAM_CW * KP; e += nthreads) {
+          const int c = e / GRAM_CW, w = e % GRAM_CW;
+          T xv = T(0), yv = T(0);
+          const int64_t i = t * NLSP_TILE + w0 + w;
+          if (c < ncx) {
+            xv = X[(t * ncols + c) * NLSP_TILE + w0 + w];
+            if (i < A.n) {
+              const NodeCoord nc = node_coord<KIND>(i, A.N);
+              yv = stencil_apply<KIND>(A, i, nc, [&](int64_t m) { return X[tiled_index(m, c, ncols)]; });
+            }
+          }
+          xs[w * LDS + c] = xv;
+          ys[w * LDS + c] = yv;
+        }
+        __syncthreads();
+        products();
       }
     }
   }
@@ -203,22 +262,33 @@ __global__ void __launch_bounds__(TD* TD) k_tsgemm(StencilView<T> A, const T* __
   }
 }
 
-// out[e] = sum_b partial[b][e] in block order (deterministic), optionally
-// symmetrised: out = (M + M^T) / 2 for an m x m matrix.
-__global__ void k_sum_partials(const double* __restrict__ partial, int nblocks, int m, int symmetrize,
-                               double* __restrict__ out) {
+// out[e] = sum_b partial[b][e] in a fixed order (deterministic): a block of
+// 256 threads covers 32 entries, warp g adding partials b = g, g + 8, ...
+// (four running sums), then the eight warp sums are added in warp order.
+__global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__ partial, int nblocks, int m,
+                                                      double* __restrict__ out) {
+  __shared__ double red[8][33];
   const int mm = m * m;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * mm + e];
-    if (symmetrize) {
-      const int i = e % m, j = e / m;
-      double s2 = 0.0;
-      const int et = i * m + j;
-      for (int b = 0; b < nblocks; ++b) s2 += partial[(int64_t)b * mm + et];
-      s = 0.5 * (s + s2);
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (e < mm) {
+    int b = g;
+    for (; b + 24 < nblocks; b += 32) {
+      s0 += partial[(int64_t)b * mm + e];
+      s1 += partial[(int64_t)(b + 8) * mm + e];
+      s2 += partial[(int64_t)(b + 16) * mm + e];
+      s3 += partial[(int64_t)(b + 24) * mm + e];
     }
-    out[e] = s;
+    for (; b < nblocks; b += 8) s0 += partial[(int64_t)b * mm + e];
+  }
+  red[g][lane] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (g == 0 && e < mm) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += red[q][lane];
+    out[e] = t;
   }
 }
 
@@ -232,10 +302,12 @@ namespace {
 // ordering, so each round applies K/2 disjoint rotations at once.  With all
 // rotations of a round disjoint, G' = J^T G J acts on 2 x 2 blocks
 // independently: block (u, v) -> J_u^T B J_v, so a thread owning block
-// (u <= v) updates it and its mirror without synchronising with others.
+// (u >= v) updates it and its mirror without synchronising with others.
 // Eigenvectors are accumulated as rows of Vt (V = Vt^T), sorted descending.
 // KP is the padded even order; a padded index has zero row/column and is
-// never rotated.
+// never rotated.  The pairs of every round are tabulated once; a round's
+// rotations are packed as {c, s, p, q} so that each is one 16-byte read, and
+// the rows of Vt are updated as 16-byte vectors.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void rr_pair(int KP, int r, int u, int* p, int* q) {
   if (u == 0) {
@@ -247,31 +319,52 @@ __device__ __forceinline__ void rr_pair(int KP, int r, int u, int* p, int* q) {
   }
 }
 
+__host__ __device__ constexpr int jacobi_ldv(int KP) { return (KP + 3) / 4 * 4; }
+
+// Dynamic shared memory of k_jacobi_eig for padded order KP: vt, rot, g,
+// red, uv (all multiples of 4 bytes, vt and rot of 16), then the pair table.
+__host__ __device__ constexpr size_t jacobi_smem(int KP) {
+  return (size_t)KP * jacobi_ldv(KP) * 4            // vt
+         + (size_t)(KP / 2) * 16                    // rot
+         + (size_t)KP * (KP + 1) * 4                // g
+         + 32 * 4                                   // red
+         + (size_t)(KP / 2) * (KP / 2 + 1) / 2 * 4  // uv
+         + (size_t)(KP - 1) * (KP / 2) * 2;         // pair table
+}
+
 __global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ G, int K, int KP, int max_sweeps,
                                                      float tol, double* __restrict__ evals,
                                                      double* __restrict__ V) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int LG = KP + 1;
-  float* g = reinterpret_cast<float*>(smem_raw);  // [KP][LG]
-  float* vt = g + KP * LG;                         // [KP][KP], row a = eigenvector a
-  float* cs = vt + KP * KP;                        // [KP/2][2]
-  int* pq = reinterpret_cast<int*>(cs + KP);       // [KP/2][2]
-  float* red = reinterpret_cast<float*>(pq + KP);  // [32]
-  short2* uv = reinterpret_cast<short2*>(red + 32);  // [H (H + 1) / 2] blocks (u >= v)
+  const int LG = KP + 1, LDV = jacobi_ldv(KP);
+  const int H = KP / 2;
+  float* vt = reinterpret_cast<float*>(smem_raw);                 // [KP][LDV], row a = eigenvector a
+  float4* rot = reinterpret_cast<float4*>(vt + KP * LDV);         // [H] {c, s, p, q}
+  float* g = reinterpret_cast<float*>(rot + H);                   // [KP][LG]
+  float* red = g + KP * LG;                                       // [32]
+  short2* uv = reinterpret_cast<short2*>(red + 32);              // [H (H + 1) / 2] blocks (u >= v)
+  const int nblk = H * (H + 1) / 2;
+  uchar2* pairs = reinterpret_cast<uchar2*>(uv + nblk);          // [KP - 1][H]
   __shared__ int converged;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int H = KP / 2;
-  const int nblk = H * (H + 1) / 2;
   for (int u = tid; u < H; u += nt)
     for (int v = 0; v <= u; ++v) uv[u * (u + 1) / 2 + v] = make_short2((short)u, (short)v);
-
+  for (int e = tid; e < (KP - 1) * H; e += nt) {
+    int pp, qq;
+    rr_pair(KP, e / H, e % H, &pp, &qq);
+    pairs[e] = make_uchar2((unsigned char)pp, (unsigned char)qq);
+  }
   for (int e = tid; e < KP * KP; e += nt) {
     const int a = e / KP, b = e % KP;
     g[a * LG + b] = (a < K && b < K) ? (float)G[(int64_t)b * K + a] : 0.0f;
-    vt[a * KP + b] = (a == b) ? 1.0f : 0.0f;
+  }
+  for (int e = tid; e < KP * LDV; e += nt) {
+    const int a = e / LDV, b = e % LDV;
+    vt[e] = (a == b) ? 1.0f : 0.0f;
   }
   __syncthreads();
 
+  const int nv4 = LDV / 4;  // 16-byte vectors per row of Vt
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence test: off-diagonal mass against the diagonal
     float off = 0.0f, dia = 0.0f;
@@ -288,8 +381,8 @@ __global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ 
 
     for (int r = 0; r < KP - 1; ++r) {
       for (int u = tid; u < H; u += nt) {
-        int p, q;
-        rr_pair(KP, r, u, &p, &q);
+        const uchar2 pq = pairs[r * H + u];
+        const int p = pq.x, q = pq.y;
         const float gpp = g[p * LG + p], gqq = g[q * LG + q], gpq = g[p * LG + q];
         float c = 1.0f, s = 0.0f;
         if (gpq != 0.0f && fabsf(gpq) > 1e-30f) {
@@ -298,18 +391,16 @@ __global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ 
           c = rsqrtf(1.0f + t * t);
           s = t * c;
         }
-        cs[2 * u] = c;
-        cs[2 * u + 1] = s;
-        pq[2 * u] = p;
-        pq[2 * u + 1] = q;
+        rot[u] = make_float4(c, s, __int_as_float(p), __int_as_float(q));
       }
       __syncthreads();
       // 2x2 block updates (u >= v, mirrored)
       for (int e = tid; e < nblk; e += nt) {
         const short2 b = uv[e];
         const int u = b.x, v = b.y;  // v <= u
-        const int pu = pq[2 * u], qu = pq[2 * u + 1], pv = pq[2 * v], qv = pq[2 * v + 1];
-        const float cu = cs[2 * u], su = cs[2 * u + 1], cv = cs[2 * v], sv = cs[2 * v + 1];
+        const float4 ru = rot[u];
+        const int pu = __float_as_int(ru.z), qu = __float_as_int(ru.w);
+        const float cu = ru.x, su = ru.y;
         if (u == v) {
           const float gpp = g[pu * LG + pu], gqq = g[qu * LG + qu], gpq = g[pu * LG + qu];
           const float t = su / cu;
@@ -318,6 +409,9 @@ __global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ 
           g[pu * LG + qu] = 0.0f;
           g[qu * LG + pu] = 0.0f;
         } else {
+          const float4 rv = rot[v];
+          const int pv = __float_as_int(rv.z), qv = __float_as_int(rv.w);
+          const float cv = rv.x, sv = rv.y;
           const float b00 = g[pu * LG + pv], b01 = g[pu * LG + qv], b10 = g[qu * LG + pv], b11 = g[qu * LG + qv];
           const float m00 = cu * b00 - su * b10, m01 = cu * b01 - su * b11;
           const float m10 = su * b00 + cu * b10, m11 = su * b01 + cu * b11;
@@ -327,14 +421,17 @@ __global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ 
           g[pv * LG + pu] = n00; g[qv * LG + pu] = n01; g[pv * LG + qu] = n10; g[qv * LG + qu] = n11;
         }
       }
-      // V <- V J: rows p, q of Vt
-      for (int e = tid; e < H * KP; e += nt) {
-        const int u = e / KP, row = e % KP;
-        const int p = pq[2 * u], q = pq[2 * u + 1];
-        const float c = cs[2 * u], s = cs[2 * u + 1];
-        const float vp = vt[p * KP + row], vq = vt[q * KP + row];
-        vt[p * KP + row] = c * vp - s * vq;
-        vt[q * KP + row] = s * vp + c * vq;
+      // V <- V J: rows p, q of Vt, four columns at a time
+      for (int e = tid; e < H * nv4; e += nt) {
+        const int u = e / nv4, c4 = e - u * nv4;
+        const float4 ru = rot[u];
+        const int p = __float_as_int(ru.z), q = __float_as_int(ru.w);
+        const float c = ru.x, s = ru.y;
+        float4* rp = reinterpret_cast<float4*>(vt + p * LDV) + c4;
+        float4* rq = reinterpret_cast<float4*>(vt + q * LDV) + c4;
+        const float4 vp = *rp, vq = *rq;
+        *rp = make_float4(c * vp.x - s * vq.x, c * vp.y - s * vq.y, c * vp.z - s * vq.z, c * vp.w - s * vq.w);
+        *rq = make_float4(s * vp.x + c * vq.x, s * vp.y + c * vq.y, s * vp.z + c * vq.z, s * vp.w + c * vq.w);
       }
       __syncthreads();
     }
@@ -348,7 +445,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ 
       pos += (lb > la) || (lb == la && b < a);
     }
     evals[pos] = (double)la;
-    for (int row = 0; row < K; ++row) V[(int64_t)pos * K + row] = (double)vt[a * KP + row];
+    for (int row = 0; row < K; ++row) V[(int64_t)pos * K + row] = (double)vt[a * LDV + row];
   }
 }
 
@@ -458,14 +555,24 @@ __global__ void k_make_basis_coeffs(const double* __restrict__ evals, const doub
 
 // Out_t = In_t * M for every node tile: In tiled with `ncin` columns, M is
 // ncin x k (row-major), Out tiled with k columns.  One thread per node of a
-// tile; outputs in register chunks of KC columns.
-template <typename T, int KC>
+// tile; outputs in register chunks of KC columns.  M sits in shared memory
+// with its rows padded with zeros to ldm, a multiple of KC, so the product
+// loop needs no column test; it is read as 16-byte broadcasts.  The input
+// column loads are issued CU at a time ahead of their products.
+template <typename T, int KC, int CU>
 __global__ void __launch_bounds__(NLSP_TILE) k_tile_times_small(const T* __restrict__ In, int ncin,
                                                                const T* __restrict__ Mg, int k, int64_t n_pad,
                                                                T* __restrict__ Out) {
+  using V = typename Vec16<T>::type;
+  constexpr int VN = Vec16<T>::N;
+  static_assert(KC % VN == 0, "KC must be a multiple of the vector width");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* M = reinterpret_cast<T*>(smem_raw);
-  for (int e = threadIdx.x; e < ncin * k; e += blockDim.x) M[e] = Mg[e];
+  const int ldm = (k + KC - 1) / KC * KC;
+  for (int e = threadIdx.x; e < ncin * ldm; e += blockDim.x) {
+    const int c = e / ldm, j = e % ldm;
+    M[e] = j < k ? Mg[c * k + j] : T(0);
+  }
   __syncthreads();
   const int64_t ntiles = n_pad / NLSP_TILE;
   const int w = threadIdx.x;
@@ -476,12 +583,33 @@ __global__ void __launch_bounds__(NLSP_TILE) k_tile_times_small(const T* __restr
       T acc[KC];
 #pragma unroll
       for (int j = 0; j < KC; ++j) acc[j] = T(0);
-      for (int c = 0; c < ncin; ++c) {
-        const T s = in[(int64_t)c * NLSP_TILE];
-        const T* mrow = M + c * k + j0;
+      int c0 = 0;
+      for (; c0 + CU <= ncin; c0 += CU) {
+        T sv[CU];
 #pragma unroll
-        for (int j = 0; j < KC; ++j)
-          if (j0 + j < k) acc[j] += s * mrow[j];
+        for (int u = 0; u < CU; ++u) sv[u] = in[(int64_t)(c0 + u) * NLSP_TILE];
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+          const T* mrow = M + (c0 + u) * ldm + j0;
+#pragma unroll
+          for (int j = 0; j < KC; j += VN) {
+            T mv[VN];
+            *reinterpret_cast<V*>(mv) = *reinterpret_cast<const V*>(mrow + j);
+#pragma unroll
+            for (int q = 0; q < VN; ++q) acc[j + q] += sv[u] * mv[q];
+          }
+        }
+      }
+      for (; c0 < ncin; ++c0) {
+        const T s = in[(int64_t)c0 * NLSP_TILE];
+        const T* mrow = M + c0 * ldm + j0;
+#pragma unroll
+        for (int j = 0; j < KC; j += VN) {
+          T mv[VN];
+          *reinterpret_cast<V*>(mv) = *reinterpret_cast<const V*>(mrow + j);
+#pragma unroll
+          for (int q = 0; q < VN; ++q) acc[j + q] += s * mv[q];
+        }
       }
 #pragma unroll
       for (int j = 0; j < KC; ++j)
@@ -491,66 +619,111 @@ __global__ void __launch_bounds__(NLSP_TILE) k_tile_times_small(const T* __restr
 }
 
 // ---------------------------------------------------------------------------
-// Dense FP64 Cholesky A = L L^T of an m x m SPD matrix in one CTA (shared
-// memory, right-looking), then the inverse A^-1 = L^-T L^-1 column by column.
-// A non-positive or non-finite pivot sets NLSP_ERR_NOT_SPD.
+// Dense FP64 Cholesky A = L L^T of an m x m SPD matrix in one CTA of 256
+// threads (right-looking, shared memory, column-major), one barrier per
+// column.  In the pass for column j every thread reads the pivot words of
+// column j (1 / d and 1 / sqrt(d), d = a_jj), writes its share of column j
+// scaled by 1 / sqrt(d) and updates the trailing lower triangle with the
+// unscaled column, a_ci -= a_ji a_jc / d (a 16 x 16 thread grid over the
+// (c, i >= c) pairs).  Thread 0's first element is a_{j+1,j+1}, so it forms
+// the next pivot words right after updating it, into the other half of a
+// double-buffered pair.  A non-positive or non-finite pivot sets
+// NLSP_ERR_NOT_SPD and L is returned as zeros.
 // ---------------------------------------------------------------------------
-__global__ void k_cholesky(const double* __restrict__ Ain, int m, double* __restrict__ Lout, int* status) {
+__device__ __forceinline__ bool chol_pivot(double d, double* piv, double* ljj) {
+  if (!(d > 0.0) || !isfinite(d)) return false;
+  const double rl = rsqrt(d);
+  piv[0] = rl * rl;
+  piv[1] = rl;
+  *ljj = d * rl;
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_cholesky(const double* __restrict__ Ain, int m, double* __restrict__ Lout,
+                                                  int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* a = reinterpret_cast<double*>(smem_raw);  // column-major m x m
+  __shared__ double piv[2][2];                       // [column parity] {1 / d, 1 / sqrt(d)}
   __shared__ int bad;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int tx = tid % 16, ty = tid / 16;
   for (int e = tid; e < m * m; e += nt) a[e] = Ain[e];
   if (tid == 0) bad = 0;
   __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    if (tid == 0) {
-      const double d = a[j * m + j];
-      if (!(d > 0.0) || !isfinite(d)) bad = 1;
-      else a[j * m + j] = sqrt(d);
-    }
-    __syncthreads();
-    if (bad) break;
-    const double ljj = a[j * m + j];
-    for (int i = j + 1 + tid; i < m; i += nt) a[j * m + i] /= ljj;
-    __syncthreads();
-    // trailing update of the lower triangle: a[i][c] -= a[i][j] a[c][j], j < c <= i
+  if (tid == 0) {
+    double l;
+    if (chol_pivot(a[0], piv[0], &l)) Lout[0] = l;
+    else bad = 1;
+  }
+  __syncthreads();
+  for (int j = 0; j < m && !bad; ++j) {
+    const double inv_d = piv[j & 1][0], inv_l = piv[j & 1][1];
+    for (int i = j + 1 + tid; i < m; i += nt) Lout[(int64_t)j * m + i] = a[j * m + i] * inv_l;
     const int rem = m - j - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      const int c = j + 1 + e / rem, i = j + 1 + e % rem;
-      if (i >= c) a[c * m + i] -= a[j * m + i] * a[j * m + c];
+    for (int cy = ty; cy < rem; cy += 16) {
+      const int c = j + 1 + cy;
+      const double t = a[j * m + c] * inv_d;
+      for (int ix = cy + tx; ix < rem; ix += 16) {
+        const int i = j + 1 + ix;
+        const double v = a[c * m + i] - a[j * m + i] * t;
+        a[c * m + i] = v;
+        if (tid == 0 && ix == 0 && cy == 0) {  // v = a_{j+1, j+1}: next pivot
+          double l;
+          if (chol_pivot(v, piv[(j + 1) & 1], &l)) Lout[(int64_t)(j + 1) * m + j + 1] = l;
+          else bad = 1;
+        }
+      }
     }
     __syncthreads();
   }
   if (tid == 0 && bad) atomicExch(status, (int)NLSP_ERR_NOT_SPD);
   for (int e = tid; e < m * m; e += nt) {
     const int i = e % m, c = e / m;
-    Lout[e] = (i >= c && !bad) ? a[e] : 0.0;
+    if (bad || i < c) Lout[e] = 0.0;
   }
 }
 
-// Column q of A^-1 = L^-T L^-1 e_q by one warp: forward then backward
-// substitution, each step a warp-parallel dot product.
-__global__ void k_spd_inverse_cols(const double* __restrict__ L, int m, double* __restrict__ Ainv) {
+// Column q of A^-1 = L^-T L^-1 e_q by one warp, in the column (axpy) form
+// of both substitutions so that no step needs a reduction: forward,
+// y_i /= L_ii then y_c -= L_ci y_i for c > i (starting at i = q, since
+// (L^-1 e_q)_i = 0 for i < q); backward, x_i = y_i / L_ii then
+// y_c -= L_ic x_i for c < i.  L is staged in shared memory with leading
+// dimension m + 1, so its columns (forward) and rows (backward) are both
+// read without bank conflicts; the reciprocal diagonal is formed once.
+__global__ void __launch_bounds__(32) k_spd_inverse_cols(const double* __restrict__ L, int m,
+                                                         double* __restrict__ Ainv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* y = reinterpret_cast<double*>(smem_raw);
+  const int ld = m + 1;
+  double* Ls = reinterpret_cast<double*>(smem_raw);  // L(i, c) at c * ld + i
+  double* y = Ls + (size_t)m * ld;
+  double* dinv = y + m;
   const int q = blockIdx.x, lane = threadIdx.x;
-  for (int i = 0; i < m; ++i) {  // L y = e_q
-    double s = 0.0;
-    for (int c = lane; c < i; c += 32) s += L[(int64_t)c * m + i] * y[c];
-    s = warp_sum(s);
-    if (lane == 0) y[i] = ((i == q ? 1.0 : 0.0) - s) / L[(int64_t)i * m + i];
+  for (int e = lane; e < m * m; e += 32) Ls[(e / m) * ld + (e % m)] = L[e];
+  __syncwarp();
+  for (int i = lane; i < m; i += 32) {
+    dinv[i] = 1.0 / Ls[i * ld + i];
+    y[i] = (i == q) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  for (int i = q; i < m; ++i) {  // L y = e_q
+    const double yi = y[i] * dinv[i];
+    __syncwarp();
+    if (lane == 0) y[i] = yi;
+    for (int c = i + 1 + lane; c < m; c += 32) y[c] -= Ls[i * ld + c] * yi;
     __syncwarp();
   }
   for (int i = m - 1; i >= 0; --i) {  // L^T x = y  (x overwrites y)
-    double s = 0.0;
-    for (int c = i + 1 + lane; c < m; c += 32) s += L[(int64_t)i * m + c] * y[c];
-    s = warp_sum(s);
-    if (lane == 0) y[i] = (y[i] - s) / L[(int64_t)i * m + i];
+    const double xi = y[i] * dinv[i];
+    __syncwarp();
+    if (lane == 0) y[i] = xi;
+    for (int c = lane; c < i; c += 32) y[c] -= Ls[c * ld + i] * xi;
     __syncwarp();
   }
   for (int i = lane; i < m; i += 32) Ainv[(int64_t)q * m + i] = y[i];
 }
+
+// Dynamic shared memory of k_spd_inverse_cols for order m.
+inline size_t spd_inverse_smem(int m) { return sizeof(double) * ((size_t)m * (m + 1) + 2 * (size_t)m); }
 
 __global__ void k_symmetrize(double* __restrict__ M, int m) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
@@ -595,10 +768,10 @@ T* slot_as(nlsp_ctx* ctx, int s, size_t count) {
 template <typename T, bool WITH_A>
 nlsp_status tsgemm(nlsp_ctx* ctx, const nlsp_op* A, const T* X, int ncols, int ncx, int64_t n_pad, double* out,
                    int symmetrize) {
-  const int blocks = ctx->num_sms;
   cudaStream_t s = ctx->stream;
-  double* partial = slot_as<double>(ctx, SLOT_PART, (size_t)blocks * ncx * ncx);
-  if (!partial) return NLSP_ERR_OOM;
+  const int64_t ntiles = n_pad / NLSP_TILE;
+  // Up to four resident blocks per SM, so that one block's staging loads
+  // overlap another's products; never more blocks than tiles.
 #define NLSP_TSGEMM_LAUNCH(RB, TD)                                                                     \
   do {                                                                                                \
     constexpr int LDS_ = RB * TD + (sizeof(T) == 4 ? 4 : 2);                                          \
@@ -606,7 +779,15 @@ nlsp_status tsgemm(nlsp_ctx* ctx, const nlsp_op* A, const T* X, int ncols, int n
     NLSP_DISPATCH_KIND(A->kind, KD, {                                                                 \
       auto fn = k_tsgemm<T, RB, TD, KD, WITH_A>;                                                      \
       NLSP_TRY(set_smem((const void*)fn, sm));                                                        \
+      int per_sm = 1;                                                                                 \
+      NLSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TD * TD, sm));             \
+      const int blocks = (int)std::min<int64_t>((int64_t)ctx->num_sms * std::min(std::max(per_sm, 1), 4), \
+                                                std::max<int64_t>(ntiles, 1));                        \
+      double* partial = slot_as<double>(ctx, SLOT_PART, (size_t)blocks * ncx * ncx);                  \
+      if (!partial) return NLSP_ERR_OOM;                                                              \
       fn<<<blocks, TD * TD, sm, s>>>(view_of<T>(A), X, ncols, ncx, n_pad, partial);                   \
+      NLSP_LAUNCH_CHECK();                                                                            \
+      k_sum_partials<<<div_up((int64_t)ncx * ncx, 32), 256, 0, s>>>(partial, blocks, ncx, out);       \
     });                                                                                               \
   } while (0)
   if (ncx <= 32) NLSP_TSGEMM_LAUNCH(2, 16);
@@ -615,20 +796,30 @@ nlsp_status tsgemm(nlsp_ctx* ctx, const nlsp_op* A, const T* X, int ncols, int n
   else return NLSP_ERR_INVALID;
 #undef NLSP_TSGEMM_LAUNCH
   NLSP_LAUNCH_CHECK();
-  k_sum_partials<<<div_up((int64_t)ncx * ncx, 256), 256, 0, s>>>(partial, blocks, ncx, symmetrize, out);
-  NLSP_LAUNCH_CHECK();
-  count_launches(ctx, 2);
+  if (symmetrize) {
+    k_symmetrize<<<div_up((int64_t)ncx * ncx, 256), 256, 0, s>>>(out, ncx);
+    NLSP_LAUNCH_CHECK();
+  }
+  count_launches(ctx, symmetrize ? 3 : 2);
   return NLSP_OK;
 }
 
 template <typename T>
 nlsp_status tile_times_small(nlsp_ctx* ctx, const T* In, int ncin, const T* M, int k, int64_t n_pad, T* Out) {
-  const size_t sm = (size_t)ncin * k * sizeof(T);
-  auto fn = k_tile_times_small<T, 32>;
-  NLSP_TRY(set_smem((const void*)fn, sm));
+  // register chunk: the smallest of 16 / 32 / 64 (FP64: 16 / 32) columns
+  // that covers k, else the largest in several passes
+  const int kc = k <= 16 ? 16 : (k <= 32 || sizeof(T) == 8) ? 32 : 64;
+  const size_t sm = (size_t)ncin * ((k + kc - 1) / kc * kc) * sizeof(T);
+  const void* fn;
+  if (kc == 16) fn = (const void*)k_tile_times_small<T, 16, 16>;
+  else if (kc == 32) fn = (const void*)k_tile_times_small<T, 32, 16>;
+  else fn = (const void*)k_tile_times_small<T, 64, 16>;
+  NLSP_TRY(set_smem(fn, sm));
   const int64_t ntiles = n_pad / NLSP_TILE;
   const int g = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 8);
-  fn<<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
+  if (kc == 16) k_tile_times_small<T, 16, 16><<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
+  else if (kc == 32) k_tile_times_small<T, 32, 16><<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
+  else k_tile_times_small<T, 64, 16><<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
   NLSP_LAUNCH_CHECK();
   count_launches(ctx, 1);
   return NLSP_OK;
@@ -719,8 +910,7 @@ nlsp_status alloc_prec_storage(nlsp_prec* M) {
 nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double* evals, double* V, double* work) {
   cudaStream_t s = ctx->stream;
   const int KP = K + (K & 1);
-  const size_t sm = (size_t)KP * (KP + 1) * 4 + (size_t)KP * KP * 4 + (size_t)KP * 4 + (size_t)KP * 4 + 32 * 4 +
-                    (size_t)(KP / 2) * (KP / 2 + 1) / 2 * 4;
+  const size_t sm = jacobi_smem(KP);
   NLSP_TRY(set_smem((const void*)k_jacobi_eig, sm));
   k_jacobi_eig<<<1, 1024, sm, s>>>(G, K, KP, 30, 4e-6f, evals, V);
   NLSP_LAUNCH_CHECK();
@@ -807,8 +997,8 @@ nlsp_status cholesky_qr(nlsp_ctx* ctx, nlsp_prec* M) {
   k_cholesky<<<1, 256, sizeof(double) * k * k, s>>>(Gp, k, Lp, M->status);
   // With P^T P = L L^T:  (L L^T)^-1 L = L^-T, so P L^-T needs only the SPD
   // inverse kernel and one small product.
-  NLSP_TRY(set_smem((const void*)k_spd_inverse_cols, sizeof(double) * k));
-  k_spd_inverse_cols<<<k, 32, sizeof(double) * k, s>>>(Lp, k, Linv);  // (L L^T)^-1
+  NLSP_TRY(set_smem((const void*)k_spd_inverse_cols, spd_inverse_smem(k)));
+  k_spd_inverse_cols<<<k, 32, spd_inverse_smem(k), s>>>(Lp, k, Linv);  // (L L^T)^-1
   k_small_gemm<<<k, 128, sizeof(double) * k, s>>>(Linv, Lp, W, k, 0);  // L^-T
   k_transpose_to<T><<<div_up((int64_t)k * k, 256), 256, 0, s>>>(W, k, Mt);
   NLSP_LAUNCH_CHECK();
@@ -887,8 +1077,8 @@ nlsp_status nlsp_internal_factor(nlsp_ctx* ctx, nlsp_prec* M, int r) {
   NLSP_TRY(set_smem((const void*)k_cholesky, sizeof(double) * r * r));
   k_cholesky<<<1, 256, sizeof(double) * r * r, s>>>(M->Ac, r, M->L, M->status);
   NLSP_LAUNCH_CHECK();
-  NLSP_TRY(set_smem((const void*)k_spd_inverse_cols, sizeof(double) * r));
-  k_spd_inverse_cols<<<r, 32, sizeof(double) * r, s>>>(M->L, r, M->Ainv);
+  NLSP_TRY(set_smem((const void*)k_spd_inverse_cols, spd_inverse_smem(r)));
+  k_spd_inverse_cols<<<r, 32, spd_inverse_smem(r), s>>>(M->L, r, M->Ainv);
   k_symmetrize<<<div_up((int64_t)r * r, 256), 256, 0, s>>>(M->Ainv, r);
   if (M->precision == NLSP_FP64)
     NLSP_CUDA(cudaMemcpyAsync(M->AinvT, M->Ainv, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, s));
