@@ -188,11 +188,13 @@ NLSP_API nlsp_status nlsp_smooth_samples(nlsp_ctx* ctx, const nlsp_op* A, int K,
    column-major, ld = n, read during the call; NULL: drawn on the device as
    N(0,1) from the counter-based generator of nlsp_random_normal with
    params->seed and stream NLSP_STREAM_S0, element (i, c) being normal number
-   c n + i): smooths them s1 times, takes
+   c n + i; the Box-Muller transform is evaluated in the setup precision, so
+   NLSP_MIXED_FP32 samples agree with the FP64 stream to a few FP32 ulps):
+   smooths them s1 times, takes
    the leading k left singular vectors of S as P (thin SVD via the Gram
    matrix S^T S, a Jacobi eigensolver and, in FP64, iterative refinement),
    then forms and factors A_c = P^T A P for the full rank k (call
-   nlsp_factor_coarse to truncate).  Requires 1 <= k <= K <= 256, K <= n,
+   nlsp_factor_coarse to truncate).  Requires 1 <= k <= K <= 128, K <= n,
    nu1 = nu2 >= 1 (PCG needs a symmetric preconditioner) and
    0 < omega < 2.  Synchronises.  Errors: NLSP_ERR_INVALID, NLSP_ERR_NOT_SPD
    (rank-deficient samples), NLSP_ERR_OOM, NLSP_ERR_CUDA. */
@@ -218,6 +220,18 @@ NLSP_API nlsp_status nlsp_prec_from_basis(nlsp_ctx* ctx, const nlsp_op* A, const
    Errors: NLSP_ERR_INVALID. */
 NLSP_API nlsp_status nlsp_random_normal(nlsp_ctx* ctx, unsigned long long seed, unsigned long long stream,
                                         unsigned long long offset, int64_t count, double* dev_out);
+
+/* Self-test of the solver's FP64 <-> FP32 conversions, which run on the
+   integer pipe (bit operations on the IEEE-754 encodings) because GB300
+   executes conversion instructions on its slow FP64 unit.  dev_bits holds n
+   64-bit patterns (device memory, read during the call): each is converted
+   as an FP64 value to FP32 (round to nearest even) and its low 32 bits as an
+   FP32 value to FP64 (exact), and both results are compared bit for bit
+   with the hardware conversions (any NaN matches any NaN).  *mismatches (host)
+   receives the number of differing results.  Synchronises.  Errors:
+   NLSP_ERR_INVALID, NLSP_ERR_CUDA. */
+NLSP_API nlsp_status nlsp_check_conversions(nlsp_ctx* ctx, const unsigned long long* dev_bits, int64_t n,
+                                            unsigned long long* mismatches);
 
 /* Truncates the coarse space to its first r columns (Algorithm 1 setup:
    P_r = P[:, 1:r], A_c = P_r^T A P_r) and factors A_c = L L^T in FP64.

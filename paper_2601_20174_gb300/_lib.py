@@ -77,6 +77,7 @@ SIGNATURES = {
     "nlsp_apply_prec_noalloc": (ci, [vp, vp, ci, vp, i64, vp, i64]),
     "nlsp_prec_phase_times": (ci, [vp, vp, C.POINTER(C.c_double), ci]),
     "nlsp_random_normal": (ci, [vp, C.c_ulonglong, C.c_ulonglong, C.c_ulonglong, i64, vp]),
+    "nlsp_check_conversions": (ci, [vp, vp, i64, C.POINTER(C.c_ulonglong)]),
     "nlsp_bench_kernel": (ci, [vp, vp, ci, ci]),
     "nlsp_solve_batched": (ci, [vp, ci, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveParams), ci,
                                 C.POINTER(SolveInfo)]),

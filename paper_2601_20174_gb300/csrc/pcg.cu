@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "convert.cuh"
 #include "kernels.cuh"
 #include "stencil.cuh"
 #include "tma.cuh"
@@ -49,6 +50,27 @@ struct Pair {
   V* v[2];
   __device__ __forceinline__ V* at(int t) const { return v[t & 1]; }
 };
+
+namespace {
+
+// Self-test: counts the inputs where either conversion differs from the
+// hardware one (bit patterns; any NaN matches any NaN).  x holds FP64 bit
+// patterns; their low 32 bits serve as the FP32 inputs.
+__global__ void k_check_conversions(const unsigned long long* __restrict__ x, int64_t n,
+                                    unsigned long long* __restrict__ bad) {
+  unsigned long long cnt = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = __longlong_as_double((long long)x[i]);
+    const float a = f64_to_f32_rn(d), b = (float)d;
+    if (!(isnan(a) && isnan(b)) && __float_as_uint(a) != __float_as_uint(b)) ++cnt;
+    const float f = __uint_as_float((unsigned)(x[i] & 0xFFFFFFFFull));
+    const double c = f32_to_f64(f), e = (double)f;
+    if (!(isnan(c) && isnan(e)) && __double_as_longlong(c) != __double_as_longlong(e)) ++cnt;
+  }
+  if (cnt) atomicAdd(bad, cnt);
+}
+
+}  // namespace
 
 namespace {
 
@@ -189,7 +211,7 @@ __global__ void __launch_bounds__(TPB) k_pcg_pre(int64_t n, double* __restrict__
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
-    if (sizeof(T) == 4) rT[i] = (T)ri;
+    if (sizeof(T) == 4) rT[i] = from_f64<T>(ri);
     s = fma(ri, ri, s);
   }
   s = block_sum_lean(s, sm);
@@ -516,7 +538,7 @@ __global__ void __launch_bounds__(TPB) k_pcg_post(StencilView<T> A, T omega, con
       const T az = stencil_apply<KIND>(A, i, c, [&](int64_t m) { return zin[m]; });
       zf = zin[i] + omega * stencil_dinv<KIND>(A, i) * (rT[i] - az);
     }
-    const double zd = (double)zf;
+    const double zd = to_f64<T>(zf);
     zout[i] = zd;
     if (st) {
       const double ri = r[i];
@@ -992,10 +1014,11 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         node_batches<4>(
             e2lo, e2hi, [&](int m) { return fma(-mg->alpha, __ldcg(a.q + m), __ldcg(mg->rc + m)); },
             [&](int m, double v) {
-              rts[m - e2lo] = (T)v;
+              const T vt = from_f64<T>(v);
+              rts[m - e2lo] = vt;
               if (m >= i0 && m < i1) {
                 mg->rn[m] = v;
-                a.rT[m] = (T)v;
+                a.rT[m] = vt;
                 a.x[m] = fma(mg->alpha, mg->pd[m], a.x[m]);
                 mg->s_rr = fma(v, v, mg->s_rr);
               }
@@ -1293,7 +1316,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
             const T az4 = stencil_apply<KIND>(a.AT, i, node_coord<KIND>(i, a.AT.N),
                                               [&](int64_t mm) { return z3c[mm - e1lo]; });
             const T zf = z3c[i - e1lo] + omega * stencil_dinv<KIND>(a.AT, i) * (a.rT[i] - az4);
-            return PostVals{(double)zf, rpost[i], flex ? zold64[i] : 0.0};
+            return PostVals{to_f64<T>(zf), rpost[i], flex ? zold64[i] : 0.0};
           },
           [&](int i, PostVals v) {
             zout64[i] = v.zd;
@@ -1317,7 +1340,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         const T az = stencil_apply<KIND>(a.AT, i, c, [&](int64_t m) { return cur[m]; });
         zf = cur[i] + omega * stencil_dinv<KIND>(a.AT, i) * (a.rT[i] - az);
       }
-      const double zd = (double)zf;
+      const double zd = to_f64<T>(zf);
       const double ri = rpost[i];
       zout64[i] = zd;
       s_rz = fma(ri, zd, s_rz);
@@ -1457,7 +1480,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         const double rn = fma(-alpha, qi, ri);
         a.x[i] = fma(alpha, pi, xi);
         a.r[i] = rn;
-        if (FP32) a.rT[i] = (T)rn;
+        if (FP32) a.rT[i] = from_f64<T>(rn);
         s = fma(rn, rn, s);
       };
 #pragma unroll
@@ -2560,4 +2583,26 @@ extern "C" nlsp_status nlsp_apply_prec_noalloc(nlsp_ctx* ctx, const nlsp_prec* M
     case ST_9PT: return apply_noalloc<ST_9PT, float>(M, base, m, dev_R, ldr, dev_Z, ldz);
     default: return apply_noalloc<ST_7PT, float>(M, base, m, dev_R, ldr, dev_Z, ldz);
   }
+}
+
+// Self-test of the solver's integer-pipe FP64 <-> FP32 conversions against
+// the hardware conversions (see f64_to_f32_rn / f32_to_f64).
+extern "C" nlsp_status nlsp_check_conversions(nlsp_ctx* ctx, const unsigned long long* dev_bits, int64_t n,
+                                              unsigned long long* mismatches) {
+  if (!ctx || !mismatches || n < 0 || (n > 0 && !dev_bits)) return NLSP_ERR_INVALID;
+  unsigned long long* d_bad = nullptr;
+  NLSP_CUDA(cudaMallocAsync(&d_bad, sizeof(unsigned long long), ctx->stream));
+  NLSP_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), ctx->stream));
+  if (n > 0) {
+    const int g = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8);
+    k_check_conversions<<<g, 256, 0, ctx->stream>>>(dev_bits, n, d_bad);
+    NLSP_LAUNCH_CHECK();
+    count_launches(ctx, 1);
+  }
+  unsigned long long h = 0;
+  NLSP_CUDA(cudaMemcpyAsync(&h, d_bad, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  NLSP_CUDA(cudaFreeAsync(d_bad, ctx->stream));
+  NLSP_CUDA(cudaStreamSynchronize(ctx->stream));
+  *mismatches = h;
+  return NLSP_OK;
 }

@@ -249,3 +249,41 @@ def test_persistent_merged_update_matches_separate_phase(ctx, name, monkeypatch)
         true = np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b)
         assert r[0].status == 0 and true <= 1e-8 * 1.01
     assert abs(r_m[0].iterations - r_s[0].iterations) <= 1
+
+
+def _conversion_patterns():
+    """64-bit patterns covering every exponent of both formats, the FP32
+    rounding halfway cases (odd and even), the edges of the FP32 normal range
+    and the special values; the low 32 bits double as FP32 inputs."""
+    rng = np.random.default_rng(11)
+    pats = [rng.integers(0, 2**63, size=200_000, dtype=np.int64).astype(np.uint64) * np.uint64(2)
+            + rng.integers(0, 2, size=200_000, dtype=np.int64).astype(np.uint64)]
+    # FP64 values with exponents across the FP32 normal range and just past
+    # it, mantissa bits below FP32 precision set to exactly half (ties), just
+    # above / below half, or random
+    e = rng.integers(1023 - 128, 1023 + 130, size=50_000).astype(np.uint64)
+    m23 = rng.integers(0, 2**23, size=50_000).astype(np.uint64)
+    sign = rng.integers(0, 2, size=50_000).astype(np.uint64) << np.uint64(63)
+    for low in (np.uint64(1 << 28), np.uint64((1 << 28) + 1), np.uint64((1 << 28) - 1), np.uint64(0),
+                rng.integers(0, 2**29, size=50_000).astype(np.uint64)):
+        pats.append(sign | (e << np.uint64(52)) | (m23 << np.uint64(29)) | low)
+    specials = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1.0, -1.0, 3.4028234663852886e38,
+                         3.4028235677973366e38, 3.4028236e38, 1.1754943508222875e-38, 1.1754942e-38,
+                         1.401298464324817e-45, 7e-46, 1e-300, 1e300, 2.0 ** -126, 2.0 ** -149, 2.0 ** 128],
+                        dtype=np.float64)
+    pats.append(specials.view(np.uint64))
+    f32 = np.array([0.0, -0.0, np.inf, np.nan, 1e-40, -1e-45, 3.4e38, 1.0], dtype=np.float32).view(np.uint32)
+    pats.append(f32.astype(np.uint64))
+    return np.concatenate(pats)
+
+
+def test_integer_pipe_conversions_match_hardware(ctx):
+    # the solver converts FP64 <-> FP32 with bit operations (GB300 runs F2F at
+    # the FP64 rate); both directions must equal the hardware conversions
+    import ctypes as C
+    pats = _conversion_patterns()
+    dev = torch.as_tensor(pats.view(np.int64)).cuda()
+    bad = C.c_ulonglong(0)
+    st = ctx._lib.nlsp_check_conversions(ctx.h, C.c_void_p(dev.data_ptr()), dev.numel(), C.byref(bad))
+    assert st == 0
+    assert bad.value == 0
