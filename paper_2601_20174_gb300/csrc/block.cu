@@ -19,7 +19,6 @@
 #include <algorithm>
 
 #include "common.cuh"
-#include "convert.cuh"
 #include "kernels.cuh"
 #include "stencil.cuh"
 #include "tma.cuh"
@@ -95,7 +94,7 @@ __global__ void __launch_bounds__(BT) k_b_update(StencilView<T> A, T omega, doub
     x[e] = fma(alpha, p[e], x[e]);
     const double rn = fma(-alpha, q[e], r[e]);
     r[e] = rn;
-    const T rt = from_f64<T>(rn);
+    const T rt = (T)rn;
     rT[e] = rt;
     z1[e] = omega * stencil_dinv<KIND>(A, i) * rt;
     s = fma(rn, rn, s);
@@ -254,7 +253,7 @@ __global__ void __launch_bounds__(BT) k_b_post4(StencilView<T> A, T omega, const
     V4<double> zd;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      zd.v[j] = to_f64<T>(z0.v[j] + di * (r0.v[j] - az.v[j]));
+      zd.v[j] = (double)(z0.v[j] + di * (r0.v[j] - az.v[j]));
       s_ro[j] = fma(ri.v[j], zo.v[j], s_ro[j]);
       s_rz[j] = fma(ri.v[j], zd.v[j], s_rz[j]);
     }
@@ -668,7 +667,7 @@ __global__ void __launch_bounds__(BT) k_b_post(StencilView<T> A, T omega, const 
   for (int64_t i = w0; i < A.n; i += ws) {
     const T az = stencil_apply<KIND>(A, i, node_coord<KIND>(i, A.N), [&](int64_t m) { return zin[m * MB + lane]; });
     const int64_t e = i * MB + lane;
-    const double zd = to_f64<T>(zin[e] + omega * stencil_dinv<KIND>(A, i) * (rT[e] - az));
+    const double zd = (double)(zin[e] + omega * stencil_dinv<KIND>(A, i) * (rT[e] - az));
     const double ri = r[e];
     s_ro = fma(ri, zout[e], s_ro);  // the previous z
     zout[e] = zd;

@@ -3,11 +3,11 @@
 #include <cuda_runtime.h>
 
 // FP64 <-> FP32 conversions on the integer pipe.  GB300 executes F2F
-// conversions on its FP64 unit (~2 lanes/clk/SM), so the solvers' per-node
-// conversions (the FP32 copy of the updated residual, also on the halo nodes
-// of the persistent solver's staged restriction, and the FP64 copy of the
-// preconditioned residual z) are done with bit operations on the IEEE-754
-// encodings instead: exact for FP32 -> FP64, round-to-nearest-even
+// conversions on its FP64 unit (~2 lanes/clk/SM), so the PCG solver's
+// per-node conversions (the FP32 copy of the updated residual, also on the
+// halo nodes of the persistent solver's staged restriction, and the FP64 copy
+// of the preconditioned residual z) are done with bit operations on the
+// IEEE-754 encodings instead: exact for FP32 -> FP64, round-to-nearest-even
 // for FP64 -> FP32, so both give the hardware conversion's result bit for
 // bit.  Inputs whose result is zero, subnormal, infinite or NaN (exponent
 // outside the normal range) take the hardware conversion.
