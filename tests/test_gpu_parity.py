@@ -67,6 +67,22 @@ def test_smooth_samples(ctx, name, precision):
     assert rel(S, ref) <= tol
 
 
+@pytest.mark.parametrize("N,K,s1", [(37, 6, 1), (37, 6, 3), (29, 5, 7), (700, 3, 3)])
+@pytest.mark.parametrize("kind", ["5pt", "9pt"])
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_smooth_samples_sweep_counts_and_shapes(ctx, N, K, s1, kind, precision):
+    # odd and even sweep counts, sample counts that are not a multiple of the
+    # kernel's four columns per thread, grid rows that span node tiles and a
+    # 700-wide grid (n = 490000, ragged last tile), for both 2D stencils
+    p = gen.poisson_2d(N, 2, K, seed=5) if kind == "5pt" else gen.aniso_9pt_2d(N=N, k=2, K=K, m=1, seed=6)
+    A = op.assemble(p)
+    Aop = _api().Operator.from_problem(ctx, p)
+    S = to_np(Aop.smooth_samples(to_dev(p.S0), s1, p.omega, precision))
+    ref = osetup.smooth_samples(A, p.S0, p.omega, s1)
+    tol = 1e-12 if precision == FP64 else 2e-5
+    assert rel(S, ref) <= tol
+
+
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_setup_fp64_subspace_sigma_and_galerkin(ctx, name):
     p = PROBLEMS[name]()
