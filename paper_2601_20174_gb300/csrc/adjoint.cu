@@ -1,4 +1,4 @@
-// Differentiation of the two objectives the method is trained or judged
+// Differentiation of the two objectives the method is trained or evaluated
 // with, on the GPU:
 //
 //   * the subspace loss L(P_hat) = ||(I - Q Q^T) B||_F^2 with Q = qf(P_hat)

@@ -3,7 +3,7 @@
 Tolerances: FP64 kernels agree with the oracle to rounding (1e-12 relative on
 operator and preconditioner applications, which sum a handful of terms per
 entry; subspace agreement to 1e-8 given the singular-value gap).  The FP32
-preconditioner is judged by what the method fixes: the solve reaches the FP64
+preconditioner is checked against what the method fixes: the solve reaches the FP64
 true relative residual 1e-8 and the preconditioner error stays at FP32 level.
 """
 import numpy as np
