@@ -366,6 +366,16 @@ NLSP_API nlsp_status nlsp_plan_teams(int count, const int64_t* n, int num_ctas, 
 NLSP_API nlsp_status nlsp_subspace_loss(nlsp_ctx* ctx, int64_t n, int k, int K, int precision,
                                         const double* dev_Phat, const double* dev_B, double* loss, double* dev_grad);
 
+/* Nested subspace loss (NLSS, Sec. 3 "Eq. nlss_loss"): with Q = qf(P_hat)
+   and S the n x K sample block, L = (1/k) sum_{l=1..k} (1 - ||Q_{1:l}^T S||_F^2 /
+   ||S||_F^2), whose minimum over P_hat is reached by the leading singular
+   vectors in order (Thm. 1 / Cor. 2), and optionally dL/dP_hat.  Unlike the
+   subspace loss it depends on the order of Q's columns, not only on
+   range(P_hat).  Arguments, precision and errors as nlsp_subspace_loss
+   (dev_S in place of dev_B). */
+NLSP_API nlsp_status nlsp_nlss_loss(nlsp_ctx* ctx, int64_t n, int k, int K, int precision, const double* dev_Phat,
+                                    const double* dev_S, double* loss, double* dev_grad);
+
 /* Unrolled-PCG loss L = ||r_T||_2 after exactly T PCG iterations (Sec. 4,
    standard beta, x0 = 0) on A x = b with the two-level preconditioner of
    Algorithm 1 built from the full-rank basis P (A_c = P^T A P, Cholesky;

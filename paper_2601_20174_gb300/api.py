@@ -291,6 +291,21 @@ def subspace_loss(ctx: Context, P_hat: torch.Tensor, B: torch.Tensor, precision:
     return out.value, (g.t() if grad else None)
 
 
+def nlss_loss(ctx: Context, P_hat: torch.Tensor, S: torch.Tensor, precision: int = L.NLSP_FP64,
+              grad: bool = True):
+    """Nested subspace loss (1/k) sum_l (1 - ||Q_{1:l}^T S||^2 / ||S||^2) with
+    Q = qf(P_hat) and dL/dP_hat (nlsp_nlss_loss).  P_hat (n, k), S (n, K)
+    float64 CUDA.  Returns (loss as a Python float, gradient (n, k) or None)."""
+    n = P_hat.shape[0]
+    ps, k = _colmajor(P_hat, n)
+    ss, K = _colmajor(S, n)
+    g = torch.empty_like(ps) if grad else None
+    out = C.c_double()
+    L.check(ctx._lib.nlsp_nlss_loss(ctx.h, n, k, K, precision, _ptr(ps), _ptr(ss), C.byref(out),
+                                    _ptr(g) if grad else None), "nlsp_nlss_loss")
+    return out.value, (g.t() if grad else None)
+
+
 def unrolled_pcg(op: Operator, P: torch.Tensor, b: torch.Tensor, T: int = 10, nu: int = 2,
                  omega: float = 2.0 / 3.0, precision: int = L.NLSP_FP64, grad: bool = True):
     """||r_T|| after T PCG iterations with the two-level preconditioner

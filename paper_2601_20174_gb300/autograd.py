@@ -5,6 +5,7 @@ the forward with its checkpoints and one reverse sweep) and keep it for the
 backward, which only scales it by the incoming gradient.
 
     loss = SubspaceLoss.apply(P_hat, B, ctx, precision)
+    loss = NlssLoss.apply(P_hat, S, ctx, precision)
     loss = UnrolledPCG.apply(P, op, b, T, nu, omega, precision)
 """
 from __future__ import annotations
@@ -21,6 +22,22 @@ class SubspaceLoss(torch.autograd.Function):
     @staticmethod
     def forward(fctx, P_hat, B, ctx, precision=L.NLSP_FP64):
         loss, grad = api.subspace_loss(ctx, P_hat.detach(), B.detach(), precision, grad=P_hat.requires_grad)
+        fctx.save_for_backward(grad if grad is not None else torch.zeros(0))
+        return torch.tensor(loss, dtype=torch.float64, device=P_hat.device)
+
+    @staticmethod
+    def backward(fctx, g):
+        (grad,) = fctx.saved_tensors
+        return g * grad, None, None, None
+
+
+class NlssLoss(torch.autograd.Function):
+    """(1/k) sum_l (1 - ||Q_{1:l}^T S||^2 / ||S||^2), Q = qf(P_hat) (Sec. 3,
+    nested subspace loss); differentiable in P_hat."""
+
+    @staticmethod
+    def forward(fctx, P_hat, S, ctx, precision=L.NLSP_FP64):
+        loss, grad = api.nlss_loss(ctx, P_hat.detach(), S.detach(), precision, grad=P_hat.requires_grad)
         fctx.save_for_backward(grad if grad is not None else torch.zeros(0))
         return torch.tensor(loss, dtype=torch.float64, device=P_hat.device)
 

@@ -599,6 +599,42 @@ __global__ void k_small_mm(const double* __restrict__ A, int ta, const double* _
   }
 }
 
+// Nested (NLSS) weights on the rows of C = Q^T B (k x K, column-major):
+// S[out] = sum_i w_i sum_j C_ij^2 with w_i = (k - i) / k (row i enters the
+// partial sums of levels i + 1 .. k), and, when Cw is given,
+// Cw = diag(w) C / S[0] with S[0] = ||B||^2.  One block of 256 threads,
+// partials combined in a fixed order.
+__global__ void __launch_bounds__(256) k_nlss_weights(const double* __restrict__ C, int k, int K, double* S, int out,
+                                                      double* __restrict__ Cw) {
+  __shared__ double red[256];
+  const int count = k * K;
+  const double inv_b = Cw ? 1.0 / S[0] : 0.0;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < count; e += blockDim.x) {
+    const int i = e % k;
+    const double w = (double)(k - i) / (double)k;
+    const double c = C[e];
+    s = fma(w * c, c, s);
+    if (Cw) Cw[e] = w * c * inv_b;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) S[out] = red[0];
+}
+
+// out = alpha * copyltu(M) for a k x k column-major M: the lower triangle
+// (diagonal included) kept and mirrored onto the upper one.
+__global__ void k_copyltu(const double* __restrict__ M, int k, double alpha, double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    const int i = e % k, j = e / k;
+    out[e] = alpha * (i >= j ? M[e] : M[(int64_t)i * k + j]);
+  }
+}
+
 // S[out] = sum of squares of x (count entries), one warp (small matrices).
 __global__ void k_small_sumsq(const double* __restrict__ x, int count, double* S, int out) {
   double s = 0.0;
@@ -962,7 +998,10 @@ nlsp_status launch_cross(nlsp_ctx* ctx, const TP* X, int ncx, const TP* Y, int n
   return NLSP_ERR_INVALID;
 }
 
-template <typename TP>
+// Subspace loss (NESTED = false) or the nested subspace loss NLSS (NESTED =
+// true) and their gradients, from G = P_hat^T P_hat = L L^T (R = L^T),
+// H = P_hat^T B and C = Q^T B = L^-1 H.
+template <typename TP, bool NESTED>
 nlsp_status subspace_impl(nlsp_ctx* ctx, int64_t n, int k, int K, const double* Ph, const double* B, double* loss,
                           double* grad) {
   cudaStream_t s = ctx->stream;
@@ -971,7 +1010,7 @@ nlsp_status subspace_impl(nlsp_ctx* ctx, int64_t n, int k, int K, const double* 
   Arena ar;
   const std::vector<size_t> parts = {sizeof(TP) * (size_t)n_pad * k, sizeof(TP) * (size_t)n_pad * K,
                                      sizeof(double) * (size_t)nb * k * std::max(k, K), sizeof(double) * 16,
-                                     sizeof(double) * (size_t)k * k * 6 + sizeof(double) * (size_t)k * K * 3,
+                                     sizeof(double) * (size_t)k * k * 6 + sizeof(double) * (size_t)k * K * 4,
                                      sizeof(double) * (size_t)nb, sizeof(int) * 4};
   NLSP_TRY(ar.reserve(arena_bytes(parts) + 4096));
   TP* Pt = ar.take<TP>((size_t)n_pad * k);
@@ -987,6 +1026,7 @@ nlsp_status subspace_impl(nlsp_ctx* ctx, int64_t n, int k, int K, const double* 
   double* H = ar.take<double>((size_t)k * K);
   double* C = ar.take<double>((size_t)k * K);
   double* X = ar.take<double>((size_t)K * k);
+  double* Cw = ar.take<double>((size_t)k * K);
   double* dpart = ar.take<double>(nb);
   int* ok = ar.take<int>(4);
   if (!ok) return NLSP_ERR_OOM;
@@ -1007,14 +1047,29 @@ nlsp_status subspace_impl(nlsp_ctx* ctx, int64_t n, int k, int K, const double* 
   k_small_chol<<<1, 256, sizeof(double) * k * k, s>>>(G, k, Lf, ok);
   k_small_trinv<<<1, 128, 0, s>>>(Lf, k, Li);
   k_small_mm<<<div_up((int64_t)k * K, 128), 128, 0, s>>>(Li, 0, H, 0, C, k, K, k, 1.0);  // C = L^-1 H
-  k_small_sumsq<<<1, 32, 0, s>>>(C, k * K, S, 1);
+  if (NESTED)
+    k_nlss_weights<<<1, 256, 0, s>>>(C, k, K, S, 1, grad ? Cw : nullptr);  // sum_i w_i ||c_i||^2, diag(w) C / ||B||^2
+  else
+    k_small_sumsq<<<1, 32, 0, s>>>(C, k * K, S, 1);
   NLSP_LAUNCH_CHECK();
   int launches = 11;
-  if (grad) {
+  if (grad && !NESTED) {
     k_small_mm<<<div_up((int64_t)K * k, 128), 128, 0, s>>>(C, 1, Li, 0, X, K, k, k, -2.0);  // -2 C^T L^-1
     k_small_mm<<<div_up((int64_t)k * k, 128), 128, 0, s>>>(C, 0, C, 1, CC, k, k, K, 1.0);   // C C^T
     k_small_mm<<<div_up((int64_t)k * k, 128), 128, 0, s>>>(CC, 0, Li, 0, Zt, k, k, k, 1.0);  // C C^T L^-1
     k_small_mm<<<div_up((int64_t)k * k, 128), 128, 0, s>>>(Li, 1, Zt, 0, Z, k, k, k, 2.0);  // 2 L^-T C C^T L^-1
+  } else if (grad) {
+    // NLSS: Q_bar = -(2 / ||B||^2) B C^T W, M = -Q_bar^T Q = (2 / ||B||^2) W C C^T (not
+    // symmetric), P_hat_bar = (Q_bar + Q copyltu(M)) R^-T
+    //                       = B (-2 Cw^T L^-1) + P_hat (L^-T copyltu(2 Cw C^T) L^-1)
+    k_small_mm<<<div_up((int64_t)K * k, 128), 128, 0, s>>>(Cw, 1, Li, 0, X, K, k, k, -2.0);  // -2 Cw^T L^-1
+    k_small_mm<<<div_up((int64_t)k * k, 128), 128, 0, s>>>(Cw, 0, C, 1, CC, k, k, K, 1.0);   // Cw C^T
+    k_copyltu<<<div_up((int64_t)k * k, 128), 128, 0, s>>>(CC, k, 2.0, Zt);                    // M
+    k_small_mm<<<div_up((int64_t)k * k, 128), 128, 0, s>>>(Zt, 0, Li, 0, CC, k, k, k, 1.0);  // M L^-1
+    k_small_mm<<<div_up((int64_t)k * k, 128), 128, 0, s>>>(Li, 1, CC, 0, Z, k, k, k, 1.0);  // L^-T M L^-1
+    launches += 1;
+  }
+  if (grad) {
     const size_t sm = sizeof(TP) * (size_t)(K + k) * tg_ldm(k);
     auto fn = k_tile_gemm2<TP>;
     if (sm > 48 * 1024) NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -1033,7 +1088,8 @@ nlsp_status subspace_impl(nlsp_ctx* ctx, int64_t n, int k, int K, const double* 
     nlsp_record_message("subspace loss: P_hat^T P_hat is not positive definite (P_hat rank deficient)");
     return NLSP_ERR_NOT_SPD;
   }
-  *loss = h[0] - h[1];
+  // subspace: ||B||^2 - ||C||^2; NLSS: (1/k) sum_l (1 - ||Q_{1:l}^T B||^2 / ||B||^2)
+  *loss = NESTED ? 1.0 - h[1] / h[0] : h[0] - h[1];
   return NLSP_OK;
 }
 
@@ -1046,6 +1102,16 @@ extern "C" nlsp_status nlsp_subspace_loss(nlsp_ctx* ctx, int64_t n, int k, int K
       (precision != NLSP_FP64 && precision != NLSP_MIXED_FP32))
     return NLSP_ERR_INVALID;
   NLSP_CUDA(cudaSetDevice(ctx->device));
-  return precision == NLSP_FP64 ? subspace_impl<double>(ctx, n, k, K, dev_Phat, dev_B, loss, dev_grad)
-                                : subspace_impl<float>(ctx, n, k, K, dev_Phat, dev_B, loss, dev_grad);
+  return precision == NLSP_FP64 ? subspace_impl<double, false>(ctx, n, k, K, dev_Phat, dev_B, loss, dev_grad)
+                                : subspace_impl<float, false>(ctx, n, k, K, dev_Phat, dev_B, loss, dev_grad);
+}
+
+extern "C" nlsp_status nlsp_nlss_loss(nlsp_ctx* ctx, int64_t n, int k, int K, int precision, const double* dev_Phat,
+                                      const double* dev_S, double* loss, double* dev_grad) {
+  if (!ctx || !dev_Phat || !dev_S || !loss || n < 1 || k < 1 || k > 128 || K < 1 || K > 256 || k > n ||
+      (precision != NLSP_FP64 && precision != NLSP_MIXED_FP32))
+    return NLSP_ERR_INVALID;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  return precision == NLSP_FP64 ? subspace_impl<double, true>(ctx, n, k, K, dev_Phat, dev_S, loss, dev_grad)
+                                : subspace_impl<float, true>(ctx, n, k, K, dev_Phat, dev_S, loss, dev_grad);
 }

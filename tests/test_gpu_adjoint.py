@@ -77,6 +77,34 @@ def test_subspace_loss_and_gradient_match_oracle(ctx, name):
     assert np.linalg.norm(to_np(g0)) <= 1e-8 * np.linalg.norm(g64)
 
 
+@pytest.mark.parametrize("name", list(SUB_CASES))
+def test_nlss_loss_and_gradient_match_oracle(ctx, name):
+    api = _api()
+    p = SUB_CASES[name]()
+    A = op.assemble(p)
+    S, U, Ph = _noisy_basis(p, A)
+    L_ref = olosses.nlss_loss(Ph, S)
+    g_ref = olosses.grad_nlss_loss(Ph, S)
+    L64, g64 = api.nlss_loss(ctx, to_dev(Ph), to_dev(S), FP64)
+    assert abs(L64 - L_ref) <= 1e-10 * abs(L_ref)
+    g64 = to_np(g64)
+    assert rel(g64, g_ref) <= 1e-8
+    # not range-only: reordering the columns of P_hat changes the loss
+    L_rev, _ = api.nlss_loss(ctx, to_dev(Ph[:, ::-1].copy()), to_dev(S), FP64, grad=False)
+    assert abs(L_rev - olosses.nlss_loss(Ph[:, ::-1], S)) <= 1e-10 * abs(L_rev)
+    assert abs(L_rev - L64) > 1e-6 * abs(L64)
+    L32, g32 = api.nlss_loss(ctx, to_dev(Ph), to_dev(S), MIXED)
+    assert abs(L32 - L_ref) <= 1e-3 * abs(L_ref)
+    assert rel(to_np(g32), g_ref) <= 1e-3
+    # the ordered SVD basis attains the closed-form minimum (Thm. 1 / Cor. 2),
+    # where the gradient vanishes to rounding
+    L0, g0 = api.nlss_loss(ctx, to_dev(U), to_dev(S), FP64)
+    sig2 = np.linalg.svd(S, compute_uv=False) ** 2
+    L_min = np.mean(1.0 - np.cumsum(sig2[: p.k]) / np.sum(sig2))
+    assert abs(L0 - L_min) <= 1e-10
+    assert np.linalg.norm(to_np(g0)) <= 1e-7 * np.linalg.norm(g64)
+
+
 UNROLL_CASES = {
     "poisson16": lambda: gen.poisson_2d(16, 6, 16, seed=1),
     "grf20": lambda: gen.grf_diffusion_2d(N=20, k=8, K=20, seed=3),
@@ -151,7 +179,7 @@ def test_subspace_gradient_finite_differences_large(ctx):
 
 
 def test_autograd_functions(ctx):
-    from paper_2601_20174_gb300.autograd import SubspaceLoss, UnrolledPCG
+    from paper_2601_20174_gb300.autograd import NlssLoss, SubspaceLoss, UnrolledPCG
     api = _api()
     p = UNROLL_CASES["grf20"]()
     A = op.assemble(p)
@@ -160,6 +188,10 @@ def test_autograd_functions(ctx):
     loss = SubspaceLoss.apply(Pt, to_dev(S), ctx, FP64)
     (3.0 * loss).backward()
     assert rel(to_np(Pt.grad), 3.0 * olosses.grad_subspace_loss(Ph, S)) <= 1e-8
+    Pn = to_dev(Ph).requires_grad_(True)
+    ln = NlssLoss.apply(Pn, to_dev(S), ctx, FP64)
+    (2.0 * ln).backward()
+    assert rel(to_np(Pn.grad), 2.0 * olosses.grad_nlss_loss(Ph, S)) <= 1e-8
     Aop = api.Operator.from_problem(ctx, p)
     P2 = to_dev(Ph).requires_grad_(True)
     l2 = UnrolledPCG.apply(P2, Aop, to_dev(p.f[:, 0]), 10, p.nu, p.omega, FP64)
@@ -177,3 +209,5 @@ def test_differentiation_rejects_bad_arguments(ctx):
         api.unrolled_pcg(Aop, P, to_dev(p.f[:, 0]), 10, 2, p.omega, FP64)
     with pytest.raises(api.L.NlspError):
         api.subspace_loss(ctx, P, to_dev(p.S0), FP64)
+    with pytest.raises(api.L.NlspError):
+        api.nlss_loss(ctx, P, to_dev(p.S0), FP64)
