@@ -87,3 +87,53 @@ def test_truncation_is_prefix():
     rng = np.random.default_rng(3)
     P, _ = np.linalg.qr(rng.standard_normal((30, 6)))
     assert np.array_equal(su.truncate(P, 4), P[:, :4])
+
+
+def _dense_sqrt(A):
+    w, V = np.linalg.eigh(A.toarray())
+    return (V * np.sqrt(w)) @ V.T
+
+
+def test_a_weighted_basis_minimises_post_correction_energy():
+    # Galerkin Convergence theorem (Appendix): J(P) is smallest when
+    # range(A^{1/2} P) is the top-k left singular subspace of A^{1/2} S, where
+    # it equals the Eckart-Young tail of A^{1/2} S
+    p = gen.grf_diffusion_2d(N=14, k=8, K=24, seed=3)
+    A = op.assemble(p)
+    S = su.smooth_samples(A, p.S0, p.omega, p.s1)
+    P, sig = su.prolongation_a_weighted(A, S, p.k)
+    assert np.allclose(P.T @ (A @ P), np.eye(p.k), atol=1e-10)
+    Z = _dense_sqrt(A) @ S                       # independent route: dense A^{1/2}, library SVD
+    Uz, sz, _ = np.linalg.svd(Z, full_matrices=False)
+    assert np.allclose(sig[: len(sz)], sz, rtol=1e-8, atol=1e-10 * sz[0])
+    J = su.post_correction_energy(A, P, S)
+    assert math.isclose(J, float(np.sum(sz[p.k:] ** 2)), rel_tol=1e-8)
+    Q = _dense_sqrt(A) @ P                        # A^{1/2} P spans the top-k subspace of Z
+    assert _projector_dist(Q, Uz[:, : p.k]) < 1e-7
+    # neither the Euclidean SVD basis nor perturbations of the A-weighted one do better
+    Pe, _ = su.prolongation(S, p.k)
+    assert su.post_correction_energy(A, Pe, S) > J
+    rng = np.random.default_rng(1)
+    for _ in range(4):
+        assert su.post_correction_energy(A, P + 0.05 * rng.standard_normal(P.shape), S) > J
+
+
+def test_randomized_basis_exact_for_low_rank_and_converges_with_power_iterations():
+    rng = np.random.default_rng(5)
+    n, K, k, over = 300, 40, 6, 4
+    # rank k + over: the range finder captures range(S) exactly, so the basis
+    # is the SVD basis
+    S = rng.standard_normal((n, k + over)) @ rng.standard_normal((k + over, K))
+    P = su.prolongation_randomized(S, k, over, 0, rng.standard_normal((K, k + over)))
+    U, _ = su.prolongation(S, k)
+    assert np.allclose(P.T @ P, np.eye(k), atol=1e-12)
+    assert _projector_dist(P, U) < 1e-8
+    # full-rank samples with a gap after k: power iterations approach the SVD
+    p = gen.iid_diffusion_2d(N=16, k=8, K=32, seed=2)
+    A = op.assemble(p)
+    S = su.smooth_samples(A, p.S0, p.omega, p.s1)
+    U, sig = su.prolongation(S, p.k)
+    Om = rng.standard_normal((p.K, p.k + 4))
+    d = [_projector_dist(su.prolongation_randomized(S, p.k, 4, q, Om), U) for q in (0, 1, 3, 6, 10)]
+    assert all(b < a for a, b in zip(d, d[1:]))
+    assert d[-1] < 1e-8
