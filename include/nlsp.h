@@ -201,6 +201,16 @@ NLSP_API nlsp_status nlsp_smooth_samples(nlsp_ctx* ctx, const nlsp_op* A, int K,
 NLSP_API nlsp_status nlsp_build_prolongation(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* params,
                                     const double* dev_S0, nlsp_prec** M_out);
 
+/* As nlsp_build_prolongation, with the A-weighted spectral basis of the
+   Appendix (Galerkin Convergence): the Gram matrix of the smoothed samples is
+   S^T A S, so that P = S V_k Sigma_k^-1 satisfies P^T A P = I and A^{1/2} P
+   spans the top-k left singular subspace of A^{1/2} S, the coarse space that
+   minimises ||A^{1/2} (I - Pi_A(P)) S||_F^2.  The singular values reported
+   (nlsp_prec_copy_sigma) are those of A^{1/2} S.  Same arguments and errors. */
+NLSP_API nlsp_status nlsp_build_prolongation_a_weighted(nlsp_ctx* ctx, const nlsp_op* A,
+                                                        const nlsp_setup_params* params, const double* dev_S0,
+                                                        nlsp_prec** M_out);
+
 /* Builds a preconditioner from a given basis dev_P (n x k column-major,
    ld = n, FP64, read during the call), e.g. the output of a learned map
    f_theta after its QR layer (Sec. 3, Algorithm 1 lines "P_hat = f_theta(S)",

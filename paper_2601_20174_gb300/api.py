@@ -143,9 +143,10 @@ class Preconditioner:
     @classmethod
     def build(cls, op: Operator, S0: torch.Tensor | None, k: int, s1: int = 20, nu: int = 2,
               omega: float = 2.0 / 3.0, precision: int = L.NLSP_FP64, K: int | None = None,
-              seed: int = 0) -> "Preconditioner":
+              seed: int = 0, a_weighted: bool = False) -> "Preconditioner":
         """S0: n x K random test vectors, or None to draw them on the device
-        (K columns, counter-based generator under `seed`)."""
+        (K columns, counter-based generator under `seed`).  a_weighted: the
+        A-orthonormal basis of nlsp_build_prolongation_a_weighted."""
         if S0 is None:
             if K is None:
                 raise ValueError("K is required when S0 is drawn on the device")
@@ -155,8 +156,8 @@ class Preconditioner:
             ptr = _ptr(store)
         p = cls._params(k, K, s1, nu, omega, precision, seed)
         h = C.c_void_p()
-        L.check(op.ctx._lib.nlsp_build_prolongation(op.ctx.h, op.h, C.byref(p), ptr, C.byref(h)),
-                "nlsp_build_prolongation")
+        name = "nlsp_build_prolongation_a_weighted" if a_weighted else "nlsp_build_prolongation"
+        L.check(getattr(op.ctx._lib, name)(op.ctx.h, op.h, C.byref(p), ptr, C.byref(h)), name)
         return cls(op, h)
 
     @classmethod

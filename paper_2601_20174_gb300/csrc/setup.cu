@@ -948,8 +948,12 @@ nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double
 }
 
 // P (tiled T, k columns) from the tiled smoothed samples S (K columns).
+// With a_weighted, the Gram matrix is S^T A S (the eigen-decomposition of
+// Z^T Z for Z = A^{1/2} S), so that P = S V_k Sigma_k^-1 is A-orthonormal and
+// A^{1/2} P spans the top-k left singular subspace of A^{1/2} S (Appendix,
+// Galerkin Convergence).
 template <typename T>
-nlsp_status basis_from_samples(nlsp_ctx* ctx, nlsp_prec* M, const T* S) {
+nlsp_status basis_from_samples(nlsp_ctx* ctx, nlsp_prec* M, const T* S, bool a_weighted) {
   cudaStream_t s = ctx->stream;
   const int K = M->K, k = M->k;
   const size_t nsmall = (size_t)K * K * 2 + K + (6 * (size_t)K * K + K) + (size_t)K * k + 8;
@@ -959,7 +963,10 @@ nlsp_status basis_from_samples(nlsp_ctx* ctx, nlsp_prec* M, const T* S) {
   double* evals = V + K * K;
   double* work = evals + K;
   T* Mc = reinterpret_cast<T*>(work + 6 * K * K + K);
-  NLSP_TRY((tsgemm<T, false>(ctx, M->A, S, K, K, M->n_pad, G, 0)));
+  if (a_weighted)
+    NLSP_TRY((tsgemm<T, true>(ctx, M->A, S, K, K, M->n_pad, G, 1)));
+  else
+    NLSP_TRY((tsgemm<T, false>(ctx, M->A, S, K, K, M->n_pad, G, 0)));
   const int refine = M->precision == NLSP_FP64 ? 2 : 0;
   NLSP_TRY(gram_eigen(ctx, G, K, refine, evals, V, work));
   k_make_basis_coeffs<T><<<div_up((int64_t)K * k, 256), 256, 0, s>>>(evals, V, K, k, Mc, M->sigma, M->status);
@@ -1010,7 +1017,7 @@ nlsp_status cholesky_qr(nlsp_ctx* ctx, nlsp_prec* M) {
 
 template <typename T>
 nlsp_status build_impl(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* p, const double* S0,
-                       nlsp_prec** out) {
+                       nlsp_prec** out, bool a_weighted) {
   nlsp_prec* M = new_prec(ctx, A, p, p->k, p->K);
   nlsp_status st = alloc_prec_storage(M);
   auto fail = [&](nlsp_status e) {
@@ -1032,8 +1039,8 @@ nlsp_status build_impl(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params*
   count_launches(ctx, 1);
   T* S = nullptr;
   if ((st = smooth_tiled<T>(ctx, A, K, p->s1, p->omega, M->n_pad, sa, sb, &S)) != NLSP_OK) return fail(st);
-  if ((st = basis_from_samples<T>(ctx, M, S)) != NLSP_OK) return fail(st);
-  if (p->precision == NLSP_FP64)
+  if ((st = basis_from_samples<T>(ctx, M, S, a_weighted)) != NLSP_OK) return fail(st);
+  if (p->precision == NLSP_FP64 && !a_weighted)  // the A-weighted basis is A-orthonormal already
     if ((st = cholesky_qr<T>(ctx, M)) != NLSP_OK) return fail(st);
   if ((st = nlsp_internal_factor(ctx, M, M->k)) != NLSP_OK) return fail(st);
   *out = M;
@@ -1138,8 +1145,19 @@ extern "C" nlsp_status nlsp_build_prolongation(nlsp_ctx* ctx, const nlsp_op* A, 
   *M_out = nullptr;
   NLSP_TRY(check_setup_params(A, params, true));
   NLSP_CUDA(cudaSetDevice(ctx->device));
-  if (params->precision == NLSP_FP64) return build_impl<double>(ctx, A, params, dev_S0, M_out);
-  return build_impl<float>(ctx, A, params, dev_S0, M_out);
+  if (params->precision == NLSP_FP64) return build_impl<double>(ctx, A, params, dev_S0, M_out, false);
+  return build_impl<float>(ctx, A, params, dev_S0, M_out, false);
+}
+
+extern "C" nlsp_status nlsp_build_prolongation_a_weighted(nlsp_ctx* ctx, const nlsp_op* A,
+                                                          const nlsp_setup_params* params, const double* dev_S0,
+                                                          nlsp_prec** M_out) {
+  if (!ctx || !M_out) return NLSP_ERR_INVALID;
+  *M_out = nullptr;
+  NLSP_TRY(check_setup_params(A, params, true));
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  if (params->precision == NLSP_FP64) return build_impl<double>(ctx, A, params, dev_S0, M_out, true);
+  return build_impl<float>(ctx, A, params, dev_S0, M_out, true);
 }
 
 extern "C" nlsp_status nlsp_prec_from_basis(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* params,

@@ -83,6 +83,37 @@ def test_smooth_samples_sweep_counts_and_shapes(ctx, N, K, s1, kind, precision):
     assert rel(S, ref) <= tol
 
 
+@pytest.mark.parametrize("name", ["grf5", "aniso9"])
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_a_weighted_setup_matches_oracle_and_solves(ctx, name, precision):
+    # the A-weighted basis (Appendix, Galerkin Convergence): the device's
+    # S^T A S Gram route against the oracle's, then a PCG solve with it
+    p = PROBLEMS[name]()
+    A = op.assemble(p)
+    S = osetup.smooth_samples(A, p.S0, p.omega, p.s1)
+    P_ref, sig_ref = osetup.prolongation_a_weighted(A, S, p.k)
+    Aop = _api().Operator.from_problem(ctx, p)
+    M = _api().Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, precision, a_weighted=True)
+    P, sig = to_np(M.basis()), to_np(M.sigma())
+    fp64 = precision == FP64
+    assert rel(sig[: p.k], sig_ref[: p.k]) <= (1e-10 if fp64 else 1e-4)
+    assert np.max(np.abs(P.T @ (A @ P) - np.eye(p.k))) <= (1e-9 if fp64 else 1e-4)
+    gap = sig_ref[p.k - 1] / sig_ref[p.k] - 1.0
+    Qg, Qr = np.linalg.qr(P)[0], np.linalg.qr(P_ref)[0]
+    assert projector_dist(Qg, Qr) <= (max(1e-8, 1e-13 / gap) if fp64 else max(1e-3, 1e-6 / gap))
+    # the coarse space never does worse on J than the Euclidean SVD basis
+    Pe, _ = osetup.prolongation(S, p.k)
+    assert osetup.post_correction_energy(A, P, S) <= osetup.post_correction_energy(A, Pe, S) * (1 + 1e-6)
+    b = p.f[:, 0]
+    x, res = M.solve(to_dev(b), tol=1e-8)
+    true = np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b)
+    assert res[0].status == 0 and true <= 1e-8 * 1.01
+    if fp64:
+        L_ref = osetup.coarse_factor(osetup.galerkin(A, P_ref))
+        o = opcg.pcg(A, opcg.two_level_solver(A, P_ref, L_ref, p.omega, p.nu, p.nu), b, 1e-8)
+        assert abs(res[0].iterations - o["iters"]) <= 1
+
+
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_setup_fp64_subspace_sigma_and_galerkin(ctx, name):
     p = PROBLEMS[name]()
