@@ -212,9 +212,10 @@ NLSP_API nlsp_status nlsp_build_prolongation_a_weighted(nlsp_ctx* ctx, const nls
                                                         nlsp_prec** M_out);
 
 /* Builds a preconditioner from a given basis dev_P (n x k column-major,
-   ld = n, FP64, read during the call), e.g. the output of a learned map
-   f_theta after its QR layer (Sec. 3, Algorithm 1 lines "P_hat = f_theta(S)",
-   "P = qf(P_hat)").  P need not be orthonormal, only of full column rank.
+   ld = n, FP64, read during the call), e.g. the basis a learned map
+   produces from the smoothed samples, after its QR layer (Sec. 3 and the
+   setup of Algorithm 1).  P need not be orthonormal, only of full column
+   rank.
    params->K and params->s1 are ignored.  Factors A_c for rank k.
    Synchronises.  Errors as nlsp_build_prolongation. */
 NLSP_API nlsp_status nlsp_prec_from_basis(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* params,
@@ -286,7 +287,8 @@ NLSP_API nlsp_status nlsp_apply_prec(nlsp_ctx* ctx, const nlsp_prec* M, int m, c
    applications whose memory pool owns all of device memory under a fixed
    cap.  M itself must have been built beforehand (that does allocate).
    Temporaries live in one static device array, sized for
-   n <= NLSP_NOALLOC_MAX_N and active rank r <= NLSP_NOALLOC_MAX_RANK (about
+   n <= NLSP_NOALLOC_MAX_N and a stored basis of k <= NLSP_NOALLOC_MAX_RANK
+   columns (the rank M was built with, whatever rank it is truncated to; about
    7 MB, held by every GPU that loads the library until the process exits);
    larger problems return NLSP_ERR_INVALID (message in nlsp_last_error).
    The first call on a device looks up the array's device address (a CUDA
@@ -363,7 +365,7 @@ NLSP_API nlsp_status nlsp_plan_teams(int count, const int64_t* n, int num_ctas, 
  * ------------------------------------------------------------------------- */
 
 /* Subspace loss L = ||(I - Q Q^T) B||_F^2 with Q = qf(P_hat), the thin-Q
-   factor of P_hat (Sec. 3, "P = qf(P_hat)"; minimising this residual energy
+   factor of P_hat (Sec. 3, the QR layer after the learned map; minimising this residual energy
    maximises the subspace energy, Appendix on the optimality of smooth error
    reduction), and optionally its gradient dL/dP_hat.  P_hat: n x k, B: n x K
    (e.g. the smoothed samples), both FP64 column-major (ld = n), read during

@@ -2,7 +2,7 @@
 // with, on the GPU:
 //
 //   * the subspace loss L(P_hat) = ||(I - Q Q^T) B||_F^2 with Q = qf(P_hat)
-//     (Sec. 3, "P = qf(P_hat)"; the residual energy whose minimisation is the
+//     (Sec. 3, the QR layer after the learned map; the residual energy whose minimisation is the
 //     maximisation of the subspace energy, Appendix on optimality) and its
 //     gradient through the thin-QR layer;
 //   * the residual norm ||r_T|| after T unrolled PCG iterations with the

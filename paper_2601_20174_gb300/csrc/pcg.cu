@@ -1741,10 +1741,17 @@ nlsp_status allow_max_smem(F fn) {
   return NLSP_OK;
 }
 
+// Shared-memory limits are per device: the opt-in is raised once per
+// instantiation and device (the device current at the call).
+constexpr int PREP_MAX_DEVICES = 64;
+
 template <int KIND, typename T>
 nlsp_status prepare_stream_kernels() {
-  static bool done = false;  // once per instantiation and process (one device)
-  if (done) return NLSP_OK;
+  static bool done_on[PREP_MAX_DEVICES];
+  int dev = 0;
+  NLSP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= PREP_MAX_DEVICES) return NLSP_ERR_INVALID;
+  if (done_on[dev]) return NLSP_OK;
   NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 1, 0>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 1, 1>));
   NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 1, 2>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 2, 0>));
   NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 2, 1>)); NLSP_TRY(allow_max_smem(k_restrict<KIND, T, 2, 2>));
@@ -1755,7 +1762,7 @@ nlsp_status prepare_stream_kernels() {
   NLSP_TRY(allow_max_smem(k_prolong<T, 3>)); NLSP_TRY(allow_max_smem(k_prolong<T, 4>));
   NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 8>)); NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 16>));
   NLSP_TRY(allow_max_smem(k_pcg_persistent<KIND, T, 32>));
-  done = true;
+  done_on[dev] = true;
   return NLSP_OK;
 }
 
@@ -2563,7 +2570,9 @@ nlsp_status apply_noalloc(const nlsp_prec* M, unsigned char* base, int m, const 
 extern "C" nlsp_status nlsp_apply_prec_noalloc(nlsp_ctx* ctx, const nlsp_prec* M, int m, const double* dev_R,
                                                int64_t ldr, double* dev_Z, int64_t ldz) {
   if (!ctx || !M || m < 0 || (m > 0 && (!dev_R || !dev_Z)) || ldr < M->n || ldz < M->n) return NLSP_ERR_INVALID;
-  if (M->n > NLSP_NOALLOC_MAX_N || M->r > NLSP_NOALLOC_MAX_RANK) {
+  // the restriction's per-block partials are strided by the stored rank k
+  // (r <= k), so k is what the scratch must hold
+  if (M->n > NLSP_NOALLOC_MAX_N || M->k > NLSP_NOALLOC_MAX_RANK) {
     nlsp_record_message("nlsp_apply_prec_noalloc: n or rank exceeds NLSP_NOALLOC_MAX_N / NLSP_NOALLOC_MAX_RANK");
     return NLSP_ERR_INVALID;
   }

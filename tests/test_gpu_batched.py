@@ -6,13 +6,14 @@ reaches with the same preconditioner: the FP64 true relative residual below
 the tolerance (checked with the oracle's assembled operator), the iteration
 count of the single-instance persistent solve within one (the team's partial
 sums are added in another order), and the same iterate to the accuracy the
-tolerance leaves."""
+tolerance leaves.  In FP64 every instance is given the oracle's basis and
+must reproduce the oracle's PCG (iterations +-1, solution to 1e-8)."""
 import numpy as np
 import pytest
 import torch
 
 from helpers import rel, to_dev, to_np
-from oracle import operator as op
+from oracle import operator as op, pcg as opcg, setup as osetup
 from paper_2601_20174_gb300 import inputs as gen
 
 pytestmark = pytest.mark.gpu
@@ -72,11 +73,30 @@ def test_batched_uneven_instances_mixed(ctx):
 def test_batched_more_instances_than_ctas_fp64(ctx):
     # 170 single-CTA teams on 152 SMs: CTAs run several instances one after
     # another (ring barriers re-initialised, tensor memory not used in FP64,
-    # most of each P streamed through the ring)
+    # most of each P streamed through the ring).  Every instance gets the
+    # oracle's basis and must reproduce the oracle's PCG: iterations +-1,
+    # solution to 1e-8.
+    api = _api()
     rng = np.random.default_rng(5)
     probs = [gen.iid_diffusion_2d(int(N), 16, 24, seed=200 + i, tol=1e-8)
              for i, N in enumerate(rng.integers(36, 45, size=170))]
-    _check_batch(ctx, probs, FP64, tiles_per_cta=1000)
+    refs, precs, bs = [], [], []
+    for p in probs:
+        A = op.assemble(p)
+        su = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+        o = opcg.pcg(A, opcg.two_level_solver(A, su["P"], su["L"], p.omega, p.nu, p.nu), p.f[:, 0], p.tol)
+        refs.append((A, o))
+        precs.append(api.Preconditioner.from_basis(api.Operator.from_problem(ctx, p), to_dev(su["P"]), p.nu,
+                                                   p.omega, FP64))
+        bs.append(to_dev(p.f[:, 0]))
+    xs, res = api.solve_batched(precs, bs, tol=1e-8, maxit=3000, tiles_per_cta=1000)
+    for p, (A, o), x, r in zip(probs, refs, xs, res):
+        xb = to_np(x)
+        assert r.status == 0 and o["status"] == "converged"
+        assert abs(r.iterations - o["iters"]) <= 1, (p.N, r.iterations, o["iters"])
+        assert rel(xb, o["x"]) <= 1e-8
+        true = np.linalg.norm(p.f[:, 0] - A @ xb) / np.linalg.norm(p.f[:, 0])
+        assert true <= 1e-8 * 1.01 and abs(r.true_relres - true) <= 1e-3 * true
 
 
 def test_batched_grf_and_team_of_all_ctas(ctx):

@@ -279,6 +279,52 @@ def test_persistent_solver_large_grids(ctx, case):
         assert abs(r2[0].iterations - it_oracle) <= 8
 
 
+LARGE_FP64 = {
+    # several 128-node tiles per CTA (152 CTAs), and an FP64 P of 64 columns
+    # (64 KB per tile) that overflows shared memory into the streamed ring
+    "grf2d_N256_k64": lambda: gen.grf_diffusion_2d(N=256, k=64, K=128, seed=12, tol=1e-8),
+    "aniso9_N192_k64": lambda: gen.aniso_9pt_2d(N=192, k=64, K=128, m=1, seed=13, tol=1e-8),
+    "iid3d_N40_k64": lambda: gen.iid_diffusion_3d(N=40, k=64, K=128, seed=14, tol=1e-8),
+}
+
+
+@pytest.mark.parametrize("name", list(LARGE_FP64))
+def test_persistent_fp64_matches_oracle_iterates_multi_tile(ctx, name):
+    # FP64 persistent solver against the oracle's own iterates (same basis,
+    # the oracle's) where each CTA owns several node tiles and part of P is
+    # streamed every phase: iterations +-1, solution to 1e-8
+    p = LARGE_FP64[name]()
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    b = p.f[:, 0]
+    o = opcg.pcg(A, opcg.two_level_solver(A, ref["P"], ref["L"], p.omega, p.nu, p.nu), b, p.tol, maxit=5000)
+    assert o["status"] == "converged"
+    M = _api().Preconditioner.from_basis(_api().Operator.from_problem(ctx, p), to_dev(ref["P"]), p.nu, p.omega, FP64)
+    x, res = M.solve(to_dev(b), tol=p.tol, maxit=5000, graph_mode=2)
+    assert res[0].status == 0
+    assert abs(res[0].iterations - o["iters"]) <= 1, (res[0].iterations, o["iters"])
+    assert rel(to_np(x), o["x"]) <= 1e-8
+    true = np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b)
+    assert true <= p.tol * 1.01
+
+
+def test_bench_workload_fp64_iterations_match_oracle(ctx):
+    # the 512^2 GRF workload, plain FP64 end to end (device setup from the same
+    # samples): the oracle's stored iteration count +-1 and its true residual
+    import json, os
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "bench_workloads.json")))
+    want = golden["grf_diffusion2d_N512_k64_K128_seed0"]
+    p = gen.grf_diffusion_2d(512, 64, 128, seed=0, tol=1e-8)
+    A = op.assemble(p)
+    Aop = _api().Operator.from_problem(ctx, p)
+    M = _api().Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, FP64)
+    b = p.f[:, 0]
+    x, res = M.solve(to_dev(b), tol=p.tol, maxit=5000, graph_mode=2)
+    true = np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b)
+    assert res[0].status == 0 and true <= 1e-8 * 1.01
+    assert abs(res[0].iterations - want["iters"]) <= 1, (res[0].iterations, want["iters"])
+
+
 @pytest.mark.parametrize("name", ["poisson5", "grf5", "aniso9"])
 def test_persistent_merged_update_matches_separate_phase(ctx, name, monkeypatch):
     # the CG update inside the staged restriction (default on 2D FP32) and

@@ -67,6 +67,34 @@ def test_noalloc_matches_apply_prec_twice(ctx, name):
     assert st == 0 and rel(Z2, Zref2) <= tol
 
 
+@pytest.mark.parametrize("name", ["grf5_mixed", "iid7_fp64"])
+def test_noalloc_leaves_free_device_memory_unchanged(ctx, name):
+    # the reason the entry point exists: once warm, a call takes no device
+    # memory (free memory reported by the driver is the same before and after
+    # each of three calls; the buffers are created before measuring)
+    from paper_2601_20174_gb300 import api
+    make, precision, tol = CASES[name]
+    p = make()
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    M = api.Preconditioner.from_basis(api.Operator.from_problem(ctx, p), to_dev(ref["P"]), p.nu, p.omega, precision)
+    R = np.random.default_rng(9).standard_normal((p.n, 1))
+    st, Zref = _apply(ctx._lib, "nlsp_apply_prec", ctx, M, R)
+    assert st == 0
+    Rs = to_dev(np.ascontiguousarray(R.T))
+    Zs = torch.empty_like(Rs)
+    call = lambda: ctx._lib.nlsp_apply_prec_noalloc(ctx.h, M.h, 1, C.c_void_p(Rs.data_ptr()), p.n,
+                                                   C.c_void_p(Zs.data_ptr()), p.n)
+    assert call() == 0  # warm: the first call on the device looks up the array
+    torch.cuda.synchronize()
+    for _ in range(3):
+        free0 = torch.cuda.mem_get_info(ctx.device)[0]
+        assert call() == 0
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info(ctx.device)[0] == free0
+    assert rel(to_np(Zs).T, Zref) <= tol
+
+
 def test_noalloc_rejects_problems_beyond_its_capacity(ctx):
     from paper_2601_20174_gb300 import api
     N = 513  # n = 263169 > 262144 nodes
