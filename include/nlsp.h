@@ -161,6 +161,26 @@ NLSP_API void nlsp_destroy(nlsp_ctx* ctx);
 NLSP_API nlsp_status nlsp_assemble_stencil(nlsp_ctx* ctx, int dim, const int64_t grid[3], int points,
                                   const double* dev_coeffs, int coeff_layout, nlsp_op** A_out);
 
+/* General sparse SPD operator from compressed sparse rows (Sec. 3, Eq.
+   discretized_pde, for any SPD A; the paper's own matrices are P1 finite-
+   element stiffness and mass matrices on unstructured meshes, Appendix "FEM
+   Dataset Generation").  Row i holds entries dev_val[q] in columns
+   dev_col[q] for q in [dev_rowptr[i], dev_rowptr[i+1]); dev_rowptr has n + 1
+   entries from 0 to nnz.  Entries of a row need not be sorted; repeated
+   (row, column) pairs are summed.  Every row must have a positive diagonal
+   (the Jacobi smoother divides by it); A must be symmetric positive definite,
+   which is not checked beyond the diagonal.  All three arrays are device
+   memory read during the call (they may be freed afterwards).  The library
+   stores the diagonal, its inverse and the off-diagonal entries in row
+   slices of 32 rows (sliced ELLPACK, each slice as wide as its longest row)
+   in FP64 and FP32.  Every entry point that takes an nlsp_op accepts it.
+   1 <= n < 2^31, nnz >= n.  Synchronises.  Errors: NLSP_ERR_INVALID (row
+   pointers not monotone from 0 to nnz, a column outside [0, n), a missing,
+   non-positive or non-finite diagonal, a non-finite entry; message in
+   nlsp_last_error), NLSP_ERR_OOM, NLSP_ERR_CUDA. */
+NLSP_API nlsp_status nlsp_assemble_csr(nlsp_ctx* ctx, int64_t n, int64_t nnz, const int64_t* dev_rowptr,
+                                       const int32_t* dev_col, const double* dev_val, nlsp_op** A_out);
+
 /* Number of unknowns n of the operator. */
 NLSP_API int64_t nlsp_op_size(const nlsp_op* A);
 

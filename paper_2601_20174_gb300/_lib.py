@@ -58,6 +58,7 @@ SIGNATURES = {
     "nlsp_set_stream": (ci, [vp, vp]),
     "nlsp_destroy": (None, [vp]),
     "nlsp_assemble_stencil": (ci, [vp, ci, C.POINTER(i64), ci, vp, ci, C.POINTER(vp)]),
+    "nlsp_assemble_csr": (ci, [vp, i64, i64, vp, vp, vp, C.POINTER(vp)]),
     "nlsp_op_size": (i64, [vp]),
     "nlsp_op_apply": (ci, [vp, vp, ci, vp, i64, vp, i64]),
     "nlsp_op_diagonal": (ci, [vp, vp, vp]),

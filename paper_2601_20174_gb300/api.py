@@ -65,7 +65,8 @@ class Context:
 
 
 class Operator:
-    """SPD stencil operator A (nlsp_assemble_stencil)."""
+    """SPD operator A: a structured-grid stencil (nlsp_assemble_stencil) or a
+    general sparse matrix (Operator.from_csr, nlsp_assemble_csr)."""
 
     def __init__(self, ctx: Context, dim: int, N: int, points: int, coeffs: torch.Tensor, layout: int):
         self.ctx = ctx
@@ -77,6 +78,27 @@ class Operator:
                 "nlsp_assemble_stencil")
         self.h = h
         self.n = int(ctx._lib.nlsp_op_size(h))
+
+    @classmethod
+    def from_csr(cls, ctx: Context, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor) -> "Operator":
+        """From compressed sparse rows: rowptr (n + 1) int64, col (nnz) int32,
+        val (nnz) float64; copied to the context's device if needed."""
+        dev = f"cuda:{ctx.device}"
+        rp = rowptr.to(device=dev, dtype=torch.int64).contiguous()
+        cc = col.to(device=dev, dtype=torch.int32).contiguous()
+        vv = val.to(device=dev, dtype=torch.float64).contiguous()
+        n, nnz = rp.numel() - 1, cc.numel()
+        if vv.numel() != nnz:
+            raise ValueError("col and val must have the same length")
+        h = C.c_void_p()
+        L.check(ctx._lib.nlsp_assemble_csr(ctx.h, n, nnz, _ptr(rp), _ptr(cc), _ptr(vv), C.byref(h)),
+                "nlsp_assemble_csr")
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        self.dim, self.N, self.points, self.layout = 0, 0, 0, -1
+        self.h = h
+        self.n = int(ctx._lib.nlsp_op_size(h))
+        return self
 
     @classmethod
     def from_problem(cls, ctx: Context, problem) -> "Operator":

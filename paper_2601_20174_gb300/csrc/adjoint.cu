@@ -936,6 +936,7 @@ nlsp_status unrolled_dispatch(nlsp_ctx* ctx, const nlsp_op* A, nlsp_prec* M, int
   switch (A->kind) {
     case ST_5PT: return Unrolled<ST_5PT, TP>::run(ctx, A, M, nu, omega, b, T, loss, grad);
     case ST_9PT: return Unrolled<ST_9PT, TP>::run(ctx, A, M, nu, omega, b, T, loss, grad);
+    case ST_CSR: return Unrolled<ST_CSR, TP>::run(ctx, A, M, nu, omega, b, T, loss, grad);
     default: return Unrolled<ST_7PT, TP>::run(ctx, A, M, nu, omega, b, T, loss, grad);
   }
 }

@@ -136,7 +136,22 @@ template <int KIND, typename T, typename Get>
 __device__ __forceinline__ V4<T> stencil_apply4(const StencilView<T>& A, int64_t idx, NodeCoord c, Get get) {
   const int N = A.N;
   V4<T> s;
-  if (KIND == ST_9PT) {
+  if (KIND == ST_CSR) {
+    const V4<T> x0 = get(idx);
+    const T d = A.diag[idx];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s.v[q] = d * x0.v[q];
+    const int64_t sl = idx >> 5;
+    const int64_t base = A.soff[sl] + (idx & 31);
+    const int wd = (int)((A.soff[sl + 1] - A.soff[sl]) >> 5);
+    for (int j = 0; j < wd; ++j) {
+      const int64_t e = base + 32 * (int64_t)j;
+      const T a = A.sval[e];
+      const V4<T> x = get((int64_t)A.scol[e]);  // padding: (own row, 0)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s.v[q] += a * x.v[q];
+    }
+  } else if (KIND == ST_9PT) {
     const bool w = c.i > 0, e = c.i < N - 1, so = c.j > 0, no = c.j < N - 1;
     const V4<T> x0 = get(idx);
     V4<T> ew, ns, d1, d2;
@@ -1048,12 +1063,14 @@ extern "C" nlsp_status nlsp_solve_block(nlsp_ctx* ctx, const nlsp_op* A, const n
     switch (A->kind) {
       case ST_5PT: return BlockSolver<ST_5PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
       case ST_9PT: return BlockSolver<ST_9PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
+      case ST_CSR: return BlockSolver<ST_CSR, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
       default: return BlockSolver<ST_7PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
     }
   }
   switch (A->kind) {
     case ST_5PT: return BlockSolver<ST_5PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
     case ST_9PT: return BlockSolver<ST_9PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
+    case ST_CSR: return BlockSolver<ST_CSR, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
     default: return BlockSolver<ST_7PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
   }
 }

@@ -64,7 +64,15 @@ __host__ __device__ inline int64_t tiled_index(int64_t i, int c, int ncols) {
 static_assert(NLSP_TILE == 128, "tiled_index assumes 128-node tiles");
 inline int64_t pad_tile(int64_t n) { return (n + NLSP_TILE - 1) / NLSP_TILE * NLSP_TILE; }
 
-enum StencilKind { ST_5PT = 0, ST_9PT = 1, ST_7PT = 2 };
+enum StencilKind { ST_5PT = 0, ST_9PT = 1, ST_7PT = 2, ST_CSR = 3 };
+
+// Row slices of the general sparse operator: 32 consecutive rows (one warp)
+// share one slice whose off-diagonal entries are stored column by column
+// (sliced ELLPACK): entry j of row i sits at soff[i / 32] + 32 j + i % 32, so
+// a warp working on 32 consecutive rows reads each of its j-th entries as one
+// coalesced 128-byte (index) / 256-byte (FP64 value) access.  A slice is as
+// wide as its longest row; shorter rows are padded with (own row, 0).
+constexpr int NLSP_SLICE = 32;
 
 // Matrix-free view of A in one precision.
 //  5-point / 7-point: positive edge weights (h^-2 included) to the +x, +y, +z
@@ -72,6 +80,9 @@ enum StencilKind { ST_5PT = 0, ST_9PT = 1, ST_7PT = 2 };
 //  its inverse.  (A x)_i = d_i x_i - sum over neighbours of w_e x_nb.
 //  9-point constant: signed entries c[0] centre, c[1] E/W, c[2] N/S,
 //  c[3] NE/SW, c[4] NW/SE.
+//  General sparse (CSR input): the diagonal, its inverse and the signed
+//  off-diagonal entries in row slices (soff, scol, sval; see NLSP_SLICE):
+//  (A x)_i = d_i x_i + sum_j a_ij x_j.
 template <typename T>
 struct StencilView {
   int N;
@@ -83,6 +94,9 @@ struct StencilView {
   const T* dinv;
   T c[5];
   T cdinv;  // 1 / c[0] for the 9-point stencil
+  const int64_t* soff;  // slice offsets (n / 32 rounded up, plus one)
+  const int* scol;      // column of each sliced entry
+  const T* sval;        // value of each sliced entry
 };
 
 // ----------------------------------------------------------------------------
@@ -114,8 +128,12 @@ struct nlsp_op {
   int device;  // kept so that freeing never touches a destroyed context
   int dim, points, kind, N;
   int64_t n;
-  double* a64;  // one allocation: diag, cx, cy, cz, dinv (n each)
+  double* a64;  // one allocation: diag, cx, cy, cz, dinv (n each); general
+                // sparse: diag, dinv (n each), then the sliced entries
   float* a32;
+  void* sidx;   // general sparse: slice offsets (int64) and entry columns (int32)
+  int64_t nnz;  // general sparse: stored entries of the CSR input
+  int64_t sliced;  // general sparse: sliced off-diagonal entries (with padding)
   double c9[5];
   StencilView<double> v64;
   StencilView<float> v32;

@@ -46,6 +46,10 @@ struct DevBuf {
       constexpr int KIND_CONST = ST_9PT;                 \
       __VA_ARGS__;                                       \
     } break;                                             \
+    case ST_CSR: {                                       \
+      constexpr int KIND_CONST = ST_CSR;                 \
+      __VA_ARGS__;                                       \
+    } break;                                             \
     default: {                                           \
       constexpr int KIND_CONST = ST_7PT;                 \
       __VA_ARGS__;                                       \

@@ -3,6 +3,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "stencil.cuh"
 #include "kernels.cuh"
@@ -172,6 +175,76 @@ __global__ void k_apply_cols(StencilView<double> A, int m, const double* __restr
   }
 }
 
+// General sparse operator from CSR (rowptr int64, col int32, val FP64):
+// per row the number of off-diagonal entries, the diagonal (sum of the row's
+// diagonal entries) and its inverse.  bad: bit 0 column out of range, bit 1
+// non-positive or non-finite diagonal, bit 2 row pointers not monotone or not
+// spanning [0, nnz), bit 3 non-finite entry.
+__global__ void k_csr_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                           const double* __restrict__ val, int* __restrict__ cnt, double* __restrict__ diag,
+                           double* __restrict__ dinv, int* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    int flags = 0;
+    if (b < 0 || e < b || e > nnz || (i == 0 && b != 0) || (i == n - 1 && e != nnz)) {
+      atomicOr(bad, 4);
+      cnt[i] = 0;
+      diag[i] = 1.0;
+      dinv[i] = 1.0;
+      continue;
+    }
+    double d = 0.0;
+    int c = 0;
+    for (int64_t q = b; q < e; ++q) {
+      const int j = col[q];
+      const double v = val[q];
+      if (j < 0 || (int64_t)j >= n) flags |= 1;
+      if (!isfinite(v)) flags |= 8;
+      if ((int64_t)j == i) d += v;
+      else ++c;
+    }
+    if (!(d > 0.0) || !isfinite(d)) flags |= 2;
+    cnt[i] = c;
+    diag[i] = d;
+    dinv[i] = 1.0 / d;
+    if (flags) atomicOr(bad, flags);
+  }
+}
+
+// Width of each 32-row slice: its longest row's off-diagonal count.
+__global__ void k_slice_width(int64_t n, const int* __restrict__ cnt, int* __restrict__ width, int64_t nslices) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslices; s += (int64_t)gridDim.x * blockDim.x) {
+    int w = 0;
+    for (int64_t i = s * NLSP_SLICE; i < n && i < (s + 1) * NLSP_SLICE; ++i) w = max(w, cnt[i]);
+    width[s] = w;
+  }
+}
+
+// Scatters each row's off-diagonal entries into its slice (entry j of row i
+// at soff[i / 32] + 32 j + i % 32) and pads the row to the slice width with
+// (own row, 0).
+__global__ void k_csr_fill(int64_t n, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                           const double* __restrict__ val, const int64_t* __restrict__ soff, int* __restrict__ scol,
+                           double* __restrict__ sval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = i / NLSP_SLICE;
+    const int64_t base = soff[sl] + i % NLSP_SLICE;
+    const int w = (int)((soff[sl + 1] - soff[sl]) / NLSP_SLICE);
+    int c = 0;
+    for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+      const int j = col[q];
+      if ((int64_t)j == i) continue;
+      scol[base + (int64_t)NLSP_SLICE * c] = j;
+      sval[base + (int64_t)NLSP_SLICE * c] = val[q];
+      ++c;
+    }
+    for (; c < w; ++c) {
+      scol[base + (int64_t)NLSP_SLICE * c] = (int)i;
+      sval[base + (int64_t)NLSP_SLICE * c] = 0.0;
+    }
+  }
+}
+
 __global__ void k_diag_9pt(double d, double* out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = d;
@@ -270,6 +343,94 @@ extern "C" nlsp_status nlsp_assemble_stencil(nlsp_ctx* ctx, int dim, const int64
   return NLSP_OK;
 }
 
+extern "C" nlsp_status nlsp_assemble_csr(nlsp_ctx* ctx, int64_t n, int64_t nnz, const int64_t* dev_rowptr,
+                                         const int32_t* dev_col, const double* dev_val, nlsp_op** A_out) {
+  if (!ctx || !A_out || !dev_rowptr || !dev_col || !dev_val) return NLSP_ERR_INVALID;
+  *A_out = nullptr;
+  if (n < 1 || n > ((int64_t)1 << 31) - 1 || nnz < n) return NLSP_ERR_INVALID;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  nlsp_op* op = new nlsp_op();
+  memset(op, 0, sizeof(*op));
+  op->ctx = ctx;
+  op->device = ctx->device;
+  op->dim = 0;
+  op->points = 0;
+  op->kind = ST_CSR;
+  op->N = 0;
+  op->n = n;
+  op->nnz = nnz;
+  cudaStream_t s = ctx->stream;
+  const int64_t nsl = (n + NLSP_SLICE - 1) / NLSP_SLICE;
+  DevBuf tmp;  // row counts (n), slice widths (nsl), error word
+  auto fail = [&](nlsp_status e) {
+    nlsp_free_op(op);
+    return e;
+  };
+  nlsp_status st = tmp.alloc(sizeof(int) * (size_t)(n + nsl + 1));
+  if (st != NLSP_OK) return fail(st);
+  int* cnt = tmp.as<int>();
+  int* width = cnt + n;
+  int* bad = width + nsl;
+  DevBuf dd;  // diagonal and inverse before the final allocation is sized
+  if ((st = dd.alloc(sizeof(double) * 2 * (size_t)n)) != NLSP_OK) return fail(st);
+  if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+  const int g = grid_for(ctx, n, 256, 8);
+  k_csr_rows<<<g, 256, 0, s>>>(n, nnz, dev_rowptr, (const int*)dev_col, dev_val, cnt, dd.as<double>(),
+                               dd.as<double>() + n, bad);
+  k_slice_width<<<grid_for(ctx, nsl, 256, 8), 256, 0, s>>>(n, cnt, width, nsl);
+  count_launches(ctx, 2);
+  if (cudaGetLastError() != cudaSuccess) return fail(NLSP_ERR_CUDA);
+  std::vector<int> hw((size_t)nsl + 1);
+  if (cudaMemcpyAsync(hw.data(), width, sizeof(int) * (size_t)(nsl + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return fail(NLSP_ERR_CUDA);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+  const int hbad = hw[(size_t)nsl];
+  if (hbad) {
+    nlsp_record_message((hbad & 4) ? "nlsp_assemble_csr: row pointers are not monotone from 0 to nnz"
+                        : (hbad & 1) ? "nlsp_assemble_csr: a column index is outside [0, n)"
+                        : (hbad & 8) ? "nlsp_assemble_csr: a non-finite entry"
+                                     : "nlsp_assemble_csr: a diagonal entry is missing, non-positive or non-finite");
+    return fail(NLSP_ERR_INVALID);
+  }
+  std::vector<int64_t> soff((size_t)nsl + 1);
+  soff[0] = 0;
+  for (int64_t q = 0; q < nsl; ++q) soff[(size_t)q + 1] = soff[(size_t)q] + (int64_t)NLSP_SLICE * hw[(size_t)q];
+  const int64_t sliced = soff[(size_t)nsl];
+  op->sliced = sliced;
+  const size_t nval = (size_t)(2 * n + sliced);
+  if (cudaMalloc(&op->a64, sizeof(double) * nval) != cudaSuccess) return fail(NLSP_ERR_OOM);
+  if (cudaMalloc(&op->a32, sizeof(float) * nval) != cudaSuccess) return fail(NLSP_ERR_OOM);
+  const size_t idx_bytes = sizeof(int64_t) * (size_t)(nsl + 1) + sizeof(int) * (size_t)std::max<int64_t>(sliced, 1);
+  if (cudaMalloc(&op->sidx, idx_bytes) != cudaSuccess) return fail(NLSP_ERR_OOM);
+  int64_t* d_soff = (int64_t*)op->sidx;
+  int* d_scol = (int*)(d_soff + nsl + 1);
+  if (cudaMemsetAsync(op->a64, 0, sizeof(double) * nval, s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+  if (cudaMemsetAsync(op->sidx, 0, idx_bytes, s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+  if (cudaMemcpyAsync(op->a64, dd.p, sizeof(double) * 2 * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return fail(NLSP_ERR_CUDA);
+  if (cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(NLSP_ERR_CUDA);
+  k_csr_fill<<<g, 256, 0, s>>>(n, dev_rowptr, (const int*)dev_col, dev_val, d_soff, d_scol, op->a64 + 2 * n);
+  k_to_float<<<grid_for(ctx, (int64_t)nval, 256, 8), 256, 0, s>>>(op->a64, op->a32, (int64_t)nval);
+  count_launches(ctx, 2);
+  if (cudaGetLastError() != cudaSuccess) return fail(NLSP_ERR_CUDA);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
+  StencilView<double>& v = op->v64;
+  StencilView<float>& w = op->v32;
+  v.N = w.N = 0;
+  v.n = w.n = n;
+  v.diag = op->a64;
+  v.dinv = op->a64 + n;
+  v.sval = op->a64 + 2 * n;
+  w.diag = op->a32;
+  w.dinv = op->a32 + n;
+  w.sval = op->a32 + 2 * n;
+  v.soff = w.soff = d_soff;
+  v.scol = w.scol = d_scol;
+  *A_out = op;
+  return NLSP_OK;
+}
+
 extern "C" int64_t nlsp_op_size(const nlsp_op* A) { return A ? A->n : -1; }
 
 extern "C" nlsp_status nlsp_op_apply(nlsp_ctx* ctx, const nlsp_op* A, int m, const double* dev_X, int64_t ldx,
@@ -282,6 +443,7 @@ extern "C" nlsp_status nlsp_op_apply(nlsp_ctx* ctx, const nlsp_op* A, int m, con
   switch (A->kind) {
     case ST_5PT: k_apply_cols<ST_5PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
     case ST_9PT: k_apply_cols<ST_9PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
+    case ST_CSR: k_apply_cols<ST_CSR><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
     default: k_apply_cols<ST_7PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
   }
   count_launches(ctx, 1);
@@ -306,5 +468,6 @@ extern "C" void nlsp_free_op(nlsp_op* A) {
   cudaSetDevice(A->device);
   if (A->a64) cudaFree(A->a64);
   if (A->a32) cudaFree(A->a32);
+  if (A->sidx) cudaFree(A->sidx);
   delete A;
 }

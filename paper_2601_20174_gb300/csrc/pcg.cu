@@ -87,6 +87,7 @@ const PcgKindOps* pcg_ops(const nlsp_prec* M) {
   switch (M->A->kind) {
     case ST_5PT: return f64 ? nlsp_pcg_ops_5pt_f64() : nlsp_pcg_ops_5pt_f32();
     case ST_9PT: return f64 ? nlsp_pcg_ops_9pt_f64() : nlsp_pcg_ops_9pt_f32();
+    case ST_CSR: return f64 ? nlsp_pcg_ops_csr_f64() : nlsp_pcg_ops_csr_f32();
     default: return f64 ? nlsp_pcg_ops_7pt_f64() : nlsp_pcg_ops_7pt_f32();
   }
 }

@@ -857,8 +857,8 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
   const int e1lo = max(0, i0 - hop), e1hi = min(n, i1 + hop);
   const int e2lo = max(0, i0 - 2 * hop), e2hi = min(n, i1 + 2 * hop);
   const int ring_elems = nstage * r * NLSP_TILE;
-  const bool stage_pre = FP32 && KIND != ST_7PT && i1 > i0 && (e2hi - e2lo) + (e1hi - e1lo) <= ring_elems;
-  const bool stage_post = FP32 && KIND != ST_7PT && i1 > i0 && (e1hi - e1lo) <= ring_elems;
+  const bool stage_pre = FP32 && (KIND == ST_5PT || KIND == ST_9PT) && i1 > i0 && (e2hi - e2lo) + (e1hi - e1lo) <= ring_elems;
+  const bool stage_post = FP32 && (KIND == ST_5PT || KIND == ST_9PT) && i1 > i0 && (e1hi - e1lo) <= ring_elems;
   unsigned gen = 0, jc = 0;
   bool ok = true;
   double tol2bn = 0.0;
@@ -1990,7 +1990,7 @@ struct Solver {
   static int merge_ok(const nlsp_prec* M, const StreamArgs& sa) {
     const char* env = getenv("NLSP_MERGE_PRE");
     if (env && env[0] == '0') return 0;
-    if (sizeof(T) != 4 || KIND == ST_7PT || M->nu1 > 2) return 0;
+    if (sizeof(T) != 4 || (KIND != ST_5PT && KIND != ST_9PT) || M->nu1 > 2) return 0;
     const int64_t hop = (int64_t)M->A->N + 1;
     const int64_t nodes = sa.max_nodes;
     const int64_t need = 2 * (nodes + 4 * hop) + (nodes + 2 * hop);
@@ -2377,6 +2377,8 @@ const PcgKindOps* nlsp_pcg_ops_9pt_f64();
 const PcgKindOps* nlsp_pcg_ops_9pt_f32();
 const PcgKindOps* nlsp_pcg_ops_7pt_f64();
 const PcgKindOps* nlsp_pcg_ops_7pt_f32();
+const PcgKindOps* nlsp_pcg_ops_csr_f64();
+const PcgKindOps* nlsp_pcg_ops_csr_f32();
 
 // Defines nlsp_pcg_ops_<NAME_>() for stencil kind KIND_ in precision T_.
 #define NLSP_PCG_OPS(KIND_, T_, NAME_)                                                                  \

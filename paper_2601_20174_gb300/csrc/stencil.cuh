@@ -1,6 +1,6 @@
-// Matrix-free stencil evaluation of A (Sec. 3, Eq. discretized_pde) on the
-// structured grids: 2D 5-point and 9-point, 3D 7-point, Dirichlet nodes
-// eliminated.  Every function evaluates in precision T and reads the vector in
+// Evaluation of A (Sec. 3, Eq. discretized_pde): matrix-free stencils on the
+// structured grids (2D 5-point and 9-point, 3D 7-point, Dirichlet nodes
+// eliminated) and the general sparse operator in row slices.  Every function evaluates in precision T and reads the vector in
 // its own storage type X (so an FP32 preconditioner can read FP64 residuals).
 #pragma once
 
@@ -14,6 +14,10 @@ struct NodeCoord {
 template <int KIND>
 __device__ __forceinline__ NodeCoord node_coord(int64_t idx, int N) {
   NodeCoord c;
+  if (KIND == ST_CSR) {  // no grid: neighbours come from the row's entries
+    c.i = c.j = c.l = 0;
+    return c;
+  }
   const unsigned u = (unsigned)idx, un = (unsigned)N;
   if (KIND == ST_7PT) {
     const unsigned nn = un * un;
@@ -44,6 +48,17 @@ __device__ __forceinline__ T stencil_dinv(const StencilView<T>& A, int64_t idx) 
 template <int KIND, typename T, typename Get>
 __device__ __forceinline__ T stencil_apply(const StencilView<T>& A, int64_t idx, NodeCoord c, Get get) {
   const int N = A.N;
+  if (KIND == ST_CSR) {
+    T s = A.diag[idx] * get(idx);
+    const int64_t sl = idx >> 5;
+    const int64_t base = A.soff[sl] + (idx & 31);
+    const int w = (int)((A.soff[sl + 1] - A.soff[sl]) >> 5);
+    for (int j = 0; j < w; ++j) {
+      const int64_t e = base + 32 * (int64_t)j;
+      s += A.sval[e] * get((int64_t)A.scol[e]);  // padding: (own row, 0)
+    }
+    return s;
+  }
   if (KIND == ST_9PT) {
     T s = A.c[0] * get(idx);
     const bool w = c.i > 0, e = c.i < N - 1, so = c.j > 0, no = c.j < N - 1;
@@ -78,6 +93,17 @@ __device__ __forceinline__ T stencil_apply(const StencilView<T>& A, int64_t idx,
 template <int KIND, typename T, typename F>
 __device__ __forceinline__ void for_each_neighbour(const StencilView<T>& A, int64_t idx, NodeCoord c, F f) {
   const int N = A.N;
+  if (KIND == ST_CSR) {
+    const int64_t sl = idx >> 5;
+    const int64_t base = A.soff[sl] + (idx & 31);
+    const int wd = (int)((A.soff[sl + 1] - A.soff[sl]) >> 5);
+    for (int j = 0; j < wd; ++j) {
+      const int64_t e = base + 32 * (int64_t)j;
+      const int64_t m = A.scol[e];
+      if (m != idx) f(m, NodeCoord{0, 0, 0}, A.sval[e]);  // padding entries point at the own row
+    }
+    return;
+  }
   const bool w = c.i > 0, e = c.i < N - 1, so = c.j > 0, no = c.j < N - 1;
   if (KIND == ST_9PT) {
     if (w) f(idx - 1, NodeCoord{c.i - 1, c.j, c.l}, A.c[1]);
