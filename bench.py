@@ -370,6 +370,105 @@ def run_small(ctx, dev, timed):
     return out
 
 
+FEM_SPMV_N = 1448
+FEM_DESC = ("P1 finite elements on jittered Delaunay meshes of the unit square (Appendix, FEM Dataset Generation), "
+            "five families, N=64 (n=4225), k=48 from K=72 smoothed samples (s1=20), nu1=nu2=5, omega=0.66, "
+            "tol 1e-6, f ~ U[-1,1] on the interior vertices; CSR input (nlsp_assemble_csr)")
+PAPER_SVD_ITERS = {"diffusion": 64, "anisotropic": 55, "screened_poisson": 46, "heat": 45, "wave": 64}
+
+
+def run_fem(ctx, dev, timed):
+    """The paper's own workload type through the general sparse operator:
+    (1) the sliced-ELLPACK SpMV (nlsp_op_apply) on a large FEM diffusion matrix,
+    against the HBM roofline; (2) each of the five FEM families at the paper's
+    two-grid settings: CSR assembly + build P + PCG (mixed precision) per
+    step, with the FP64 iteration count beside the paper's SVD column (Table
+    iter_counts; other machine, same method)."""
+    import ctypes as C
+    import statistics as st
+
+    import torch
+
+    from paper_2601_20174_gb300 import _lib as L, api, fem
+
+    out = {"workload": FEM_DESC}
+    # ---- SpMV ---------------------------------------------------------------
+    pts, tri = fem.mesh(FEM_SPMV_N, 0)
+    ip, ix, dv, _ = fem.family_matrix("diffusion", pts, tri, FEM_SPMV_N, 0)
+    n, nnz = ip.size - 1, ix.size
+    rp_d = torch.as_tensor(ip).to(dev)
+    ci_d = torch.as_tensor(ix).to(dev)
+    va_d = torch.as_tensor(dv).to(dev)
+    A = api.Operator.from_csr(ctx, rp_d, ci_d, va_d)
+    x = torch.randn(n, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    call = lambda: L.check(ctx._lib.nlsp_op_apply(ctx.h, A.h, 1, C.c_void_p(x.data_ptr()), n,
+                                                   C.c_void_p(y.data_ptr()), n), "nlsp_op_apply")
+    for _ in range(3):
+        call()
+    ms, _ = timed(call, 20, read_flush=True)
+    avg = st.mean(ms) / 1000.0
+    offdiag = nnz - n
+    alg = offdiag * 12 + n * 24  # off-diagonal value + column, diagonal, x, y (FP64)
+    peak, kind = _peaks()
+    ncu_tr = _fem_spmv_traffic()
+    out["csr_spmv"] = {"n": n, "nnz": nnz, "mesh": f"N={FEM_SPMV_N} jittered Delaunay, diffusion family",
+                       "avg_us_cold_l2": avg * 1e6, "algorithmic_bytes": alg, "achieved_gbs": alg / avg / 1e9,
+                       "frac_of_hbm": alg / avg / 1e9 / peak, "peak_gbs": peak, "peak_kind": kind,
+                       "traffic": ncu_tr,
+                       "bytes_note": "algorithmic = off-diagonal entries x (8-byte value + 4-byte column) + n x "
+                                     "(diagonal + x + y, 8 bytes each); the sliced storage adds the padding of each "
+                                     "32-row slice to its longest row"}
+    A.close()
+    del rp_d, ci_d, va_d, x, y
+    # ---- the five families at the paper's settings --------------------------
+    fam_out = {}
+    for family in fem.FAMILIES:
+        pr = fem.fem_problem(family, N=64, seed=0)
+        rp = torch.as_tensor(pr.indptr).to(dev)
+        ci = torch.as_tensor(pr.indices).to(dev)
+        va = torch.as_tensor(pr.data).to(dev)
+        S0 = torch.as_tensor(pr.S0.T.copy()).to(dev)
+        f = torch.as_tensor(pr.f[:, 0].copy()).to(dev)
+
+        def step(precision):
+            Aop = api.Operator.from_csr(ctx, rp, ci, va)
+            M = api.Preconditioner.build(Aop, S0.t(), pr.k, pr.s1, pr.nu, pr.omega, precision)
+            xs, res = M.solve(f, tol=pr.tol, graph_mode=2)
+            return Aop, M, xs, res[0]
+
+        for _ in range(2):
+            step(L.NLSP_MIXED_FP32)
+        ms_m, (_, M, _, info_m) = timed(lambda: step(L.NLSP_MIXED_FP32), 5)
+        ms_so, _ = timed(lambda: M.solve(f, tol=pr.tol, graph_mode=2), 5)
+        step(L.NLSP_FP64)
+        ms_d, (_, _, _, info_d) = timed(lambda: step(L.NLSP_FP64), 3)
+        fam_out[family] = {"solves_per_s": 1e3 / st.median(ms_m), "ms_per_step": st.median(ms_m),
+                           "solve_only_ms": st.median(ms_so), "iterations_mixed": info_m.iterations,
+                           "iterations_fp64": info_d.iterations, "fp64_ms_per_step": st.median(ms_d),
+                           "converged": info_m.status == 0 and info_d.status == 0,
+                           "paper_svd_median_iterations": PAPER_SVD_ITERS[family], "params": pr.params}
+    out["families"] = fam_out
+    out["paper_context"] = ("Table iter_counts of the paper: median PCG iterations with the SVD basis at coarse "
+                            "dimension 48 (Apple M1 CPU; the iteration count is machine-independent)")
+    return out
+
+
+def _fem_spmv_traffic():
+    """DRAM bytes per launch of the sparse SpMV from the committed ncu
+    summary, while op.cu is unchanged since that capture (else None)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "csr_spmv_fem1448.json")) as f:
+            prof = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2601_20174_gb300", "csrc", "op.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != prof["op_cu_sha256"]:
+            return None
+        return prof["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 BLOCK = dict(N=1024, k=128, K=128, m=32, s1=20, nu=2, omega=2.0 / 3.0, tol=1e-8, seed=0, seq_cols=4)
 BLOCK_DESC = ("2D rotated anisotropic diffusion, 9-point, 1024^2 (n=1046529), theta ~ U[0,pi), eps=1e-3, k=128 "
               "from K=128 device-drawn smoothed samples (s1=20, omega=2/3), nu=2; 32 RHS U[-1,1] by block PCG "
@@ -614,6 +713,7 @@ def run_ours(args):
     differentiation = None if args.no_differentiation else run_differentiation(ctx, dev, timed)
     block = None if args.no_block else run_block(ctx, dev, timed)
     small = run_small(ctx, dev, timed)
+    fem_leg = None if args.no_fem else run_fem(ctx, dev, timed)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -644,7 +744,7 @@ def run_ours(args):
                 "roofline": roof, "kernels": kern,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * 8},
                 "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu, "batched": batched,
-                "differentiation": differentiation, "block": block, "small": small}
+                "differentiation": differentiation, "block": block, "small": small, "fem": fem_leg}
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
@@ -662,6 +762,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched leg")
     ap.add_argument("--no-differentiation", action="store_true", help="skip the differentiation leg")
     ap.add_argument("--no-block", action="store_true", help="skip the 32-RHS block PCG leg")
+    ap.add_argument("--no-fem", action="store_true", help="skip the finite-element (CSR) leg")
     ap.add_argument("--graph-mode", type=int, default=2, choices=[0, 1, 2],
                     help="2: one persistent cooperative kernel per solve (default); 1: PCG loop as one graph "
                          "with a device-side while node; 0: one-iteration graph relaunched by the host "

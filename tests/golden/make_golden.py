@@ -1,9 +1,15 @@
-"""Writes tests/golden/bench_workloads.json by running ONLY the FP64 oracle on
-the benchmark workloads (seeded synthetic inputs).  The stored iteration
-counts let the CPU baseline time a bounded sample (setup plus a fixed number
-of PCG iterations) and extrapolate to a full solve.
+"""Writes the stored expected values by running ONLY the FP64 oracle on seeded
+synthetic inputs:
 
-    python tests/golden/make_golden.py
+  bench_workloads.json  iteration counts of the benchmark workloads (the CPU
+                        baseline times a bounded sample and scales it);
+  fem_iterations.json   PCG iteration counts with the exact SVD basis on the
+                        five finite-element families at the paper's two-grid
+                        settings (Sec. 4: N = 64, K = 72, coarse dimension 48,
+                        tolerance 1e-6, nu1 = nu2 = 5, omega = 0.66), ten
+                        instances each, with their medians.
+
+    python tests/golden/make_golden.py [--fem-only]
 """
 import json
 import os
@@ -14,7 +20,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 from oracle import operator as op, pcg, setup as su  # noqa: E402
-from paper_2601_20174_gb300 import inputs as gen  # noqa: E402
+from paper_2601_20174_gb300 import fem, inputs as gen  # noqa: E402
 
 WORKLOADS = {
     # 2D variable-coefficient diffusion, 5-point, 512 x 512, GRF log kappa
@@ -26,7 +32,33 @@ WORKLOADS = {
 }
 
 
+FEM_INSTANCES = 10
+
+
+def fem_iterations():
+    import numpy as np
+    import scipy.sparse as sparse
+    out = {}
+    for family in fem.FAMILIES:
+        its = []
+        for seed in range(FEM_INSTANCES):
+            p = fem.fem_problem(family, N=64, seed=seed)
+            A = sparse.csr_matrix((p.data, p.indices, p.indptr), shape=(p.n, p.n))
+            st = su.build(A, p.S0, p.k, p.omega, p.s1)
+            res = pcg.pcg(A, pcg.two_level_solver(A, st["P"], st["L"], p.omega, p.nu, p.nu), p.f[:, 0], p.tol)
+            assert res["status"] == "converged"
+            its.append(res["iters"])
+        out[family] = {"iters": its, "median": float(np.median(its)), "N": 64, "k": 48, "K": 72, "tol": 1e-6,
+                       "nu": 5, "omega": 0.66, "s1": 20}
+        print(family, out[family], flush=True)
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "fem_iterations.json"), "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+
+
 def main():
+    fem_iterations()
+    if "--fem-only" in sys.argv:
+        return
     out = {}
     for name, make in WORKLOADS.items():
         p = make()
