@@ -103,6 +103,8 @@ typedef struct {
 /* Stream number of the random test vectors S0 in the counter-based generator
    (SplitMix64 counter streams, Box-Muller normals). */
 #define NLSP_STREAM_S0 3
+/* Stream number of the Gaussian sketch of the randomised-SVD setup. */
+#define NLSP_STREAM_SKETCH 11
 
 typedef struct {
   double tol;     /* stop when ||r||_2 <= tol ||b||_2 (recursive residual)  */
@@ -229,6 +231,25 @@ NLSP_API nlsp_status nlsp_build_prolongation(nlsp_ctx* ctx, const nlsp_op* A, co
    (nlsp_prec_copy_sigma) are those of A^{1/2} S.  Same arguments and errors. */
 NLSP_API nlsp_status nlsp_build_prolongation_a_weighted(nlsp_ctx* ctx, const nlsp_op* A,
                                                         const nlsp_setup_params* params, const double* dev_S0,
+                                                        nlsp_prec** M_out);
+
+/* As nlsp_build_prolongation, with the randomised SVD in place of the exact
+   thin SVD (the paper's RandomSVD basis, Sec. 4 baselines; Halko, Martinsson
+   and Tropp 2011: randomised range finder with power iterations, then the SVD
+   of the small projected matrix): with l = k + oversample columns of a
+   Gaussian sketch Omega (K x l), Q = qf(S Omega), power_iters times
+   Q = qf(S qf(S^T Q)), then P = Q U_B[:, :k] for the left singular vectors
+   U_B of B = Q^T S.  dev_sketch: Omega, FP64 column-major K x l (device,
+   read during the call), or NULL to draw it on the device from the
+   counter-based generator of nlsp_random_normal with params->seed and stream
+   NLSP_STREAM_SKETCH (element (c, j) is normal number j K + c).  The
+   singular values reported are those of B (l values, zeros beyond).
+   Requires 0 <= oversample, k + oversample <= K, 0 <= power_iters <= 16;
+   other arguments and errors as nlsp_build_prolongation (NLSP_ERR_NOT_SPD
+   also when S Omega is rank deficient). */
+NLSP_API nlsp_status nlsp_build_prolongation_randomized(nlsp_ctx* ctx, const nlsp_op* A,
+                                                        const nlsp_setup_params* params, const double* dev_S0,
+                                                        int oversample, int power_iters, const double* dev_sketch,
                                                         nlsp_prec** M_out);
 
 /* Builds a preconditioner from a given basis dev_P (n x k column-major,

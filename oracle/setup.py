@@ -119,16 +119,18 @@ def post_correction_energy(A, P: np.ndarray, S: np.ndarray) -> float:
 
 
 def prolongation_randomized(S: np.ndarray, k: int, oversample: int, power_iters: int,
-                            Omega: np.ndarray) -> np.ndarray:
+                            Omega: np.ndarray, return_sigma: bool = False):
     """Randomised SVD basis (Halko, Martinsson, Tropp 2011): Y = S Omega with
     a Gaussian test matrix Omega (K x (k + oversample), passed in), q power
     iterations Y <- S (S^T Y) with re-orthonormalisation (their Algorithm
-    4.4), Q = qr(Y), then the SVD of the small matrix Q^T S (their Algorithm
-    5.1): P = Q U_B[:, :k]."""
+    4.4), Q = qr(Y), then the SVD of the small matrix B = Q^T S (their
+    Algorithm 5.1): P = Q U_B[:, :k].  With return_sigma, also the singular
+    values of B."""
     assert Omega.shape == (S.shape[1], k + oversample)
     Q, _ = np.linalg.qr(S @ Omega)
     for _ in range(power_iters):
         W, _ = np.linalg.qr(S.T @ Q)
         Q, _ = np.linalg.qr(S @ W)
-    UB, _, _ = np.linalg.svd(Q.T @ S, full_matrices=False)
-    return Q @ UB[:, :k]
+    UB, sB, _ = np.linalg.svd(Q.T @ S, full_matrices=False)
+    P = Q @ UB[:, :k]
+    return (P, sB) if return_sigma else P

@@ -66,6 +66,7 @@ SIGNATURES = {
     "nlsp_smooth_samples": (ci, [vp, vp, ci, ci, cd, ci, vp, vp]),
     "nlsp_build_prolongation": (ci, [vp, vp, C.POINTER(SetupParams), vp, C.POINTER(vp)]),
     "nlsp_build_prolongation_a_weighted": (ci, [vp, vp, C.POINTER(SetupParams), vp, C.POINTER(vp)]),
+    "nlsp_build_prolongation_randomized": (ci, [vp, vp, C.POINTER(SetupParams), vp, ci, ci, vp, C.POINTER(vp)]),
     "nlsp_prec_from_basis": (ci, [vp, vp, C.POINTER(SetupParams), vp, ci, C.POINTER(vp)]),
     "nlsp_factor_coarse": (ci, [vp, vp, vp, ci]),
     "nlsp_prec_dims": (ci, [vp, C.POINTER(i64), C.POINTER(ci), C.POINTER(ci), C.POINTER(ci), C.POINTER(ci)]),

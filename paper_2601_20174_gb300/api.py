@@ -183,6 +183,32 @@ class Preconditioner:
         return cls(op, h)
 
     @classmethod
+    def build_randomized(cls, op: Operator, S0: torch.Tensor | None, k: int, oversample: int = 10,
+                         power_iters: int = 2, sketch: torch.Tensor | None = None, s1: int = 20, nu: int = 2,
+                         omega: float = 2.0 / 3.0, precision: int = L.NLSP_FP64, K: int | None = None,
+                         seed: int = 0) -> "Preconditioner":
+        """Randomised-SVD basis (nlsp_build_prolongation_randomized).  sketch:
+        the K x (k + oversample) Gaussian test matrix, or None to draw it on
+        the device from `seed`."""
+        if S0 is None:
+            if K is None:
+                raise ValueError("K is required when S0 is drawn on the device")
+            ptr = C.c_void_p(0)
+        else:
+            store, K = _colmajor(S0, op.n)
+            ptr = _ptr(store)
+        sk = C.c_void_p(0)
+        if sketch is not None:
+            sks, _ = _colmajor(sketch, K)
+            sk = _ptr(sks)
+        p = cls._params(k, K, s1, nu, omega, precision, seed)
+        h = C.c_void_p()
+        L.check(op.ctx._lib.nlsp_build_prolongation_randomized(op.ctx.h, op.h, C.byref(p), ptr, oversample,
+                                                                power_iters, sk, C.byref(h)),
+                "nlsp_build_prolongation_randomized")
+        return cls(op, h)
+
+    @classmethod
     def from_basis(cls, op: Operator, P: torch.Tensor, nu: int = 2, omega: float = 2.0 / 3.0,
                    precision: int = L.NLSP_FP64) -> "Preconditioner":
         store, k = _colmajor(P, op.n)

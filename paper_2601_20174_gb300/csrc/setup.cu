@@ -725,6 +725,47 @@ __global__ void __launch_bounds__(32) k_spd_inverse_cols(const double* __restric
 // Dynamic shared memory of k_spd_inverse_cols for order m.
 inline size_t spd_inverse_smem(int m) { return sizeof(double) * ((size_t)m * (m + 1) + 2 * (size_t)m); }
 
+// C (m x n) = op(A) op(B), op(A) m x kk, op(B) kk x n, all FP64 column-major
+// with leading dimensions; ta / tb select the transposes.  One block per
+// column of C; the column of op(B) is staged in shared memory (kk <= 256).
+__global__ void k_gemm_small(const double* __restrict__ A, int lda, int ta, const double* __restrict__ B, int ldb,
+                             int tb, double* __restrict__ C, int ldc, int m, int n, int kk) {
+  __shared__ double bcol[256];
+  const int j = blockIdx.x;
+  for (int q = threadIdx.x; q < kk; q += blockDim.x) bcol[q] = tb ? B[(int64_t)q * ldb + j] : B[(int64_t)j * ldb + q];
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double s = 0.0;
+    if (ta)
+      for (int q = 0; q < kk; ++q) s += A[(int64_t)i * lda + q] * bcol[q];
+    else
+      for (int q = 0; q < kk; ++q) s += A[(int64_t)q * lda + i] * bcol[q];
+    C[(int64_t)j * ldc + i] = s;
+  }
+}
+
+// Coefficients of the randomised basis: M = X V[:, :k] (K x k, row-major
+// M[c * k + j], precision T) from X (K x l) and the eigenvectors V (l x l) of
+// B B^T; sigma = sqrt of its l eigenvalues (zero beyond l, up to K).  Flags a
+// non-positive eigenvalue among the first k.
+template <typename T>
+__global__ void k_randomized_coeffs(const double* __restrict__ X, const double* __restrict__ V,
+                                    const double* __restrict__ evals, int K, int l, int k, T* __restrict__ M,
+                                    double* __restrict__ sigma, int* status) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * k; e += gridDim.x * blockDim.x) {
+    const int c = e / k, j = e % k;
+    double s = 0.0;
+    for (int q = 0; q < l; ++q) s += X[(int64_t)q * K + c] * V[(int64_t)j * l + q];
+    M[e] = (T)s;
+  }
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+      const double lj = j < l ? evals[j] : 0.0;
+      sigma[j] = lj > 0.0 ? sqrt(lj) : 0.0;
+      if (j < k && !(lj > 0.0)) atomicExch(status, (int)NLSP_ERR_NOT_SPD);
+    }
+}
+
 __global__ void k_symmetrize(double* __restrict__ M, int m) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
     const int i = e % m, j = e / m;
@@ -976,6 +1017,103 @@ nlsp_status basis_from_samples(nlsp_ctx* ctx, nlsp_prec* M, const T* S, bool a_w
   return NLSP_OK;
 }
 
+// C = op(A) op(B) (FP64, column-major, see k_gemm_small).
+nlsp_status gemm64(nlsp_ctx* ctx, int ta, int tb, int m, int n, int kk, const double* A, int lda, const double* B,
+                   int ldb, double* C, int ldc) {
+  if (kk > 256) return NLSP_ERR_INVALID;
+  k_gemm_small<<<n, 128, 0, ctx->stream>>>(A, lda, ta, B, ldb, tb, C, ldc, m, n, kk);
+  NLSP_LAUNCH_CHECK();
+  count_launches(ctx, 1);
+  return NLSP_OK;
+}
+
+// X (K x l) <- X L^-T where L L^T = X^T W X (W = G, or the identity when G is
+// null): the columns of X become orthonormal in the metric W.  work: 5 l^2 +
+// K l doubles.  A rank-deficient X gives NLSP_ERR_NOT_SPD in M->status.
+nlsp_status orthonormalize_small(nlsp_ctx* ctx, nlsp_prec* M, const double* G, int K, int l, double* X,
+                                 double* work) {
+  cudaStream_t s = ctx->stream;
+  double* WX = work;                 // K x l
+  double* H = WX + (size_t)K * l;    // l x l
+  double* Lf = H + (size_t)l * l;
+  double* Hinv = Lf + (size_t)l * l;
+  double* Lit = Hinv + (size_t)l * l;
+  double* Xn = Lit + (size_t)l * l;  // l x l scratch is enough for nothing else: X L^-T goes to WX
+  (void)Xn;
+  const double* WXp = X;
+  if (G) {
+    NLSP_TRY(gemm64(ctx, 0, 0, K, l, K, G, K, X, K, WX, K));
+    WXp = WX;
+  }
+  NLSP_TRY(gemm64(ctx, 1, 0, l, l, K, X, K, WXp, K, H, l));
+  k_symmetrize<<<div_up((int64_t)l * l, 256), 256, 0, s>>>(H, l);
+  NLSP_TRY(set_smem((const void*)k_cholesky, sizeof(double) * l * l));
+  k_cholesky<<<1, 256, sizeof(double) * l * l, s>>>(H, l, Lf, M->status);
+  NLSP_TRY(set_smem((const void*)k_spd_inverse_cols, spd_inverse_smem(l)));
+  k_spd_inverse_cols<<<l, 32, spd_inverse_smem(l), s>>>(Lf, l, Hinv);
+  NLSP_LAUNCH_CHECK();
+  count_launches(ctx, 3);
+  NLSP_TRY(gemm64(ctx, 0, 0, l, l, l, Hinv, l, Lf, l, Lit, l));  // (L L^T)^-1 L = L^-T
+  NLSP_TRY(gemm64(ctx, 0, 0, K, l, l, X, K, Lit, l, WX, K));
+  NLSP_CUDA(cudaMemcpyAsync(X, WX, sizeof(double) * K * l, cudaMemcpyDeviceToDevice, s));
+  return NLSP_OK;
+}
+
+// Randomised-SVD basis (Halko, Martinsson, Tropp, "Finding structure with
+// randomness", SIAM Review 2011: the randomised range finder with power
+// iterations, their Algorithm 4.4, then the SVD of the small projected
+// matrix, their Algorithm 5.1) of the tiled smoothed samples S (n x K), with
+// l = k + oversample columns of the Gaussian sketch Omega (K x l, FP64
+// column-major) and q power iterations.  Every n-sized iterate lies in the
+// column space of S, Y = S X with X K x l, so the algorithm runs in the
+// K-dimensional coefficient space through the Gram matrix G = S^T S (one
+// tall-skinny product, the n-proportional cost):
+//   Q = S X is orthonormal      <=>  X^T G X = I  (X <- X L^-T)
+//   S^T Q = G X                       (power step; orthonormalised as W)
+//   Q <- S W, re-orthonormalised      (X <- W, X^T G X = I)
+//   B = Q^T S = X^T G, B B^T = (G X)^T (G X), eigenvectors U_B (l x l)
+//   P = Q U_B[:, :k] = S (X U_B[:, :k])  (one tile product)
+// The singular values reported are those of B (the first l).
+template <typename T>
+nlsp_status randomized_from_samples(nlsp_ctx* ctx, nlsp_prec* M, const T* S, int l, int power_iters,
+                                    const double* sketch) {
+  cudaStream_t s = ctx->stream;
+  const int K = M->K, k = M->k;
+  const size_t nsmall = (size_t)K * K + 2 * (size_t)K * l + (size_t)l * l * 2 + l + (6 * (size_t)l * l + l) +
+                        (5 * (size_t)l * l + (size_t)K * l) + (size_t)K * k + 16;
+  double* G = slot_as<double>(ctx, SLOT_SMALL, nsmall);
+  if (!G) return NLSP_ERR_OOM;
+  double* X = G + (size_t)K * K;                // K x l
+  double* Z = X + (size_t)K * l;                // K x l
+  double* BB = Z + (size_t)K * l;               // l x l
+  double* V = BB + (size_t)l * l;               // l x l
+  double* evals = V + (size_t)l * l;            // l
+  double* ework = evals + l;                    // eigen refinement work
+  double* owork = ework + 6 * (size_t)l * l + l;  // orthonormalisation work
+  T* Mc = reinterpret_cast<T*>(owork + 5 * (size_t)l * l + (size_t)K * l);
+  NLSP_TRY((tsgemm<T, false>(ctx, M->A, S, K, K, M->n_pad, G, 1)));
+  NLSP_CUDA(cudaMemcpyAsync(X, sketch, sizeof(double) * K * l, cudaMemcpyDeviceToDevice, s));
+  NLSP_TRY(orthonormalize_small(ctx, M, G, K, l, X, owork));  // Q = qr(S Omega)
+  for (int it = 0; it < power_iters; ++it) {
+    NLSP_TRY(gemm64(ctx, 0, 0, K, l, K, G, K, X, K, Z, K));    // S^T Q
+    NLSP_TRY(orthonormalize_small(ctx, M, nullptr, K, l, Z, owork));  // W = qr(S^T Q)
+    NLSP_CUDA(cudaMemcpyAsync(X, Z, sizeof(double) * K * l, cudaMemcpyDeviceToDevice, s));
+    NLSP_TRY(orthonormalize_small(ctx, M, G, K, l, X, owork));  // Q = qr(S W)
+  }
+  NLSP_TRY(gemm64(ctx, 0, 0, K, l, K, G, K, X, K, Z, K));      // B^T = G X
+  NLSP_TRY(gemm64(ctx, 1, 0, l, l, K, Z, K, Z, K, BB, l));      // B B^T
+  k_symmetrize<<<div_up((int64_t)l * l, 256), 256, 0, s>>>(BB, l);
+  NLSP_LAUNCH_CHECK();
+  count_launches(ctx, 1);
+  const int refine = M->precision == NLSP_FP64 ? 2 : 0;
+  NLSP_TRY(gram_eigen(ctx, BB, l, refine, evals, V, ework));
+  k_randomized_coeffs<T><<<div_up((int64_t)K * k, 256), 256, 0, s>>>(X, V, evals, K, l, k, Mc, M->sigma, M->status);
+  NLSP_LAUNCH_CHECK();
+  count_launches(ctx, 1);
+  NLSP_TRY(tile_times_small<T>(ctx, S, K, Mc, k, M->n_pad, (T*)M->P));
+  return NLSP_OK;
+}
+
 // Transposes the column-major k x k FP64 matrix W into row-major T.
 template <typename T>
 __global__ void k_transpose_to(const double* __restrict__ W, int k, T* __restrict__ out) {
@@ -1015,9 +1153,20 @@ nlsp_status cholesky_qr(nlsp_ctx* ctx, nlsp_prec* M) {
   return NLSP_OK;
 }
 
+// How the basis is taken from the smoothed samples: the exact thin SVD, the
+// A-weighted spectral basis, or the randomised SVD (sketch columns l = k +
+// oversample, q power iterations, the sketch Omega on the device or drawn).
+struct BasisChoice {
+  int mode;  // 0 exact, 1 A-weighted, 2 randomised
+  int oversample, power_iters;
+  const double* sketch;
+  unsigned long long seed;
+};
+
 template <typename T>
 nlsp_status build_impl(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* p, const double* S0,
-                       nlsp_prec** out, bool a_weighted) {
+                       nlsp_prec** out, BasisChoice bc) {
+  const bool a_weighted = bc.mode == 1;
   nlsp_prec* M = new_prec(ctx, A, p, p->k, p->K);
   nlsp_status st = alloc_prec_storage(M);
   auto fail = [&](nlsp_status e) {
@@ -1039,7 +1188,22 @@ nlsp_status build_impl(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params*
   count_launches(ctx, 1);
   T* S = nullptr;
   if ((st = smooth_tiled<T>(ctx, A, K, p->s1, p->omega, M->n_pad, sa, sb, &S)) != NLSP_OK) return fail(st);
-  if ((st = basis_from_samples<T>(ctx, M, S, a_weighted)) != NLSP_OK) return fail(st);
+  if (bc.mode == 2) {
+    const int l = p->k + bc.oversample;
+    const double* sketch = bc.sketch;
+    if (!sketch) {  // Omega (K x l) from the counter-based generator: element (c, j) is normal j K + c
+      double* d = slot_as<double>(ctx, SLOT_PNEW, (size_t)K * l);
+      if (!d) return fail(NLSP_ERR_OOM);
+      k_random_normal<<<grid_for(ctx, (int64_t)K * l, 256, 8), 256, 0, s>>>(
+          splitmix_stream_base(bc.seed, NLSP_STREAM_SKETCH), 0, (int64_t)K * l, d);
+      if (cudaGetLastError() != cudaSuccess) return fail(NLSP_ERR_CUDA);
+      count_launches(ctx, 1);
+      sketch = d;
+    }
+    if ((st = randomized_from_samples<T>(ctx, M, S, l, bc.power_iters, sketch)) != NLSP_OK) return fail(st);
+  } else if ((st = basis_from_samples<T>(ctx, M, S, a_weighted)) != NLSP_OK) {
+    return fail(st);
+  }
   if (p->precision == NLSP_FP64 && !a_weighted)  // the A-weighted basis is A-orthonormal already
     if ((st = cholesky_qr<T>(ctx, M)) != NLSP_OK) return fail(st);
   if ((st = nlsp_internal_factor(ctx, M, M->k)) != NLSP_OK) return fail(st);
@@ -1145,8 +1309,9 @@ extern "C" nlsp_status nlsp_build_prolongation(nlsp_ctx* ctx, const nlsp_op* A, 
   *M_out = nullptr;
   NLSP_TRY(check_setup_params(A, params, true));
   NLSP_CUDA(cudaSetDevice(ctx->device));
-  if (params->precision == NLSP_FP64) return build_impl<double>(ctx, A, params, dev_S0, M_out, false);
-  return build_impl<float>(ctx, A, params, dev_S0, M_out, false);
+  const BasisChoice bc{0, 0, 0, nullptr, 0};
+  if (params->precision == NLSP_FP64) return build_impl<double>(ctx, A, params, dev_S0, M_out, bc);
+  return build_impl<float>(ctx, A, params, dev_S0, M_out, bc);
 }
 
 extern "C" nlsp_status nlsp_build_prolongation_a_weighted(nlsp_ctx* ctx, const nlsp_op* A,
@@ -1156,8 +1321,27 @@ extern "C" nlsp_status nlsp_build_prolongation_a_weighted(nlsp_ctx* ctx, const n
   *M_out = nullptr;
   NLSP_TRY(check_setup_params(A, params, true));
   NLSP_CUDA(cudaSetDevice(ctx->device));
-  if (params->precision == NLSP_FP64) return build_impl<double>(ctx, A, params, dev_S0, M_out, true);
-  return build_impl<float>(ctx, A, params, dev_S0, M_out, true);
+  const BasisChoice bc{1, 0, 0, nullptr, 0};
+  if (params->precision == NLSP_FP64) return build_impl<double>(ctx, A, params, dev_S0, M_out, bc);
+  return build_impl<float>(ctx, A, params, dev_S0, M_out, bc);
+}
+
+extern "C" nlsp_status nlsp_build_prolongation_randomized(nlsp_ctx* ctx, const nlsp_op* A,
+                                                          const nlsp_setup_params* params, const double* dev_S0,
+                                                          int oversample, int power_iters, const double* dev_sketch,
+                                                          nlsp_prec** M_out) {
+  if (!ctx || !M_out) return NLSP_ERR_INVALID;
+  *M_out = nullptr;
+  NLSP_TRY(check_setup_params(A, params, true));
+  if (oversample < 0 || params->k + oversample > params->K || power_iters < 0 || power_iters > 16) {
+    nlsp_record_message("nlsp_build_prolongation_randomized: need 0 <= oversample, k + oversample <= K, "
+                        "0 <= power_iters <= 16");
+    return NLSP_ERR_INVALID;
+  }
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  const BasisChoice bc{2, oversample, power_iters, dev_sketch, params->seed};
+  if (params->precision == NLSP_FP64) return build_impl<double>(ctx, A, params, dev_S0, M_out, bc);
+  return build_impl<float>(ctx, A, params, dev_S0, M_out, bc);
 }
 
 extern "C" nlsp_status nlsp_prec_from_basis(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_setup_params* params,

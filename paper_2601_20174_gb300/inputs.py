@@ -42,6 +42,7 @@ STREAM_THETA = 4
 STREAM_SIZES = 5
 STREAM_NOISE = 6
 STREAM_DIRECTION = 7
+STREAM_SKETCH = 11  # Gaussian sketch of the randomised SVD (same number as the library's)
 
 
 def _fin(z: np.ndarray) -> np.ndarray:
@@ -127,6 +128,11 @@ def rotated_aniso_tensor(theta: float, eps: float) -> np.ndarray:
 def rhs_uniform(n: int, m: int, seed: int) -> np.ndarray:
     """Right-hand sides f ~ U[-1, 1], column-major n x m (m columns)."""
     return uniform(seed, STREAM_RHS, n * m, -1.0, 1.0).reshape(m, n).T.copy()
+
+
+def sketch_normal(K: int, l: int, seed: int) -> np.ndarray:
+    """Gaussian sketch Omega ~ N(0, 1), K x l (column j = draws j*K ..)."""
+    return normal(seed, STREAM_SKETCH, K * l).reshape(l, K).T.copy()
 
 
 def samples_normal(n: int, K: int, seed: int) -> np.ndarray:

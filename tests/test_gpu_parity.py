@@ -114,6 +114,58 @@ def test_a_weighted_setup_matches_oracle_and_solves(ctx, name, precision):
         assert abs(res[0].iterations - o["iters"]) <= 1
 
 
+@pytest.mark.parametrize("name", ["grf5", "aniso9", "iid7"])
+@pytest.mark.parametrize("oversample,power_iters", [(0, 0), (6, 1), (8, 2)])
+def test_randomized_setup_matches_oracle(ctx, name, oversample, power_iters):
+    # the randomised SVD basis (Halko, Martinsson, Tropp: range finder with
+    # power iterations, SVD of the projected matrix) given the same sketch
+    p = PROBLEMS[name]()
+    A = op.assemble(p)
+    S = osetup.smooth_samples(A, p.S0, p.omega, p.s1)
+    l = p.k + oversample
+    sk = gen.sketch_normal(p.K, l, seed=5)
+    P_ref, sB = osetup.prolongation_randomized(S, p.k, oversample, power_iters, sk, return_sigma=True)
+    Aop = _api().Operator.from_problem(ctx, p)
+    gap = (sB[p.k - 1] ** 2 - (sB[p.k] ** 2 if l > p.k else 0.0)) / sB[0] ** 2
+    for precision in (FP64, MIXED):
+        M = _api().Preconditioner.build_randomized(Aop, to_dev(p.S0), p.k, oversample, power_iters, to_dev(sk),
+                                                   p.s1, p.nu, p.omega, precision)
+        P, sig = to_np(M.basis()), to_np(M.sigma())
+        fp64 = precision == FP64
+        assert rel(sig[:l], sB) <= (1e-9 if fp64 else 1e-4), (sig[:l], sB)
+        assert np.all(sig[l:] == 0.0)
+        Q = np.linalg.qr(P)[0]
+        assert projector_dist(Q, P_ref) <= (max(1e-8, 1e-12 / gap) if fp64 else max(2e-3, 1e-6 / gap))
+        if fp64:
+            assert np.max(np.abs(P.T @ P - np.eye(p.k))) <= 1e-12
+    # a sketch drawn on the device is the counter-based stream the host draws
+    Md = _api().Preconditioner.build_randomized(Aop, to_dev(p.S0), p.k, oversample, power_iters, None, p.s1, p.nu,
+                                                p.omega, FP64, seed=5)
+    assert projector_dist(to_np(Md.basis()), P_ref) <= max(1e-8, 1e-12 / gap)
+
+
+def test_randomized_setup_solves_and_rejects_bad_arguments(ctx):
+    p = PROBLEMS["grf5"]()
+    A = op.assemble(p)
+    S = osetup.smooth_samples(A, p.S0, p.omega, p.s1)
+    sk = gen.sketch_normal(p.K, p.k + 8, seed=2)
+    P_ref = osetup.prolongation_randomized(S, p.k, 8, 2, sk)
+    L_ref = osetup.coarse_factor(osetup.galerkin(A, P_ref))
+    b = p.f[:, 0]
+    o = opcg.pcg(A, opcg.two_level_solver(A, P_ref, L_ref, p.omega, p.nu, p.nu), b, 1e-8)
+    Aop = _api().Operator.from_problem(ctx, p)
+    for precision in (FP64, MIXED):
+        M = _api().Preconditioner.build_randomized(Aop, to_dev(p.S0), p.k, 8, 2, to_dev(sk), p.s1, p.nu, p.omega,
+                                                   precision)
+        x, res = M.solve(to_dev(b), tol=1e-8, graph_mode=2)
+        true = np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b)
+        assert res[0].status == 0 and true <= 1e-8 * 1.01
+        assert abs(res[0].iterations - o["iters"]) <= (1 if precision == FP64 else 2)
+    with pytest.raises(_api().L.NlspError):  # k + oversample > K
+        _api().Preconditioner.build_randomized(Aop, to_dev(p.S0), p.k, p.K - p.k + 1, 1, None, p.s1, p.nu, p.omega,
+                                               FP64)
+
+
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_setup_fp64_subspace_sigma_and_galerkin(ctx, name):
     p = PROBLEMS[name]()
