@@ -504,6 +504,21 @@ def run_block(ctx, dev, timed):
            "single_column_solver": {"columns_timed": cols, "ms": ms1[0], "value": cols / (ms1[0] / 1e3),
                                     "unit": "solves/s", "iterations": [r.iterations for r in res1]}}
     M.close()
+    # the same block with BF16 / TF32 tensor-core restriction and
+    # prolongation (FP32 accumulation), same device-drawn samples
+    out["reduced_precision"] = {}
+    for name, prec in (("bf16", L.NLSP_MIXED_BF16), ("tf32", L.NLSP_MIXED_TF32)):
+        Ml = api.Preconditioner.build(A, None, BLOCK["k"], BLOCK["s1"], BLOCK["nu"], BLOCK["omega"], prec,
+                                      K=BLOCK["K"], seed=p.seed)
+        Ml.solve_block(F, tol=BLOCK["tol"], maxit=16)  # warm (repacking, graph build)
+        msl, (_, resl) = timed(lambda: Ml.solve_block(F, tol=BLOCK["tol"], maxit=20000), 1)
+        itl = [r.iterations for r in resl]
+        out["reduced_precision"][name] = {
+            "ms": msl[0], "value": BLOCK["m"] / (msl[0] / 1e3), "unit": "solves/s",
+            "iterations": {"min": min(itl), "max": max(itl)}, "ms_per_iteration": msl[0] / max(itl),
+            "all_converged": all(r.status == 0 for r in resl),
+            "max_true_relres": max(r.true_relres for r in resl)}
+        Ml.close()
     A.close()
     return out
 

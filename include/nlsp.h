@@ -74,8 +74,14 @@ typedef enum {
 /* Arithmetic of the preconditioner (outer PCG recurrences are always FP64). */
 typedef enum {
   NLSP_FP64 = 0,        /* everything FP64                                   */
-  NLSP_MIXED_FP32 = 1   /* setup and preconditioner FP32 (FP64 reductions),
+  NLSP_MIXED_FP32 = 1,  /* setup and preconditioner FP32 (FP64 reductions),
                            A_c Cholesky and the PCG recurrences FP64         */
+  NLSP_MIXED_BF16 = 2,  /* as NLSP_MIXED_FP32, and in the block solver
+                           (nlsp_solve_block) the restriction P_r^T rho and
+                           the prolongation P_r E run on tensor cores with
+                           BF16 operands (P and rho / E rounded to nearest)
+                           and FP32 accumulation                             */
+  NLSP_MIXED_TF32 = 3   /* the same with TF32 operands                       */
 } nlsp_precision;
 
 /* Coefficient layouts for nlsp_assemble_stencil. */
@@ -359,7 +365,12 @@ NLSP_API nlsp_status nlsp_solve(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec
    restriction is the dense product P_r^T rho (r x m) and the prolongation
    P_r E (n x m).  Same arguments, stopping rule and per-column results as
    nlsp_solve (params->graph_mode is ignored); x0 = 0.  Uses the active rank
-   r <= 128 of M.  Allocates its block workspace (about 80 m n bytes) for the
+   r <= 128 of M.  The two products run on tcgen05 tensor cores: with FP32
+   inputs split into TF32 high and low parts (three products, FP32 accuracy)
+   for NLSP_MIXED_FP32 (restriction only; the prolongation on CUDA cores),
+   with BF16 or TF32 operands and FP32 accumulation (both products, from a
+   copy of P repacked once per call) for NLSP_MIXED_BF16 / NLSP_MIXED_TF32;
+   FP64 preconditioners use CUDA cores.  Allocates its block workspace (about 80 m n bytes) for the
    duration of the call.  Synchronises.  Errors: NLSP_ERR_INVALID,
    NLSP_ERR_CUDA, NLSP_ERR_OOM; per-column NLSP_NOT_CONVERGED /
    NLSP_ERR_BREAKDOWN as nlsp_solve. */

@@ -23,6 +23,8 @@ NLSP_ERR_OOM = -6
 
 NLSP_FP64 = 0
 NLSP_MIXED_FP32 = 1
+NLSP_MIXED_BF16 = 2
+NLSP_MIXED_TF32 = 3
 
 NLSP_COEF_CELL_KAPPA = 0
 NLSP_COEF_CONST_TENSOR = 1

@@ -22,6 +22,7 @@
 #include "kernels.cuh"
 #include "stencil.cuh"
 #include "tma.cuh"
+#include "block_lp.cuh"
 
 namespace {
 
@@ -669,6 +670,269 @@ __global__ void __launch_bounds__(BT, 2) k_b_prolong_tc(const float* __restrict_
   if (tid == 0 && bad) atomicExch(&st->err, 1);
 }
 
+// ---- reduced-precision restriction and prolongation (block_lp.cuh) -------
+constexpr int LP_NS = 4;  // stages of the operand ring
+
+// Restriction with TF32 / BF16 operands: per block, over its tiles' 64-node
+// chunks, D[j][c] += sum_node R[j][node] rho[node][c] in TMEM, with R the
+// repacked chunk of P (bulk-copied into a ring of LP_NS stages) and rho =
+// rT - A z computed by the threads into one of two B buffers.  Thread 0
+// issues the MMAs of a chunk once its copy has landed and commits them to the
+// stage's and the B buffer's "free" barriers; it refills the stage of the
+// previous chunk when that chunk's MMAs are done.  The block's r x 32 result
+// goes to cpart (FP32).
+template <int KIND, int OP>
+__global__ void __launch_bounds__(BT) k_b_restrict_lp(StencilView<float> A, const float* __restrict__ rT,
+                                                      const float* __restrict__ z,
+                                                      const unsigned char* __restrict__ Rc, int k, int64_t ntiles,
+                                                      float* __restrict__ cpart, BlockState* st) {
+  using Sx = typename lp::Op<OP>::S;
+  constexpr int ES = lp::Op<OP>::ES;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int rr = lp::rows_r(k);
+  const unsigned a_bytes = 128u * lp::RCH * ES;           // one A stage (128 rows)
+  const unsigned chunk_bytes = (unsigned)rr * lp::RCH * ES;  // rows that the copy fills
+  const unsigned b_bytes = (unsigned)lp::MBC * lp::RCH * ES;
+  unsigned char* sa = smem_raw;                               // LP_NS stages
+  unsigned char* sb = smem_raw + (size_t)LP_NS * a_bytes;     // 2 B buffers
+  __shared__ __align__(8) uint64_t full[LP_NS], afree[LP_NS], bfree[2];
+  __shared__ unsigned tbase_s;
+  __shared__ int bad, nmma;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int nchunk = (int)(my_tiles * 2);
+  auto chunk_src = [&](int c) {  // chunk c of this block: tile blockIdx.x + (c / 2) gridDim.x, half c % 2
+    const int64_t t = blockIdx.x + (int64_t)(c >> 1) * gridDim.x;
+    return Rc + (size_t)(t * 2 + (c & 1)) * chunk_bytes;
+  };
+  if (tid == 0) {
+    for (int q = 0; q < LP_NS; ++q) {
+      tma::mbar_init(&full[q], 1);
+      tma::mbar_init(&afree[q], 1);
+    }
+    tma::mbar_init(&bfree[0], 1);
+    tma::mbar_init(&bfree[1], 1);
+    tma::fence_barrier_init();
+    bad = 0;
+    nmma = 0;
+  }
+  // rows rr .. 127 of every stage stay zero (the copies fill rows < rr)
+  for (unsigned e = tid; e < (unsigned)LP_NS * (a_bytes - chunk_bytes) / 16; e += BT) {
+    const unsigned per = (a_bytes - chunk_bytes) / 16;
+    *reinterpret_cast<uint4*>(sa + (size_t)(e / per) * a_bytes + chunk_bytes + (size_t)(e % per) * 16) =
+        make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (warp == 0) tmem::alloc(&tbase_s, 32);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  const unsigned td = tbase_s;
+  if (tid == 0)
+    for (int c = 0; c < LP_NS && c < nchunk; ++c) {
+      tma::mbar_arrive_expect_tx(&full[c], chunk_bytes);
+      tma::bulk_g2s(sa + (size_t)c * a_bytes, chunk_src(c), chunk_bytes, &full[c]);
+    }
+  const unsigned a_sbo = (lp::RCH / lp::Op<OP>::EPC) * 128, b_sbo = a_sbo;
+  const int ksteps = lp::RCH / lp::Op<OP>::KSTEP;
+  int q = 0;
+  for (; q < nchunk; ++q) {
+    const int b = q & 1;
+    if (q >= 2 && !tma::mbar_wait(&bfree[b], (unsigned)(((q - 2) >> 1) & 1))) bad = 1;
+    __syncthreads();
+    if (bad) break;
+    // rho of the chunk's 64 nodes -> B buffer b (8 threads per node, four columns each)
+    const int64_t t = blockIdx.x + (int64_t)(q >> 1) * gridDim.x;
+    unsigned char* bb = sb + (size_t)b * b_bytes;
+    for (int wn = tid >> 3; wn < lp::RCH; wn += BT / 8) {
+      const int qd = tid & 7;
+      const int64_t i = t * NLSP_TILE + (q & 1) * lp::RCH + wn;
+      V4<float> rho;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rho.v[j] = 0.0f;
+      if (i < A.n) {
+        const V4<float> az = stencil_apply4<KIND>(A, i, node_coord<KIND>(i, A.N),
+                                                  [&](int64_t m) { return ld4(z + m * MB + 4 * qd); });
+        const V4<float> r0 = ld4(rT + i * MB + 4 * qd);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) rho.v[j] = r0.v[j] - az.v[j];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) *reinterpret_cast<Sx*>(bb + lp::off<OP>(4 * qd + j, wn, lp::RCH)) = lp::Op<OP>::cvt(rho.v[j]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      const int s = q % LP_NS;
+      if (!tma::mbar_wait(&full[s], (unsigned)((q / LP_NS) & 1))) {
+        bad = 1;
+      } else {
+        tmem::fence_after_sync();
+        lp::mma_run<OP>(td, tma::smem_addr(sa + (size_t)s * a_bytes), a_sbo, tma::smem_addr(bb), b_sbo, ksteps, q > 0);
+        lp::commit(&afree[s]);
+        lp::commit(&bfree[b]);
+        nmma = q + 1;
+        // refill the stage of the previous chunk once its MMAs are done
+        const int pc = q - 1;
+        if (pc >= 0 && pc + LP_NS < nchunk) {
+          const int ps = pc % LP_NS;
+          if (!tma::mbar_wait(&afree[ps], (unsigned)((pc / LP_NS) & 1))) {
+            bad = 1;
+          } else {
+            tma::mbar_arrive_expect_tx(&full[ps], chunk_bytes);
+            tma::bulk_g2s(sa + (size_t)ps * a_bytes, chunk_src(pc + LP_NS), chunk_bytes, &full[ps]);
+          }
+        }
+      }
+    }
+  }
+  // every MMA issued so far is complete once the last one's commit arrived
+  // (a commit tracks all earlier MMAs of the thread); copies still in
+  // flight after a failure are drained (bounded) before leaving
+  __syncthreads();
+  const int issued = nmma;  // chunks whose MMAs were issued (all of them unless a wait gave up)
+  if (issued > 0 && !tma::mbar_wait(&bfree[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1))) bad = 1;
+  __syncthreads();
+  if (tid == 0 && bad) {
+    // copies were issued for chunks below max(LP_NS, issued + LP_NS - 1) and
+    // consumed below `issued`: wait (bounded) for the rest to land
+    const int hi = min(nchunk, max(LP_NS, issued + LP_NS - 1));
+    for (int c = issued; c < hi; ++c) tma::mbar_wait(&full[c % LP_NS], (unsigned)((c / LP_NS) & 1));
+    atomicExch(&st->err, 1);
+  }
+  tmem::fence_after_sync();
+  if (!bad && issued > 0) {
+    float v[16];
+    tc::ld16(td + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(16 * (warp >> 2)), v);
+    const int j = 32 * (warp & 3) + lane;
+    if (j < k) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) cpart[((int64_t)blockIdx.x * k + j) * MB + 16 * (warp >> 2) + c] = v[c];
+    }
+  } else {
+    for (int e = tid; e < k * MB; e += BT) cpart[(int64_t)blockIdx.x * k * MB + e] = 0.0f;
+  }
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  if (warp == 0) tmem::dealloc(td, 32);
+}
+
+// Prolongation with TF32 / BF16 operands: per tile, D = Q_t E (128 nodes x
+// 32 columns) with Q_t the repacked tile of P (bulk-copied into a ring of
+// LP_NS stages) and B = E^T (32 x r, converted once per block), then
+// z += D.  Two TMEM accumulators alternate, so thread 0 issues the MMAs of
+// tile i + 1 before the block adds tile i's result to z.
+template <int OP>
+__global__ void __launch_bounds__(BT) k_b_prolong_lp(const unsigned char* __restrict__ Qc, int k, int64_t n,
+                                                     const float* __restrict__ E, float* __restrict__ z,
+                                                     int ns, BlockState* st) {
+  using Sx = typename lp::Op<OP>::S;
+  constexpr int ES = lp::Op<OP>::ES;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int kq = lp::kcols_q(k);
+  const unsigned tile_bytes = (unsigned)NLSP_TILE * kq * ES;
+  unsigned char* sa = smem_raw;                             // ns <= LP_NS stages
+  unsigned char* sbm = smem_raw + (size_t)ns * tile_bytes;   // E^T: 32 x kq
+  __shared__ __align__(8) uint64_t full[LP_NS], afree[LP_NS], dfull[2];
+  __shared__ unsigned tbase_s;
+  __shared__ int bad, nmma;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (n + NLSP_TILE - 1) / NLSP_TILE;
+  const int nt = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  auto tile_src = [&](int i) { return Qc + (size_t)(blockIdx.x + (int64_t)i * gridDim.x) * tile_bytes; };
+  if (tid == 0) {
+    for (int q = 0; q < LP_NS; ++q) {
+      tma::mbar_init(&full[q], 1);
+      tma::mbar_init(&afree[q], 1);
+    }
+    tma::mbar_init(&dfull[0], 1);
+    tma::mbar_init(&dfull[1], 1);
+    tma::fence_barrier_init();
+    bad = 0;
+    nmma = 0;
+  }
+  for (int e = tid; e < lp::MBC * kq; e += BT) {  // B = E^T, zero beyond k
+    const int c = e % lp::MBC, j = e / lp::MBC;
+    *reinterpret_cast<Sx*>(sbm + lp::off<OP>(c, j, kq)) = lp::Op<OP>::cvt(j < k ? E[j * MB + c] : 0.0f);
+  }
+  if (warp == 0) tmem::alloc(&tbase_s, 64);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  const unsigned td = tbase_s;
+  const unsigned a_sbo = (unsigned)(kq / lp::Op<OP>::EPC) * 128, b_sbo = a_sbo;
+  const int ksteps = kq / lp::Op<OP>::KSTEP;
+  // thread 0: MMAs of tile i into accumulator i % 2 once its copy landed,
+  // then the refill of the stage of tile i - 1 (whose MMAs are done)
+  auto issue = [&](int i) {
+    const int s = i % ns;
+    if (!tma::mbar_wait(&full[s], (unsigned)((i / ns) & 1))) {
+      bad = 1;
+      return;
+    }
+    tmem::fence_after_sync();
+    lp::mma_run<OP>(td + (unsigned)(32 * (i & 1)), tma::smem_addr(sa + (size_t)s * tile_bytes), a_sbo,
+                    tma::smem_addr(sbm), b_sbo, ksteps, false);
+    lp::commit(&afree[s]);
+    lp::commit(&dfull[i & 1]);
+    nmma = i + 1;
+    const int pi = i - 1;
+    if (pi >= 0 && pi + ns < nt) {
+      const int ps = pi % ns;
+      if (!tma::mbar_wait(&afree[ps], (unsigned)((pi / ns) & 1))) {
+        bad = 1;
+        return;
+      }
+      tma::mbar_arrive_expect_tx(&full[ps], tile_bytes);
+      tma::bulk_g2s(sa + (size_t)ps * tile_bytes, tile_src(pi + ns), tile_bytes, &full[ps]);
+    }
+  };
+  if (tid == 0) {
+    for (int i = 0; i < ns && i < nt; ++i) {
+      tma::mbar_arrive_expect_tx(&full[i], tile_bytes);
+      tma::bulk_g2s(sa + (size_t)i * tile_bytes, tile_src(i), tile_bytes, &full[i]);
+    }
+    if (nt > 0) issue(0);
+  }
+  for (int i = 0; i < nt; ++i) {
+    __syncthreads();  // accumulator (i + 1) % 2 was drained by the previous iteration
+    if (tid == 0 && !bad && i + 1 < nt) issue(i + 1);
+    if (!tma::mbar_wait(&dfull[i & 1], (unsigned)((i >> 1) & 1))) bad = 1;
+    __syncthreads();
+    if (bad) break;
+    tmem::fence_after_sync();
+    float v[16];
+    tc::ld16(td + (unsigned)(32 * (i & 1)) + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(16 * (warp >> 2)), v);
+    const int64_t node = (blockIdx.x + (int64_t)i * gridDim.x) * NLSP_TILE + 32 * (warp & 3) + lane;
+    if (node < n) {
+      float* zr = z + node * MB + 16 * (warp >> 2);
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        V4<float> zv = ld4(zr + 4 * c4);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) zv.v[c] += v[4 * c4 + c];
+        st4(zr + 4 * c4, zv);
+      }
+    }
+    tmem::fence_before_sync();
+  }
+  __syncthreads();
+  if (tid == 0 && bad) {
+    // drain: the last issued MMAs, then the copies issued beyond them
+    const int issued = nmma;
+    if (issued > 0) tma::mbar_wait(&afree[(issued - 1) % ns], (unsigned)(((issued - 1) / ns) & 1));
+    const int hi = min(nt, max(ns, issued + ns - 1));
+    for (int c = issued; c < hi; ++c) tma::mbar_wait(&full[c % ns], (unsigned)((c / ns) & 1));
+    atomicExch(&st->err, 1);
+  }
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  if (warp == 0) tmem::dealloc(td, 64);
+}
+
 // Last post-sweep: z = zin + w D^-1 (rT - A zin) stored in FP64, with the
 // per-column partials of r^T z and r^T z_old (flexible beta).
 template <int KIND, typename T>
@@ -861,9 +1125,17 @@ struct BlockSolver {
     const int flexible = prm->flexible < 0 ? (M->precision != NLSP_FP64) : (prm->flexible != 0);
     // workspace
     const size_t nv = (size_t)n * MB;
+    // reduced-precision tensor-core contractions (NLSP_MIXED_TF32 / _BF16):
+    // repacked operand copies of P, sized for the active rank
+    const int lp_op = M->precision == NLSP_MIXED_BF16 ? lp::OP_BF16 : lp::OP_TF32;
+    const bool use_lp = sizeof(T) == 4 && (M->precision == NLSP_MIXED_BF16 || M->precision == NLSP_MIXED_TF32);
+    const int lp_es = lp_op == lp::OP_BF16 ? 2 : 4;
+    const size_t lp_rchunk = (size_t)lp::rows_r(k) * lp::RCH * lp_es;
+    const size_t lp_qtile = (size_t)NLSP_TILE * lp::kcols_q(k) * lp_es;
+    const size_t lp_bytes = use_lp ? (size_t)ntiles * (2 * lp_rchunk + lp_qtile) + 512 : 0;
     const size_t bytes = sizeof(double) * nv * 6 + sizeof(T) * nv * 4 + sizeof(double) * (size_t)2 * nb * MB +
                          sizeof(T) * (size_t)nbr * k * MB + (sizeof(T) + sizeof(double)) * (size_t)k * MB +
-                         sizeof(BlockState) + 8192;
+                         sizeof(BlockState) + 8192 + lp_bytes;
     DevBuf buf;
     NLSP_TRY(buf.alloc(bytes));
     unsigned char* base = buf.as<unsigned char>();
@@ -887,6 +1159,8 @@ struct BlockSolver {
     double* part = (double*)take(sizeof(double) * (size_t)2 * nb * MB);
     T* cpart = (T*)take(sizeof(T) * (size_t)nbr * k * MB);
     BlockState* st = (BlockState*)take(sizeof(BlockState));
+    unsigned char* lp_R = use_lp ? take((size_t)ntiles * 2 * lp_rchunk) : nullptr;
+    unsigned char* lp_Q = use_lp ? take((size_t)ntiles * lp_qtile) : nullptr;
     (void)zb;
     // restriction / prolongation shared memory
     const size_t sm_r = sizeof(T) * ((size_t)NLSP_TILE * ((k + 3) / 4 * 4 + 4) + (size_t)NLSP_TILE * 36);
@@ -910,6 +1184,27 @@ struct BlockSolver {
       NLSP_CUDA(cudaFuncSetAttribute(k_b_restrict_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rtc));
       NLSP_CUDA(cudaFuncSetAttribute(k_b_prolong_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ptc));
     }
+    // reduced-precision kernels: restriction ring of LP_NS 128-row stages
+    // plus two residual buffers; prolongation ring of as many tile stages as
+    // fit (at most LP_NS) plus E^T
+    const size_t sm_rlp = (size_t)LP_NS * 128 * lp::RCH * lp_es + (size_t)2 * lp::MBC * lp::RCH * lp_es;
+    const size_t lp_bt = (size_t)lp::MBC * lp::kcols_q(k) * lp_es;
+    int optin = 0;
+    NLSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    const int lp_ns = (int)std::max<size_t>(1, std::min<size_t>(LP_NS, ((size_t)optin - 4096 - lp_bt) / lp_qtile));
+    const size_t sm_plp = (size_t)lp_ns * lp_qtile + lp_bt;
+    auto fr_lp = lp_op == lp::OP_BF16 ? k_b_restrict_lp<KIND, lp::OP_BF16> : k_b_restrict_lp<KIND, lp::OP_TF32>;
+    auto fp_lp = lp_op == lp::OP_BF16 ? k_b_prolong_lp<lp::OP_BF16> : k_b_prolong_lp<lp::OP_TF32>;
+    if (use_lp) {
+      NLSP_CUDA(cudaFuncSetAttribute(fr_lp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rlp));
+      NLSP_CUDA(cudaFuncSetAttribute(fp_lp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plp));
+      const int gp = grid_for(ctx, ntiles * NLSP_TILE * (int64_t)lp::kcols_q(k), BT, 8);
+      if (lp_op == lp::OP_BF16)
+        lp::k_pack<lp::OP_BF16><<<gp, BT, 0, s>>>((const float*)M->P, M->k, k, ntiles, lp_R, lp_Q);
+      else
+        lp::k_pack<lp::OP_TF32><<<gp, BT, 0, s>>>((const float*)M->P, M->k, k, ntiles, lp_R, lp_Q);
+      NLSP_LAUNCH_CHECK();
+    }
     // state
     BlockState h;
     memset(&h, 0, sizeof(h));
@@ -928,7 +1223,7 @@ struct BlockSolver {
     NLSP_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * nv, s));
     NLSP_CUDA(cudaMemsetAsync(q, 0, sizeof(double) * nv, s));
     NLSP_LAUNCH_CHECK();
-    int launches = 6;
+    int launches = use_lp ? 7 : 6;
     // z = B r.  In the iteration the update kernel forms x, r with alpha and
     // then rT and the first pre-sweep; for the initial application alpha = 0
     // leaves x and r as they are.
@@ -946,7 +1241,10 @@ struct BlockSolver {
         k_b_sweep4<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, oth);
         std::swap(cur, oth);
       }
-      if (use_tc)
+      if (use_lp)
+        fr_lp<<<nbr, BT, sm_rlp, ss>>>(*reinterpret_cast<const StencilView<float>*>(&AT), (const float*)rT,
+                                       (const float*)cur, lp_R, k, ntiles, (float*)cpart, st);
+      else if (use_tc)
         k_b_restrict_tc<KIND><<<nbr, BT, sm_rtc, ss>>>(*reinterpret_cast<const StencilView<float>*>(&AT),
                                                        (const float*)rT, (const float*)cur, (const float*)M->P,
                                                        M->k, k, ntiles, (float*)cpart, st);
@@ -954,7 +1252,9 @@ struct BlockSolver {
         fr<<<nbr, BT, sm_r, ss>>>(AT, rT, cur, (const T*)M->P, M->k, k, ntiles, cpart);
       k_b_csum<T><<<div_up((int64_t)k * MB, 128), 128, 0, ss>>>(cpart, nbr, k, Csum);
       k_b_coarse<T><<<div_up((int64_t)k * MB, 128), 128, 0, ss>>>(Csum, k, M->Ainv, E);
-      if (use_tc_prolong)
+      if (use_lp)
+        fp_lp<<<nbr, BT, sm_plp, ss>>>(lp_Q, k, n, (const float*)E, (float*)cur, lp_ns, st);
+      else if (use_tc_prolong)
         k_b_prolong_tc<<<nbr, BT, sm_ptc, ss>>>((const float*)M->P, M->k, k, n, (const float*)E, (float*)cur, st);
       else
         fp<<<nb, BT, sm_p, ss>>>((const T*)M->P, M->k, k, n, E, cur);

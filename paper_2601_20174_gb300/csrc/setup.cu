@@ -889,7 +889,7 @@ nlsp_status smooth_tiled(nlsp_ctx* ctx, const nlsp_op* A, int K, int s1, double 
 
 nlsp_status check_setup_params(const nlsp_op* A, const nlsp_setup_params* p, bool need_K) {
   if (!A || !p) return NLSP_ERR_INVALID;
-  if (p->precision != NLSP_FP64 && p->precision != NLSP_MIXED_FP32) return NLSP_ERR_INVALID;
+  if (p->precision < NLSP_FP64 || p->precision > NLSP_MIXED_TF32) return NLSP_ERR_INVALID;
   if (p->k < 1 || p->k > 128 || p->k > A->n) return NLSP_ERR_INVALID;
   if (need_K && (p->K < p->k || p->K > 128 || p->K > A->n || p->s1 < 0)) return NLSP_ERR_INVALID;
   if (p->nu1 < 1 || p->nu2 != p->nu1 || p->nu1 > 64) return NLSP_ERR_INVALID;

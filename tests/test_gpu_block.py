@@ -138,3 +138,48 @@ def test_block_anisotropic_256_mixed(ctx):
     for c in range(p.f.shape[1]):
         true = np.linalg.norm(p.f[:, c] - A @ X[:, c]) / np.linalg.norm(p.f[:, c])
         assert res[c].status == 0 and true <= 1e-8 * 1.01, (c, res[c], true)
+
+
+BF16, TF32 = 2, 3
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision", [BF16, TF32])
+def test_block_reduced_precision_contractions(ctx, name, precision):
+    # BF16 / TF32 tensor-core restriction and prolongation (FP32 accumulate):
+    # after one iteration the iterate equals the FP32 path's to the operand
+    # precision (a wrong operand layout would give O(1) errors), and every
+    # column still reaches the FP64 true residual 1e-8 (flexible CG) within a
+    # few more iterations than the FP32 preconditioner
+    api = _api()
+    p = CASES[name]()
+    A = op.assemble(p)
+    B = gen.rhs_uniform(p.n, 6, seed=31)
+    Aop = api.Operator.from_problem(ctx, p)
+    M32 = api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, MIXED)
+    Mlp = api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, precision)
+    X1, _ = M32.solve_block(to_dev(B), tol=1e-8, maxit=1)
+    Y1, _ = Mlp.solve_block(to_dev(B), tol=1e-8, maxit=1)
+    assert rel(to_np(Y1), to_np(X1)) <= (3e-2 if precision == BF16 else 4e-3)
+    X, r32 = M32.solve_block(to_dev(B), tol=1e-8)
+    Y, rlp = Mlp.solve_block(to_dev(B), tol=1e-8)
+    Y = to_np(Y)
+    for c in range(B.shape[1]):
+        true = np.linalg.norm(B[:, c] - A @ Y[:, c]) / np.linalg.norm(B[:, c])
+        assert rlp[c].status == 0 and true <= 1e-8 * 1.01, (c, rlp[c], true)
+        assert rlp[c].iterations <= 1.5 * r32[c].iterations + 3, (rlp[c].iterations, r32[c].iterations)
+
+
+@pytest.mark.parametrize("precision", [BF16, TF32])
+def test_block_reduced_precision_anisotropic_256(ctx, precision):
+    # several tiles per block, k = 64: every column of 32 converges
+    api = _api()
+    p = gen.aniso_9pt_2d(N=256, k=64, K=128, m=32, seed=5, tol=1e-8)
+    A = op.assemble(p)
+    Aop = api.Operator.from_problem(ctx, p)
+    M = api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, precision)
+    X, res = M.solve_block(to_dev(p.f), tol=p.tol, maxit=5000)
+    X = to_np(X)
+    for c in range(p.f.shape[1]):
+        true = np.linalg.norm(p.f[:, c] - A @ X[:, c]) / np.linalg.norm(p.f[:, c])
+        assert res[c].status == 0 and true <= 1e-8 * 1.01, (c, res[c], true)
