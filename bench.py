@@ -472,13 +472,17 @@ def _fem_spmv_traffic():
 BLOCK = dict(N=1024, k=128, K=128, m=32, s1=20, nu=2, omega=2.0 / 3.0, tol=1e-8, seed=0, seq_cols=4)
 BLOCK_DESC = ("2D rotated anisotropic diffusion, 9-point, 1024^2 (n=1046529), theta ~ U[0,pi), eps=1e-3, k=128 "
               "from K=128 device-drawn smoothed samples (s1=20, omega=2/3), nu=2; 32 RHS U[-1,1] by block PCG "
-              "(FP32 preconditioner, FP64 recurrences), tol 1e-8")
+              "(BF16 tensor-core restriction/prolongation with FP32 accumulation, FP32 smoothing, FP64 "
+              "recurrences), tol 1e-8")
 
 
 def run_block(ctx, dev, timed):
-    """32 right-hand sides advanced together (nlsp_solve_block) against the
-    same columns solved one at a time by the persistent single-column solver
-    (a bounded sample of seq_cols columns, scaled to 32)."""
+    """32 right-hand sides advanced together (nlsp_solve_block).  The
+    configuration's precision: BF16 tensor-core restriction and prolongation
+    with FP32 accumulation, FP64 recurrences; TF32 operands and the FP32
+    (split-TF32 restriction, CUDA-core prolongation) preconditioner are
+    reported beside it, and the persistent single-column solver on a bounded
+    sample of the columns (scaled to 32)."""
     import statistics as st
 
     import torch
@@ -488,36 +492,32 @@ def run_block(ctx, dev, timed):
     p = gen.aniso_9pt_2d(BLOCK["N"], BLOCK["k"], BLOCK["K"], m=BLOCK["m"], seed=BLOCK["seed"], tol=BLOCK["tol"],
                          with_samples=False)
     A = api.Operator.from_problem(ctx, p)
-    M = api.Preconditioner.build(A, None, BLOCK["k"], BLOCK["s1"], BLOCK["nu"], BLOCK["omega"], L.NLSP_MIXED_FP32,
-                                 K=BLOCK["K"], seed=p.seed)
     F = torch.as_tensor(p.f).to(dev)
-    M.solve_block(F, tol=BLOCK["tol"], maxit=20000)  # warm
-    ms, (X, res) = timed(lambda: M.solve_block(F, tol=BLOCK["tol"], maxit=20000), 1)
+
+    def leg(prec):
+        M = api.Preconditioner.build(A, None, BLOCK["k"], BLOCK["s1"], BLOCK["nu"], BLOCK["omega"], prec,
+                                     K=BLOCK["K"], seed=p.seed)
+        M.solve_block(F, tol=BLOCK["tol"], maxit=16)  # warm (repacking, graph build)
+        ms, (X, res) = timed(lambda: M.solve_block(F, tol=BLOCK["tol"], maxit=20000), 1)
+        its = [r.iterations for r in res]
+        out = {"ms": ms[0], "value": BLOCK["m"] / (ms[0] / 1e3), "unit": "solves/s",
+               "iterations": {"min": min(its), "max": max(its)}, "ms_per_iteration": ms[0] / max(its),
+               "all_converged": all(r.status == 0 for r in res),
+               "max_true_relres": max(r.true_relres for r in res)}
+        return M, out
+
+    M, out = leg(L.NLSP_MIXED_BF16)
+    out = {"workload": BLOCK_DESC, "rhs": BLOCK["m"], "precision": "BF16 tensor-core P^T R and P E, FP32 accum",
+           **out}
     cols = BLOCK["seq_cols"]
     ms1, (X1, res1) = timed(lambda: M.solve(F[:, :cols], tol=BLOCK["tol"], maxit=20000, graph_mode=2), 1)
-    its = [r.iterations for r in res]
-    out = {"workload": BLOCK_DESC, "rhs": BLOCK["m"], "ms": ms[0], "value": BLOCK["m"] / (ms[0] / 1e3),
-           "unit": "solves/s", "iterations": {"min": min(its), "max": max(its)},
-           "all_converged": all(r.status == 0 for r in res),
-           "max_true_relres": max(r.true_relres for r in res),
-           "ms_per_iteration": ms[0] / max(its),
-           "single_column_solver": {"columns_timed": cols, "ms": ms1[0], "value": cols / (ms1[0] / 1e3),
-                                    "unit": "solves/s", "iterations": [r.iterations for r in res1]}}
+    out["single_column_solver"] = {"columns_timed": cols, "ms": ms1[0], "value": cols / (ms1[0] / 1e3),
+                                   "unit": "solves/s", "iterations": [r.iterations for r in res1]}
     M.close()
-    # the same block with BF16 / TF32 tensor-core restriction and
-    # prolongation (FP32 accumulation), same device-drawn samples
-    out["reduced_precision"] = {}
-    for name, prec in (("bf16", L.NLSP_MIXED_BF16), ("tf32", L.NLSP_MIXED_TF32)):
-        Ml = api.Preconditioner.build(A, None, BLOCK["k"], BLOCK["s1"], BLOCK["nu"], BLOCK["omega"], prec,
-                                      K=BLOCK["K"], seed=p.seed)
-        Ml.solve_block(F, tol=BLOCK["tol"], maxit=16)  # warm (repacking, graph build)
-        msl, (_, resl) = timed(lambda: Ml.solve_block(F, tol=BLOCK["tol"], maxit=20000), 1)
-        itl = [r.iterations for r in resl]
-        out["reduced_precision"][name] = {
-            "ms": msl[0], "value": BLOCK["m"] / (msl[0] / 1e3), "unit": "solves/s",
-            "iterations": {"min": min(itl), "max": max(itl)}, "ms_per_iteration": msl[0] / max(itl),
-            "all_converged": all(r.status == 0 for r in resl),
-            "max_true_relres": max(r.true_relres for r in resl)}
+    out["other_precisions"] = {}
+    for name, prec in (("tf32", L.NLSP_MIXED_TF32), ("fp32_split_tf32", L.NLSP_MIXED_FP32)):
+        Ml, o = leg(prec)
+        out["other_precisions"][name] = o
         Ml.close()
     A.close()
     return out

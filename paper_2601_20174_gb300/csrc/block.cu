@@ -681,11 +681,11 @@ constexpr int LP_NS = 4;  // stages of the operand ring
 // stage's and the B buffer's "free" barriers; it refills the stage of the
 // previous chunk when that chunk's MMAs are done.  The block's r x 32 result
 // goes to cpart (FP32).
-template <int KIND, int OP>
-__global__ void __launch_bounds__(BT) k_b_restrict_lp(StencilView<float> A, const float* __restrict__ rT,
+template <int KIND, int OP, int NT>
+__global__ void __launch_bounds__(NT) k_b_restrict_lp(StencilView<float> A, const float* __restrict__ rT,
                                                       const float* __restrict__ z,
                                                       const unsigned char* __restrict__ Rc, int k, int64_t ntiles,
-                                                      float* __restrict__ cpart, BlockState* st) {
+                                                      float* __restrict__ cpart, int ns, BlockState* st) {
   using Sx = typename lp::Op<OP>::S;
   constexpr int ES = lp::Op<OP>::ES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -693,8 +693,8 @@ __global__ void __launch_bounds__(BT) k_b_restrict_lp(StencilView<float> A, cons
   const unsigned a_bytes = 128u * lp::RCH * ES;           // one A stage (128 rows)
   const unsigned chunk_bytes = (unsigned)rr * lp::RCH * ES;  // rows that the copy fills
   const unsigned b_bytes = (unsigned)lp::MBC * lp::RCH * ES;
-  unsigned char* sa = smem_raw;                               // LP_NS stages
-  unsigned char* sb = smem_raw + (size_t)LP_NS * a_bytes;     // 2 B buffers
+  unsigned char* sa = smem_raw;                            // ns <= LP_NS stages
+  unsigned char* sb = smem_raw + (size_t)ns * a_bytes;     // 2 B buffers
   __shared__ __align__(8) uint64_t full[LP_NS], afree[LP_NS], bfree[2];
   __shared__ unsigned tbase_s;
   __shared__ int bad, nmma;
@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(BT) k_b_restrict_lp(StencilView<float> A, cons
     nmma = 0;
   }
   // rows rr .. 127 of every stage stay zero (the copies fill rows < rr)
-  for (unsigned e = tid; e < (unsigned)LP_NS * (a_bytes - chunk_bytes) / 16; e += BT) {
+  for (unsigned e = tid; e < (unsigned)ns * (a_bytes - chunk_bytes) / 16; e += NT) {
     const unsigned per = (a_bytes - chunk_bytes) / 16;
     *reinterpret_cast<uint4*>(sa + (size_t)(e / per) * a_bytes + chunk_bytes + (size_t)(e % per) * 16) =
         make_uint4(0u, 0u, 0u, 0u);
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(BT) k_b_restrict_lp(StencilView<float> A, cons
   tmem::fence_after_sync();
   const unsigned td = tbase_s;
   if (tid == 0)
-    for (int c = 0; c < LP_NS && c < nchunk; ++c) {
+    for (int c = 0; c < ns && c < nchunk; ++c) {
       tma::mbar_arrive_expect_tx(&full[c], chunk_bytes);
       tma::bulk_g2s(sa + (size_t)c * a_bytes, chunk_src(c), chunk_bytes, &full[c]);
     }
@@ -744,27 +744,38 @@ __global__ void __launch_bounds__(BT) k_b_restrict_lp(StencilView<float> A, cons
     // rho of the chunk's 64 nodes -> B buffer b (8 threads per node, four columns each)
     const int64_t t = blockIdx.x + (int64_t)(q >> 1) * gridDim.x;
     unsigned char* bb = sb + (size_t)b * b_bytes;
-    for (int wn = tid >> 3; wn < lp::RCH; wn += BT / 8) {
-      const int qd = tid & 7;
-      const int64_t i = t * NLSP_TILE + (q & 1) * lp::RCH + wn;
-      V4<float> rho;
+    // both node-quads of a thread are evaluated before either is stored, so
+    // that their loads are in flight together
+    constexpr int PER = lp::RCH / (NT / 8);
+    static_assert(PER >= 1 && PER * (NT / 8) == lp::RCH, "a chunk splits evenly over the block");
+    const int qd = tid & 7;
+    V4<float> rho[PER];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) rho.v[j] = 0.0f;
+    for (int u = 0; u < PER; ++u) {
+      const int wn = (tid >> 3) + u * (NT / 8);
+      const int64_t i = t * NLSP_TILE + (q & 1) * lp::RCH + wn;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rho[u].v[j] = 0.0f;
       if (i < A.n) {
         const V4<float> az = stencil_apply4<KIND>(A, i, node_coord<KIND>(i, A.N),
                                                   [&](int64_t m) { return ld4(z + m * MB + 4 * qd); });
         const V4<float> r0 = ld4(rT + i * MB + 4 * qd);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) rho.v[j] = r0.v[j] - az.v[j];
+        for (int j = 0; j < 4; ++j) rho[u].v[j] = r0.v[j] - az.v[j];
       }
+    }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) *reinterpret_cast<Sx*>(bb + lp::off<OP>(4 * qd + j, wn, lp::RCH)) = lp::Op<OP>::cvt(rho.v[j]);
+    for (int u = 0; u < PER; ++u) {
+      const int wn = (tid >> 3) + u * (NT / 8);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<Sx*>(bb + lp::off<OP>(4 * qd + j, wn, lp::RCH)) = lp::Op<OP>::cvt(rho[u].v[j]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
-      const int s = q % LP_NS;
-      if (!tma::mbar_wait(&full[s], (unsigned)((q / LP_NS) & 1))) {
+      const int s = q % ns;
+      if (!tma::mbar_wait(&full[s], (unsigned)((q / ns) & 1))) {
         bad = 1;
       } else {
         tmem::fence_after_sync();
@@ -772,15 +783,17 @@ __global__ void __launch_bounds__(BT) k_b_restrict_lp(StencilView<float> A, cons
         lp::commit(&afree[s]);
         lp::commit(&bfree[b]);
         nmma = q + 1;
-        // refill the stage of the previous chunk once its MMAs are done
-        const int pc = q - 1;
-        if (pc >= 0 && pc + LP_NS < nchunk) {
-          const int ps = pc % LP_NS;
-          if (!tma::mbar_wait(&afree[ps], (unsigned)((pc / LP_NS) & 1))) {
+        // refill the stage of an earlier chunk once its MMAs are done: two
+        // chunks back when the ring has room (its MMAs finished long ago, so
+        // the wait does not hold up this thread's warp), else the previous one
+        const int pc = q - (ns >= 3 ? 2 : 1);
+        if (pc >= 0 && pc + ns < nchunk) {
+          const int ps = pc % ns;
+          if (!tma::mbar_wait(&afree[ps], (unsigned)((pc / ns) & 1))) {
             bad = 1;
           } else {
             tma::mbar_arrive_expect_tx(&full[ps], chunk_bytes);
-            tma::bulk_g2s(sa + (size_t)ps * a_bytes, chunk_src(pc + LP_NS), chunk_bytes, &full[ps]);
+            tma::bulk_g2s(sa + (size_t)ps * a_bytes, chunk_src(pc + ns), chunk_bytes, &full[ps]);
           }
         }
       }
@@ -794,14 +807,14 @@ __global__ void __launch_bounds__(BT) k_b_restrict_lp(StencilView<float> A, cons
   if (issued > 0 && !tma::mbar_wait(&bfree[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1))) bad = 1;
   __syncthreads();
   if (tid == 0 && bad) {
-    // copies were issued for chunks below max(LP_NS, issued + LP_NS - 1) and
+    // copies were issued for chunks below max(ns, issued + ns - lag) and
     // consumed below `issued`: wait (bounded) for the rest to land
-    const int hi = min(nchunk, max(LP_NS, issued + LP_NS - 1));
-    for (int c = issued; c < hi; ++c) tma::mbar_wait(&full[c % LP_NS], (unsigned)((c / LP_NS) & 1));
+    const int hi = min(nchunk, max(ns, issued + ns - (ns >= 3 ? 2 : 1)));
+    for (int c = issued; c < hi; ++c) tma::mbar_wait(&full[c % ns], (unsigned)((c / ns) & 1));
     atomicExch(&st->err, 1);
   }
   tmem::fence_after_sync();
-  if (!bad && issued > 0) {
+  if (!bad && issued > 0 && warp < 8) {  // warps 0-7 read the 128 lanes x 32 columns of D
     float v[16];
     tc::ld16(td + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(16 * (warp >> 2)), v);
     const int j = 32 * (warp & 3) + lane;
@@ -809,8 +822,8 @@ __global__ void __launch_bounds__(BT) k_b_restrict_lp(StencilView<float> A, cons
 #pragma unroll
       for (int c = 0; c < 16; ++c) cpart[((int64_t)blockIdx.x * k + j) * MB + 16 * (warp >> 2) + c] = v[c];
     }
-  } else {
-    for (int e = tid; e < k * MB; e += BT) cpart[(int64_t)blockIdx.x * k * MB + e] = 0.0f;
+  } else if (bad || issued == 0) {
+    for (int e = tid; e < k * MB; e += NT) cpart[(int64_t)blockIdx.x * k * MB + e] = 0.0f;
   }
   tmem::fence_before_sync();
   __syncthreads();
@@ -898,6 +911,15 @@ __global__ void __launch_bounds__(BT) k_b_prolong_lp(const unsigned char* __rest
   }
   for (int i = 0; i < nt; ++i) {
     __syncthreads();  // accumulator (i + 1) % 2 was drained by the previous iteration
+    // the z rows this thread updates are loaded before the wait for the
+    // accumulator (they do not depend on it)
+    const int64_t node = (blockIdx.x + (int64_t)i * gridDim.x) * NLSP_TILE + 32 * (warp & 3) + lane;
+    float* zr = z + node * MB + 16 * (warp >> 2);
+    V4<float> zv[4];
+    if (node < n) {
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) zv[c4] = ld4(zr + 4 * c4);
+    }
     if (tid == 0 && !bad && i + 1 < nt) issue(i + 1);
     if (!tma::mbar_wait(&dfull[i & 1], (unsigned)((i >> 1) & 1))) bad = 1;
     __syncthreads();
@@ -905,15 +927,12 @@ __global__ void __launch_bounds__(BT) k_b_prolong_lp(const unsigned char* __rest
     tmem::fence_after_sync();
     float v[16];
     tc::ld16(td + (unsigned)(32 * (i & 1)) + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(16 * (warp >> 2)), v);
-    const int64_t node = (blockIdx.x + (int64_t)i * gridDim.x) * NLSP_TILE + 32 * (warp & 3) + lane;
     if (node < n) {
-      float* zr = z + node * MB + 16 * (warp >> 2);
 #pragma unroll
       for (int c4 = 0; c4 < 4; ++c4) {
-        V4<float> zv = ld4(zr + 4 * c4);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) zv.v[c] += v[4 * c4 + c];
-        st4(zr + 4 * c4, zv);
+        for (int c = 0; c < 4; ++c) zv[c4].v[c] += v[4 * c4 + c];
+        st4(zr + 4 * c4, zv[c4]);
       }
     }
     tmem::fence_before_sync();
@@ -1187,13 +1206,22 @@ struct BlockSolver {
     // reduced-precision kernels: restriction ring of LP_NS 128-row stages
     // plus two residual buffers; prolongation ring of as many tile stages as
     // fit (at most LP_NS) plus E^T
-    const size_t sm_rlp = (size_t)LP_NS * 128 * lp::RCH * lp_es + (size_t)2 * lp::MBC * lp::RCH * lp_es;
-    const size_t lp_bt = (size_t)lp::MBC * lp::kcols_q(k) * lp_es;
+    // stage counts: at least two CTAs per SM where two stages fit (the
+    // kernels are latency-bound per chunk, so resident CTAs matter more than
+    // ring depth), else as many stages as one CTA holds
     int optin = 0;
     NLSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-    const int lp_ns = (int)std::max<size_t>(1, std::min<size_t>(LP_NS, ((size_t)optin - 4096 - lp_bt) / lp_qtile));
+    const size_t lp_achunk = (size_t)128 * lp::RCH * lp_es, lp_bbuf = (size_t)2 * lp::MBC * lp::RCH * lp_es;
+    const size_t half = (size_t)optin / 2 - 2048;
+    const int lp_nsr = (int)std::max<size_t>(2, std::min<size_t>(LP_NS, (half - lp_bbuf) / lp_achunk));
+    const size_t sm_rlp = (size_t)lp_nsr * lp_achunk + lp_bbuf;
+    const size_t lp_bt = (size_t)lp::MBC * lp::kcols_q(k) * lp_es;
+    const size_t ns2 = (half - lp_bt) / lp_qtile;
+    const int lp_ns = (int)(ns2 >= 2 ? std::min<size_t>(LP_NS, ns2)
+                                     : std::max<size_t>(1, std::min<size_t>(LP_NS, ((size_t)optin - 4096 - lp_bt) / lp_qtile)));
     const size_t sm_plp = (size_t)lp_ns * lp_qtile + lp_bt;
-    auto fr_lp = lp_op == lp::OP_BF16 ? k_b_restrict_lp<KIND, lp::OP_BF16> : k_b_restrict_lp<KIND, lp::OP_TF32>;
+    constexpr int LPT = 512;  // threads of the reduced-precision restriction (one node-quad each per chunk)
+    auto fr_lp = lp_op == lp::OP_BF16 ? k_b_restrict_lp<KIND, lp::OP_BF16, LPT> : k_b_restrict_lp<KIND, lp::OP_TF32, LPT>;
     auto fp_lp = lp_op == lp::OP_BF16 ? k_b_prolong_lp<lp::OP_BF16> : k_b_prolong_lp<lp::OP_TF32>;
     if (use_lp) {
       NLSP_CUDA(cudaFuncSetAttribute(fr_lp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rlp));
@@ -1242,8 +1270,8 @@ struct BlockSolver {
         std::swap(cur, oth);
       }
       if (use_lp)
-        fr_lp<<<nbr, BT, sm_rlp, ss>>>(*reinterpret_cast<const StencilView<float>*>(&AT), (const float*)rT,
-                                       (const float*)cur, lp_R, k, ntiles, (float*)cpart, st);
+        fr_lp<<<nbr, LPT, sm_rlp, ss>>>(*reinterpret_cast<const StencilView<float>*>(&AT), (const float*)rT,
+                                       (const float*)cur, lp_R, k, ntiles, (float*)cpart, lp_nsr, st);
       else if (use_tc)
         k_b_restrict_tc<KIND><<<nbr, BT, sm_rtc, ss>>>(*reinterpret_cast<const StencilView<float>*>(&AT),
                                                        (const float*)rT, (const float*)cur, (const float*)M->P,

@@ -11,7 +11,8 @@ solver's per-phase times are printed (microseconds per iteration).
 
 With --block the 2D rotated anisotropic 9-point workload (N^2 nodes, k from K
 device-drawn samples, 32 right-hand sides) runs --iters iterations of the
-block PCG instead.
+block PCG instead (--precision bf16 / tf32: reduced-precision tensor-core
+restriction and prolongation).
 """
 from __future__ import annotations
 
@@ -25,7 +26,7 @@ from . import _lib as L, api, inputs as gen
 
 def main() -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "bf16", "tf32"])
     ap.add_argument("--iters", type=int, default=4)
     ap.add_argument("--N", type=int, default=512)
     ap.add_argument("--k", type=int, default=64)
@@ -62,7 +63,8 @@ def main() -> int:
         p = gen.aniso_9pt_2d(args.N, args.k, args.K, m=32, seed=0, tol=1e-8, with_samples=False)
         ctx = api.Context(0)
         A = api.Operator.from_problem(ctx, p)
-        prec = L.NLSP_MIXED_FP32 if args.precision == "mixed" else L.NLSP_FP64
+        prec = {"mixed": L.NLSP_MIXED_FP32, "fp64": L.NLSP_FP64, "bf16": L.NLSP_MIXED_BF16,
+                "tf32": L.NLSP_MIXED_TF32}[args.precision]
         M = api.Preconditioner.build(A, None, args.k, p.s1, p.nu, p.omega, prec, K=args.K, seed=p.seed)
         F = torch.as_tensor(p.f).cuda()
         _, res = M.solve_block(F, tol=1e-8, maxit=args.iters)
