@@ -1579,6 +1579,8 @@ __global__ void __launch_bounds__(PT, 1) k_pcg_persistent(PersistArgs<T> one, co
 // ============================================================================
 // Host side
 // ============================================================================
+#include "pcg_cluster.cuh"
+
 struct PcgWork {
   int64_t n = 0;
   int tsize = 0;
@@ -2045,6 +2047,87 @@ struct Solver {
     return a;
   }
 
+  // Cluster-resident solver for small systems (graph_mode 2): the smallest
+  // power-of-two cluster of C <= 16 CTAs whose ranks' shared memory holds the
+  // vectors and P rows of about n / C nodes, preferring C with at most ~96
+  // nodes per rank (the FP64 work of a rank is what an iteration waits for).
+  // Off with NLSP_CLUSTER=0.  Returns false when the system does not fit.
+  static bool cluster_plan(const nlsp_prec* M, int* C, int* nl, int* nlp, size_t* smem) {
+    const char* env = getenv("NLSP_CLUSTER");
+    if (env && env[0] == '0') return false;
+    if (M->n > 16 * 4096) return false;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, (const void*)k_pcg_cluster<KIND, T>) != cudaSuccess) return false;
+    const size_t avail = (size_t)optin - fa.sharedSizeBytes - 1024;
+    int c = 1;
+    while (c < CL_MAX && (M->n + c - 1) / c > 96) c *= 2;
+    const char* csz = getenv("NLSP_CLUSTER_SIZE");  // a fixed cluster size (1, 2, 4, 8 or 16)
+    if (csz && atoi(csz) >= 1 && atoi(csz) <= CL_MAX && (atoi(csz) & (atoi(csz) - 1)) == 0) c = atoi(csz);
+    for (; c <= CL_MAX; c *= 2) {
+      const int l = (int)((M->n + c - 1) / c);
+      const int lp = l | 1;
+      const size_t need = cluster_smem<T>(l, lp, M->r);
+      if (need <= avail) {
+        *C = c;
+        *nl = l;
+        *nlp = lp;
+        *smem = need;
+        return true;
+      }
+    }
+    return false;
+  }
+
+  static nlsp_status launch_cluster(nlsp_prec* M, const double* b, double* xout, const nlsp_solve_params* prm,
+                                    int flexible, PcgState* st_out, int C, int nl, int nlp, size_t smem) {
+    nlsp_ctx* ctx = M->ctx;
+    auto fn = k_pcg_cluster<KIND, T>;
+    NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    ClusterArgs a;
+    a.n = M->n;
+    a.nl = nl;
+    a.nlp = nlp;
+    a.k = M->k;
+    a.r = M->r;
+    a.nu1 = M->nu1;
+    a.nu2 = M->nu2;
+    a.flexible = flexible;
+    a.maxit = prm->maxit;
+    a.tol = prm->tol;
+    a.b = b;
+    a.x = xout;
+    a.P = M->P;
+    a.Ainv = M->AinvT;
+    a.st = st_out;
+    a.ptimes = M->pcg ? M->pcg->ptimes : nullptr;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(CT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    NLSP_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg));
+    if (nclusters < 1) {
+      nlsp_record_message("cluster solver: the cluster does not fit on the device");
+      return NLSP_ERR_INVALID;
+    }
+    NLSP_CUDA(cudaLaunchKernelEx(&cfg, fn, M->A->v64, view_T<T>(M->A), (T)M->omega, a));
+    count_launches(ctx, 1);
+    return NLSP_OK;
+  }
+
   // The persistent cooperative solver (graph_mode 2): one launch per column,
   // all CTAs on the one instance.
   static nlsp_status launch_persistent(nlsp_prec* M, const double* b, double* xout, const nlsp_solve_params* prm,
@@ -2096,8 +2179,15 @@ struct Solver {
     PcgWork* w = M->pcg;
     if (prm->graph_mode == 2) {
       const int flexible = prm->flexible < 0 ? (M->precision != NLSP_FP64) : (prm->flexible != 0);
-      for (int col = 0; col < m; ++col)
-        NLSP_TRY(launch_persistent(M, B + col * ldb, X + col * ldx, prm, flexible, w->st_all + col));
+      int C = 0, nl = 0, nlp = 0;
+      size_t csmem = 0;
+      const bool clus = cluster_plan(M, &C, &nl, &nlp, &csmem);
+      for (int col = 0; col < m; ++col) {
+        if (clus)
+          NLSP_TRY(launch_cluster(M, B + col * ldb, X + col * ldx, prm, flexible, w->st_all + col, C, nl, nlp, csmem));
+        else
+          NLSP_TRY(launch_persistent(M, B + col * ldb, X + col * ldx, prm, flexible, w->st_all + col));
+      }
       NLSP_CUDA(cudaMemcpyAsync(w->h_st, w->st_all, sizeof(PcgState) * m, cudaMemcpyDeviceToHost, s));
       NLSP_CUDA(cudaStreamSynchronize(s));
       return summarize(w, m, infos, 0);

@@ -17,6 +17,7 @@ restriction and prolongation).
 from __future__ import annotations
 
 import argparse
+import os
 
 import numpy as np
 import torch
@@ -88,6 +89,13 @@ def main() -> int:
         import ctypes as C
         out = (C.c_double * 31)()
         L.check(ctx._lib.nlsp_prec_phase_times(ctx.h, M.h, out, 31), "nlsp_prec_phase_times")
+        if os.environ.get("NLSP_CLUSTER", "1") != "0" and p.n <= 16 * 4096:
+            cmarks = ["S1 wait", "update", "S2 wait", "pre sweeps", "rho wait", "rho", "restrict", "c wait",
+                      "coarse", "prolong", "post sweeps", "rz wait", "direction"]
+            it = max(1, res[0].iterations)
+            print("  cluster solver marks (rank 0, us per iteration):")
+            for i, name in enumerate(cmarks):
+                print(f"  {name:18s} {out[14 + i] / 1e3 / it:8.2f}")
         names = ["spmv", "pre", "stored sweeps", "restrict", "prolong", "post", "other"]
         marks = ["spmv totals", "spmv nodes", "pre totals", "pre nodes", "restrict rho", "restrict resident",
                  "restrict streamed", "restrict reduce", "prolong coarse", "prolong resident", "prolong streamed",

@@ -239,6 +239,38 @@ def test_pcg_fp64_matches_oracle_iterates(ctx, name, graph_mode):
 
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("cluster", ["1", "0"])
+def test_single_launch_solvers_match_oracle(ctx, name, cluster, monkeypatch):
+    # graph_mode 2 runs small systems on the cluster-resident solver (one
+    # thread-block cluster, vectors in distributed shared memory) and the
+    # rest on the grid-wide persistent solver; NLSP_CLUSTER=0 forces the
+    # latter.  Both must reproduce the oracle's iterates (FP64, the oracle's
+    # basis) and reach the FP64 true residual in mixed precision.
+    monkeypatch.setenv("NLSP_CLUSTER", cluster)
+    p = PROBLEMS[name]()
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    b = p.f[:, 0]
+    o = opcg.pcg(A, opcg.two_level_solver(A, ref["P"], ref["L"], p.omega, p.nu, p.nu), b, p.tol)
+    Aop = _api().Operator.from_problem(ctx, p)
+    M = _api().Preconditioner.from_basis(Aop, to_dev(ref["P"]), p.nu, p.omega, FP64)
+    x, res = M.solve(to_dev(b), tol=p.tol, graph_mode=2)
+    assert res[0].status == 0 and abs(res[0].iterations - o["iters"]) <= 1
+    assert rel(to_np(x), o["x"]) <= 1e-8
+    true = np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b)
+    assert abs(res[0].true_relres - true) <= 1e-3 * true
+    Mm = _api().Preconditioner.from_basis(Aop, to_dev(ref["P"]), p.nu, p.omega, MIXED)
+    x, res = Mm.solve(to_dev(b), tol=1e-8, graph_mode=2)
+    true = np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b)
+    assert res[0].status == 0 and true <= 1e-8 * 1.01
+    # zero right-hand side and maxit through the same launch
+    x0, r0 = M.solve(to_dev(np.zeros(p.n)), tol=p.tol, graph_mode=2)
+    assert r0[0].iterations == 0 and r0[0].status == 0 and np.all(to_np(x0) == 0)
+    _, r3 = M.solve(to_dev(b), tol=1e-14, maxit=3, graph_mode=2)
+    assert r3[0].status == 1 and r3[0].iterations == 3
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
 @pytest.mark.parametrize("graph_mode", [1, 2])
 def test_pcg_end_to_end_both_precisions(ctx, name, graph_mode):
     p = PROBLEMS[name]()
