@@ -47,8 +47,8 @@ def _profiled_traffic(k: int, iterations: int):
     try:
         with open(os.path.join(ROOT, "profiles", "k_pcg_persistent_grf512_k64.json")) as f:
             prof = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2601_20174_gb300", "csrc", "pcg.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest() != prof["pcg_cu_sha256"] or prof["k"] != k:
+        src = open(os.path.join(ROOT, "paper_2601_20174_gb300", "csrc", "pcg_impl.cuh"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != prof.get("pcg_impl_sha256") or prof["k"] != k:
             return None
         return prof["dram_bytes_fixed"] + prof["dram_bytes_per_iteration"] * iterations
     except Exception:
@@ -547,13 +547,10 @@ def run_batched(ctx, dev, timed, rank):
         return ops, precs
 
     ops, precs = build_all()
-    tune = {}
-    for tpc in BATCH["tiles_per_cta"]:
-        api.solve_batched(precs, fs, tol=BATCH["tol"], tiles_per_cta=tpc)  # warm
-        ms, _ = timed(lambda: api.solve_batched(precs, fs, tol=BATCH["tol"], tiles_per_cta=tpc), 1)
-        tune[tpc] = ms[0]
-    best = min(tune, key=tune.get)
-    so_ms, (xs, res) = timed(lambda: api.solve_batched(precs, fs, tol=BATCH["tol"], tiles_per_cta=best), 3)
+    # the library's autotuner picks the team size and the context remembers it
+    # for batches of these sizes; the solves below pass tiles_per_cta = 0
+    best, tune = api.tune_batched(precs, fs, candidates=BATCH["tiles_per_cta"], tol=BATCH["tol"])
+    so_ms, (xs, res) = timed(lambda: api.solve_batched(precs, fs, tol=BATCH["tol"], tiles_per_cta=0), 3)
     # one by one with the single-instance persistent solver, for comparison
     def one_by_one():
         return [M.solve(f, tol=BATCH["tol"], graph_mode=2)[1][0] for M, f in zip(precs, fs)]
@@ -567,7 +564,7 @@ def run_batched(ctx, dev, timed, rank):
     # the full step: setup of every instance + the batched solve
     def full_step():
         o, m = build_all()
-        x, r = api.solve_batched(m, fs, tol=BATCH["tol"], tiles_per_cta=best)
+        x, r = api.solve_batched(m, fs, tol=BATCH["tol"], tiles_per_cta=0)
         return o, m, r
     full_ms, (o2, m2, res2) = timed(full_step, 2)
     for M in m2:
@@ -582,7 +579,8 @@ def run_batched(ctx, dev, timed, rank):
             "ms_per_step": st.median(full_ms), "step": "assemble + setup (device-drawn samples) of all 256 instances, "
                                                        "then one batched persistent solve",
             "solve_only": {"value": cnt / (st.median(so_ms) / 1000.0), "unit": "solves/s", "ms": st.median(so_ms),
-                           "tiles_per_cta": best, "autotune_ms": {str(k): v for k, v in tune.items()}},
+                           "tiles_per_cta": best, "autotune_ms": {str(k): v for k, v in tune.items()},
+                           "autotune": "nlsp_tune_batched (library), remembered per context; solves pass 0"},
             "one_by_one_solve_only": {"value": cnt / (seq_ms[0] / 1000.0), "unit": "solves/s", "ms": seq_ms[0],
                                       "iterations_total": sum(r.iterations for r in seq_res)},
             "iterations": {"min": min(its), "median": int(st.median(its)), "max": max(its), "total": sum(its)},
@@ -689,6 +687,22 @@ def run_ours(args):
             "algorithmic_bytes_per_iteration": alg_iter, "iterations": it_s,
             "timing": "solve-only launches (one persistent kernel per solve), CUDA events on the library stream, "
                       "L2 flushed before each"}
+    # What binds the persistent kernel instead of HBM: its FP64 arithmetic on
+    # GB300's 1/64-rate FP64 pipe and its team barriers.  Per node and
+    # iteration the FP64 operations are: spmv 8 (5-point A z 5, the q / p
+    # updates 2, p^T q 1), CG update 4 (x, r, r^T r, the FP32 copy of r),
+    # post-smoothing 3 (z stored in FP64, r^T z, r^T z_old); the rate is the
+    # measured FP64 FMA rate counted per lane-operation (1.20 TFLOP/s = 0.60 T
+    # operations/s) and each of the 4 barriers per iteration costs the measured
+    # 1.22 us of a 152-CTA bounded grid barrier (both microbenchmarks on this
+    # pool's GB300).
+    fp64_ops = 15 * n
+    floor_us = fp64_ops / 0.60e12 * 1e6 + 4 * 1.22
+    us_it = 1000.0 * statistics.median(so_ms) / max(1, it_s)
+    roof["binding_floor"] = {"bound": "fp64 pipe + grid barriers", "fp64_ops_per_iteration": fp64_ops,
+                             "fp64_ops_per_s": 0.60e12, "barriers_per_iteration": 4, "barrier_us": 1.22,
+                             "floor_us_per_iteration": floor_us, "achieved_us_per_iteration": us_it,
+                             "frac": floor_us / us_it}
     # the multi-kernel path's two P-streaming kernels, replayed alone
     kern = {}
     alg_bytes = {"restrict": n * (4 * WL["k"] + 8 + 4 + 12), "prolong": n * (4 * WL["k"] + 8)}

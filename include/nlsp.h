@@ -389,7 +389,8 @@ NLSP_API nlsp_status nlsp_solve_block(nlsp_ctx* ctx, const nlsp_op* A, const nls
    `count` device pointers to FP64 vectors of length n_i; x0 = 0 and x_i is
    output only (must not be b_i).  params: tol, maxit and flexible as in
    nlsp_solve (graph_mode is ignored).  tiles_per_cta: target number of
-   128-node tiles per CTA of a team (0: 16).  infos: host array of `count`
+   128-node tiles per CTA of a team (0: the value nlsp_tune_batched measured
+   for a batch of the same sizes on this context, else 16).  infos: host array of `count`
    entries (may be NULL).  Synchronises.  A team barrier gives up after 2 s
    without progress anywhere in the launch (no instance finished an
    iteration), and its instance ends with NLSP_ERR_TIMEOUT.  Returns as nlsp_solve
@@ -398,6 +399,21 @@ NLSP_API nlsp_status nlsp_solve_block(nlsp_ctx* ctx, const nlsp_op* A, const nls
 NLSP_API nlsp_status nlsp_solve_batched(nlsp_ctx* ctx, int count, nlsp_prec* const* M, const double* const* dev_b,
                                         double* const* dev_x, const nlsp_solve_params* params, int tiles_per_cta,
                                         nlsp_solve_info* infos);
+
+/* Autotuner of the batched solver's team size: times one nlsp_solve_batched
+   of these instances for each of the `ncand` candidate tiles_per_cta values
+   (after one untimed warm-up solve each; CUDA events on the context stream),
+   stores the fastest in *best (host) and the times in ms_out[ncand] (host,
+   may be NULL), and remembers it in the context for this signature of the
+   batch (stencil kind, precision and every instance's node count and active
+   rank, in order; the last 8 signatures are kept): later nlsp_solve_batched
+   calls with tiles_per_cta = 0 on instances of the same sizes use it.  The
+   paper has no counterpart.  dev_x receive the solutions (each solve
+   overwrites them).  Arguments as nlsp_solve_batched; candidates >= 1.
+   Synchronises.  Errors: NLSP_ERR_INVALID, and any error of the solves. */
+NLSP_API nlsp_status nlsp_tune_batched(nlsp_ctx* ctx, int count, nlsp_prec* const* M, const double* const* dev_b,
+                                       double* const* dev_x, const nlsp_solve_params* params, const int* candidates,
+                                       int ncand, int* best, double* ms_out);
 
 /* The batched solver's team plan (host computation only, no device work).
    Instance i of n[i] nodes (n[i] >= 1) gets team_size[i] =

@@ -86,6 +86,8 @@ SIGNATURES = {
     "nlsp_bench_kernel": (ci, [vp, vp, ci, ci]),
     "nlsp_solve_batched": (ci, [vp, ci, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveParams), ci,
                                 C.POINTER(SolveInfo)]),
+    "nlsp_tune_batched": (ci, [vp, ci, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveParams),
+                               C.POINTER(ci), ci, C.POINTER(ci), C.POINTER(cd)]),
     "nlsp_plan_teams": (ci, [ci, C.POINTER(i64), ci, ci, C.POINTER(ci), C.POINTER(ci), C.POINTER(cd)]),
     "nlsp_solve_block": (ci, [vp, vp, vp, ci, vp, i64, vp, i64, C.POINTER(SolveParams), C.POINTER(SolveInfo)]),
     "nlsp_subspace_loss": (ci, [vp, i64, ci, ci, ci, vp, vp, C.POINTER(cd), vp]),

@@ -311,6 +311,28 @@ def solve_batched(precs: list[Preconditioner], bs: list[torch.Tensor], tol: floa
     return xs, [SolveResult(i.iterations, i.status, i.relres, i.true_relres) for i in infos]
 
 
+def tune_batched(precs: list[Preconditioner], bs: list[torch.Tensor], candidates=(2, 4, 8, 16, 32, 64),
+                 tol: float = 1e-8, maxit: int = 2000, flexible: int = -1):
+    """Measures nlsp_solve_batched for each candidate tiles_per_cta and lets
+    the context remember the fastest for batches of these sizes
+    (nlsp_tune_batched; later solve_batched(..., tiles_per_cta=0) uses it).
+    Returns (best, {candidate: ms})."""
+    count = len(precs)
+    ctx = precs[0].ctx
+    bvec = [b.contiguous() for b in bs]
+    xs = [torch.empty_like(b) for b in bvec]
+    hp = (C.c_void_p * count)(*[M.h.value for M in precs])
+    hb = (C.c_void_p * count)(*[b.data_ptr() for b in bvec])
+    hx = (C.c_void_p * count)(*[x.data_ptr() for x in xs])
+    cand = (C.c_int * len(candidates))(*candidates)
+    ms = (C.c_double * len(candidates))()
+    best = C.c_int()
+    prm = L.SolveParams(tol=tol, maxit=maxit, flexible=flexible, graph_mode=2)
+    L.check(ctx._lib.nlsp_tune_batched(ctx.h, count, hp, hb, hx, C.byref(prm), cand, len(candidates),
+                                       C.byref(best), ms), "nlsp_tune_batched")
+    return best.value, {c: m for c, m in zip(candidates, ms)}
+
+
 def plan_teams(n: list[int], num_ctas: int, tiles_per_cta: int = 0):
     """The batched solver's team plan for instances of n[i] nodes
     (nlsp_plan_teams; host computation).  Returns (first_cta, team_size,

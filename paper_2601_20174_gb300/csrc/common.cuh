@@ -116,6 +116,11 @@ struct nlsp_ctx {
   void* slot[SLOT_COUNT];
   size_t slot_bytes[SLOT_COUNT];
   unsigned long long launches;  // kernels this context has enqueued
+  // batched-solve tuning (nlsp_tune_batched): signature of a set of instance
+  // sizes -> fastest tiles per CTA measured for it
+  unsigned long long tune_key[8];
+  int tune_tpc[8];
+  int tune_next;
 };
 
 // Returns slot `s` with at least `bytes` (grows it, synchronising the

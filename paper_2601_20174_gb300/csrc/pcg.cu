@@ -125,6 +125,48 @@ extern "C" nlsp_status nlsp_plan_teams(int count, const int64_t* n, int num_ctas
   return nlsp_internal_plan_teams(count, n, nullptr, num_ctas, tiles_per_cta, first_cta, team_size, start);
 }
 
+namespace {
+
+// Signature of a batch: FNV-1a over the stencil kind, precision and every
+// instance's node count and active rank, in instance order.
+unsigned long long batch_signature(int count, nlsp_prec* const* M) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](unsigned long long v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xFFull;
+      h *= 1099511628211ull;
+    }
+  };
+  mix((unsigned long long)count);
+  mix((unsigned long long)M[0]->A->kind);
+  mix((unsigned long long)M[0]->precision);
+  for (int i = 0; i < count; ++i) {
+    mix((unsigned long long)M[i]->n);
+    mix((unsigned long long)M[i]->r);
+  }
+  return h;
+}
+
+int tuned_tiles(const nlsp_ctx* ctx, unsigned long long key) {
+  for (int i = 0; i < 8; ++i)
+    if (ctx->tune_tpc[i] > 0 && ctx->tune_key[i] == key) return ctx->tune_tpc[i];
+  return 0;
+}
+
+void remember_tiles(nlsp_ctx* ctx, unsigned long long key, int tpc) {
+  for (int i = 0; i < 8; ++i)
+    if (ctx->tune_tpc[i] > 0 && ctx->tune_key[i] == key) {
+      ctx->tune_tpc[i] = tpc;
+      return;
+    }
+  const int slot = ctx->tune_next;
+  ctx->tune_key[slot] = key;
+  ctx->tune_tpc[slot] = tpc;
+  ctx->tune_next = (slot + 1) % 8;
+}
+
+}  // namespace
+
 extern "C" nlsp_status nlsp_solve_batched(nlsp_ctx* ctx, int count, nlsp_prec* const* M, const double* const* dev_b,
                                           double* const* dev_x, const nlsp_solve_params* params, int tiles_per_cta,
                                           nlsp_solve_info* infos) {
@@ -145,7 +187,51 @@ extern "C" nlsp_status nlsp_solve_batched(nlsp_ctx* ctx, int count, nlsp_prec* c
     return NLSP_ERR_INVALID;
   }
   NLSP_CUDA(cudaSetDevice(ctx->device));
+  if (tiles_per_cta == 0) tiles_per_cta = tuned_tiles(ctx, batch_signature(count, M));  // 0: the plan's default
   return pcg_ops(M[0])->solve_batched(ctx, count, M, dev_b, dev_x, params, tiles_per_cta, infos);
+}
+
+extern "C" nlsp_status nlsp_tune_batched(nlsp_ctx* ctx, int count, nlsp_prec* const* M, const double* const* dev_b,
+                                         double* const* dev_x, const nlsp_solve_params* params,
+                                         const int* candidates, int ncand, int* best, double* ms_out) {
+  if (!ctx || !params || count < 1 || !M || !candidates || ncand < 1 || !best) return NLSP_ERR_INVALID;
+  for (int c = 0; c < ncand; ++c)
+    if (candidates[c] < 1) return NLSP_ERR_INVALID;
+  NLSP_CUDA(cudaSetDevice(ctx->device));
+  cudaEvent_t e0, e1;
+  NLSP_CUDA(cudaEventCreate(&e0));
+  NLSP_CUDA(cudaEventCreate(&e1));
+  double best_ms = 0.0;
+  int best_t = 0;
+  nlsp_status worst = NLSP_OK;
+  for (int c = 0; c < ncand && worst >= 0; ++c) {
+    nlsp_status st = nlsp_solve_batched(ctx, count, M, dev_b, dev_x, params, candidates[c], nullptr);  // warm
+    if (st >= 0) {
+      cudaEventRecord(e0, ctx->stream);
+      st = nlsp_solve_batched(ctx, count, M, dev_b, dev_x, params, candidates[c], nullptr);
+      cudaEventRecord(e1, ctx->stream);
+    }
+    if (st < 0) {
+      worst = st;
+      break;
+    }
+    float ms = 0.0f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      worst = NLSP_ERR_CUDA;
+      break;
+    }
+    if (ms_out) ms_out[c] = ms;
+    if (best_t == 0 || ms < best_ms) {
+      best_ms = ms;
+      best_t = candidates[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (worst < 0) return worst;
+  *best = best_t;
+  remember_tiles(ctx, batch_signature(count, M), best_t);
+  return NLSP_OK;
 }
 
 extern "C" void nlsp_free_prec(nlsp_prec* M) {

@@ -146,3 +146,21 @@ def test_build_with_device_samples_matches_uploaded_samples(ctx):
         P1, P2 = to_np(M_host.basis()), to_np(M_dev.basis())
         # same subspace: the projectors agree
         assert np.linalg.norm(P1 @ (P1.T @ P2) - P2, 2) <= (1e-9 if precision == FP64 else 1e-3)
+
+
+def test_tuner_remembers_the_fastest_team_size(ctx):
+    # nlsp_tune_batched times the candidates and the context then uses the
+    # fastest for batches of the same sizes when tiles_per_cta = 0: the
+    # result is the one an explicit call with that value gives, bit for bit
+    # (the team plan, and so every partial sum's order, is the same)
+    api = _api()
+    probs = [gen.iid_diffusion_2d(N, k, 2 * k, seed=300 + i, tol=1e-8)
+             for i, (N, k) in enumerate(zip([24, 40, 64, 33], [8, 16, 32, 12]))]
+    _, precs = _build(ctx, probs, MIXED)
+    bs = [to_dev(p.f[:, 0]) for p in probs]
+    best, ms = api.tune_batched(precs, bs, candidates=(1, 4, 1000))
+    assert best in (1, 4, 1000) and set(ms) == {1, 4, 1000} and all(v > 0 for v in ms.values())
+    xa, ra = api.solve_batched(precs, bs, tiles_per_cta=0)
+    xb, rb = api.solve_batched(precs, bs, tiles_per_cta=best)
+    for a, b, r1, r2 in zip(xa, xb, ra, rb):
+        assert r1.iterations == r2.iterations and torch.equal(a, b)
