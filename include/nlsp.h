@@ -378,6 +378,24 @@ NLSP_API nlsp_status nlsp_solve_block(nlsp_ctx* ctx, const nlsp_op* A, const nls
                                       const double* dev_B, int64_t ldb, double* dev_X, int64_t ldx,
                                       const nlsp_solve_params* params, nlsp_solve_info* infos);
 
+/* Block Krylov solve of A X = B for m <= 32 right-hand sides: the columns
+   share one search space (the block conjugate gradient of O'Leary 1980, in
+   the breakdown-free form of Ji & Li 2017: every iteration the search block
+   Z + P beta is re-orthonormalised by a pivoted Cholesky QR that drops the
+   directions whose relative pivot is below 1e-14 -- converged columns,
+   dependent right-hand sides), preconditioned by the two-level
+   preconditioner of Algorithm 1 through the same kernels as
+   nlsp_solve_block.  The paper solves each right-hand side by its own PCG;
+   this is the block-Krylov alternative.  Arguments and results as
+   nlsp_solve_block; infos[c].iterations is the block iteration at which
+   column c first met ||r_c|| <= tol ||b_c|| (the block continues until every
+   column has).  All block quantities (X, R, P, A P, the Gram matrices and
+   small solves) are FP64.  Allocates its workspace for the call.
+   Synchronises.  Errors as nlsp_solve_block. */
+NLSP_API nlsp_status nlsp_solve_block_cg(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec* M, int m,
+                                         const double* dev_B, int64_t ldb, double* dev_X, int64_t ldx,
+                                         const nlsp_solve_params* params, nlsp_solve_info* infos);
+
 /* Batched solve: instance i solves A_i x_i = b_i by PCG with its own
    preconditioner M[i] (Sec. 4 per instance; the paper solves its instances
    one after another and has no batched counterpart).  One cooperative launch

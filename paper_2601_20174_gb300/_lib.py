@@ -90,6 +90,7 @@ SIGNATURES = {
                                C.POINTER(ci), ci, C.POINTER(ci), C.POINTER(cd)]),
     "nlsp_plan_teams": (ci, [ci, C.POINTER(i64), ci, ci, C.POINTER(ci), C.POINTER(ci), C.POINTER(cd)]),
     "nlsp_solve_block": (ci, [vp, vp, vp, ci, vp, i64, vp, i64, C.POINTER(SolveParams), C.POINTER(SolveInfo)]),
+    "nlsp_solve_block_cg": (ci, [vp, vp, vp, ci, vp, i64, vp, i64, C.POINTER(SolveParams), C.POINTER(SolveInfo)]),
     "nlsp_subspace_loss": (ci, [vp, i64, ci, ci, ci, vp, vp, C.POINTER(cd), vp]),
     "nlsp_nlss_loss": (ci, [vp, i64, ci, ci, ci, vp, vp, C.POINTER(cd), vp]),
     "nlsp_unrolled_pcg": (ci, [vp, vp, vp, ci, ci, cd, ci, vp, ci, C.POINTER(cd), vp]),

@@ -272,6 +272,19 @@ class Preconditioner:
         res = [SolveResult(i.iterations, i.status, i.relres, i.true_relres) for i in infos]
         return _out_like(out, B.dim() == 1), res
 
+    def solve_block_cg(self, B: torch.Tensor, tol: float = 1e-8, maxit: int = 2000):
+        """Breakdown-free block CG for A X = B, up to 32 columns sharing one
+        search space (nlsp_solve_block_cg).  Returns (X, [SolveResult per column])."""
+        store, m = _colmajor(B, self.n)
+        out = torch.empty_like(store)
+        infos = (L.SolveInfo * m)()
+        prm = L.SolveParams(tol=tol, maxit=maxit, flexible=0, graph_mode=0)
+        st = self.ctx._lib.nlsp_solve_block_cg(self.ctx.h, self.op.h, self.h, m, _ptr(store), self.n, _ptr(out),
+                                               self.n, C.byref(prm), infos)
+        L.check(st, "nlsp_solve_block_cg", allow=(L.NLSP_OK, L.NLSP_NOT_CONVERGED, L.NLSP_ERR_BREAKDOWN))
+        res = [SolveResult(i.iterations, i.status, i.relres, i.true_relres) for i in infos]
+        return _out_like(out, B.dim() == 1), res
+
     def close(self):
         if getattr(self, "h", None):
             self.ctx._lib.nlsp_free_prec(self.h)

@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(NT) k_b_restrict_lp(StencilView<float> A, cons
                                                       float* __restrict__ cpart, int ns, BlockState* st) {
   using Sx = typename lp::Op<OP>::S;
   constexpr int ES = lp::Op<OP>::ES;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rr = lp::rows_r(k);
   const unsigned a_bytes = 128u * lp::RCH * ES;           // one A stage (128 rows)
   const unsigned chunk_bytes = (unsigned)rr * lp::RCH * ES;  // rows that the copy fills
@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(BT) k_b_prolong_lp(const unsigned char* __rest
                                                      int ns, BlockState* st) {
   using Sx = typename lp::Op<OP>::S;
   constexpr int ES = lp::Op<OP>::ES;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int kq = lp::kcols_q(k);
   const unsigned tile_bytes = (unsigned)NLSP_TILE * kq * ES;
   unsigned char* sa = smem_raw;                             // ns <= LP_NS stages
@@ -1127,10 +1127,127 @@ const StencilView<T>& bview(const nlsp_op* A) {
   return *reinterpret_cast<const StencilView<T>*>(sizeof(T) == 8 ? (const void*)&A->v64 : (const void*)&A->v32);
 }
 
+#include "block_cg.cuh"
+
 template <int KIND, typename T>
 struct BlockSolver {
+  // Breakdown-free block CG (block_cg.cuh) on the block workspace: every
+  // iteration Q = A P, the Gram products and small solves for alpha and beta,
+  // X and R updates, Z = M R through the block preconditioner kernels, and the
+  // re-orthonormalised search block.  The host reads the state word after each
+  // iteration (one small copy).
+  template <typename Prec>
+  static nlsp_status block_cg(nlsp_ctx* ctx, const nlsp_prec* M, int m, const double* B, int64_t ldb, double* X,
+                              int64_t ldx, const nlsp_solve_params* prm, nlsp_solve_info* infos, double* b,
+                              double* x, double* r, double* P, double* Q, double* z, T* rT, T* za, BlockState* bst,
+                              Prec& precond_rest, int nb, int ge) {
+    cudaStream_t s = ctx->stream;
+    const nlsp_op* A = M->A;
+    const int64_t n = A->n;
+    const StencilView<T>& AT = bview<T>(A);
+    const T omega = (T)M->omega;
+    const int nw = nb * BW;  // warp partials of the Gram products (grid nb)
+    const size_t nv = (size_t)n * MB;
+    DevBuf wbuf;
+    NLSP_TRY(wbuf.alloc(sizeof(double) * (nv + (size_t)nw * MB * MB + 6 * MB * MB) + sizeof(BcgState) + 1024));
+    double* W = wbuf.as<double>();
+    double* part = W + nv;
+    double* G1 = part + (size_t)nw * MB * MB;
+    double* G2 = G1 + MB * MB;
+    double* Dfac = G2 + MB * MB;
+    double* coef = Dfac + MB * MB;
+    double* G3 = coef + MB * MB;
+    BcgState* st = (BcgState*)(G3 + 2 * MB * MB);
+    BcgState h;
+    memset(&h, 0, sizeof(h));
+    h.m = m;
+    h.maxit = prm->maxit;
+    NLSP_CUDA(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    int launches = 0;
+    auto gram = [&](const double* Xa, const double* Yb, double* out) {
+      k_bcg_gram<<<nb, BT, 0, s>>>(Xa, Yb, n, part);
+      k_bcg_sum<<<MB, 256, 0, s>>>(part, nw, out);
+      launches += 2;
+    };
+    // R = B, X = 0; column norms; Z = M R; P = orth(Z)
+    k_b_gather<<<ge, BT, 0, s>>>(B, ldb, m, n, b);
+    NLSP_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+    NLSP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, s));
+    NLSP_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * nv, s));
+    gram(r, r, G3);
+    k_bcg_state<<<1, 32, 0, s>>>(G3, st, 0, prm->tol);
+    k_bcg_prep<KIND, T><<<nb, BT, 0, s>>>(AT, omega, r, rT, za, n);
+    launches += 3 + precond_rest(s);
+    gram(z, z, G1);
+    k_bcg_small<<<1, 1024, 0, s>>>(BCG_ORTH, G1, nullptr, Dfac, coef, st);
+    k_bcg_mm<<<nb, BT, 0, s>>>(P, nullptr, z, coef, n, 1.0, 0);
+    launches += 2;
+    NLSP_LAUNCH_CHECK();
+    NLSP_CUDA(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    NLSP_CUDA(cudaStreamSynchronize(s));
+    int it = 0;
+    while (!h.all_done && h.s > 0 && it < prm->maxit) {
+      k_b_spmv4<KIND><<<nb, BT, 0, s>>>(A->v64, P, Q, part);       // Q = A P
+      gram(P, Q, G1);                                                // D = P^T Q
+      gram(P, r, G2);                                                // P^T R
+      k_bcg_small<<<1, 1024, 0, s>>>(BCG_ALPHA, G1, G2, Dfac, coef, st);
+      k_bcg_mm<<<nb, BT, 0, s>>>(x, nullptr, P, coef, n, 1.0, 1);  // X += P alpha
+      k_bcg_mm<<<nb, BT, 0, s>>>(r, nullptr, Q, coef, n, -1.0, 1); // R -= Q alpha
+      k_bcg_tick<<<1, 32, 0, s>>>(st);
+      gram(r, r, G3);
+      k_bcg_state<<<1, 32, 0, s>>>(G3, st, 1, prm->tol);
+      launches += 6;
+      ++it;
+      NLSP_LAUNCH_CHECK();
+      NLSP_CUDA(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
+      NLSP_CUDA(cudaStreamSynchronize(s));
+      if (h.all_done || it >= prm->maxit) break;
+      k_bcg_prep<KIND, T><<<nb, BT, 0, s>>>(AT, omega, r, rT, za, n);  // Z = M R
+      launches += 1 + precond_rest(s);
+      gram(Q, z, G1);                                                   // Q^T Z
+      k_bcg_small<<<1, 1024, 0, s>>>(BCG_BETA, G1, nullptr, Dfac, coef, st);
+      k_bcg_mm<<<nb, BT, 0, s>>>(W, z, P, coef, n, 1.0, 0);             // W = Z + P beta
+      gram(W, W, G1);
+      k_bcg_small<<<1, 1024, 0, s>>>(BCG_ORTH, G1, nullptr, Dfac, coef, st);
+      k_bcg_mm<<<nb, BT, 0, s>>>(P, nullptr, W, coef, n, 1.0, 0);       // P = orth(W)
+      launches += 5;
+    }
+    // true residuals b - A x (FP64) per column, then x out
+    k_b_true<KIND><<<nb, BT, 0, s>>>(A->v64, b, x, part);
+    k_b_scatter<<<ge, BT, 0, s>>>(x, m, n, X, ldx);
+    launches += 2;
+    NLSP_LAUNCH_CHECK();
+    std::vector<double> hp((size_t)nb * MB);
+    NLSP_CUDA(cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s));
+    NLSP_CUDA(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    int herr = 0;
+    NLSP_CUDA(cudaMemcpyAsync(&herr, &bst->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NLSP_CUDA(cudaStreamSynchronize(s));
+    count_launches(ctx, (unsigned long long)launches);
+    if (herr) {
+      nlsp_record_message("block CG: a tensor-core completion wait gave up");
+      return NLSP_ERR_TIMEOUT;
+    }
+    nlsp_status worst = NLSP_OK;
+    for (int c = 0; c < m; ++c) {
+      double tr = 0.0;
+      for (int q = 0; q < nb; ++q) tr += hp[(size_t)q * MB + c];
+      int stc = h.status[c];
+      if (stc == NLSP_OK && !h.done[c]) stc = h.bad ? NLSP_ERR_BREAKDOWN : NLSP_NOT_CONVERGED;
+      if (infos) {
+        infos[c].iterations = h.iter[c];
+        infos[c].status = stc;
+        infos[c].relres = h.bb[c] > 0 ? sqrt(h.rr[c] / h.bb[c]) : 0.0;
+        infos[c].true_relres = h.bb[c] > 0 ? sqrt(tr / h.bb[c]) : 0.0;
+      }
+      if (stc == NLSP_ERR_BREAKDOWN) worst = NLSP_ERR_BREAKDOWN;
+      else if (stc == NLSP_NOT_CONVERGED && worst == NLSP_OK) worst = NLSP_NOT_CONVERGED;
+    }
+    return worst;
+  }
+
   static nlsp_status run(nlsp_ctx* ctx, const nlsp_prec* M, int m, const double* B, int64_t ldb, double* X,
-                         int64_t ldx, const nlsp_solve_params* prm, nlsp_solve_info* infos) {
+                         int64_t ldx, const nlsp_solve_params* prm, nlsp_solve_info* infos, bool krylov) {
     cudaStream_t s = ctx->stream;
     const nlsp_op* A = M->A;
     const int64_t n = A->n, n_pad = M->n_pad;
@@ -1255,14 +1372,11 @@ struct BlockSolver {
     // z = B r.  In the iteration the update kernel forms x, r with alpha and
     // then rT and the first pre-sweep; for the initial application alpha = 0
     // leaves x and r as they are.
-    auto apply = [&](cudaStream_t ss, bool with_rr) -> int {
+    // the preconditioner after the first pre-sweep (za holds it): the other
+    // pre-sweeps, restriction, coarse solve, prolongation, post-sweeps; the
+    // last one writes z in FP64 with the per-column r^T z partials
+    auto precond_rest = [&](cudaStream_t ss) -> int {
       int nl = 0;
-      k_b_update<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, x, r, p, q, rT, za, st, part);
-      ++nl;
-      if (with_rr) {  // r^T r of the updated residual: convergence, maxit
-        k_b_scalars<<<1, 1024, 0, ss>>>(part, nb, st, BS_RR);
-        ++nl;
-      }
       T* cur = za;
       T* oth = zb;
       for (int sw = 1; sw < nu; ++sw, ++nl) {
@@ -1292,10 +1406,26 @@ struct BlockSolver {
         std::swap(cur, oth);
       }
       k_b_post4<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, rT, cur, r, z, part);
-      k_b_scalars<<<1, 1024, 0, ss>>>(part, nb, st, BS_RZ);
-      nl += 2;
-      return nl;
+      return nl + 1;
     };
+    auto apply = [&](cudaStream_t ss, bool with_rr) -> int {
+      int nl = 0;
+      k_b_update<KIND, T><<<nb, BT, 0, ss>>>(AT, omega, x, r, p, q, rT, za, st, part);
+      ++nl;
+      if (with_rr) {  // r^T r of the updated residual: convergence, maxit
+        k_b_scalars<<<1, 1024, 0, ss>>>(part, nb, st, BS_RR);
+        ++nl;
+      }
+      nl += precond_rest(ss);
+      k_b_scalars<<<1, 1024, 0, ss>>>(part, nb, st, BS_RZ);
+      return nl + 1;
+    };
+    if (krylov) {
+      const nlsp_status bst = block_cg(ctx, M, m, B, ldb, X, ldx, prm, infos, b, x, r, p, q, z, rT, za, st,
+                                       precond_rest, nb, ge);
+      NLSP_CUDA(cudaStreamSynchronize(s));
+      return bst;
+    }
     launches += apply(s, false);
     NLSP_LAUNCH_CHECK();
     // one iteration: p = z + beta p, q = A p, alpha, update, z = B r, beta
@@ -1379,9 +1509,11 @@ struct BlockSolver {
 
 }  // namespace
 
-extern "C" nlsp_status nlsp_solve_block(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec* M, int m,
-                                        const double* dev_B, int64_t ldb, double* dev_X, int64_t ldx,
-                                        const nlsp_solve_params* params, nlsp_solve_info* infos) {
+namespace {
+
+nlsp_status solve_block_any(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec* M, int m, const double* dev_B,
+                            int64_t ldb, double* dev_X, int64_t ldx, const nlsp_solve_params* params,
+                            nlsp_solve_info* infos, bool krylov) {
   if (!ctx || !A || !M || !params || M->A != A || m < 0 || m > MB || ldb < A->n || ldx < A->n) return NLSP_ERR_INVALID;
   if (m > 0 && (!dev_B || !dev_X)) return NLSP_ERR_INVALID;
   if (!(params->tol >= 0.0) || params->maxit < 1 || M->r > 128) return NLSP_ERR_INVALID;
@@ -1389,16 +1521,30 @@ extern "C" nlsp_status nlsp_solve_block(nlsp_ctx* ctx, const nlsp_op* A, const n
   NLSP_CUDA(cudaSetDevice(ctx->device));
   if (M->precision == NLSP_FP64) {
     switch (A->kind) {
-      case ST_5PT: return BlockSolver<ST_5PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
-      case ST_9PT: return BlockSolver<ST_9PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
-      case ST_CSR: return BlockSolver<ST_CSR, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
-      default: return BlockSolver<ST_7PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
+      case ST_5PT: return BlockSolver<ST_5PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos, krylov);
+      case ST_9PT: return BlockSolver<ST_9PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos, krylov);
+      case ST_CSR: return BlockSolver<ST_CSR, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos, krylov);
+      default: return BlockSolver<ST_7PT, double>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos, krylov);
     }
   }
   switch (A->kind) {
-    case ST_5PT: return BlockSolver<ST_5PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
-    case ST_9PT: return BlockSolver<ST_9PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
-    case ST_CSR: return BlockSolver<ST_CSR, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
-    default: return BlockSolver<ST_7PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos);
+    case ST_5PT: return BlockSolver<ST_5PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos, krylov);
+    case ST_9PT: return BlockSolver<ST_9PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos, krylov);
+    case ST_CSR: return BlockSolver<ST_CSR, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos, krylov);
+    default: return BlockSolver<ST_7PT, float>::run(ctx, M, m, dev_B, ldb, dev_X, ldx, params, infos, krylov);
   }
+}
+
+}  // namespace
+
+extern "C" nlsp_status nlsp_solve_block(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec* M, int m,
+                                        const double* dev_B, int64_t ldb, double* dev_X, int64_t ldx,
+                                        const nlsp_solve_params* params, nlsp_solve_info* infos) {
+  return solve_block_any(ctx, A, M, m, dev_B, ldb, dev_X, ldx, params, infos, false);
+}
+
+extern "C" nlsp_status nlsp_solve_block_cg(nlsp_ctx* ctx, const nlsp_op* A, const nlsp_prec* M, int m,
+                                           const double* dev_B, int64_t ldb, double* dev_X, int64_t ldx,
+                                           const nlsp_solve_params* params, nlsp_solve_info* infos) {
+  return solve_block_any(ctx, A, M, m, dev_B, ldb, dev_X, ldx, params, infos, true);
 }

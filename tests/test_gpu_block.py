@@ -183,3 +183,71 @@ def test_block_reduced_precision_anisotropic_256(ctx, precision):
     for c in range(p.f.shape[1]):
         true = np.linalg.norm(p.f[:, c] - A @ X[:, c]) / np.linalg.norm(p.f[:, c])
         assert res[c].status == 0 and true <= 1e-8 * 1.01, (c, res[c], true)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_block_cg_matches_oracle_block_cg(ctx, name):
+    # breakdown-free block CG (shared search space): FP64 with the oracle's
+    # basis reproduces the oracle's block CG (iterations per column +-1,
+    # solution 1e-7); mixed precision reaches the FP64 true residual
+    from oracle import setup as osetup
+    api = _api()
+    p = CASES[name]()
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    B = gen.rhs_uniform(p.n, 6, seed=41)
+    apply_B = opcg.two_level_solver(A, ref["P"], ref["L"], p.omega, p.nu, p.nu)
+    Xo, its_o, true_o = opcg.block_cg(A, apply_B, B, 1e-8)
+    Aop = api.Operator.from_problem(ctx, p)
+    M = api.Preconditioner.from_basis(Aop, to_dev(ref["P"]), p.nu, p.omega, FP64)
+    X, res = M.solve_block_cg(to_dev(B), tol=1e-8)
+    X = to_np(X)
+    for c in range(B.shape[1]):
+        true = np.linalg.norm(B[:, c] - A @ X[:, c]) / np.linalg.norm(B[:, c])
+        assert res[c].status == 0 and true <= 1e-8 * 1.01, (c, res[c], true)
+        assert abs(res[c].iterations - its_o[c]) <= 1, (c, res[c].iterations, its_o[c])
+        assert abs(res[c].true_relres - true) <= 1e-3 * true + 1e-14
+    assert rel(X, Xo) <= 1e-7
+    Mm = api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, MIXED)
+    Y, rm = Mm.solve_block_cg(to_dev(B), tol=1e-8)
+    Y = to_np(Y)
+    for c in range(B.shape[1]):
+        true = np.linalg.norm(B[:, c] - A @ Y[:, c]) / np.linalg.norm(B[:, c])
+        assert rm[c].status == 0 and true <= 1e-8 * 1.01
+
+
+def test_block_cg_deflation_and_maxit(ctx):
+    api = _api()
+    p = CASES["grf5"]()
+    A = op.assemble(p)
+    Aop = api.Operator.from_problem(ctx, p)
+    M = api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, FP64)
+    b, b2 = p.f[:, 0], gen.rhs_uniform(p.n, 1, seed=7)[:, 0]
+    B = np.stack([b, 2.0 * b, np.zeros(p.n), b2], axis=1)
+    X, res = M.solve_block_cg(to_dev(B), tol=1e-9)
+    X = to_np(X)
+    assert res[2].iterations == 0 and res[2].status == 0 and np.all(X[:, 2] == 0)
+    assert rel(X[:, 1], 2.0 * X[:, 0]) <= 1e-8
+    for c in (0, 1, 3):
+        assert res[c].status == 0
+        assert np.linalg.norm(B[:, c] - A @ X[:, c]) / np.linalg.norm(B[:, c]) <= 1e-9 * 1.01
+    _, r3 = M.solve_block_cg(to_dev(B[:, [0, 3]]), tol=1e-14, maxit=3)
+    assert all(r.status == 1 for r in r3)
+
+
+def test_block_cg_fewer_iterations_than_independent_columns(ctx):
+    # the shared block space: no column needs more block iterations than its
+    # own PCG, on the 256^2 anisotropic 9-point problem with 16 columns
+    api = _api()
+    p = gen.aniso_9pt_2d(N=128, k=32, K=64, m=16, seed=5, tol=1e-8)
+    A = op.assemble(p)
+    Aop = api.Operator.from_problem(ctx, p)
+    M = api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, FP64)
+    X, res = M.solve_block_cg(to_dev(p.f), tol=1e-8, maxit=5000)
+    _, res1 = M.solve_block(to_dev(p.f), tol=1e-8, maxit=5000)
+    X = to_np(X)
+    for c in range(p.f.shape[1]):
+        true = np.linalg.norm(p.f[:, c] - A @ X[:, c]) / np.linalg.norm(p.f[:, c])
+        assert res[c].status == 0 and true <= 1e-8 * 1.01
+        assert res[c].iterations <= res1[c].iterations + 1
+    assert max(r.iterations for r in res) < max(r.iterations for r in res1)

@@ -89,3 +89,52 @@ def test_breakdown_on_indefinite_operator():
     st = su.build(A, p.S0, p.k, p.omega, p.s1)
     res = pcg.pcg(-A, pcg.two_level_solver(A, st["P"], st["L"], p.omega, 2, 2), p.f[:, 0], 1e-8)
     assert res["status"] == "breakdown"
+
+
+def _grf_setup():
+    from oracle import operator as op, setup as su
+    p = gen.grf_diffusion_2d(N=24, k=8, K=20, seed=31)
+    A = op.assemble(p)
+    st = su.build(A, p.S0, p.k, p.omega, p.s1)
+    return p, A, pcg.two_level_solver(A, st["P"], st["L"], p.omega, p.nu, p.nu)
+
+
+def test_block_cg_one_column_is_pcg():
+    p, A, apply_B = _grf_setup()
+    b = p.f[:, 0]
+    o = pcg.pcg(A, apply_B, b, 1e-10)
+    X, its, true = pcg.block_cg(A, apply_B, b[:, None], 1e-10)
+    assert its[0] == o["iters"]
+    assert np.linalg.norm(X[:, 0] - o["x"]) <= 1e-10 * np.linalg.norm(o["x"])
+
+
+def test_block_cg_needs_no_more_iterations_than_each_column():
+    p, A, apply_B = _grf_setup()
+    Bm = gen.rhs_uniform(p.n, 6, seed=5)
+    X, its, true = pcg.block_cg(A, apply_B, Bm, 1e-8)
+    single = [pcg.pcg(A, apply_B, Bm[:, c], 1e-8)["iters"] for c in range(6)]
+    assert np.all(true <= 1e-8 * 1.01)
+    assert max(its) <= max(single) and np.all(its <= np.array(single))
+    assert max(its) < max(single)  # the shared space helps on this problem
+
+
+def test_block_cg_deflates_dependent_and_zero_columns():
+    p, A, apply_B = _grf_setup()
+    b, b2 = p.f[:, 0], gen.rhs_uniform(p.n, 1, seed=7)[:, 0]
+    Bm = np.stack([b, 2.0 * b, np.zeros(p.n), b2], axis=1)
+    X, its, true = pcg.block_cg(A, apply_B, Bm, 1e-9)
+    assert its[2] == 0 and np.all(X[:, 2] == 0)
+    assert np.linalg.norm(X[:, 1] - 2.0 * X[:, 0]) <= 1e-9 * np.linalg.norm(X[:, 1])
+    assert np.all(true[[0, 1, 3]] <= 1e-9 * 1.01)
+
+
+def test_block_cg_exact_on_tiny_grid():
+    from oracle import operator as op
+    p = gen.poisson_2d(4, 4, 8, seed=2)
+    A = op.assemble(p)
+    Bm = gen.rhs_uniform(p.n, 3, seed=3)
+    ident = lambda R: R.copy()  # no preconditioner: plain block CG
+    X, its, true = pcg.block_cg(A, ident, Bm, 1e-12, maxit=50)
+    ref = np.linalg.solve(A.toarray(), Bm)
+    assert np.max(np.abs(X - ref)) <= 1e-10 * np.max(np.abs(ref))
+    assert max(its) <= p.n // 3 + 2  # block Krylov: about n / m steps in exact arithmetic
