@@ -142,9 +142,9 @@ __device__ __forceinline__ V4<T> stencil_apply4(const StencilView<T>& A, int64_t
     const T d = A.diag[idx];
 #pragma unroll
     for (int q = 0; q < 4; ++q) s.v[q] = d * x0.v[q];
-    const int64_t sl = idx >> 5;
-    const int64_t base = A.soff[sl] + (idx & 31);
-    const int wd = (int)((A.soff[sl + 1] - A.soff[sl]) >> 5);
+    int64_t base;
+    int wd;
+    csr_row(A, idx, &base, &wd);
     for (int j = 0; j < wd; ++j) {
       const int64_t e = base + 32 * (int64_t)j;
       const T a = A.sval[e];

@@ -66,13 +66,20 @@ inline int64_t pad_tile(int64_t n) { return (n + NLSP_TILE - 1) / NLSP_TILE * NL
 
 enum StencilKind { ST_5PT = 0, ST_9PT = 1, ST_7PT = 2, ST_CSR = 3 };
 
-// Row slices of the general sparse operator: 32 consecutive rows (one warp)
-// share one slice whose off-diagonal entries are stored column by column
-// (sliced ELLPACK): entry j of row i sits at soff[i / 32] + 32 j + i % 32, so
-// a warp working on 32 consecutive rows reads each of its j-th entries as one
-// coalesced 128-byte (index) / 256-byte (FP64 value) access.  A slice is as
-// wide as its longest row; shorter rows are padded with (own row, 0).
+// Row slices of the general sparse operator (sliced ELLPACK with sorting
+// windows, "SELL-C-sigma"): within each window of NLSP_SIGMA consecutive rows
+// the rows are ordered by decreasing length, and every 32 consecutive
+// positions of that order form a slice whose off-diagonal entries are stored
+// column by column: entry j of the row at position p sits at
+// soff[p / 32] + 32 j + p % 32, so a warp on 32 consecutive positions reads
+// each of its j-th entries as one coalesced 128-byte (index) / 256-byte (FP64
+// value) access.  A slice is as wide as its longest row; shorter rows are
+// padded with (own row, 0).  Sorting within windows keeps the padding small
+// (rows of similar length share slices) while a window's rows stay close in
+// memory.  ppos[i] is the position of row i, prow[p] the row at position p
+// (-1 past the last row).
 constexpr int NLSP_SLICE = 32;
+constexpr int NLSP_SIGMA = 256;
 
 // Matrix-free view of A in one precision.
 //  5-point / 7-point: positive edge weights (h^-2 included) to the +x, +y, +z
@@ -95,6 +102,7 @@ struct StencilView {
   T c[5];
   T cdinv;  // 1 / c[0] for the 9-point stencil
   const int64_t* soff;  // slice offsets (n / 32 rounded up, plus one)
+  const int* ppos;      // position of each row in the sliced order
   const int* scol;      // column of each sliced entry
   const T* sval;        // value of each sliced entry
 };
@@ -136,9 +144,12 @@ struct nlsp_op {
   double* a64;  // one allocation: diag, cx, cy, cz, dinv (n each); general
                 // sparse: diag, dinv (n each), then the sliced entries
   float* a32;
-  void* sidx;   // general sparse: slice offsets (int64) and entry columns (int32)
+  void* sidx;   // general sparse: slice offsets (int64), row positions and the
+                // row at each position (int32), entry columns (int32)
   int64_t nnz;  // general sparse: stored entries of the CSR input
   int64_t sliced;  // general sparse: sliced off-diagonal entries (with padding)
+  const int* prow;  // general sparse: row at each slice position (-1: none)
+  int64_t npos;     // general sparse: slice positions (n rounded up to 32)
   double c9[5];
   StencilView<double> v64;
   StencilView<float> v32;

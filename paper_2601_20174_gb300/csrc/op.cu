@@ -211,24 +211,16 @@ __global__ void k_csr_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ r
   }
 }
 
-// Width of each 32-row slice: its longest row's off-diagonal count.
-__global__ void k_slice_width(int64_t n, const int* __restrict__ cnt, int* __restrict__ width, int64_t nslices) {
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslices; s += (int64_t)gridDim.x * blockDim.x) {
-    int w = 0;
-    for (int64_t i = s * NLSP_SLICE; i < n && i < (s + 1) * NLSP_SLICE; ++i) w = max(w, cnt[i]);
-    width[s] = w;
-  }
-}
-
-// Scatters each row's off-diagonal entries into its slice (entry j of row i
-// at soff[i / 32] + 32 j + i % 32) and pads the row to the slice width with
-// (own row, 0).
+// Scatters each row's off-diagonal entries into its slice (entry j of the
+// row at position p at soff[p / 32] + 32 j + p % 32) and pads the row to the
+// slice width with (own row, 0).
 __global__ void k_csr_fill(int64_t n, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
-                           const double* __restrict__ val, const int64_t* __restrict__ soff, int* __restrict__ scol,
-                           double* __restrict__ sval) {
+                           const double* __restrict__ val, const int64_t* __restrict__ soff,
+                           const int* __restrict__ ppos, int* __restrict__ scol, double* __restrict__ sval) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t sl = i / NLSP_SLICE;
-    const int64_t base = soff[sl] + i % NLSP_SLICE;
+    const int p = ppos[i];
+    const int64_t sl = p / NLSP_SLICE;
+    const int64_t base = soff[sl] + p % NLSP_SLICE;
     const int w = (int)((soff[sl + 1] - soff[sl]) / NLSP_SLICE);
     int c = 0;
     for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
@@ -242,6 +234,42 @@ __global__ void k_csr_fill(int64_t n, const int64_t* __restrict__ rowptr, const 
       scol[base + (int64_t)NLSP_SLICE * c] = (int)i;
       sval[base + (int64_t)NLSP_SLICE * c] = 0.0;
     }
+  }
+}
+
+// y = A x for the general sparse operator in position order: thread per
+// slice position, so each warp's j-th entries are one coalesced access; the
+// row's result goes to y[prow[p]] (rows of one sorting window stay within a
+// few cache lines).  Column-batched over blockIdx.y like k_apply_cols.
+__global__ void __launch_bounds__(256) k_csr_spmv(StencilView<double> A, const int* __restrict__ prow, int64_t npos,
+                                                  const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
+                                                  int64_t ldy) {
+  const double* x = X + blockIdx.y * ldx;
+  double* y = Y + blockIdx.y * ldy;
+  const double* __restrict__ sval = A.sval;
+  const int* __restrict__ scol = A.scol;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npos; p += (int64_t)gridDim.x * blockDim.x) {
+    const int i = prow[p];
+    const int64_t sl = p >> 5;
+    const int64_t s0 = A.soff[sl];
+    const int64_t base = s0 + (p & 31);
+    const int w = (int)((A.soff[sl + 1] - s0) >> 5);
+    double s = 0.0;
+    int j = 0;
+    for (; j + 4 <= w; j += 4) {  // four entries' loads in flight
+      const int64_t e = base + 32 * (int64_t)j;
+      const int c0 = __ldg(scol + e), c1 = __ldg(scol + e + 32), c2 = __ldg(scol + e + 64), c3 = __ldg(scol + e + 96);
+      const double v0 = __ldg(sval + e), v1 = __ldg(sval + e + 32), v2 = __ldg(sval + e + 64), v3 = __ldg(sval + e + 96);
+      s = fma(v0, x[c0], s);
+      s = fma(v1, x[c1], s);
+      s = fma(v2, x[c2], s);
+      s = fma(v3, x[c3], s);
+    }
+    for (; j < w; ++j) {
+      const int64_t e = base + 32 * (int64_t)j;
+      s = fma(__ldg(sval + e), x[__ldg(scol + e)], s);
+    }
+    if (i >= 0) y[i] = fma(A.diag[i], x[i], s);
   }
 }
 
@@ -361,30 +389,28 @@ extern "C" nlsp_status nlsp_assemble_csr(nlsp_ctx* ctx, int64_t n, int64_t nnz, 
   op->nnz = nnz;
   cudaStream_t s = ctx->stream;
   const int64_t nsl = (n + NLSP_SLICE - 1) / NLSP_SLICE;
-  DevBuf tmp;  // row counts (n), slice widths (nsl), error word
+  DevBuf tmp;  // row counts (n), error word
   auto fail = [&](nlsp_status e) {
     nlsp_free_op(op);
     return e;
   };
-  nlsp_status st = tmp.alloc(sizeof(int) * (size_t)(n + nsl + 1));
+  nlsp_status st = tmp.alloc(sizeof(int) * (size_t)(n + 1));
   if (st != NLSP_OK) return fail(st);
   int* cnt = tmp.as<int>();
-  int* width = cnt + n;
-  int* bad = width + nsl;
+  int* bad = cnt + n;
   DevBuf dd;  // diagonal and inverse before the final allocation is sized
   if ((st = dd.alloc(sizeof(double) * 2 * (size_t)n)) != NLSP_OK) return fail(st);
   if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
   const int g = grid_for(ctx, n, 256, 8);
   k_csr_rows<<<g, 256, 0, s>>>(n, nnz, dev_rowptr, (const int*)dev_col, dev_val, cnt, dd.as<double>(),
                                dd.as<double>() + n, bad);
-  k_slice_width<<<grid_for(ctx, nsl, 256, 8), 256, 0, s>>>(n, cnt, width, nsl);
-  count_launches(ctx, 2);
+  count_launches(ctx, 1);
   if (cudaGetLastError() != cudaSuccess) return fail(NLSP_ERR_CUDA);
-  std::vector<int> hw((size_t)nsl + 1);
-  if (cudaMemcpyAsync(hw.data(), width, sizeof(int) * (size_t)(nsl + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  std::vector<int> hc((size_t)n + 1);
+  if (cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * (size_t)(n + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return fail(NLSP_ERR_CUDA);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
-  const int hbad = hw[(size_t)nsl];
+  const int hbad = hc[(size_t)n];
   if (hbad) {
     nlsp_record_message((hbad & 4) ? "nlsp_assemble_csr: row pointers are not monotone from 0 to nnz"
                         : (hbad & 1) ? "nlsp_assemble_csr: a column index is outside [0, n)"
@@ -392,25 +418,46 @@ extern "C" nlsp_status nlsp_assemble_csr(nlsp_ctx* ctx, int64_t n, int64_t nnz, 
                                      : "nlsp_assemble_csr: a diagonal entry is missing, non-positive or non-finite");
     return fail(NLSP_ERR_INVALID);
   }
+  // positions: rows of each window of NLSP_SIGMA ordered by decreasing
+  // off-diagonal count (ties by row), then slice widths and offsets
+  const int64_t npos = nsl * NLSP_SLICE;
+  std::vector<int> prow((size_t)npos, -1), ppos((size_t)n);
+  for (int64_t w0 = 0; w0 < n; w0 += NLSP_SIGMA) {
+    const int64_t w1 = std::min<int64_t>(n, w0 + NLSP_SIGMA);
+    for (int64_t i = w0; i < w1; ++i) prow[(size_t)i] = (int)i;
+    std::stable_sort(prow.begin() + w0, prow.begin() + w1, [&](int a, int b) { return hc[(size_t)a] > hc[(size_t)b]; });
+    for (int64_t q = w0; q < w1; ++q) ppos[(size_t)prow[(size_t)q]] = (int)q;
+  }
   std::vector<int64_t> soff((size_t)nsl + 1);
   soff[0] = 0;
-  for (int64_t q = 0; q < nsl; ++q) soff[(size_t)q + 1] = soff[(size_t)q] + (int64_t)NLSP_SLICE * hw[(size_t)q];
+  for (int64_t q = 0; q < nsl; ++q) {
+    int wmax = 0;
+    for (int64_t p = q * NLSP_SLICE; p < (q + 1) * NLSP_SLICE && p < n; ++p) wmax = std::max(wmax, hc[(size_t)prow[(size_t)p]]);
+    soff[(size_t)q + 1] = soff[(size_t)q] + (int64_t)NLSP_SLICE * wmax;
+  }
   const int64_t sliced = soff[(size_t)nsl];
   op->sliced = sliced;
   const size_t nval = (size_t)(2 * n + sliced);
   if (cudaMalloc(&op->a64, sizeof(double) * nval) != cudaSuccess) return fail(NLSP_ERR_OOM);
   if (cudaMalloc(&op->a32, sizeof(float) * nval) != cudaSuccess) return fail(NLSP_ERR_OOM);
-  const size_t idx_bytes = sizeof(int64_t) * (size_t)(nsl + 1) + sizeof(int) * (size_t)std::max<int64_t>(sliced, 1);
+  const size_t idx_bytes = sizeof(int64_t) * (size_t)(nsl + 1) + sizeof(int) * (size_t)(n + npos) +
+                           sizeof(int) * (size_t)std::max<int64_t>(sliced, 1);
   if (cudaMalloc(&op->sidx, idx_bytes) != cudaSuccess) return fail(NLSP_ERR_OOM);
   int64_t* d_soff = (int64_t*)op->sidx;
-  int* d_scol = (int*)(d_soff + nsl + 1);
+  int* d_ppos = (int*)(d_soff + nsl + 1);
+  int* d_prow = d_ppos + n;
+  int* d_scol = d_prow + npos;
+  op->prow = d_prow;
+  op->npos = npos;
   if (cudaMemsetAsync(op->a64, 0, sizeof(double) * nval, s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
   if (cudaMemsetAsync(op->sidx, 0, idx_bytes, s) != cudaSuccess) return fail(NLSP_ERR_CUDA);
   if (cudaMemcpyAsync(op->a64, dd.p, sizeof(double) * 2 * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return fail(NLSP_ERR_CUDA);
-  if (cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(d_ppos, ppos.data(), sizeof(int) * ppos.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(d_prow, prow.data(), sizeof(int) * prow.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return fail(NLSP_ERR_CUDA);
-  k_csr_fill<<<g, 256, 0, s>>>(n, dev_rowptr, (const int*)dev_col, dev_val, d_soff, d_scol, op->a64 + 2 * n);
+  k_csr_fill<<<g, 256, 0, s>>>(n, dev_rowptr, (const int*)dev_col, dev_val, d_soff, d_ppos, d_scol, op->a64 + 2 * n);
   k_to_float<<<grid_for(ctx, (int64_t)nval, 256, 8), 256, 0, s>>>(op->a64, op->a32, (int64_t)nval);
   count_launches(ctx, 2);
   if (cudaGetLastError() != cudaSuccess) return fail(NLSP_ERR_CUDA);
@@ -426,6 +473,7 @@ extern "C" nlsp_status nlsp_assemble_csr(nlsp_ctx* ctx, int64_t n, int64_t nnz, 
   w.dinv = op->a32 + n;
   w.sval = op->a32 + 2 * n;
   v.soff = w.soff = d_soff;
+  v.ppos = w.ppos = d_ppos;
   v.scol = w.scol = d_scol;
   *A_out = op;
   return NLSP_OK;
@@ -443,7 +491,10 @@ extern "C" nlsp_status nlsp_op_apply(nlsp_ctx* ctx, const nlsp_op* A, int m, con
   switch (A->kind) {
     case ST_5PT: k_apply_cols<ST_5PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
     case ST_9PT: k_apply_cols<ST_9PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
-    case ST_CSR: k_apply_cols<ST_CSR><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
+    case ST_CSR:
+      k_csr_spmv<<<dim3(grid_for(ctx, A->npos, 256, 8), m), 256, 0, ctx->stream>>>(A->v64, A->prow, A->npos, dev_X,
+                                                                                   ldx, dev_Y, ldy);
+      break;
     default: k_apply_cols<ST_7PT><<<g, 256, 0, ctx->stream>>>(A->v64, m, dev_X, ldx, dev_Y, ldy); break;
   }
   count_launches(ctx, 1);

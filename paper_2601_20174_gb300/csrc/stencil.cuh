@@ -33,6 +33,17 @@ __device__ __forceinline__ NodeCoord node_coord(int64_t idx, int N) {
   return c;
 }
 
+// Entries of row idx of the general sparse operator: first entry at *base,
+// the following ones 32 apart, *w of them (the row's slice width).
+template <typename T>
+__device__ __forceinline__ void csr_row(const StencilView<T>& A, int64_t idx, int64_t* base, int* w) {
+  const int p = A.ppos[idx];
+  const int sl = p >> 5;
+  const int64_t s0 = A.soff[sl];
+  *base = s0 + (p & 31);
+  *w = (int)((A.soff[sl + 1] - s0) >> 5);
+}
+
 template <int KIND, typename T>
 __device__ __forceinline__ T stencil_diag(const StencilView<T>& A, int64_t idx) {
   return KIND == ST_9PT ? A.c[0] : A.diag[idx];
@@ -50,9 +61,9 @@ __device__ __forceinline__ T stencil_apply(const StencilView<T>& A, int64_t idx,
   const int N = A.N;
   if (KIND == ST_CSR) {
     T s = A.diag[idx] * get(idx);
-    const int64_t sl = idx >> 5;
-    const int64_t base = A.soff[sl] + (idx & 31);
-    const int w = (int)((A.soff[sl + 1] - A.soff[sl]) >> 5);
+    int64_t base;
+    int w;
+    csr_row(A, idx, &base, &w);
     for (int j = 0; j < w; ++j) {
       const int64_t e = base + 32 * (int64_t)j;
       s += A.sval[e] * get((int64_t)A.scol[e]);  // padding: (own row, 0)
@@ -94,9 +105,9 @@ template <int KIND, typename T, typename F>
 __device__ __forceinline__ void for_each_neighbour(const StencilView<T>& A, int64_t idx, NodeCoord c, F f) {
   const int N = A.N;
   if (KIND == ST_CSR) {
-    const int64_t sl = idx >> 5;
-    const int64_t base = A.soff[sl] + (idx & 31);
-    const int wd = (int)((A.soff[sl + 1] - A.soff[sl]) >> 5);
+    int64_t base;
+    int wd;
+    csr_row(A, idx, &base, &wd);
     for (int j = 0; j < wd; ++j) {
       const int64_t e = base + 32 * (int64_t)j;
       const int64_t m = A.scol[e];
