@@ -34,9 +34,29 @@ def main() -> int:
     ap.add_argument("--K", type=int, default=128)
     ap.add_argument("--mode", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--block", action="store_true", help="block PCG on the anisotropic 9-point workload")
+    ap.add_argument("--csr-spmv", action="store_true",
+                    help="sparse SpMV (nlsp_op_apply) on the FEM diffusion matrix of an N x N jittered mesh")
     ap.add_argument("--adjoint", action="store_true",
                     help="subspace loss and T=10 unrolled-PCG loss with gradients on the 3D 7-point N^3 workload")
     args = ap.parse_args()
+    if args.csr_spmv:
+        import ctypes as C
+        from . import fem
+        pts, tri = fem.mesh(args.N, 0)
+        ip, ix, dv, _ = fem.family_matrix("diffusion", pts, tri, args.N, 0)
+        ctx = api.Context(0)
+        A = api.Operator.from_csr(ctx, torch.as_tensor(ip), torch.as_tensor(ix), torch.as_tensor(dv))
+        n = A.n
+        x = torch.randn(n, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(args.iters):
+            L.check(ctx._lib.nlsp_op_apply(ctx.h, A.h, 1, C.c_void_p(x.data_ptr()), n, C.c_void_p(y.data_ptr()), n),
+                    "nlsp_op_apply")
+        torch.cuda.synchronize()
+        print(f"profile case (csr spmv): n={n} nnz={ix.size} launches={args.iters}")
+        A.close()
+        ctx.close()
+        return 0
     if args.adjoint:
         import ctypes as C
         p = gen.iid_diffusion_3d(args.N, args.k, args.K, seed=0, with_samples=False)
