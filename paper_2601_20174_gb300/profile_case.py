@@ -9,6 +9,9 @@ solver's per-phase times are printed (microseconds per iteration).
 
     python -m paper_2601_20174_gb300.profile_case [--precision mixed|fp64] [--iters 4] [--N 512] [--mode 0|1|2]
 
+With --fem FAMILY a P1 finite-element system of the paper's Appendix (CSR
+input) replaces it.
+
 With --block the 2D rotated anisotropic 9-point workload (N^2 nodes, k from K
 device-drawn samples, 32 right-hand sides) runs --iters iterations of the
 block PCG instead (--precision bf16 / tf32: reduced-precision tensor-core
@@ -36,6 +39,9 @@ def main() -> int:
     ap.add_argument("--block", action="store_true", help="block PCG on the anisotropic 9-point workload")
     ap.add_argument("--csr-spmv", action="store_true",
                     help="sparse SpMV (nlsp_op_apply) on the FEM diffusion matrix of an N x N jittered mesh")
+    ap.add_argument("--fem", default=None, choices=["diffusion", "anisotropic", "screened_poisson", "heat", "wave"],
+                    help="P1 finite-element family on an N x N jittered mesh (k = 48 from K = 72, nu = 5, "
+                         "omega = 0.66, tol 1e-6), CSR input, solved with --mode")
     ap.add_argument("--adjoint", action="store_true",
                     help="subspace loss and T=10 unrolled-PCG loss with gradients on the 3D 7-point N^3 workload")
     args = ap.parse_args()
@@ -95,14 +101,21 @@ def main() -> int:
         A.close()
         ctx.close()
         return 0
-    p = gen.grf_diffusion_2d(args.N, args.k, args.K, seed=0)
     ctx = api.Context(0)
-    A = api.Operator.from_problem(ctx, p)
-    S0 = torch.as_tensor(np.ascontiguousarray(p.S0.T)).cuda()
     prec = L.NLSP_MIXED_FP32 if args.precision == "mixed" else L.NLSP_FP64
+    if args.fem:
+        from . import fem
+        p = fem.fem_problem(args.fem, N=args.N, seed=0)
+        A = api.Operator.from_csr(ctx, torch.as_tensor(p.indptr), torch.as_tensor(p.indices), torch.as_tensor(p.data))
+        tol = p.tol
+    else:
+        p = gen.grf_diffusion_2d(args.N, args.k, args.K, seed=0)
+        A = api.Operator.from_problem(ctx, p)
+        tol = 1e-8
+    S0 = torch.as_tensor(np.ascontiguousarray(p.S0.T)).cuda()
     M = api.Preconditioner.build(A, S0.t(), p.k, p.s1, p.nu, p.omega, prec)
     f = torch.as_tensor(p.f[:, 0].copy()).cuda()
-    _, res = M.solve(f, tol=1e-8, maxit=args.iters, graph_mode=args.mode)
+    _, res = M.solve(f, tol=tol, maxit=args.iters, graph_mode=args.mode)
     torch.cuda.synchronize()
     print(f"profile case: n={p.n} k={p.k} iterations={res[0].iterations} status={res[0].status}")
     if args.mode == 2:
