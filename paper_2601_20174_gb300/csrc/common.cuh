@@ -150,6 +150,7 @@ struct nlsp_op {
   int64_t sliced;  // general sparse: sliced off-diagonal entries (with padding)
   const int* prow;  // general sparse: row at each slice position (-1: none)
   int64_t npos;     // general sparse: slice positions (n rounded up to 32)
+  int wmax;         // general sparse: most off-diagonal entries of a row
   double c9[5];
   StencilView<double> v64;
   StencilView<float> v32;

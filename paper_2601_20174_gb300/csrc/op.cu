@@ -428,6 +428,8 @@ extern "C" nlsp_status nlsp_assemble_csr(nlsp_ctx* ctx, int64_t n, int64_t nnz, 
     std::stable_sort(prow.begin() + w0, prow.begin() + w1, [&](int a, int b) { return hc[(size_t)a] > hc[(size_t)b]; });
     for (int64_t q = w0; q < w1; ++q) ppos[(size_t)prow[(size_t)q]] = (int)q;
   }
+  op->wmax = 0;
+  for (int64_t i = 0; i < n; ++i) op->wmax = std::max(op->wmax, hc[(size_t)i]);
   std::vector<int64_t> soff((size_t)nsl + 1);
   soff[0] = 0;
   for (int64_t q = 0; q < nsl; ++q) {

@@ -2,10 +2,17 @@
 // preconditioner of Algorithm 1): one thread-block cluster of C <= 16 CTAs
 // (one per SM) keeps every vector of the solve and its rows of P in shared
 // memory for the whole solve.  Rank q of the cluster owns nodes
-// [q nl, (q + 1) nl); stencil or sparse neighbours owned by another rank are
-// read through distributed shared memory (generic addresses of the cluster's
-// shared-memory window), and the phases of an iteration are separated by the
-// cluster's hardware barrier instead of a grid barrier through L2.  Scalars
+// [q nl, (q + 1) nl) and copies its rows of A once into shared memory as a
+// rank-local ELL block (entry j of local row i at j nlp + i: the value and a
+// reference to the neighbour, owner rank and index within the owner, resolved
+// once), together with D^-1 and A_c^-1; after that an iteration reads only
+// shared memory, its own and, for neighbours owned by another rank, the
+// owner's through distributed shared memory (generic addresses of the
+// cluster's shared-memory window).  Global memory is not touched inside the
+// loop: every cluster barrier acquires at cluster scope, which would send
+// cached global reads back to L2 in every phase.  The phases of an iteration
+// are separated by the cluster's hardware barrier instead of a grid barrier
+// through L2.  Scalars
 // (p^T q, r^T r, r^T z) and the coarse right-hand side P^T rho are added up by
 // every rank from all ranks' partials in rank order, so all ranks take
 // identical decisions (stop, breakdown, maxit) and pass the same sequence of
@@ -37,17 +44,33 @@ struct ClusterArgs {
   double* x;
   const void* P;     // tiled P (precision T), k columns
   const void* Ainv;  // A_c^-1, r x r column-major (precision T)
+  int ew;            // ELL width: most off-diagonal entries of a row
+  int rg;            // threads per column of the restriction (power of two <= 32)
+  int lc;            // lanes per column of the coarse solve (power of two <= 16)
+  int ainv_smem;     // A_c^-1 is copied into shared memory
   PcgState* st;
   unsigned long long* ptimes;  // optional: rank 0's time between marks, ns (slots 14 + mark)
 };
 
-// Dynamic shared memory of one rank: 5 FP64 vectors (x, r, p, q, z), 3
-// vectors in the preconditioner precision (rT, w0, w1), the rank's rows of P
-// (r x nlp) and the coarse vectors (partial, total, correction: 3 r).
+// Off-diagonal entries per row of the stencil kinds (the sparse kind takes
+// the operator's widest row).
+template <int KIND>
+__host__ __device__ constexpr int cluster_stencil_width() {
+  return KIND == ST_5PT ? 4 : KIND == ST_7PT ? 6 : KIND == ST_9PT ? 8 : 0;
+}
+
+// Dynamic shared memory of one rank, FP64 arrays first: 5 FP64 vectors (x, r,
+// p, q, z), the ELL values and diagonal in FP64 when T is narrower; then in
+// precision T 3 vectors (rT, w0, w1), the rank's rows of P (r x nlp), the
+// coarse vectors (partial, total, correction: 3 r), the ELL values, diagonal
+// and D^-1, A_c^-1 (r x r, when copied); then the ELL references (int).
 template <typename T>
-__host__ __device__ inline size_t cluster_smem(int nl, int nlp, int r) {
-  return (size_t)5 * nl * sizeof(double) + (size_t)3 * nl * sizeof(T) + (size_t)r * nlp * sizeof(T) +
-         (size_t)3 * r * sizeof(T) + 64;
+__host__ __device__ inline size_t cluster_smem(int nl, int nlp, int r, int ew, bool ainv) {
+  const size_t wide = sizeof(T) < sizeof(double) ? (size_t)ew * nlp + nl : 0;
+  return ((size_t)5 * nl + wide) * sizeof(double) +
+         ((size_t)3 * nl + (size_t)r * nlp + (size_t)3 * r + (size_t)ew * nlp + 2 * (size_t)nl +
+          (ainv ? (size_t)r * r : 0)) * sizeof(T) +
+         (size_t)ew * nlp * sizeof(int) + 64;
 }
 
 // Scalars of the solve, kept in shared memory and updated by thread 0 only:
@@ -62,7 +85,7 @@ struct ClScalars {
 template <int KIND, typename T>
 __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, StencilView<T> AT, T omega,
                                                        ClusterArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double slot[8];             // this rank's published partials
   __shared__ double red[CT];              // per-thread partials of a CTA sum
   __shared__ double stot[8];             // cluster totals of the slots (thread 0)
@@ -78,6 +101,9 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
   const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks();
   const int tid = threadIdx.x;
   const int nl = a.nl, nlp = a.nlp, r = a.r;
+  constexpr int EW = cluster_stencil_width<KIND>();
+  const int ew = EW ? EW : a.ew;
+  constexpr bool narrow = sizeof(T) < sizeof(double);
   const int lo = rank * nl;
   const int cnt = max(0, min((int)a.n, lo + nl) - lo);
   double* xv = reinterpret_cast<double*>(smem_raw);
@@ -85,13 +111,24 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
   double* pv = rv + nl;
   double* qv = pv + nl;
   double* zv = qv + nl;
-  T* rT = reinterpret_cast<T*>(zv + nl);
+  double* e64 = zv + nl;               // ELL values in FP64 (narrow T only)
+  double* d64 = e64 + (narrow ? (size_t)ew * nlp : 0);
+  T* rT = reinterpret_cast<T*>(d64 + (narrow ? nl : 0));
   T* w0 = rT + nl;
   T* w1 = w0 + nl;
   T* Pl = w1 + nl;           // Pl[j * nlp + i]
   T* cpart = Pl + (size_t)r * nlp;
   T* ctot = cpart + r;
   T* ev = ctot + r;
+  T* eT = ev + r;            // ELL values in T: eT[j * nlp + i]
+  T* dT = eT + (size_t)ew * nlp;
+  T* diT = dT + nl;          // D^-1
+  T* As = diT + nl;          // A_c^-1 (column-major), when copied
+  int* eref = reinterpret_cast<int*>(As + (a.ainv_smem ? (size_t)r * r : 0));
+  if (!narrow) {  // FP64 preconditioner: one copy of the values serves both
+    e64 = reinterpret_cast<double*>(eT);
+    d64 = reinterpret_cast<double*>(dT);
+  }
   if (tid < C) {
     rp_x[tid] = cl.map_shared_rank(xv, tid);
     rp_p[tid] = cl.map_shared_rank(pv, tid);
@@ -101,13 +138,19 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
     rp_c[tid] = cl.map_shared_rank(cpart, tid);
     rp_slot[tid] = cl.map_shared_rank(&slot[0], tid);
   }
-  // node m of the cluster-distributed vector with per-rank bases `base`
-  // (own nodes straight from this rank's shared memory)
-  auto at = [&](auto* const* base, int64_t m) {
-    const int mi = (int)m;
-    if (mi >= lo && mi < lo + nl) return base[rank][mi - lo];
-    const int o = mi / nl;
-    return base[o][mi - o * nl];
+  // (A v)_i of local row i from the ELL block: values `val`, diagonal `dg`,
+  // this rank's vector `own`, the ranks' vectors `rem` (own rows straight
+  // from this rank's shared memory)
+  auto ell = [&](auto* own, auto* const* rem, const auto* val, const auto* dg, int i) {
+    auto s = dg[i] * own[i];
+#pragma unroll 4
+    for (int j = 0; j < ew; ++j) {
+      const int rf = eref[j * nlp + i];
+      const int o = rf >> 16;
+      const auto* bp = o == rank ? own : rem[o];
+      s += val[j * nlp + i] * bp[rf & 0xffff];
+    }
+    return s;
   };
   // Cross-rank totals of the slots in `mask` into stot: warp sl reads slot
   // sl of rank q in lane q (remote reads in parallel) and adds them by a
@@ -123,18 +166,21 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
     }
     __syncthreads();
   };
-  // this rank's partial of a sum over its nodes into slot `sl`: warp sums,
-  // then warp 0 adds the 16 warp sums (two shuffle trees)
+  // this rank's partial of a sum over its nodes into slot `sl`: every thread
+  // stores its value, warp 0 adds the values of the warps that hold rows
+  // column by column and then its 32 lane sums by a shuffle tree.  One FP64
+  // add per value instead of the five of a shuffle tree in every warp: GB300
+  // executes FP64 at 1/64 of the FP32 rate, and threads without rows hold 0.
+  const int nact = (min(cnt, CT) + 31) >> 5;
   auto partial = [&](double v, int sl) {
-    const int w = tid >> 5, lane = tid & 31;
-    v = warp_sum(v);
     __syncthreads();  // red is free again
-    if (lane == 0) red[w] = v;
+    red[tid] = v;
     __syncthreads();
-    if (w == 0) {
-      double t = lane < CT / 32 ? red[lane] : 0.0;
+    if (tid < 32) {
+      double t = red[tid];
+      for (int w = 1; w < nact; ++w) t += red[w * 32 + tid];
       t = warp_sum(t);
-      if (lane == 0) slot[sl] = t;
+      if (tid == 0) slot[sl] = t;
     }
   };
   // phase marks (NLSP_PHASE_TIMERS=1): time since the previous mark, rank 0
@@ -166,6 +212,38 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
     const int j = e / cnt, i = e - j * cnt;
     Pl[j * nlp + i] = Pg[tiled_index(lo + i, j, a.k)];
   }
+  if (a.ainv_smem)
+    for (int e = tid; e < r * r; e += CT) As[e] = Ainv[e];
+  // the rank's rows as an ELL block: neighbours in the order the operator
+  // visits them, then (own row, 0) up to the width
+  for (int i = tid; i < cnt; i += CT) {
+    const int64_t g = lo + i;
+    int j = 0;
+    for_each_neighbour<KIND>(AT, g, node_coord<KIND>(g, AT.N), [&](int64_t m, NodeCoord, T v) {
+      if (j < ew) {
+        const int o = (int)(m / nl);
+        eref[j * nlp + i] = (o << 16) | (int)(m - (int64_t)o * nl);
+        eT[j * nlp + i] = v;
+      }
+      ++j;
+    });
+    for (; j < ew; ++j) {
+      eref[j * nlp + i] = (rank << 16) | i;
+      eT[j * nlp + i] = T(0);
+    }
+    dT[i] = stencil_diag<KIND>(AT, g);
+    diT[i] = stencil_dinv<KIND>(AT, g);
+    if (narrow) {
+      int j2 = 0;
+      for_each_neighbour<KIND>(A64, g, node_coord<KIND>(g, A64.N), [&](int64_t, NodeCoord, double v) {
+        if (j2 < ew) e64[j2 * nlp + i] = v;
+        ++j2;
+      });
+      for (; j2 < ew; ++j2) e64[j2 * nlp + i] = 0.0;
+      d64[i] = stencil_diag<KIND>(A64, g);
+    }
+  }
+  const T* Ac = a.ainv_smem ? As : Ainv;
   partial(bb, 4);
   cl.sync();
   gather(1u << 4);
@@ -198,9 +276,8 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
     for (int sw = 1; sw < a.nu1; ++sw) {
       cl.sync();
       for (int i = tid; i < cnt; i += CT) {
-        const int64_t g = lo + i;
-        const T az = stencil_apply<KIND>(AT, g, node_coord<KIND>(g, AT.N), [&](int64_t m) { return at(rc, m); });
-        oth[i] = cur[i] + omega * stencil_dinv<KIND>(AT, g) * (rT[i] - az);
+        const T az = ell(cur, rc, eT, dT, i);
+        oth[i] = cur[i] + omega * diT[i] * (rT[i] - az);
       }
       T* t = cur; cur = oth; oth = t;
       T* const* tt = rc; rc = ro; ro = tt;
@@ -210,48 +287,49 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
     mark(4);
     // rho = rT - A cur into oth (nobody reads oth in this phase)
     for (int i = tid; i < cnt; i += CT) {
-      const int64_t g = lo + i;
-      const T az = stencil_apply<KIND>(AT, g, node_coord<KIND>(g, AT.N), [&](int64_t m) { return at(rc, m); });
-      oth[i] = rT[i] - az;
+      oth[i] = rT[i] - ell(cur, rc, eT, dT, i);
     }
     __syncthreads();
     mark(5);
-    // restriction partial: c_j = sum over the rank's nodes of P_ij rho_i, four
-    // threads per column
-    for (int base = 0; base < 4 * r; base += CT) {  // uniform trip count: whole warps shuffle
+    // restriction partial: c_j = sum over the rank's nodes of P_ij rho_i, rg
+    // threads per column (rg a power of two <= 32, so a column's threads are
+    // lanes of one warp)
+    const int rg = a.rg;
+    for (int base = 0; base < rg * r; base += CT) {  // uniform trip count: whole warps shuffle
       const int jj = base + tid;
-      const int j = jj >> 2, part = jj & 3;
+      const int j = jj / rg, part = jj & (rg - 1);
       T s = T(0);
       if (j < r)
-        for (int i = part; i < cnt; i += 4) s += Pl[j * nlp + i] * oth[i];
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
+        for (int i = part; i < cnt; i += rg) s += Pl[j * nlp + i] * oth[i];
+      for (int off = rg >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
       if (part == 0 && j < r) cpart[j] = s;
     }
     mark(6);
     cl.sync();
     mark(7);
-    // c = sum of the ranks' partials and e = A_c^-1 c, 16 lanes per column
-    // (shuffle trees keep the dependent FP64 chains short)
-    for (int base = 0; base < 16 * r; base += CT) {  // uniform trip count: whole warps shuffle
-      const int j = (base + tid) >> 4, q = tid & 15;
-      T v = (j < r && q < C) ? rp_c[q][j] : T(0);
-      v += __shfl_xor_sync(0xffffffffu, v, 8);
-      v += __shfl_xor_sync(0xffffffffu, v, 4);
-      v += __shfl_xor_sync(0xffffffffu, v, 2);
-      v += __shfl_xor_sync(0xffffffffu, v, 1);
+    // c = sum of the ranks' partials and e = A_c^-1 c, lc lanes per column
+    // (lc a power of two <= 16; each lane adds the ranks q, q + lc, ... and
+    // the rows q, q + lc, ... of A_c^-1, then a shuffle tree over the lanes,
+    // in the same order on every rank)
+    const int lc = a.lc;
+    for (int base = 0; base < lc * r; base += CT) {  // uniform trip count: whole warps shuffle
+      const int jj = base + tid;
+      const int j = jj / lc, q = jj & (lc - 1);
+      T v = T(0);
+      if (j < r)
+#pragma unroll 4
+        for (int o = q; o < C; o += lc) v += rp_c[o][j];
+      for (int off = lc >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       if (q == 0 && j < r) ctot[j] = v;
     }
     __syncthreads();
-    for (int base = 0; base < 16 * r; base += CT) {
-      const int j = (base + tid) >> 4, q = tid & 15;
+    for (int base = 0; base < lc * r; base += CT) {
+      const int jj = base + tid;
+      const int j = jj / lc, q = jj & (lc - 1);
       T v = T(0);
       if (j < r)
-        for (int l = q; l < r; l += 16) v += Ainv[(int64_t)l * r + j] * ctot[l];
-      v += __shfl_xor_sync(0xffffffffu, v, 8);
-      v += __shfl_xor_sync(0xffffffffu, v, 4);
-      v += __shfl_xor_sync(0xffffffffu, v, 2);
-      v += __shfl_xor_sync(0xffffffffu, v, 1);
+        for (int l = q; l < r; l += lc) v += Ac[(int64_t)l * r + j] * ctot[l];
+      for (int off = lc >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       if (q == 0 && j < r) ev[j] = v;
     }
     __syncthreads();
@@ -269,9 +347,8 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
       cl.sync();
       const bool last = sw == a.nu2;
       for (int i = tid; i < cnt; i += CT) {
-        const int64_t g = lo + i;
-        const T az = stencil_apply<KIND>(AT, g, node_coord<KIND>(g, AT.N), [&](int64_t m) { return at(rc, m); });
-        const T v = cur[i] + omega * stencil_dinv<KIND>(AT, g) * (rT[i] - az);
+        const T az = ell(cur, rc, eT, dT, i);
+        const T v = cur[i] + omega * diT[i] * (rT[i] - az);
         if (last) {
           const double zn = (double)v;
           pzo += rv[i] * zv[i];
@@ -295,8 +372,7 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
   auto direction = [&](double bt) {
     double s = 0.0;
     for (int i = tid; i < cnt; i += CT) {
-      const int64_t g = lo + i;
-      const double az = stencil_apply<KIND>(A64, g, node_coord<KIND>(g, A64.N), [&](int64_t m) { return at(rp_z, m); });
+      const double az = ell(zv, rp_z, e64, d64, i);
       const double pn = zv[i] + bt * pv[i];
       const double qn = az + bt * qv[i];
       pv[i] = pn;
@@ -307,7 +383,7 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
   };
 
   if (!cs.done) {
-    for (int i = tid; i < cnt; i += CT) w0[i] = omega * stencil_dinv<KIND>(AT, lo + i) * rT[i];
+    for (int i = tid; i < cnt; i += CT) w0[i] = omega * diT[i] * rT[i];
     precondition();
     cl.sync();
     gather(1u << 2);
@@ -347,7 +423,7 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
       rv[i] = ri;
       const T rt = (T)ri;
       rT[i] = rt;
-      w0[i] = omega * stencil_dinv<KIND>(AT, lo + i) * rt;
+      w0[i] = omega * diT[i] * rt;
       s += ri * ri;
     }
     partial(s, 1);
@@ -391,9 +467,7 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(StencilView<double> A64, 
   cl.sync();
   double tr = 0.0;
   for (int i = tid; i < cnt; i += CT) {
-    const int64_t g = lo + i;
-    const double ax = stencil_apply<KIND>(A64, g, node_coord<KIND>(g, A64.N), [&](int64_t m) { return at(rp_x, m); });
-    const double d = a.b[g] - ax;
+    const double d = a.b[lo + i] - ell(xv, rp_x, e64, d64, i);
     tr += d * d;
   }
   partial(tr, 5);

@@ -2052,7 +2052,15 @@ struct Solver {
   // vectors and P rows of about n / C nodes, preferring C with at most ~96
   // nodes per rank (the FP64 work of a rank is what an iteration waits for).
   // Off with NLSP_CLUSTER=0.  Returns false when the system does not fit.
-  static bool cluster_plan(const nlsp_prec* M, int* C, int* nl, int* nlp, size_t* smem) {
+  struct ClusterPlan {
+    int C, nl, nlp, ew, ainv;
+    size_t smem;
+  };
+
+  // Cluster size and shared-memory layout of the cluster-resident solver, or
+  // false when the system does not fit one cluster (the grid-wide persistent
+  // kernel then runs).  A_c^-1 is copied into shared memory when it still fits.
+  static bool cluster_plan(const nlsp_prec* M, ClusterPlan* pl) {
     const char* env = getenv("NLSP_CLUSTER");
     if (env && env[0] == '0') return false;
     if (M->n > 16 * 4096) return false;
@@ -2062,35 +2070,39 @@ struct Solver {
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, (const void*)k_pcg_cluster<KIND, T>) != cudaSuccess) return false;
     const size_t avail = (size_t)optin - fa.sharedSizeBytes - 1024;
+    const int ew = KIND == ST_CSR ? M->A->wmax : cluster_stencil_width<KIND>();
+    if (ew < 0 || ew > 64) return false;
     int c = 1;
     while (c < CL_MAX && (M->n + c - 1) / c > 96) c *= 2;
     const char* csz = getenv("NLSP_CLUSTER_SIZE");  // a fixed cluster size (1, 2, 4, 8 or 16)
     if (csz && atoi(csz) >= 1 && atoi(csz) <= CL_MAX && (atoi(csz) & (atoi(csz) - 1)) == 0) c = atoi(csz);
     for (; c <= CL_MAX; c *= 2) {
       const int l = (int)((M->n + c - 1) / c);
+      if (l > 32767) continue;  // node references keep the index within the owner in 16 bits
       const int lp = l | 1;
-      const size_t need = cluster_smem<T>(l, lp, M->r);
-      if (need <= avail) {
-        *C = c;
-        *nl = l;
-        *nlp = lp;
-        *smem = need;
-        return true;
+      for (int ainv = 1; ainv >= 0; --ainv) {
+        const size_t need = cluster_smem<T>(l, lp, M->r, ew, ainv != 0);
+        if (need <= avail) {
+          *pl = ClusterPlan{c, l, lp, ew, ainv, need};
+          return true;
+        }
       }
     }
     return false;
   }
 
   static nlsp_status launch_cluster(nlsp_prec* M, const double* b, double* xout, const nlsp_solve_params* prm,
-                                    int flexible, PcgState* st_out, int C, int nl, int nlp, size_t smem) {
+                                    int flexible, PcgState* st_out, const ClusterPlan& pl) {
+    const int C = pl.C;
+    const size_t smem = pl.smem;
     nlsp_ctx* ctx = M->ctx;
     auto fn = k_pcg_cluster<KIND, T>;
     NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     ClusterArgs a;
     a.n = M->n;
-    a.nl = nl;
-    a.nlp = nlp;
+    a.nl = pl.nl;
+    a.nlp = pl.nlp;
     a.k = M->k;
     a.r = M->r;
     a.nu1 = M->nu1;
@@ -2102,6 +2114,12 @@ struct Solver {
     a.x = xout;
     a.P = M->P;
     a.Ainv = M->AinvT;
+    a.ew = pl.ew;
+    a.ainv_smem = pl.ainv;
+    a.rg = 1;
+    while (a.rg < 32 && 2 * a.rg * M->r <= CT) a.rg *= 2;
+    a.lc = 1;
+    while (a.lc < CL_MAX && 2 * a.lc * M->r <= CT) a.lc *= 2;
     a.st = st_out;
     a.ptimes = M->pcg ? M->pcg->ptimes : nullptr;
     cudaLaunchConfig_t cfg;
@@ -2179,12 +2197,11 @@ struct Solver {
     PcgWork* w = M->pcg;
     if (prm->graph_mode == 2) {
       const int flexible = prm->flexible < 0 ? (M->precision != NLSP_FP64) : (prm->flexible != 0);
-      int C = 0, nl = 0, nlp = 0;
-      size_t csmem = 0;
-      const bool clus = cluster_plan(M, &C, &nl, &nlp, &csmem);
+      ClusterPlan pl{};
+      const bool clus = cluster_plan(M, &pl);
       for (int col = 0; col < m; ++col) {
         if (clus)
-          NLSP_TRY(launch_cluster(M, B + col * ldb, X + col * ldx, prm, flexible, w->st_all + col, C, nl, nlp, csmem));
+          NLSP_TRY(launch_cluster(M, B + col * ldb, X + col * ldx, prm, flexible, w->st_all + col, pl));
         else
           NLSP_TRY(launch_persistent(M, B + col * ldb, X + col * ldx, prm, flexible, w->st_all + col));
       }
