@@ -450,6 +450,214 @@ __global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Eigen-decomposition of the positive semi-definite Gram matrix for the FP32
+// preconditioner, one CTA, FP32: pivoted Cholesky G = L L^T (the largest
+// remaining diagonal first; it stops where the pivot is no longer positive),
+// then one-sided (Hestenes) Jacobi on the columns of L: plane rotations from
+// the right make them mutually orthogonal, L W = U Sigma with W orthogonal,
+// so G = U Sigma^2 U^T: the normalised columns are eigenvectors and their
+// squared norms the eigenvalues, and W is never formed.  L is the transposed
+// triangular factor of a column-pivoted QR of the samples, the starting point
+// of the preconditioned Jacobi SVD of Drmac and Veselic (SIAM J. Matrix Anal.
+// Appl. 29, 2008).  A round rotates disjoint pairs of the round-robin
+// ordering, one warp per pair with its lanes holding rows, so a round needs
+// no per-element bookkeeping and no eigenvector accumulation.  Eigenpairs
+// beyond the numerical rank come out as zeros; K <= 128.
+// ---------------------------------------------------------------------------
+constexpr int CE_THREADS = 512;
+constexpr int CE_MAX_SWEEPS = 32;
+
+// Rows of a column, padded to whole 32-row groups (one float4 per lane of an
+// eight-lane pair group and group).
+__host__ __device__ constexpr int chol_eig_ldx(int K) { return (K + 31) / 32 * 32; }
+
+// Dynamic shared memory: two buffers of the trailing matrix (K x (K + 1)),
+// later reused for the pair table; the factor L (K columns of
+// chol_eig_ldx(K) rows); positions' original indices (two buffers); column
+// norms.
+__host__ __device__ constexpr size_t chol_eig_smem(int K) {
+  return (size_t)2 * K * (K + 1) * 4 + (size_t)K * chol_eig_ldx(K) * 4 + (size_t)K * 12 + 64;
+}
+
+// NV = chol_eig_ldx(K) / 32 float4 per lane and column.
+template <int NV>
+__global__ void __launch_bounds__(CE_THREADS) k_chol_jacobi_eig(const double* __restrict__ G, int K, float tol,
+                                                                double* __restrict__ evals,
+                                                                double* __restrict__ V) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LD = K + 1, LDX = 32 * NV;
+  float* cur = reinterpret_cast<float*>(smem_raw);  // trailing matrix, lower triangle, by position
+  float* nxt = cur + K * LD;
+  float* X = nxt + K * LD;                          // X[c * LDX + i]: column c of L, row = original index
+  int* oc = reinterpret_cast<int*>(X + K * LDX);    // original index of each position (two buffers)
+  int* on = oc + K;
+  float* lam = reinterpret_cast<float*>(on + K);
+  uchar2* pairs = reinterpret_cast<uchar2*>(smem_raw);  // after the factorisation
+  __shared__ int rotated[CE_MAX_SWEEPS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = CE_THREADS / 32;
+  for (int e = tid; e < K * K; e += CE_THREADS) {
+    const int i = e / K, m = e - i * K;
+    if (m <= i) cur[i * LD + m] = (float)G[(int64_t)m * K + i];
+  }
+  for (int e = tid; e < K * LDX; e += CE_THREADS) X[e] = 0.0f;
+  for (int i = tid; i < K; i += CE_THREADS) oc[i] = i;
+  for (int i = tid; i < CE_MAX_SWEEPS; i += CE_THREADS) rotated[i] = 0;
+  __syncthreads();
+  // entry (x, y) of the symmetric trailing matrix from its lower triangle;
+  // the index is selected, not the load, so lanes do not diverge
+  auto sym = [&](const float* a, int x, int y) { return a[max(x, y) * LD + min(x, y)]; };
+
+  // pivoted Cholesky; step j moves the pivot to position j (rows and columns
+  // of the trailing matrix are read through the swap, the new trailing
+  // matrix goes to the other buffer)
+  int r = K;
+  float d0 = 0.0f;
+  for (int j = 0; j < K; ++j) {
+    // every warp finds the pivot itself: largest diagonal, ties by position
+    float best = -1.0f;
+    int bi = j;
+    for (int i = j + lane; i < K; i += 32) {
+      const float v = cur[i * LD + i];
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    const int p = bi;
+    const float d = best;
+    if (j == 0) d0 = d;
+    if (!(d > 0.0f) || !(d >= 1e-30f * d0)) {  // (NaN fails too) numerical rank reached
+      r = j;
+      break;
+    }
+    const float sd = sqrtf(d), isd = 1.0f / sd, id = 1.0f / d;
+    const int t = tid >> 2, sub = tid & 3;  // four threads per trailing row
+    const int i = j + 1 + t;
+    if (i < K) {
+      const int si = i == p ? j : i;
+      const int oi = oc[si];  // the row's original index
+      const float lip = sym(cur, si, p);
+      if (sub == 0) {
+        on[i] = oi;
+        X[j * LDX + oi] = lip * isd;
+      }
+      const float f = lip * id;
+#pragma unroll 4
+      for (int m = j + 1 + sub; m <= i; m += 4) {
+        const int sm = m == p ? j : m;
+        nxt[i * LD + m] = fmaf(-f, sym(cur, sm, p), sym(cur, si, sm));
+      }
+    }
+    if (tid == 0) X[j * LDX + oc[p]] = sd;
+    __syncthreads();
+    float* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    int* ti = oc;
+    oc = on;
+    on = ti;
+  }
+
+  // one-sided Jacobi on the r columns of L.  Eight lanes rotate one pair
+  // (lane g holds rows 4g..4g+3 of every 32-row group), four pairs per warp;
+  // the round-robin pairs of every round are tabulated first.
+  const int R = r + (r & 1), H = R / 2;
+  for (int e = tid; e < (R - 1) * H; e += CE_THREADS) {
+    int pp, qq;
+    rr_pair(R, e / H, e % H, &pp, &qq);
+    pairs[e] = make_uchar2((unsigned char)pp, (unsigned char)qq);
+  }
+  __syncthreads();
+  const int g = lane & 7;
+  const int u = warp * 4 + (lane >> 3);  // this group's pair (K <= 128: one pass)
+  for (int sweep = 0; sweep < CE_MAX_SWEEPS && R >= 2; ++sweep) {
+    for (int rd = 0; rd < R - 1; ++rd) {
+      int p = R, q = R;
+      if (u < H) {
+        const uchar2 pq = pairs[rd * H + u];
+        p = pq.x;
+        q = pq.y;
+      }
+      const bool act = p < r && q < r;  // (the padding column of an odd rank stays)
+      float4 vp[NV], vq[NV];
+      float a = 0.0f, b = 0.0f, c = 0.0f;
+      if (act) {
+        const float4* xp = reinterpret_cast<const float4*>(X + p * LDX) + g;
+        const float4* xq = reinterpret_cast<const float4*>(X + q * LDX) + g;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          vp[v] = xp[8 * v];
+          vq[v] = xq[8 * v];
+          a = fmaf(vp[v].x, vp[v].x, fmaf(vp[v].y, vp[v].y, fmaf(vp[v].z, vp[v].z, fmaf(vp[v].w, vp[v].w, a))));
+          b = fmaf(vq[v].x, vq[v].x, fmaf(vq[v].y, vq[v].y, fmaf(vq[v].z, vq[v].z, fmaf(vq[v].w, vq[v].w, b))));
+          c = fmaf(vp[v].x, vq[v].x, fmaf(vp[v].y, vq[v].y, fmaf(vp[v].z, vq[v].z, fmaf(vp[v].w, vq[v].w, c))));
+        }
+      }
+      // butterfly within the eight-lane group: identical sums in its lanes
+      for (int off = 1; off < 8; off <<= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
+        c += __shfl_xor_sync(0xffffffffu, c, off);
+      }
+      if (act && fabsf(c) > tol * sqrtf(a) * sqrtf(b)) {
+        // the rotation zeroing the pair's inner product (Rutishauser's
+        // formulas); |zeta| is capped so that zeta^2 stays finite
+        const float zeta = __fdividef(b - a, 2.0f * c);
+        const float z = fminf(fabsf(zeta), 1e18f);
+        const float w = fmaf(z, z, 1.0f);
+        const float tt = copysignf(__frcp_rn(z + w * rsqrtf(w)), zeta);
+        const float cs = rsqrtf(fmaf(tt, tt, 1.0f)), sn = cs * tt;
+        float4* xp = reinterpret_cast<float4*>(X + p * LDX) + g;
+        float4* xq = reinterpret_cast<float4*>(X + q * LDX) + g;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float4 P0 = vp[v], Q0 = vq[v];
+          xp[8 * v] = make_float4(cs * P0.x - sn * Q0.x, cs * P0.y - sn * Q0.y, cs * P0.z - sn * Q0.z,
+                                  cs * P0.w - sn * Q0.w);
+          xq[8 * v] = make_float4(sn * P0.x + cs * Q0.x, sn * P0.y + cs * Q0.y, sn * P0.z + cs * Q0.z,
+                                  sn * P0.w + cs * Q0.w);
+        }
+        if (g == 0) rotated[sweep] = 1;
+      }
+      __syncthreads();
+    }
+    if (!rotated[sweep]) break;  // written only in this sweep, read after its last barrier
+  }
+
+  // eigenvalues = squared column norms, sorted descending (ties by column)
+  for (int c = warp; c < r; c += NW) {
+    float s = 0.0f;
+    for (int i = lane; i < K; i += 32) s = fmaf(X[c * LDX + i], X[c * LDX + i], s);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) lam[c] = s;
+  }
+  __syncthreads();
+  for (int c = warp; c < K; c += NW) {
+    if (c < r) {
+      const float lc = lam[c];
+      int pos = 0;
+      for (int b2 = lane; b2 < r; b2 += 32) pos += (lam[b2] > lc) || (lam[b2] == lc && b2 < c);
+      for (int off = 16; off > 0; off >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, off);
+      const float inv = lc > 0.0f ? 1.0f / sqrtf(lc) : 0.0f;
+      if (lane == 0) evals[pos] = (double)lc;
+      for (int i = lane; i < K; i += 32) V[(int64_t)pos * K + i] = (double)(X[c * LDX + i] * inv);
+    } else {
+      if (lane == 0) evals[c] = 0.0;
+      for (int i = lane; i < K; i += 32) V[(int64_t)c * K + i] = 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Small dense FP64 products for the K x K refinement: C = op(A) * B, all
 // column-major K x K; one block per output column.
 // ---------------------------------------------------------------------------
@@ -945,11 +1153,31 @@ nlsp_status alloc_prec_storage(nlsp_prec* M) {
   return NLSP_OK;
 }
 
+// Launches the pivoted-Cholesky / one-sided Jacobi eigensolver (K <= 128).
+nlsp_status chol_jacobi_eig(cudaStream_t s, const double* G, int K, double* evals, double* V) {
+  const size_t sm = chol_eig_smem(K);
+  const int nv = chol_eig_ldx(K) / 32;
+  const void* fn = nv == 1   ? (const void*)k_chol_jacobi_eig<1>
+                   : nv == 2 ? (const void*)k_chol_jacobi_eig<2>
+                   : nv == 3 ? (const void*)k_chol_jacobi_eig<3>
+                             : (const void*)k_chol_jacobi_eig<4>;
+  NLSP_TRY(set_smem(fn, sm));
+  const float tol = 4e-6f;
+  void* args[] = {(void*)&G, (void*)&K, (void*)&tol, (void*)&evals, (void*)&V};
+  NLSP_CUDA(cudaLaunchKernel(fn, dim3(1), dim3(CE_THREADS), args, sm, s));
+  return NLSP_OK;
+}
+
 // Eigen-decomposition of the FP64 Gram matrix G (K x K): descending evals and
 // eigenvectors V (column-major).  refine = number of FP64 refinement steps.
 // work: 6 K^2 + K doubles.
 nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double* evals, double* V, double* work) {
   cudaStream_t s = ctx->stream;
+  if (refine == 0 && K <= 128) {  // FP32 preconditioner: pivoted Cholesky + one-sided Jacobi
+    NLSP_TRY(chol_jacobi_eig(s, G, K, evals, V));
+    count_launches(ctx, 1);
+    return NLSP_OK;
+  }
   const int KP = K + (K & 1);
   const size_t sm = jacobi_smem(KP);
   NLSP_TRY(set_smem((const void*)k_jacobi_eig, sm));

@@ -190,6 +190,59 @@ def test_setup_fp64_subspace_sigma_and_galerkin(ctx, name):
 
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
+def test_setup_mixed_sigma_and_subspace(ctx, name):
+    # FP32 preconditioner: the Gram matrix is decomposed in FP32 (pivoted
+    # Cholesky, then one-sided Jacobi on the factor); sigma and span(P)
+    # against the oracle's SVD to FP32 accuracy
+    p = PROBLEMS[name]()
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    M = _api().Preconditioner.build(_api().Operator.from_problem(ctx, p), to_dev(p.S0), p.k, p.s1, p.nu, p.omega,
+                                    MIXED)
+    sig = to_np(M.sigma())
+    s_ref = ref["sigma"]
+    assert np.all(np.abs(sig[: p.k + 1] - s_ref[: p.k + 1]) <= 1e-4 * s_ref[0]), (sig[: p.k + 1] - s_ref[: p.k + 1])
+    gap = (s_ref[p.k - 1] ** 2 - s_ref[p.k] ** 2) / s_ref[0] ** 2
+    Q = np.linalg.qr(to_np(M.basis()))[0]
+    assert projector_dist(Q, ref["P"]) <= max(1e-3, 1e-6 / gap)
+
+
+@pytest.mark.parametrize("K,k", [(7, 3), (3, 3), (1, 1)])
+def test_setup_mixed_odd_and_tiny_sample_counts(ctx, K, k):
+    p = gen.grf_diffusion_2d(N=30, k=k, K=K, seed=21, tol=1e-8)
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    Aop = _api().Operator.from_problem(ctx, p)
+    M = _api().Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, MIXED)
+    sig = to_np(M.sigma())
+    assert np.all(np.abs(sig[:K] - ref["sigma"][:K]) <= 1e-4 * ref["sigma"][0])
+    x, res = M.solve(to_dev(p.f[:, 0]), tol=1e-8)
+    assert res[0].status == 0
+
+
+def test_setup_mixed_rank_deficient_samples(ctx):
+    # K = 2k samples whose second half repeats the first: G = S^T S has rank k,
+    # the factorisation stops at the numerical rank and the top k eigenpairs
+    # are those of the distinct half
+    p = PROBLEMS["grf5"]()
+    A = op.assemble(p)
+    half = p.S0[:, : p.K // 2]
+    S0 = np.concatenate([half, half], axis=1)
+    k = min(p.k, p.K // 2)
+    ref = osetup.build(A, half, k, p.omega, p.s1)
+    Aop = _api().Operator.from_problem(ctx, p)
+    M = _api().Preconditioner.build(Aop, to_dev(np.ascontiguousarray(S0)), k, p.s1, p.nu, p.omega, MIXED)
+    sig = to_np(M.sigma())
+    s_ref = np.sqrt(2.0) * ref["sigma"][:k]  # every direction counted twice
+    assert np.all(np.abs(sig[:k] - s_ref) <= 1e-4 * s_ref[0]), (sig[:k], s_ref)
+    assert np.all(sig[p.K // 2:] <= 1e-2 * s_ref[0])
+    b = p.f[:, 0]
+    x, res = M.solve(to_dev(b), tol=1e-8)
+    assert res[0].status == 0
+    assert np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b) <= 1e-8 * 1.01
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
 @pytest.mark.parametrize("precision", [FP64, MIXED])
 def test_apply_matches_algorithm1(ctx, name, precision):
     # The oracle's basis is handed to the GPU so both apply the same B.
