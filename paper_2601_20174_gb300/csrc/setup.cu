@@ -201,12 +201,15 @@ __global__ void __launch_bounds__(TD* TD) k_tsgemm(StencilView<T> A, const T* __
     constexpr int PER = GRAM_CW * KP / nthreads;
     static_assert(PER * nthreads == GRAM_CW * KP, "chunk must split evenly over the block");
     constexpr int CPT = NLSP_TILE / GRAM_CW;  // chunks per tile
-    const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t nchunks = my_tiles * CPT;
+    // chunks are dealt round-robin over the blocks (a small system still
+    // spreads over CPT blocks per tile)
+    const int64_t all = ntiles * CPT;
+    const int64_t nchunks = blockIdx.x < all ? (all - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     T pre[PER];
     auto load = [&](int64_t q) {
-      const int64_t t = blockIdx.x + (q / CPT) * gridDim.x;
-      const int w0 = (int)(q % CPT) * GRAM_CW;
+      const int64_t gq = blockIdx.x + q * gridDim.x;
+      const int64_t t = gq / CPT;
+      const int w0 = (int)(gq % CPT) * GRAM_CW;
 #pragma unroll
       for (int u = 0; u < PER; ++u) {
         const int e = threadIdx.x + u * nthreads;
@@ -227,8 +230,10 @@ __global__ void __launch_bounds__(TD* TD) k_tsgemm(StencilView<T> A, const T* __
       products();
     }
   } else {
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      for (int w0 = 0; w0 < NLSP_TILE; w0 += GRAM_CW) {
+    for (int64_t gq = blockIdx.x; gq < ntiles * (NLSP_TILE / GRAM_CW); gq += gridDim.x) {
+      const int64_t t = gq / (NLSP_TILE / GRAM_CW);
+      const int w0 = (int)(gq % (NLSP_TILE / GRAM_CW)) * GRAM_CW;
+      {
         __syncthreads();
         // stage the X chunk and the A X chunk transposed: element (w, c)
         for (int e = threadIdx.x; e < GRAM_CW * KP; e += nthreads) {
@@ -480,9 +485,12 @@ __host__ __device__ constexpr size_t chol_eig_smem(int K) {
 }
 
 // NV = chol_eig_ldx(K) / 32 float4 per lane and column.
+// complete != 0: the eigenvectors beyond the numerical rank are replaced by
+// an orthonormal basis of the complement (unit vectors orthogonalised twice
+// against the columns before them), so that V is a full orthonormal basis.
 template <int NV>
 __global__ void __launch_bounds__(CE_THREADS) k_chol_jacobi_eig(const double* __restrict__ G, int K, float tol,
-                                                                double* __restrict__ evals,
+                                                                int complete, double* __restrict__ evals,
                                                                 double* __restrict__ V) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LD = K + 1, LDX = 32 * NV;
@@ -633,48 +641,80 @@ __global__ void __launch_bounds__(CE_THREADS) k_chol_jacobi_eig(const double* __
     if (!rotated[sweep]) break;  // written only in this sweep, read after its last barrier
   }
 
-  // eigenvalues = squared column norms, sorted descending (ties by column)
+  // eigenvalues = squared column norms; columns normalised in place
   for (int c = warp; c < r; c += NW) {
     float s = 0.0f;
     for (int i = lane; i < K; i += 32) s = fmaf(X[c * LDX + i], X[c * LDX + i], s);
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const float inv = s > 0.0f ? 1.0f / sqrtf(s) : 0.0f;
+    for (int i = lane; i < K; i += 32) X[c * LDX + i] *= inv;
     if (lane == 0) lam[c] = s;
   }
   __syncthreads();
+  if (complete && r < K) {
+    // unit vectors e_m (the first m whose remainder is not too small), made
+    // orthogonal to the columns before them by two classical Gram-Schmidt
+    // passes; some e_m keeps at least 1/sqrt(K) of its length
+    float* v = nxt;           // K (free after the factorisation)
+    float* h = nxt + LDX;     // K
+    __shared__ float nrm;
+    const float accept = 0.3f * rsqrtf((float)K);
+    for (int c = r; c < K; ++c) {
+      for (int m = 0; m < K; ++m) {
+        for (int i = tid; i < K; i += CE_THREADS) {
+          float s = i == m ? 1.0f : 0.0f;
+          for (int b = 0; b < c; ++b) s = fmaf(-X[b * LDX + i], X[b * LDX + m], s);
+          v[i] = s;
+        }
+        __syncthreads();
+        for (int b = warp; b < c; b += NW) {
+          float s = 0.0f;
+          for (int i = lane; i < K; i += 32) s = fmaf(X[b * LDX + i], v[i], s);
+          for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+          if (lane == 0) h[b] = s;
+        }
+        __syncthreads();
+        float vmine = 0.0f;  // entry tid of the remainder (K <= 128 < CE_THREADS)
+        if (tid < K) {
+          float s = v[tid];
+          for (int b = 0; b < c; ++b) s = fmaf(-h[b], X[b * LDX + tid], s);
+          vmine = s;
+        }
+        if (warp == 0) {
+          float s = 0.0f;
+          for (int i = lane; i < K; i += 32) {
+            float w = v[i];
+            for (int b = 0; b < c; ++b) w = fmaf(-h[b], X[b * LDX + i], w);
+            s = fmaf(w, w, s);
+          }
+          for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+          if (lane == 0) nrm = sqrtf(s);
+        }
+        __syncthreads();
+        const float nv = nrm;
+        if (nv > accept) {
+          if (tid < K) X[c * LDX + tid] = vmine / nv;
+          __syncthreads();
+          break;
+        }
+      }
+      if (tid == 0) lam[c] = 0.0f;
+    }
+    __syncthreads();
+  }
+  // sort descending (ties by column); zero columns past the rank unless completed
   for (int c = warp; c < K; c += NW) {
     if (c < r) {
       const float lc = lam[c];
       int pos = 0;
       for (int b2 = lane; b2 < r; b2 += 32) pos += (lam[b2] > lc) || (lam[b2] == lc && b2 < c);
       for (int off = 16; off > 0; off >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, off);
-      const float inv = lc > 0.0f ? 1.0f / sqrtf(lc) : 0.0f;
       if (lane == 0) evals[pos] = (double)lc;
-      for (int i = lane; i < K; i += 32) V[(int64_t)pos * K + i] = (double)(X[c * LDX + i] * inv);
+      for (int i = lane; i < K; i += 32) V[(int64_t)pos * K + i] = (double)X[c * LDX + i];
     } else {
       if (lane == 0) evals[c] = 0.0;
-      for (int i = lane; i < K; i += 32) V[(int64_t)c * K + i] = 0.0;
+      for (int i = lane; i < K; i += 32) V[(int64_t)c * K + i] = complete ? (double)X[c * LDX + i] : 0.0;
     }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Small dense FP64 products for the K x K refinement: C = op(A) * B, all
-// column-major K x K; one block per output column.
-// ---------------------------------------------------------------------------
-__global__ void k_small_gemm(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
-                             int K, int transA) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* bcol = reinterpret_cast<double*>(smem_raw);
-  const int j = blockIdx.x;
-  for (int m = threadIdx.x; m < K; m += blockDim.x) bcol[m] = B[(int64_t)j * K + m];
-  __syncthreads();
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    double s = 0.0;
-    if (transA)
-      for (int m = 0; m < K; ++m) s += A[(int64_t)i * K + m] * bcol[m];
-    else
-      for (int m = 0; m < K; ++m) s += A[(int64_t)m * K + i] * bcol[m];
-    C[(int64_t)j * K + i] = s;
   }
 }
 
@@ -707,14 +747,17 @@ __global__ void k_oa_step(const double* __restrict__ XtX, const double* __restri
   }
   so = block_sum(so, red);
   rr = block_sum(rr, red);
-  // max via sum of a one-hot is not possible; reduce max with a loop
-  __shared__ double mx;
-  if (tid == 0) mx = 0.0;
+  // max |lambda| over the block: warp maxima, then warp 0
+  for (int off = 16; off > 0; off >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
+  if ((tid & 31) == 0) red[tid >> 5] = lmax;
   __syncthreads();
-  for (int i = 0; i < nt; ++i) {
-    if (tid == i) mx = fmax(mx, lmax);
-    __syncthreads();
+  __shared__ double mx;
+  if (tid < 32) {
+    double m = tid < (nt >> 5) ? red[tid] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (tid == 0) mx = m;
   }
+  __syncthreads();
   const double delta = 2.0 * (sqrt(so) + mx * sqrt(rr));
   for (int e = tid; e < K * K; e += nt) {
     const int i = e % K, j = e / K;
@@ -731,15 +774,18 @@ __global__ void k_add(double* __restrict__ X, const double* __restrict__ Y, int 
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) X[e] += Y[e];
 }
 
-// Sorts eigenpairs descending: lam (K), X (K x K, columns) -> evals, V.
+// Sorts eigenpairs descending: lam (K), X (K x K, columns) -> evals, V.  One
+// warp per eigenpair (its rank counted by the lanes, then its column copied).
 __global__ void k_sort_eig(const double* __restrict__ lam, const double* __restrict__ X, int K,
                            double* __restrict__ evals, double* __restrict__ V) {
-  for (int a = threadIdx.x; a < K; a += blockDim.x) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int a = threadIdx.x >> 5; a < K; a += nw) {
     const double la = lam[a];
     int pos = 0;
-    for (int b = 0; b < K; ++b) pos += (lam[b] > la) || (lam[b] == la && b < a);
-    evals[pos] = la;
-    for (int row = 0; row < K; ++row) V[(int64_t)pos * K + row] = X[(int64_t)a * K + row];
+    for (int b = lane; b < K; b += 32) pos += (lam[b] > la) || (lam[b] == la && b < a);
+    for (int off = 16; off > 0; off >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, off);
+    if (lane == 0) evals[pos] = la;
+    for (int row = lane; row < K; row += 32) V[(int64_t)pos * K + row] = X[(int64_t)a * K + row];
   }
 }
 
@@ -934,22 +980,28 @@ __global__ void __launch_bounds__(32) k_spd_inverse_cols(const double* __restric
 inline size_t spd_inverse_smem(int m) { return sizeof(double) * ((size_t)m * (m + 1) + 2 * (size_t)m); }
 
 // C (m x n) = op(A) op(B), op(A) m x kk, op(B) kk x n, all FP64 column-major
-// with leading dimensions; ta / tb select the transposes.  One block per
-// column of C; the column of op(B) is staged in shared memory (kk <= 256).
-__global__ void k_gemm_small(const double* __restrict__ A, int lda, int ta, const double* __restrict__ B, int ldb,
-                             int tb, double* __restrict__ C, int ldc, int m, int n, int kk) {
-  __shared__ double bcol[256];
-  const int j = blockIdx.x;
-  for (int q = threadIdx.x; q < kk; q += blockDim.x) bcol[q] = tb ? B[(int64_t)q * ldb + j] : B[(int64_t)j * ldb + q];
-  __syncthreads();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double s = 0.0;
-    if (ta)
-      for (int q = 0; q < kk; ++q) s += A[(int64_t)i * lda + q] * bcol[q];
-    else
-      for (int q = 0; q < kk; ++q) s += A[(int64_t)q * lda + i] * bcol[q];
-    C[(int64_t)j * ldc + i] = s;
+// with leading dimensions; ta / tb select the transposes.  A 16 x 16 block
+// grid over C.
+__global__ void __launch_bounds__(256) k_gemm_small(const double* __restrict__ A, int lda, int ta,
+                                                    const double* __restrict__ B, int ldb, int tb,
+                                                    double* __restrict__ C, int ldc, int m, int n, int kk) {
+  // one 16 x 16 tile of C per block; the inner dimension in chunks of 16,
+  // op(A) and op(B) chunks staged in shared memory
+  __shared__ double As[16][17], Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.x * 16, j0 = blockIdx.y * 16;
+  double acc = 0.0;
+  for (int l0 = 0; l0 < kk; l0 += 16) {
+    const int ai = i0 + tx, al = l0 + ty;  // op(A)(ai, al)
+    As[ty][tx] = (ai < m && al < kk) ? (ta ? A[(int64_t)ai * lda + al] : A[(int64_t)al * lda + ai]) : 0.0;
+    const int bl = l0 + tx, bj = j0 + ty;  // op(B)(bl, bj)
+    Bs[ty][tx] = (bl < kk && bj < n) ? (tb ? B[(int64_t)bl * ldb + bj] : B[(int64_t)bj * ldb + bl]) : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) acc = fma(As[t][tx], Bs[ty][t], acc);
+    __syncthreads();
   }
+  if (i0 + tx < m && j0 + ty < n) C[(int64_t)(j0 + ty) * ldc + i0 + tx] = acc;
 }
 
 // Coefficients of the randomised basis: M = X V[:, :k] (K x k, row-major
@@ -1020,7 +1072,7 @@ nlsp_status tsgemm(nlsp_ctx* ctx, const nlsp_op* A, const T* X, int ncols, int n
   cudaStream_t s = ctx->stream;
   const int64_t ntiles = n_pad / NLSP_TILE;
   // Up to four resident blocks per SM, so that one block's staging loads
-  // overlap another's products; never more blocks than tiles.
+  // overlap another's products; never more blocks than node chunks.
 #define NLSP_TSGEMM_LAUNCH(RB, TD)                                                                     \
   do {                                                                                                \
     constexpr int LDS_ = RB * TD + (sizeof(T) == 4 ? 4 : 2);                                          \
@@ -1031,7 +1083,7 @@ nlsp_status tsgemm(nlsp_ctx* ctx, const nlsp_op* A, const T* X, int ncols, int n
       int per_sm = 1;                                                                                 \
       NLSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TD * TD, sm));             \
       const int blocks = (int)std::min<int64_t>((int64_t)ctx->num_sms * std::min(std::max(per_sm, 1), 4), \
-                                                std::max<int64_t>(ntiles, 1));                        \
+                                                std::max<int64_t>(ntiles * (NLSP_TILE / GRAM_CW), 1)); \
       double* partial = slot_as<double>(ctx, SLOT_PART, (size_t)blocks * ncx * ncx);                  \
       if (!partial) return NLSP_ERR_OOM;                                                              \
       fn<<<blocks, TD * TD, sm, s>>>(view_of<T>(A), X, ncols, ncx, n_pad, partial);                   \
@@ -1065,10 +1117,11 @@ nlsp_status tile_times_small(nlsp_ctx* ctx, const T* In, int ncin, const T* M, i
   else fn = (const void*)k_tile_times_small<T, 64, 16>;
   NLSP_TRY(set_smem(fn, sm));
   const int64_t ntiles = n_pad / NLSP_TILE;
+  const int bt = NLSP_TILE;
   const int g = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 8);
-  if (kc == 16) k_tile_times_small<T, 16, 16><<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
-  else if (kc == 32) k_tile_times_small<T, 32, 16><<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
-  else k_tile_times_small<T, 64, 16><<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
+  if (kc == 16) k_tile_times_small<T, 16, 16><<<g, bt, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
+  else if (kc == 32) k_tile_times_small<T, 32, 16><<<g, bt, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
+  else k_tile_times_small<T, 64, 16><<<g, bt, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
   NLSP_LAUNCH_CHECK();
   count_launches(ctx, 1);
   return NLSP_OK;
@@ -1154,7 +1207,7 @@ nlsp_status alloc_prec_storage(nlsp_prec* M) {
 }
 
 // Launches the pivoted-Cholesky / one-sided Jacobi eigensolver (K <= 128).
-nlsp_status chol_jacobi_eig(cudaStream_t s, const double* G, int K, double* evals, double* V) {
+nlsp_status chol_jacobi_eig(cudaStream_t s, const double* G, int K, int complete, double* evals, double* V) {
   const size_t sm = chol_eig_smem(K);
   const int nv = chol_eig_ldx(K) / 32;
   const void* fn = nv == 1   ? (const void*)k_chol_jacobi_eig<1>
@@ -1163,7 +1216,7 @@ nlsp_status chol_jacobi_eig(cudaStream_t s, const double* G, int K, double* eval
                              : (const void*)k_chol_jacobi_eig<4>;
   NLSP_TRY(set_smem(fn, sm));
   const float tol = 4e-6f;
-  void* args[] = {(void*)&G, (void*)&K, (void*)&tol, (void*)&evals, (void*)&V};
+  void* args[] = {(void*)&G, (void*)&K, (void*)&tol, (void*)&complete, (void*)&evals, (void*)&V};
   NLSP_CUDA(cudaLaunchKernel(fn, dim3(1), dim3(CE_THREADS), args, sm, s));
   return NLSP_OK;
 }
@@ -1173,17 +1226,18 @@ nlsp_status chol_jacobi_eig(cudaStream_t s, const double* G, int K, double* eval
 // work: 6 K^2 + K doubles.
 nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double* evals, double* V, double* work) {
   cudaStream_t s = ctx->stream;
-  if (refine == 0 && K <= 128) {  // FP32 preconditioner: pivoted Cholesky + one-sided Jacobi
-    NLSP_TRY(chol_jacobi_eig(s, G, K, evals, V));
+  if (K <= 128) {  // FP32 pivoted Cholesky + one-sided Jacobi (a complete basis when it is refined)
+    NLSP_TRY(chol_jacobi_eig(s, G, K, refine > 0, evals, V));
     count_launches(ctx, 1);
-    return NLSP_OK;
+    if (refine == 0) return NLSP_OK;
+  } else {
+    const int KP = K + (K & 1);
+    const size_t sm = jacobi_smem(KP);
+    NLSP_TRY(set_smem((const void*)k_jacobi_eig, sm));
+    k_jacobi_eig<<<1, 1024, sm, s>>>(G, K, KP, 30, 4e-6f, evals, V);
+    NLSP_LAUNCH_CHECK();
+    count_launches(ctx, 1);
   }
-  const int KP = K + (K & 1);
-  const size_t sm = jacobi_smem(KP);
-  NLSP_TRY(set_smem((const void*)k_jacobi_eig, sm));
-  k_jacobi_eig<<<1, 1024, sm, s>>>(G, K, KP, 30, 4e-6f, evals, V);
-  NLSP_LAUNCH_CHECK();
-  count_launches(ctx, 1);
   if (refine > 0) {
     double* XtX = work;
     double* GX = XtX + K * K;
@@ -1192,24 +1246,27 @@ nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double
     double* XE = E + K * K;
     double* vcopy = XE + K * K;
     double* lam = vcopy + K * K;
-    const size_t gsm = sizeof(double) * K;
-    const int th = K < 128 ? 128 : 256;
+    // K x K products C = op(A) B
+    const dim3 gg((unsigned)div_up(K, 16), (unsigned)div_up(K, 16));
+    auto mm = [&](const double* A_, int ta, const double* B_, double* C_) {
+      k_gemm_small<<<gg, 256, 0, s>>>(A_, K, ta, B_, K, 0, C_, K, K, K, K);
+    };
     for (int it = 0; it < refine; ++it) {
-      k_small_gemm<<<K, th, gsm, s>>>(V, V, XtX, K, 1);
-      k_small_gemm<<<K, th, gsm, s>>>(G, V, GX, K, 0);
-      k_small_gemm<<<K, th, gsm, s>>>(V, GX, S, K, 1);
-      k_oa_step<<<1, 256, 0, s>>>(XtX, S, K, E, lam);
-      k_small_gemm<<<K, th, gsm, s>>>(V, E, XE, K, 0);
+      mm(V, 1, V, XtX);
+      mm(G, 0, V, GX);
+      mm(V, 1, GX, S);
+      k_oa_step<<<1, 512, 0, s>>>(XtX, S, K, E, lam);
+      mm(V, 0, E, XE);
       k_add<<<div_up((int64_t)K * K, 256), 256, 0, s>>>(V, XE, K * K);
       NLSP_LAUNCH_CHECK();
     }
     // eigenvalues of the refined basis (Rayleigh quotients), then sort
-    k_small_gemm<<<K, th, gsm, s>>>(V, V, XtX, K, 1);
-    k_small_gemm<<<K, th, gsm, s>>>(G, V, GX, K, 0);
-    k_small_gemm<<<K, th, gsm, s>>>(V, GX, S, K, 1);
-    k_oa_step<<<1, 256, 0, s>>>(XtX, S, K, E, lam);
+    mm(V, 1, V, XtX);
+    mm(G, 0, V, GX);
+    mm(V, 1, GX, S);
+    k_oa_step<<<1, 512, 0, s>>>(XtX, S, K, E, lam);
     NLSP_CUDA(cudaMemcpyAsync(vcopy, V, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
-    k_sort_eig<<<1, 256, 0, s>>>(lam, vcopy, K, evals, V);
+    k_sort_eig<<<1, 1024, 0, s>>>(lam, vcopy, K, evals, V);
     NLSP_LAUNCH_CHECK();
     count_launches(ctx, 6 * refine + 5);
   }
@@ -1248,8 +1305,9 @@ nlsp_status basis_from_samples(nlsp_ctx* ctx, nlsp_prec* M, const T* S, bool a_w
 // C = op(A) op(B) (FP64, column-major, see k_gemm_small).
 nlsp_status gemm64(nlsp_ctx* ctx, int ta, int tb, int m, int n, int kk, const double* A, int lda, const double* B,
                    int ldb, double* C, int ldc) {
-  if (kk > 256) return NLSP_ERR_INVALID;
-  k_gemm_small<<<n, 128, 0, ctx->stream>>>(A, lda, ta, B, ldb, tb, C, ldc, m, n, kk);
+  if (m <= 0 || n <= 0 || kk < 0) return NLSP_ERR_INVALID;
+  k_gemm_small<<<dim3((unsigned)div_up(m, 16), (unsigned)div_up(n, 16)), 256, 0, ctx->stream>>>(A, lda, ta, B, ldb, tb,
+                                                                                                 C, ldc, m, n, kk);
   NLSP_LAUNCH_CHECK();
   count_launches(ctx, 1);
   return NLSP_OK;
@@ -1372,7 +1430,8 @@ nlsp_status cholesky_qr(nlsp_ctx* ctx, nlsp_prec* M) {
   // inverse kernel and one small product.
   NLSP_TRY(set_smem((const void*)k_spd_inverse_cols, spd_inverse_smem(k)));
   k_spd_inverse_cols<<<k, 32, spd_inverse_smem(k), s>>>(Lp, k, Linv);  // (L L^T)^-1
-  k_small_gemm<<<k, 128, sizeof(double) * k, s>>>(Linv, Lp, W, k, 0);  // L^-T
+  k_gemm_small<<<dim3((unsigned)div_up(k, 16), (unsigned)div_up(k, 16)), 256, 0, s>>>(Linv, k, 0, Lp, k, 0, W, k, k,
+                                                                                     k, k);  // L^-T
   k_transpose_to<T><<<div_up((int64_t)k * k, 256), 256, 0, s>>>(W, k, Mt);
   NLSP_LAUNCH_CHECK();
   count_launches(ctx, 4);

@@ -220,7 +220,8 @@ def test_setup_mixed_odd_and_tiny_sample_counts(ctx, K, k):
     assert res[0].status == 0
 
 
-def test_setup_mixed_rank_deficient_samples(ctx):
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_setup_rank_deficient_samples(ctx, precision):
     # K = 2k samples whose second half repeats the first: G = S^T S has rank k,
     # the factorisation stops at the numerical rank and the top k eigenpairs
     # are those of the distinct half
@@ -231,11 +232,42 @@ def test_setup_mixed_rank_deficient_samples(ctx):
     k = min(p.k, p.K // 2)
     ref = osetup.build(A, half, k, p.omega, p.s1)
     Aop = _api().Operator.from_problem(ctx, p)
-    M = _api().Preconditioner.build(Aop, to_dev(np.ascontiguousarray(S0)), k, p.s1, p.nu, p.omega, MIXED)
+    M = _api().Preconditioner.build(Aop, to_dev(np.ascontiguousarray(S0)), k, p.s1, p.nu, p.omega, precision)
     sig = to_np(M.sigma())
     s_ref = np.sqrt(2.0) * ref["sigma"][:k]  # every direction counted twice
-    assert np.all(np.abs(sig[:k] - s_ref) <= 1e-4 * s_ref[0]), (sig[:k], s_ref)
-    assert np.all(sig[p.K // 2:] <= 1e-2 * s_ref[0])
+    tol = 1e-9 * s_ref + 1e-13 * s_ref[0] ** 2 / s_ref if precision == FP64 else 1e-4 * s_ref[0]
+    assert np.all(np.abs(sig[:k] - s_ref) <= tol), (sig[:k], s_ref)
+    assert np.all(sig[p.K // 2:] <= (1e-6 if precision == FP64 else 1e-2) * s_ref[0])
+    b = p.f[:, 0]
+    x, res = M.solve(to_dev(b), tol=1e-8)
+    assert res[0].status == 0
+    assert np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b) <= 1e-8 * 1.01
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_setup_zero_sample_column(ctx, precision):
+    # a zero sample column makes G singular with an exactly zero pivot: the
+    # FP32 factorisation stops one short of K and the basis is completed by
+    # the complement before the FP64 refinement; the leading k pairs are
+    # those of the remaining samples
+    p = PROBLEMS["grf5"]()
+    A = op.assemble(p)
+    S0 = p.S0.copy()
+    S0[:, -1] = 0.0
+    ref = osetup.build(A, S0[:, :-1], p.k, p.omega, p.s1)
+    Aop = _api().Operator.from_problem(ctx, p)
+    M = _api().Preconditioner.build(Aop, to_dev(S0), p.k, p.s1, p.nu, p.omega, precision)
+    sig, P = to_np(M.sigma()), to_np(M.basis())
+    s_ref = ref["sigma"][: p.k]
+    fp64 = precision == FP64
+    assert np.all(np.abs(sig[: p.k] - s_ref) <= (1e-9 * s_ref + 1e-13 * s_ref[0] ** 2 / s_ref if fp64
+                                                  else 1e-4 * s_ref[0])), (sig[: p.k] - s_ref) / s_ref
+    assert abs(sig[-1]) <= (1e-6 if fp64 else 1e-2) * s_ref[0]
+    if fp64:
+        assert np.max(np.abs(P.T @ P - np.eye(p.k))) <= 1e-12
+    gap = (s_ref[p.k - 1] ** 2 - ref["sigma"][p.k] ** 2) / s_ref[0] ** 2
+    Q = np.linalg.qr(P)[0]
+    assert projector_dist(Q, ref["P"]) <= (max(1e-8, 1e-13 / gap) if fp64 else max(1e-3, 1e-6 / gap))
     b = p.f[:, 0]
     x, res = M.solve(to_dev(b), tol=1e-8)
     assert res[0].status == 0
