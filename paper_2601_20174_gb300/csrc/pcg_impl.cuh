@@ -255,9 +255,8 @@ __global__ void __launch_bounds__(TPB) k_sweep(StencilView<T> A, T omega, const 
 }
 
 // ----------------------------------------------------------------------------
-// restrict: rho = rT - A z, c = P_r^T rho (per-block partials in T), and in the
-// last block c = sum of partials, e_c = A_c^-1 c (in T, A_c^-1 rounded once
-// from the FP64 inverse of the FP64 Cholesky factor).
+// restrict: rho = rT - A z, c = P_r^T rho as per-block partials in T (the
+// coarse solve is the prolongation's first step).
 //   ZMODE 0: z read from zin;  ZMODE 1 / 2: z = 1 / 2 pre-sweeps recomputed
 //   from rT and stored to zout.
 // Block = 8 warps; columns are split into NCH chunks of 32, each chunk handled
@@ -321,16 +320,12 @@ template <int KIND, typename T, int NCH, int ZMODE>
 __global__ void __launch_bounds__(128 * NCH) k_restrict(StencilView<T> A, T omega, const T* __restrict__ rT,
                                                         const T* __restrict__ zin, T* __restrict__ zout,
                                                         const T* __restrict__ P, int k, int r, StreamArgs sa,
-                                                        const T* __restrict__ Ainv, T* __restrict__ cpart,
-                                                        T* __restrict__ ec, unsigned* counter, PcgState* st,
-                                                        int* err) {
+                                                        T* __restrict__ cpart, PcgState* st, int* err) {
   constexpr int NT = 128 * NCH;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[8];
   __shared__ T sacc[NT / 32][32];
-  __shared__ T red[NT];
-  __shared__ T cfull[128];
-  __shared__ int flag, abort_s;
+  __shared__ int abort_s;
   if (load_done(st)) return;
   const int nstage = sa.nstage;
   const int ntiles = (int)((A.n + NLSP_TILE - 1) / NLSP_TILE);
@@ -350,8 +345,10 @@ __global__ void __launch_bounds__(128 * NCH) k_restrict(StencilView<T> A, T omeg
       tma::mbar_arrive_expect_tx(&bar[s], tile_bytes);
       tma::bulk_g2s(buf + (size_t)s * r * NLSP_TILE, P + (size_t)(t0 + s) * k * NLSP_TILE, tile_bytes, &bar[s]);
     }
-  // phase 1 (overlaps the first copies): rho = rT - A z for the CTA's nodes
-  for (int e = threadIdx.x; e < nt * NLSP_TILE; e += NT) {
+  // phase 1 (overlaps the first copies): rho = rT - A z for the CTA's nodes,
+  // four nodes per thread at a time as independent chains, so that their
+  // loads are in flight together
+  auto rho_at = [&](int e) {
     const int i = t0 * NLSP_TILE + e;
     T rho = T(0);
     if (i < A.n) {
@@ -368,7 +365,16 @@ __global__ void __launch_bounds__(128 * NCH) k_restrict(StencilView<T> A, T omeg
         zout[i] = zi;
       }
     }
-    rho_s[e] = rho;
+    return rho;
+  };
+  const int total = nt * NLSP_TILE;
+  for (int e0 = threadIdx.x; e0 < total; e0 += 4 * NT) {
+    T rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) rv[u] = e0 + u * NT < total ? rho_at(e0 + u * NT) : T(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (e0 + u * NT < total) rho_s[e0 + u * NT] = rv[u];
   }
   __syncthreads();
   // phase 2: stream the tiles, acc[j] = sum over the CTA's nodes of rho * P
@@ -407,39 +413,24 @@ __global__ void __launch_bounds__(128 * NCH) k_restrict(StencilView<T> A, T omeg
     for (int q = 0; q < 4; ++q) s += sacc[hh * 4 + q][j];
     cpart[(int64_t)blockIdx.x * k + col] = s;
   }
-  if (last_block_arrive(counter, &flag)) {
-    const int S = NT / r > 0 ? NT / r : 1;  // slices per column
-    T part = T(0);
-    if (threadIdx.x < S * r) {
-      const int col = threadIdx.x % r, sl = threadIdx.x / r;
-      for (int b = sl; b < (int)gridDim.x; b += S) part += cpart[(int64_t)b * k + col];
-    }
-    red[threadIdx.x] = part;
-    __syncthreads();
-    for (int col = threadIdx.x; col < r; col += NT) {
-      T s = T(0);
-      for (int sl = 0; sl < S; ++sl) s += red[sl * r + col];
-      cfull[col] = s;
-    }
-    __syncthreads();
-    for (int row = threadIdx.x; row < r; row += NT) {
-      T s = T(0);
-      for (int col = 0; col < r; ++col) s += Ainv[(int64_t)col * r + row] * cfull[col];
-      ec[row] = s;
-    }
-  }
 }
 
-// prolong: z += P_r e_c, streaming the tiles like restrict.
+// prolong: e_c = A_c^-1 (sum of the restriction's nb per-block partials; A_c^-1
+// in T, rounded once from the FP64 inverse of the FP64 Cholesky factor), then
+// z += P_r e_c, streaming the tiles like restrict.  Every CTA forms e_c itself
+// in the same fixed order while its first tiles are in flight.
 template <typename T, int NCH>
 __global__ void __launch_bounds__(128 * NCH) k_prolong(int64_t n, const T* __restrict__ P, int k, int r,
-                                                       StreamArgs sa, const T* __restrict__ ec, T* __restrict__ z,
-                                                       PcgState* st, int* err) {
+                                                       StreamArgs sa, const T* __restrict__ cpart, int nb,
+                                                       const T* __restrict__ Ainv, T* __restrict__ z, PcgState* st,
+                                                       int* err) {
   constexpr int NT = 128 * NCH;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[8];
   __shared__ T zpart[2][NCH][NLSP_TILE];
   __shared__ T e[128];
+  __shared__ T cfull[128];
+  __shared__ T red[NT];
   __shared__ int abort_s;
   if (load_done(st)) return;
   const int nstage = sa.nstage;
@@ -448,7 +439,6 @@ __global__ void __launch_bounds__(128 * NCH) k_prolong(int64_t n, const T* __res
   const int nt = (int)((int64_t)ntiles * (blockIdx.x + 1) / gridDim.x) - t0;
   const unsigned tile_bytes = (unsigned)r * NLSP_TILE * (unsigned)sizeof(T);
   T* buf = reinterpret_cast<T*>(smem_raw);
-  for (int j = threadIdx.x; j < r; j += NT) e[j] = ec[j];
   if (threadIdx.x == 0) {
     abort_s = 0;
     for (int s = 0; s < nstage; ++s) tma::mbar_init(&bar[s], 1);
@@ -460,9 +450,67 @@ __global__ void __launch_bounds__(128 * NCH) k_prolong(int64_t n, const T* __res
       tma::mbar_arrive_expect_tx(&bar[s], tile_bytes);
       tma::bulk_g2s(buf + (size_t)s * r * NLSP_TILE, P + (size_t)(t0 + s) * k * NLSP_TILE, tile_bytes, &bar[s]);
     }
+  {
+    // c: thread (col, sl) adds partials sl, sl + S, ... sixteen loads at a
+    // time (all in flight together), then the S slices in order
+    const int S = NT / r > 0 ? NT / r : 1;
+    T part = T(0);
+    if (threadIdx.x < S * r) {
+      const int col = threadIdx.x % r, sl = threadIdx.x / r;
+      for (int b0 = sl; b0 < nb; b0 += 16 * S) {
+        T v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int b = b0 + u * S;
+          v[u] = b < nb ? cpart[(int64_t)b * k + col] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) part += v[u];
+      }
+    }
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int col = threadIdx.x; col < r; col += NT) {
+      T c = T(0);
+      for (int sl = 0; sl < S; ++sl) c += red[sl * r + col];
+      cfull[col] = c;
+    }
+    __syncthreads();
+    // e = A_c^-1 c: thread (row, g) adds the columns g, g + S, ... (r / S <=
+    // 32 of them), sixteen loads at a time
+    T v = T(0);
+    if (threadIdx.x < S * r) {
+      const int row = threadIdx.x % r, g = threadIdx.x / r;
+      for (int c0 = g; c0 < r; c0 += 16 * S) {
+        T a[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int col = c0 + u * S;
+          a[u] = col < r ? Ainv[(int64_t)col * r + row] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int col = c0 + u * S;
+          if (col < r) v += a[u] * cfull[col];
+        }
+      }
+    }
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int row = threadIdx.x; row < r; row += NT) {
+      T ev = T(0);
+      for (int g = 0; g < S; ++g) ev += red[g * r + row];
+      e[row] = ev;
+    }
+    __syncthreads();
+  }
   const int w = threadIdx.x & (NLSP_TILE - 1), h = threadIdx.x >> 7;
   const int c0 = h * 32;
   for (int it = 0; it < nt; ++it) {
+    // this tile's z is loaded before the wait for its P tile, so that the
+    // read's latency runs under the copy
+    const int64_t i = (int64_t)(t0 + it) * NLSP_TILE + w;
+    const T zold = (h == 0 && i < n) ? z[i] : T(0);
     stream_wait(bar, it, nstage, &abort_s);
     const T* tile = buf + (size_t)(it % nstage) * r * NLSP_TILE;
     T a = T(0);
@@ -486,8 +534,7 @@ __global__ void __launch_bounds__(128 * NCH) k_prolong(int64_t n, const T* __res
       T sum = zpart[it & 1][0][w];
 #pragma unroll
       for (int q = 1; q < NCH; ++q) sum += zpart[it & 1][q][w];
-      const int64_t i = (int64_t)(t0 + it) * NLSP_TILE + w;
-      if (i < n) z[i] += sum;
+      if (i < n) z[i] = zold + sum;
     }
   }
 }
@@ -1765,8 +1812,7 @@ nlsp_status launch_restrict_n(const nlsp_prec* M, const PrecWork& pw, cudaStream
   const StencilView<T>& A = view_T<T>(M->A);
   auto go = [&](auto fn) -> nlsp_status {
     fn<<<pl.grid, 128 * NCH, pl.smem_restrict, s>>>(A, (T)M->omega, rT, z, z, (const T*)M->P, M->k, M->r, pl.sa,
-                                                    (const T*)M->AinvT, (T*)pw.cpart, (T*)pw.ec, pw.counter, st,
-                                                    pw.err);
+                                                    (T*)pw.cpart, st, pw.err);
     return NLSP_OK;
   };
   if (zm == 0) return go(k_restrict<KIND, T, NCH, 0>);
@@ -1789,8 +1835,8 @@ template <typename T>
 nlsp_status launch_prolong(const nlsp_prec* M, const PrecWork& pw, cudaStream_t s, const StreamPlan& pl, T* z,
                            PcgState* st) {
   auto go = [&](auto fn, int nt) -> nlsp_status {
-    fn<<<pl.grid, nt, pl.smem_prolong, s>>>(M->n, (const T*)M->P, M->k, M->r, pl.sa, (const T*)pw.ec, z, st,
-                                            pw.err);
+    fn<<<pl.grid, nt, pl.smem_prolong, s>>>(M->n, (const T*)M->P, M->k, M->r, pl.sa, (const T*)pw.cpart, pl.grid,
+                                            (const T*)M->AinvT, z, st, pw.err);
     return NLSP_OK;
   };
   switch (pl.nch) {
