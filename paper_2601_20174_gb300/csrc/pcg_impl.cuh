@@ -780,21 +780,23 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Sums NV values over the CTA (warp sums first); result valid in thread 0.
-// Ends with a __syncthreads after every thread has contributed.
+// Sums the first nv of NV values over the CTA; result valid in thread 0.
+// Per value every thread stores it and warp 0 adds the PT / 32 values of its
+// lane column, then its 32 lane sums by a shuffle tree: one FP64 add per
+// value, instead of a shuffle tree in every warp (GB300 executes FP64 at 1/64
+// of the FP32 rate, charged per warp instruction).  Ends after a
+// __syncthreads that every thread has passed with its values stored.
 template <int NV>
-__device__ __forceinline__ void cta_sums(const double (&val)[NV], double* sm_d, double (&out)[NV]) {
+__device__ __forceinline__ void cta_sums(const double (&val)[NV], double* sm_d, double (&out)[NV], int nv) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int v = 0; v < nv; ++v) {
+    if (v > 0) __syncthreads();  // warp 0 has read the previous value
+    sm_d[threadIdx.x] = val[v];
+    __syncthreads();
+    if (warp == 0) {
+      double s = sm_d[lane];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const double w = warp_sum(val[v]);
-    if (lane == 0) sm_d[v * (PT / 32) + warp] = w;
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      double s = lane < PT / 32 ? sm_d[v * (PT / 32) + lane] : 0.0;
+      for (int w = 1; w < PT / 32; ++w) s += sm_d[w * 32 + lane];
       out[v] = warp_sum(s);
     }
   }
@@ -875,7 +877,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
   __shared__ T cfull[128];
   __shared__ T e_s[128];
   __shared__ T zpart[2][4][NLSP_TILE];
-  __shared__ double bc[2];
+  __shared__ double bc[4];  // totals, then scalars derived from them by one thread
   __shared__ __align__(16) double tot_s[2][XMAX_RANKS];  // copies of the team's partial slots
   __shared__ int ok_s, abort_s;
 
@@ -966,7 +968,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
   auto put = [&](int nv, double v0, double v1) {
     const double in[2] = {v0, v1};
     double s[2] = {0.0, 0.0};
-    cta_sums<2>(in, sm_d, s);
+    cta_sums<2>(in, sm_d, s, nv);
     if (tid == 0) {
       slot_of(gen + 1, 0)[cta] = s[0];
       if (nv > 1) slot_of(gen + 1, 1)[cta] = s[1];
@@ -991,7 +993,10 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       for (int v = 0; v < nv; ++v) tma::bulk_g2s(tot_s[v], slot_of(gen, v), bytes, &mbar[XBAR]);
     }
   };
-  auto tot_finish = [&](int nv, double* out) -> bool {
+  // derive(bc) runs in thread 0 once the totals are in bc[0 .. nv): scalar
+  // FP64 work (alpha, beta: divisions) done once instead of by every thread,
+  // since GB300 executes FP64 at 1/64 of the FP32 rate.
+  auto tot_finish_d = [&](int nv, double* out, auto derive) -> bool {
     if (tid < 32) {
       const bool got = tma::mbar_wait(&mbar[XBAR], tpar & 1u);
       if (!got && tid == 0) {
@@ -1008,6 +1013,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         s = warp_sum(s);
         if (tid == 0) bc[v] = s;
       }
+      if (tid == 0) derive(bc);
     }
     ++tpar;
     __syncthreads();
@@ -1017,6 +1023,7 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
     if (!good) ok = false;
     return good;
   };
+  auto tot_finish = [&](int nv, double* out) -> bool { return tot_finish_d(nv, out, [](double*) {}); };
   auto total1 = [&]() -> double {
     double o[1] = {0.0};
     tot_issue(1);
@@ -1439,12 +1446,13 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       }
       mark(MK_SPMV_ISSUE);
       double tot[2] = {0.0, 0.0};
-      if (!tot_finish(2, tot)) break;
+      if (!tot_finish_d(2, tot, [&](double* b) { b[2] = t > 0 ? (b[0] - (a.flexible ? b[1] : 0.0)) / rz : 0.0; }))
+        break;
       mark(MK_SPMV_FINISH);
-      const double rzn = tot[0], ro = a.flexible ? tot[1] : 0.0;
+      const double rzn = tot[0];
       if (!(rzn > 0.0) || !isfinite(rzn)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
       if (t > 0) {
-        beta = (rzn - ro) / rz;
+        beta = bc[2];
         if (iter >= a.maxit) { status = (int)NLSP_NOT_CONVERGED; break; }
       }
       rz = rzn;
@@ -1474,11 +1482,11 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
       // two buffers so that halo nodes read the previous residual
       tot_issue(1);
       double tot[1] = {0.0};
-      if (!tot_finish(1, tot)) break;
+      if (!tot_finish_d(1, tot, [&](double* b) { b[2] = rz / b[0]; })) break;
       const double pq = tot[0];
       if (!(pq > 0.0) || !isfinite(pq)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
       MergeArgs mg;
-      mg.alpha = rz / pq;
+      mg.alpha = bc[2];
       mg.rc = (t & 1) ? a.r1 : a.r;
       mg.rn = (t & 1) ? a.r : a.r1;
       mg.pd = pout;
@@ -1508,10 +1516,10 @@ __device__ __forceinline__ bool solve_instance(const PersistArgs<T>& a, const in
         rv[u] = in ? a.r[iu] : 0.0;
       }
       double tot[1] = {0.0};
-      if (!tot_finish(1, tot)) break;
+      if (!tot_finish_d(1, tot, [&](double* b) { b[2] = rz / b[0]; })) break;
       const double pq = tot[0];
       if (!(pq > 0.0) || !isfinite(pq)) { status = (int)NLSP_ERR_BREAKDOWN; break; }
-      const double alpha = rz / pq;
+      const double alpha = bc[2];
       mark(MK_PRE_TOTALS);
       double s = 0.0;
       auto update = [&](int i, double pi, double xi, double qi, double ri) {
