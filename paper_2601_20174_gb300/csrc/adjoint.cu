@@ -213,48 +213,59 @@ __global__ void __launch_bounds__(RV_THREADS) k_restrict_vec(const T* __restrict
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc[j] += pv[j][u] * xv[u];
   }
+  // warp sums in T (the accumulation precision; FP32 shuffles and adds are
+  // cheap), stored as FP64 block partials
 #pragma unroll
   for (int j = 0; j < RV_MAXC; ++j) {
     const int col = warp + 8 * j;
-    const double s = warp_sum((double)acc[j]);
-    if (lane == 0 && col < k) part[(int64_t)blockIdx.x * k + col] = s;
+    const T s = warp_sum(acc[j]);
+    if (lane == 0 && col < k) part[(int64_t)blockIdx.x * k + col] = (double)s;
   }
 }
 
-// c = sum of the block partials; e = A_c^-1 c (FP64).  Both may be stored
-// (c_out / e_out nullable).  One block of 256 threads: 256 / k groups add
-// interleaved blocks of the partials, then the groups are added in order.
-constexpr int CA_THREADS = 1024;
+// c = sum of the nb block partials, e = A_c^-1 c (FP64; k <= 128).  Block j
+// adds column j in a fixed order (the threads' strided sums, then a tree) and
+// stores it in cbuf; the last block to finish forms e from cbuf.  Spreading
+// the nb k FP64 additions over k blocks keeps them off one SM's FP64 pipe
+// (GB300 runs FP64 at 1/64 of the FP32 rate).  c_out / e_out may be null.
+constexpr int CC_THREADS = 256;
 
-__global__ void __launch_bounds__(CA_THREADS) k_coarse_apply(const double* __restrict__ part, int nb, int k,
-                                                            const double* __restrict__ Ainv,
-                                                            double* __restrict__ c_out, double* __restrict__ e_out) {
-  __shared__ double gsum[CA_THREADS];
+__global__ void __launch_bounds__(CC_THREADS) k_coarse_cols(const double* __restrict__ part, int nb, int k,
+                                                            const double* __restrict__ Ainv, double* cbuf,
+                                                            unsigned* counter, double* __restrict__ c_out,
+                                                            double* __restrict__ e_out) {
+  __shared__ double sm[CC_THREADS];
   __shared__ double c[128];
-  const int groups = CA_THREADS / k;  // k <= 128: at least 8
-  const int j = threadIdx.x % k, g = threadIdx.x / k;
+  __shared__ int flag;
+  const int j = blockIdx.x, tid = threadIdx.x;
   double s = 0.0;
-  if (g < groups)
-    for (int b = g; b < nb; b += groups) s += part[(int64_t)b * k + j];
-  gsum[threadIdx.x] = s;
+  for (int b = tid; b < nb; b += CC_THREADS) s += part[(int64_t)b * k + j];
+  sm[tid] = s;
   __syncthreads();
-  if (threadIdx.x < k) {
+  if (tid < 32) {
     double t = 0.0;
-    for (int q = 0; q < groups; ++q) t += gsum[q * k + threadIdx.x];
-    c[threadIdx.x] = t;
-    if (c_out) c_out[threadIdx.x] = t;
+    for (int q = tid; q < CC_THREADS; q += 32) t += sm[q];
+    t = warp_sum(t);
+    if (tid == 0) {
+      cbuf[j] = t;
+      if (c_out) c_out[j] = t;
+    }
   }
+  if (!last_block_arrive(counter, &flag)) return;
+  for (int q = tid; q < k; q += CC_THREADS) c[q] = __ldcg(cbuf + q);
   __syncthreads();
-  // e = A_c^-1 c: group g adds columns jj = g, g + groups, ... of row i
+  // e = A_c^-1 c: thread (row, g) adds the columns g, g + G, ... of its row
+  const int G = CC_THREADS / k;  // >= 2
+  const int row = tid % k, g = tid / k;
   double t = 0.0;
-  if (g < groups)
-    for (int jj = g; jj < k; jj += groups) t = fma(Ainv[(int64_t)jj * k + j], c[jj], t);
-  gsum[threadIdx.x] = t;
+  if (g < G)
+    for (int jj = g; jj < k; jj += G) t = fma(Ainv[(int64_t)jj * k + row], c[jj], t);
+  sm[tid] = t;
   __syncthreads();
-  if (threadIdx.x < k) {
+  if (tid < k) {
     double e = 0.0;
-    for (int q = 0; q < groups; ++q) e += gsum[q * k + threadIdx.x];
-    if (e_out) e_out[threadIdx.x] = e;
+    for (int q = 0; q < G; ++q) e += sm[q * k + tid];
+    if (e_out) e_out[tid] = e;
   }
 }
 
@@ -650,17 +661,16 @@ __global__ void k_small_sumsq(const double* __restrict__ x, int count, double* S
 // ============================================================================
 namespace {
 
-// Device workspace of one call, carved from one allocation (freed at the end
-// of the call: these entry points are not on a per-iteration path).
+// Device workspace of one call, carved from the context's grow-only adjoint
+// scratch slot (kept for the next call: an allocation and a free per call
+// would cost more than a short call's kernels, and the free synchronises).
 struct Arena {
   unsigned char* base = nullptr;
   size_t used = 0, cap = 0;
-  ~Arena() {
-    if (base) cudaFree(base);
-  }
-  nlsp_status reserve(size_t bytes) {
+  nlsp_status reserve(nlsp_ctx* ctx, size_t bytes) {
+    base = reinterpret_cast<unsigned char*>(ctx_slot(ctx, SLOT_ADJ, bytes));
+    if (!base) return NLSP_ERR_OOM;
     cap = bytes;
-    NLSP_CUDA(cudaMalloc(&base, bytes));
     return NLSP_OK;
   }
   template <typename U>
@@ -705,6 +715,8 @@ struct Unrolled {
   double* E;           // e of application j    T x k
   TP* YB;              // ybar of application j T x n_pad
   double* CB;          // cbar of application j T x k
+  double* cbuf;        // coarse right-hand side of the current application (k)
+  unsigned* counter;   // arrival counter of the coarse step (zero between launches)
   TP* w0;              // preconditioner work vectors (n_pad)
   TP* w1;
   double* vtmp;        // FP64 scratch vectors
@@ -759,7 +771,7 @@ struct Unrolled {
     k_resid<KIND, TP><<<g, VB, 0, s>>>(AT, v, cur, rho);
     k_restrict_vec<TP><<<nb, RV_THREADS, 0, s>>>((const TP*)M->P, k, n_pad, rho, part);
     double* e = j >= 0 ? E + (size_t)j * k : vtmp + n;  // vtmp holds n + k doubles
-    k_coarse_apply<<<1, CA_THREADS, 0, s>>>(part, nb, k, M->Ainv, nullptr, e);
+    k_coarse_cols<<<k, CC_THREADS, 0, s>>>(part, nb, k, M->Ainv, cbuf, counter, nullptr, e);
     k_prolong_vec<TP><<<ntb, NLSP_TILE, 0, s>>>((const TP*)M->P, k, n, e, cur);
     for (int sw = 0; sw < nu; ++sw) {
       k_jsweep<KIND, TP><<<g, VB, 0, s>>>(AT, omega, v, cur, oth);
@@ -784,7 +796,7 @@ struct Unrolled {
     TP* yb = YB + (size_t)j * n_pad;
     cudaMemcpyAsync(yb, cur, sizeof(TP) * n_pad, cudaMemcpyDeviceToDevice, s);
     k_restrict_vec<TP><<<nb, RV_THREADS, 0, s>>>((const TP*)M->P, k, n_pad, yb, part);
-    k_coarse_apply<<<1, CA_THREADS, 0, s>>>(part, nb, k, M->Ainv, nullptr, CB + (size_t)j * k);
+    k_coarse_cols<<<k, CC_THREADS, 0, s>>>(part, nb, k, M->Ainv, cbuf, counter, nullptr, CB + (size_t)j * k);
     launches += nu + 3;
   }
 
@@ -888,10 +900,12 @@ struct Unrolled {
         sizeof(double) * (size_t)(T + 1) * n, sizeof(double) * (size_t)T * n * 3,
         sizeof(TP) * (size_t)T * n_pad * 2, sizeof(double) * (size_t)T * k * 2, sizeof(TP) * (size_t)n_pad * 2,
         sizeof(double) * (size_t)(n + k), sizeof(double) * (size_t)n * 4, sizeof(TP) * (size_t)n_pad * k,
-        sizeof(double) * (size_t)k * k};
-    NLSP_TRY(ar.reserve(arena_bytes(parts) + 4096));
+        sizeof(double) * (size_t)k * k, sizeof(double) * (size_t)k, sizeof(unsigned) * 8};
+    NLSP_TRY(ar.reserve(ctx, arena_bytes(parts) + 4096));
     u.S = ar.take<double>(u.ix.count());
     u.part = ar.take<double>((size_t)u.nb * k);
+    u.cbuf = ar.take<double>((size_t)k);
+    u.counter = ar.take<unsigned>(8);
     u.R = ar.take<double>((size_t)(T + 1) * n);
     u.Pv = ar.take<double>((size_t)T * n);
     u.Q = ar.take<double>((size_t)T * n);
@@ -913,6 +927,7 @@ struct Unrolled {
     // padding rows of the work vectors stay zero (the restriction reads them)
     NLSP_CUDA(cudaMemsetAsync(u.RHO, 0, sizeof(TP) * (size_t)T * n_pad, u.s));
     NLSP_CUDA(cudaMemsetAsync(u.w0, 0, sizeof(TP) * n_pad, u.s));
+    NLSP_CUDA(cudaMemsetAsync(u.counter, 0, sizeof(unsigned) * 8, u.s));
     NLSP_CUDA(cudaMemsetAsync(u.w1, 0, sizeof(TP) * n_pad, u.s));
     u.forward(b);
     NLSP_LAUNCH_CHECK();
@@ -1013,7 +1028,7 @@ nlsp_status subspace_impl(nlsp_ctx* ctx, int64_t n, int k, int K, const double* 
                                      sizeof(double) * (size_t)nb * k * std::max(k, K), sizeof(double) * 16,
                                      sizeof(double) * (size_t)k * k * 6 + sizeof(double) * (size_t)k * K * 4,
                                      sizeof(double) * (size_t)nb, sizeof(int) * 4};
-  NLSP_TRY(ar.reserve(arena_bytes(parts) + 4096));
+  NLSP_TRY(ar.reserve(ctx, arena_bytes(parts) + 4096));
   TP* Pt = ar.take<TP>((size_t)n_pad * k);
   TP* Bt = ar.take<TP>((size_t)n_pad * K);
   double* part = ar.take<double>((size_t)nb * k * std::max(k, K));

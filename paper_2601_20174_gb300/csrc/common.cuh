@@ -114,7 +114,7 @@ struct StencilView {
 // temporaries are carved from them, so repeated calls allocate nothing once
 // the slots have grown to the working size.  Valid until the next call that
 // uses the same slot on this context.
-enum ScratchSlot { SLOT_SA = 0, SLOT_SB, SLOT_PART, SLOT_SMALL, SLOT_PNEW, SLOT_BATCH, SLOT_COUNT };
+enum ScratchSlot { SLOT_SA = 0, SLOT_SB, SLOT_PART, SLOT_SMALL, SLOT_PNEW, SLOT_BATCH, SLOT_ADJ, SLOT_COUNT };
 
 struct nlsp_ctx {
   int device;
