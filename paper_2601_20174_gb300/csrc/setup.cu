@@ -14,6 +14,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -164,14 +166,18 @@ __global__ void __launch_bounds__(256) k_smooth_sweep(StencilView<T> A, T omega,
 // ---------------------------------------------------------------------------
 constexpr int GRAM_CW = 32;  // nodes per staged chunk
 
-template <typename T, int RB, int TD, int KIND, bool WITH_A>
+// The block's products are X_t[:, cx0 .. cx0 + ncx)^T Y_t[:, cy0 .. cy0 + ncy)
+// with Y = A X, or (TWO) Y = X with a column range of its own (quadrants of
+// a Gram matrix wider than KP); X^T X itself uses the pipelined path.
+template <typename T, int RB, int TD, int KIND, bool WITH_A, bool TWO = false>
 __global__ void __launch_bounds__(TD* TD) k_tsgemm(StencilView<T> A, const T* __restrict__ X, int ncols, int ncx,
-                                                  int64_t n_pad, double* __restrict__ partial) {
+                                                  int64_t n_pad, double* __restrict__ partial, int cx0, int cy0,
+                                                  int ncy) {
   constexpr int KP = RB * TD;
   constexpr int LDS = KP + (sizeof(T) == 4 ? 4 : 2);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);  // [CW][LDS]
-  T* ys = WITH_A ? xs + GRAM_CW * LDS : xs;
+  T* ys = (WITH_A || TWO) ? xs + GRAM_CW * LDS : xs;
   const int tx = threadIdx.x % TD, ty = threadIdx.x / TD;
   T acc[RB][RB];
 #pragma unroll
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(TD* TD) k_tsgemm(StencilView<T> A, const T* __
         for (int b = 0; b < RB; ++b) acc[a][b] += xa[a] * yb[b];
     }
   };
-  if constexpr (!WITH_A) {
+  if constexpr (!WITH_A && !TWO) {
     // Software pipeline over the block's chunks (CW nodes of one tile each):
     // the loads of chunk q + 1 are in flight while chunk q is multiplied.
     constexpr int PER = GRAM_CW * KP / nthreads;
@@ -235,16 +241,19 @@ __global__ void __launch_bounds__(TD* TD) k_tsgemm(StencilView<T> A, const T* __
       const int w0 = (int)(gq % (NLSP_TILE / GRAM_CW)) * GRAM_CW;
       {
         __syncthreads();
-        // stage the X chunk and the A X chunk transposed: element (w, c)
+        // stage the X chunk and the Y chunk (A X, or X's other columns)
+        // transposed: element (w, c)
         for (int e = threadIdx.x; e < GRAM_CW * KP; e += nthreads) {
           const int c = e / GRAM_CW, w = e % GRAM_CW;
           T xv = T(0), yv = T(0);
           const int64_t i = t * NLSP_TILE + w0 + w;
-          if (c < ncx) {
-            xv = X[(t * ncols + c) * NLSP_TILE + w0 + w];
-            if (i < A.n) {
+          if (c < ncx) xv = X[(t * ncols + cx0 + c) * NLSP_TILE + w0 + w];
+          if (c < ncy) {
+            if (TWO) {
+              yv = X[(t * ncols + cy0 + c) * NLSP_TILE + w0 + w];
+            } else if (i < A.n) {
               const NodeCoord nc = node_coord<KIND>(i, A.N);
-              yv = stencil_apply<KIND>(A, i, nc, [&](int64_t m) { return X[tiled_index(m, c, ncols)]; });
+              yv = stencil_apply<KIND>(A, i, nc, [&](int64_t m) { return X[tiled_index(m, cy0 + c, ncols)]; });
             }
           }
           xs[w * LDS + c] = xv;
@@ -255,25 +264,27 @@ __global__ void __launch_bounds__(TD* TD) k_tsgemm(StencilView<T> A, const T* __
       }
     }
   }
-  double* out = partial + (int64_t)blockIdx.x * ncx * ncx;
+  double* out = partial + (int64_t)blockIdx.x * ncx * ncy;
 #pragma unroll
   for (int a = 0; a < RB; ++a) {
     const int row = ty * RB + a;
 #pragma unroll
     for (int b = 0; b < RB; ++b) {
       const int col = tx * RB + b;
-      if (row < ncx && col < ncx) out[(int64_t)col * ncx + row] = (double)acc[a][b];
+      if (row < ncx && col < ncy) out[(int64_t)col * ncx + row] = (double)acc[a][b];
     }
   }
 }
 
-// out[e] = sum_b partial[b][e] in a fixed order (deterministic): a block of
-// 256 threads covers 32 entries, warp g adding partials b = g, g + 8, ...
-// (four running sums), then the eight warp sums are added in warp order.
-__global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__ partial, int nblocks, int m,
-                                                      double* __restrict__ out) {
+// out = sum_b partial[b] in a fixed order (deterministic); a partial is a
+// rows x cols block (column-major) that lands at (r0, c0) of out (leading
+// dimension ld).  A block of 256 threads covers 32 entries, warp g adding
+// partials b = g, g + 8, ... (four running sums), then the eight warp sums
+// are added in warp order.
+__global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__ partial, int nblocks, int rows,
+                                                      int cols, double* __restrict__ out, int ld, int r0, int c0) {
   __shared__ double red[8][33];
-  const int mm = m * m;
+  const int mm = rows * cols;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int e = blockIdx.x * 32 + lane;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -293,7 +304,8 @@ __global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__
     double t = 0.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) t += red[q][lane];
-    out[e] = t;
+    const int row = e % rows, col = e / rows;
+    out[(int64_t)(c0 + col) * ld + r0 + row] = t;
   }
 }
 
@@ -302,17 +314,9 @@ __global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__
 namespace {
 
 // ---------------------------------------------------------------------------
-// Symmetric eigensolver for the K x K Gram matrix, one CTA, FP32: cyclic
-// Jacobi (Golub & Van Loan, sym.schur2 rotations) with the round-robin
-// ordering, so each round applies K/2 disjoint rotations at once.  With all
-// rotations of a round disjoint, G' = J^T G J acts on 2 x 2 blocks
-// independently: block (u, v) -> J_u^T B J_v, so a thread owning block
-// (u >= v) updates it and its mirror without synchronising with others.
-// Eigenvectors are accumulated as rows of Vt (V = Vt^T), sorted descending.
-// KP is the padded even order; a padded index has zero row/column and is
-// never rotated.  The pairs of every round are tabulated once; a round's
-// rotations are packed as {c, s, p, q} so that each is one 16-byte read, and
-// the rows of Vt are updated as 16-byte vectors.
+// Round-robin ordering of the Jacobi pairs: in round r of an even order KP
+// the KP / 2 pairs u = 0 .. KP/2 - 1 are disjoint and every pair of indices
+// meets once in KP - 1 rounds.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void rr_pair(int KP, int r, int u, int* p, int* q) {
   if (u == 0) {
@@ -321,136 +325,6 @@ __device__ __forceinline__ void rr_pair(int KP, int r, int u, int* p, int* q) {
   } else {
     *p = (r + u) % (KP - 1);
     *q = (r - u + (KP - 1)) % (KP - 1);
-  }
-}
-
-__host__ __device__ constexpr int jacobi_ldv(int KP) { return (KP + 3) / 4 * 4; }
-
-// Dynamic shared memory of k_jacobi_eig for padded order KP: vt, rot, g,
-// red, uv (all multiples of 4 bytes, vt and rot of 16), then the pair table.
-__host__ __device__ constexpr size_t jacobi_smem(int KP) {
-  return (size_t)KP * jacobi_ldv(KP) * 4            // vt
-         + (size_t)(KP / 2) * 16                    // rot
-         + (size_t)KP * (KP + 1) * 4                // g
-         + 32 * 4                                   // red
-         + (size_t)(KP / 2) * (KP / 2 + 1) / 2 * 4  // uv
-         + (size_t)(KP - 1) * (KP / 2) * 2;         // pair table
-}
-
-__global__ void __launch_bounds__(1024) k_jacobi_eig(const double* __restrict__ G, int K, int KP, int max_sweeps,
-                                                     float tol, double* __restrict__ evals,
-                                                     double* __restrict__ V) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int LG = KP + 1, LDV = jacobi_ldv(KP);
-  const int H = KP / 2;
-  float* vt = reinterpret_cast<float*>(smem_raw);                 // [KP][LDV], row a = eigenvector a
-  float4* rot = reinterpret_cast<float4*>(vt + KP * LDV);         // [H] {c, s, p, q}
-  float* g = reinterpret_cast<float*>(rot + H);                   // [KP][LG]
-  float* red = g + KP * LG;                                       // [32]
-  short2* uv = reinterpret_cast<short2*>(red + 32);              // [H (H + 1) / 2] blocks (u >= v)
-  const int nblk = H * (H + 1) / 2;
-  uchar2* pairs = reinterpret_cast<uchar2*>(uv + nblk);          // [KP - 1][H]
-  __shared__ int converged;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int u = tid; u < H; u += nt)
-    for (int v = 0; v <= u; ++v) uv[u * (u + 1) / 2 + v] = make_short2((short)u, (short)v);
-  for (int e = tid; e < (KP - 1) * H; e += nt) {
-    int pp, qq;
-    rr_pair(KP, e / H, e % H, &pp, &qq);
-    pairs[e] = make_uchar2((unsigned char)pp, (unsigned char)qq);
-  }
-  for (int e = tid; e < KP * KP; e += nt) {
-    const int a = e / KP, b = e % KP;
-    g[a * LG + b] = (a < K && b < K) ? (float)G[(int64_t)b * K + a] : 0.0f;
-  }
-  for (int e = tid; e < KP * LDV; e += nt) {
-    const int a = e / LDV, b = e % LDV;
-    vt[e] = (a == b) ? 1.0f : 0.0f;
-  }
-  __syncthreads();
-
-  const int nv4 = LDV / 4;  // 16-byte vectors per row of Vt
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // convergence test: off-diagonal mass against the diagonal
-    float off = 0.0f, dia = 0.0f;
-    for (int e = tid; e < KP * KP; e += nt) {
-      const int a = e / KP, b = e % KP;
-      const float x = g[a * LG + b];
-      if (a == b) dia += x * x; else off += x * x;
-    }
-    off = block_sum(off, red);
-    dia = block_sum(dia, red);
-    if (tid == 0) converged = (off <= tol * tol * dia);
-    __syncthreads();
-    if (converged) break;
-
-    for (int r = 0; r < KP - 1; ++r) {
-      for (int u = tid; u < H; u += nt) {
-        const uchar2 pq = pairs[r * H + u];
-        const int p = pq.x, q = pq.y;
-        const float gpp = g[p * LG + p], gqq = g[q * LG + q], gpq = g[p * LG + q];
-        float c = 1.0f, s = 0.0f;
-        if (gpq != 0.0f && fabsf(gpq) > 1e-30f) {
-          const float tau = (gqq - gpp) / (2.0f * gpq);
-          const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-          c = rsqrtf(1.0f + t * t);
-          s = t * c;
-        }
-        rot[u] = make_float4(c, s, __int_as_float(p), __int_as_float(q));
-      }
-      __syncthreads();
-      // 2x2 block updates (u >= v, mirrored)
-      for (int e = tid; e < nblk; e += nt) {
-        const short2 b = uv[e];
-        const int u = b.x, v = b.y;  // v <= u
-        const float4 ru = rot[u];
-        const int pu = __float_as_int(ru.z), qu = __float_as_int(ru.w);
-        const float cu = ru.x, su = ru.y;
-        if (u == v) {
-          const float gpp = g[pu * LG + pu], gqq = g[qu * LG + qu], gpq = g[pu * LG + qu];
-          const float t = su / cu;
-          g[pu * LG + pu] = gpp - t * gpq;
-          g[qu * LG + qu] = gqq + t * gpq;
-          g[pu * LG + qu] = 0.0f;
-          g[qu * LG + pu] = 0.0f;
-        } else {
-          const float4 rv = rot[v];
-          const int pv = __float_as_int(rv.z), qv = __float_as_int(rv.w);
-          const float cv = rv.x, sv = rv.y;
-          const float b00 = g[pu * LG + pv], b01 = g[pu * LG + qv], b10 = g[qu * LG + pv], b11 = g[qu * LG + qv];
-          const float m00 = cu * b00 - su * b10, m01 = cu * b01 - su * b11;
-          const float m10 = su * b00 + cu * b10, m11 = su * b01 + cu * b11;
-          const float n00 = m00 * cv - m01 * sv, n01 = m00 * sv + m01 * cv;
-          const float n10 = m10 * cv - m11 * sv, n11 = m10 * sv + m11 * cv;
-          g[pu * LG + pv] = n00; g[pu * LG + qv] = n01; g[qu * LG + pv] = n10; g[qu * LG + qv] = n11;
-          g[pv * LG + pu] = n00; g[qv * LG + pu] = n01; g[pv * LG + qu] = n10; g[qv * LG + qu] = n11;
-        }
-      }
-      // V <- V J: rows p, q of Vt, four columns at a time
-      for (int e = tid; e < H * nv4; e += nt) {
-        const int u = e / nv4, c4 = e - u * nv4;
-        const float4 ru = rot[u];
-        const int p = __float_as_int(ru.z), q = __float_as_int(ru.w);
-        const float c = ru.x, s = ru.y;
-        float4* rp = reinterpret_cast<float4*>(vt + p * LDV) + c4;
-        float4* rq = reinterpret_cast<float4*>(vt + q * LDV) + c4;
-        const float4 vp = *rp, vq = *rq;
-        *rp = make_float4(c * vp.x - s * vq.x, c * vp.y - s * vq.y, c * vp.z - s * vq.z, c * vp.w - s * vq.w);
-        *rq = make_float4(s * vp.x + c * vq.x, s * vp.y + c * vq.y, s * vp.z + c * vq.z, s * vp.w + c * vq.w);
-      }
-      __syncthreads();
-    }
-  }
-  // sort descending (ties by index) and write out
-  for (int a = tid; a < K; a += nt) {
-    const float la = g[a * LG + a];
-    int pos = 0;
-    for (int b = 0; b < K; ++b) {
-      const float lb = g[b * LG + b];
-      pos += (lb > la) || (lb == la && b < a);
-    }
-    evals[pos] = (double)la;
-    for (int row = 0; row < K; ++row) V[(int64_t)pos * K + row] = (double)vt[a * LDV + row];
   }
 }
 
@@ -716,6 +590,140 @@ __global__ void __launch_bounds__(CE_THREADS) k_chol_jacobi_eig(const double* __
       for (int i = lane; i < K; i += 32) V[(int64_t)c * K + i] = complete ? (double)X[c * LDX + i] : 0.0;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Eigen-decomposition of the Gram matrix for 128 < K <= 256 on a cluster of
+// two CTAs, FP32: one-sided (Hestenes) Jacobi on the columns of G itself.
+// For the symmetric positive semi-definite G, G W = U Lambda with W
+// orthogonal, so the normalised columns are eigenvectors and the column
+// norms the eigenvalues.  The K x K columns (256 KB in FP32) do not fit one
+// CTA: each rank keeps Kc = K / 2 of them in shared memory, a round's disjoint
+// pairs alternate between the ranks (pair u on rank u % 2), and a column
+// owned by the other rank is read and written through distributed shared
+// memory; the cluster barrier ends every round.  Eight lanes rotate one
+// pair as in k_chol_jacobi_eig.  NV = ceil(K / 32) float4 per lane and
+// column.
+// ---------------------------------------------------------------------------
+constexpr int CJ_THREADS = 512;
+constexpr int CJ_RANKS = 2;
+constexpr int CJ_MAX_SWEEPS = 40;
+
+__host__ __device__ constexpr size_t cluster_eig_smem(int K) {
+  return (size_t)((K + CJ_RANKS - 1) / CJ_RANKS) * ((K + 31) / 32 * 32) * 4 + (size_t)K * 8 + 64;
+}
+
+template <int NV>
+__global__ void __launch_bounds__(CJ_THREADS, 1) k_cluster_jacobi_eig(const double* __restrict__ G, int K, float tol,
+                                                                      double* __restrict__ evals,
+                                                                      double* __restrict__ V) {
+  namespace cgx = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int LDX = 32 * NV;
+  cgx::cluster_group cl = cgx::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int Kc = (K + CJ_RANKS - 1) / CJ_RANKS;
+  float* X = reinterpret_cast<float*>(smem_raw);  // [Kc][LDX]: columns rank Kc ..
+  float* lam = X + (size_t)Kc * LDX;              // [K]: this rank's entries (read by the others)
+  float* lall = lam + K;                          // [K]: every rank's, gathered
+  __shared__ int rotated[CJ_MAX_SWEEPS];
+  __shared__ float* xr[CJ_RANKS];
+  __shared__ float* lr[CJ_RANKS];
+  __shared__ int* rr[CJ_RANKS];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int e = tid; e < Kc * LDX; e += CJ_THREADS) {
+    const int c = e / LDX, i = e - c * LDX;
+    const int gc = rank * Kc + c;
+    X[e] = (gc < K && i < K) ? (float)G[(int64_t)gc * K + i] : 0.0f;
+  }
+  for (int i = tid; i < CJ_MAX_SWEEPS; i += CJ_THREADS) rotated[i] = 0;
+  if (tid < CJ_RANKS) {
+    xr[tid] = cl.map_shared_rank(X, tid);
+    lr[tid] = cl.map_shared_rank(lam, tid);
+    rr[tid] = cl.map_shared_rank(&rotated[0], tid);
+  }
+  cl.sync();
+  auto col = [&](int c) { return xr[c / Kc] + (size_t)(c % Kc) * LDX; };
+  const int R = K + (K & 1), H = R / 2;
+  const int g = lane & 7;
+  const int u = rank + CJ_RANKS * (tid >> 3);  // this group's pair (H <= 128: one pass)
+  for (int sweep = 0; sweep < CJ_MAX_SWEEPS; ++sweep) {
+    for (int rd = 0; rd < R - 1; ++rd) {
+      int p = R, q = R;
+      if (u < H) rr_pair(R, rd, u, &p, &q);
+      const bool act = p < K && q < K;
+      float4 vp[NV], vq[NV];
+      float a = 0.0f, b = 0.0f, c = 0.0f;
+      float4* xp = nullptr;
+      float4* xq = nullptr;
+      if (act) {
+        xp = reinterpret_cast<float4*>(col(p)) + g;
+        xq = reinterpret_cast<float4*>(col(q)) + g;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          vp[v] = xp[8 * v];
+          vq[v] = xq[8 * v];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          a = fmaf(vp[v].x, vp[v].x, fmaf(vp[v].y, vp[v].y, fmaf(vp[v].z, vp[v].z, fmaf(vp[v].w, vp[v].w, a))));
+          b = fmaf(vq[v].x, vq[v].x, fmaf(vq[v].y, vq[v].y, fmaf(vq[v].z, vq[v].z, fmaf(vq[v].w, vq[v].w, b))));
+          c = fmaf(vp[v].x, vq[v].x, fmaf(vp[v].y, vq[v].y, fmaf(vp[v].z, vq[v].z, fmaf(vp[v].w, vq[v].w, c))));
+        }
+      }
+      for (int off = 1; off < 8; off <<= 1) {  // butterfly within the eight-lane group
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
+        c += __shfl_xor_sync(0xffffffffu, c, off);
+      }
+      if (act && fabsf(c) > tol * sqrtf(a) * sqrtf(b)) {
+        const float zeta = __fdividef(b - a, 2.0f * c);
+        const float z = fminf(fabsf(zeta), 1e18f);
+        const float w = fmaf(z, z, 1.0f);
+        const float tt = copysignf(__frcp_rn(z + w * rsqrtf(w)), zeta);
+        const float cs = rsqrtf(fmaf(tt, tt, 1.0f)), sn = cs * tt;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float4 P0 = vp[v], Q0 = vq[v];
+          xp[8 * v] = make_float4(cs * P0.x - sn * Q0.x, cs * P0.y - sn * Q0.y, cs * P0.z - sn * Q0.z,
+                                  cs * P0.w - sn * Q0.w);
+          xq[8 * v] = make_float4(sn * P0.x + cs * Q0.x, sn * P0.y + cs * Q0.y, sn * P0.z + cs * Q0.z,
+                                  sn * P0.w + cs * Q0.w);
+        }
+        if (g == 0) rotated[sweep] = 1;
+      }
+      cl.sync();
+    }
+    // any rotation on any rank (flags of this sweep are final after the barrier)
+    int any = 0;
+    for (int q2 = 0; q2 < CJ_RANKS; ++q2) any |= rr[q2][sweep];
+    if (!any) break;  // the same decision on every rank
+  }
+  // eigenvalues = column norms (G W = U Lambda)
+  const int warp = tid >> 5;
+  for (int c = warp; c < Kc; c += CJ_THREADS / 32) {
+    const int gc = rank * Kc + c;
+    float s2 = 0.0f;
+    for (int i = lane; i < K; i += 32) s2 = fmaf(X[(size_t)c * LDX + i], X[(size_t)c * LDX + i], s2);
+    for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    if (lane == 0 && gc < K) lam[gc] = sqrtf(s2);
+  }
+  cl.sync();
+  // every rank's eigenvalues, then the position and output of the own columns
+  for (int c = tid; c < K; c += CJ_THREADS) lall[c] = lr[c / Kc][c];
+  __syncthreads();
+  for (int c = warp; c < Kc; c += CJ_THREADS / 32) {
+    const int gc = rank * Kc + c;
+    if (gc >= K) continue;
+    const float lc = lall[gc];
+    int pos = 0;
+    for (int b2 = lane; b2 < K; b2 += 32) pos += (lall[b2] > lc) || (lall[b2] == lc && b2 < gc);
+    for (int off = 16; off > 0; off >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, off);
+    const float inv = lc > 0.0f ? 1.0f / lc : 0.0f;
+    if (lane == 0) evals[pos] = (double)lc;
+    for (int i = lane; i < K; i += 32) V[(int64_t)pos * K + i] = (double)(X[(size_t)c * LDX + i] * inv);
+  }
+  cl.sync();  // no rank leaves while another may still read its shared memory
 }
 
 // Ogita & Aishima, "Iterative refinement for symmetric eigenvalue
@@ -1071,37 +1079,53 @@ nlsp_status tsgemm(nlsp_ctx* ctx, const nlsp_op* A, const T* X, int ncols, int n
                    int symmetrize) {
   cudaStream_t s = ctx->stream;
   const int64_t ntiles = n_pad / NLSP_TILE;
-  // Up to four resident blocks per SM, so that one block's staging loads
-  // overlap another's products; never more blocks than node chunks.
-#define NLSP_TSGEMM_LAUNCH(RB, TD)                                                                     \
-  do {                                                                                                \
-    constexpr int LDS_ = RB * TD + (sizeof(T) == 4 ? 4 : 2);                                          \
-    const size_t sm = (size_t)GRAM_CW * LDS_ * sizeof(T) * (WITH_A ? 2 : 1);                          \
-    NLSP_DISPATCH_KIND(A->kind, KD, {                                                                 \
-      auto fn = k_tsgemm<T, RB, TD, KD, WITH_A>;                                                      \
-      NLSP_TRY(set_smem((const void*)fn, sm));                                                        \
-      int per_sm = 1;                                                                                 \
-      NLSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TD * TD, sm));             \
+  int launches = 0;
+  // One product of X's columns [cx0, cx0 + nx) with Y's columns [cy0, cy0 +
+  // ny) (Y = X, or A X), summed into out at (cx0, cy0).  Up to four resident
+  // blocks per SM, so that one block's staging loads overlap another's
+  // products; never more blocks than node chunks.
+#define NLSP_TSGEMM_LAUNCH(RB, TD, TWO_, CX0, CY0, NX, NY)                                                \
+  do {                                                                                                   \
+    constexpr int LDS_ = RB * TD + (sizeof(T) == 4 ? 4 : 2);                                             \
+    const size_t sm = (size_t)GRAM_CW * LDS_ * sizeof(T) * ((WITH_A || TWO_) ? 2 : 1);                   \
+    NLSP_DISPATCH_KIND(A->kind, KD, {                                                                    \
+      auto fn = k_tsgemm<T, RB, TD, KD, WITH_A, TWO_>;                                                   \
+      NLSP_TRY(set_smem((const void*)fn, sm));                                                           \
+      int per_sm = 1;                                                                                    \
+      NLSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TD * TD, sm));                \
       const int blocks = (int)std::min<int64_t>((int64_t)ctx->num_sms * std::min(std::max(per_sm, 1), 4), \
-                                                std::max<int64_t>(ntiles * (NLSP_TILE / GRAM_CW), 1)); \
-      double* partial = slot_as<double>(ctx, SLOT_PART, (size_t)blocks * ncx * ncx);                  \
-      if (!partial) return NLSP_ERR_OOM;                                                              \
-      fn<<<blocks, TD * TD, sm, s>>>(view_of<T>(A), X, ncols, ncx, n_pad, partial);                   \
-      NLSP_LAUNCH_CHECK();                                                                            \
-      k_sum_partials<<<div_up((int64_t)ncx * ncx, 32), 256, 0, s>>>(partial, blocks, ncx, out);       \
-    });                                                                                               \
+                                                std::max<int64_t>(ntiles * (NLSP_TILE / GRAM_CW), 1));    \
+      double* partial = slot_as<double>(ctx, SLOT_PART, (size_t)blocks * (NX) * (NY));                   \
+      if (!partial) return NLSP_ERR_OOM;                                                                 \
+      fn<<<blocks, TD * TD, sm, s>>>(view_of<T>(A), X, ncols, NX, n_pad, partial, CX0, CY0, NY);         \
+      NLSP_LAUNCH_CHECK();                                                                               \
+      k_sum_partials<<<div_up((int64_t)(NX) * (NY), 32), 256, 0, s>>>(partial, blocks, NX, NY, out, ncx,  \
+                                                                     CX0, CY0);                          \
+      launches += 2;                                                                                     \
+    });                                                                                                  \
   } while (0)
-  if (ncx <= 32) NLSP_TSGEMM_LAUNCH(2, 16);
-  else if (ncx <= 64) NLSP_TSGEMM_LAUNCH(4, 16);
-  else if (ncx <= 128) NLSP_TSGEMM_LAUNCH(8, 16);
-  else return NLSP_ERR_INVALID;
+  if (ncx <= 32) NLSP_TSGEMM_LAUNCH(2, 16, false, 0, 0, ncx, ncx);
+  else if (ncx <= 64) NLSP_TSGEMM_LAUNCH(4, 16, false, 0, 0, ncx, ncx);
+  else if (ncx <= 128) NLSP_TSGEMM_LAUNCH(8, 16, false, 0, 0, ncx, ncx);
+  else if (ncx <= 256) {
+    // four quadrants of at most 128 x 128 (the off-diagonal ones computed
+    // rather than mirrored, so that the A-product variant needs no symmetry)
+    const int h = 128, rr = ncx - 128;
+    NLSP_TSGEMM_LAUNCH(8, 16, !WITH_A, 0, 0, h, h);
+    NLSP_TSGEMM_LAUNCH(8, 16, !WITH_A, 0, h, h, rr);
+    NLSP_TSGEMM_LAUNCH(8, 16, !WITH_A, h, 0, rr, h);
+    NLSP_TSGEMM_LAUNCH(8, 16, !WITH_A, h, h, rr, rr);
+  } else {
+    return NLSP_ERR_INVALID;
+  }
 #undef NLSP_TSGEMM_LAUNCH
   NLSP_LAUNCH_CHECK();
   if (symmetrize) {
     k_symmetrize<<<div_up((int64_t)ncx * ncx, 256), 256, 0, s>>>(out, ncx);
     NLSP_LAUNCH_CHECK();
+    ++launches;
   }
-  count_launches(ctx, symmetrize ? 3 : 2);
+  count_launches(ctx, launches);
   return NLSP_OK;
 }
 
@@ -1221,6 +1245,34 @@ nlsp_status chol_jacobi_eig(cudaStream_t s, const double* G, int K, int complete
   return NLSP_OK;
 }
 
+// Launches the two-CTA cluster eigensolver (128 < K <= 256).
+nlsp_status cluster_jacobi_eig(cudaStream_t s, const double* G, int K, double* evals, double* V) {
+  const size_t sm = cluster_eig_smem(K);
+  const int nv = (K + 31) / 32;
+  const void* fn = nv == 5   ? (const void*)k_cluster_jacobi_eig<5>
+                   : nv == 6 ? (const void*)k_cluster_jacobi_eig<6>
+                   : nv == 7 ? (const void*)k_cluster_jacobi_eig<7>
+                             : (const void*)k_cluster_jacobi_eig<8>;
+  NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(CJ_RANKS);
+  cfg.blockDim = dim3(CJ_THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CJ_RANKS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const float tol = 4e-6f;
+  void* args[] = {(void*)&G, (void*)&K, (void*)&tol, (void*)&evals, (void*)&V};
+  NLSP_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+  return NLSP_OK;
+}
+
 // Eigen-decomposition of the FP64 Gram matrix G (K x K): descending evals and
 // eigenvectors V (column-major).  refine = number of FP64 refinement steps.
 // work: 6 K^2 + K doubles.
@@ -1228,16 +1280,13 @@ nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double
   cudaStream_t s = ctx->stream;
   if (K <= 128) {  // FP32 pivoted Cholesky + one-sided Jacobi (a complete basis when it is refined)
     NLSP_TRY(chol_jacobi_eig(s, G, K, refine > 0, evals, V));
-    count_launches(ctx, 1);
-    if (refine == 0) return NLSP_OK;
+  } else if (K <= 256) {  // FP32 one-sided Jacobi on G over a cluster of two CTAs
+    NLSP_TRY(cluster_jacobi_eig(s, G, K, evals, V));
   } else {
-    const int KP = K + (K & 1);
-    const size_t sm = jacobi_smem(KP);
-    NLSP_TRY(set_smem((const void*)k_jacobi_eig, sm));
-    k_jacobi_eig<<<1, 1024, sm, s>>>(G, K, KP, 30, 4e-6f, evals, V);
-    NLSP_LAUNCH_CHECK();
-    count_launches(ctx, 1);
+    return NLSP_ERR_INVALID;
   }
+  count_launches(ctx, 1);
+  if (refine == 0) return NLSP_OK;
   if (refine > 0) {
     double* XtX = work;
     double* GX = XtX + K * K;
