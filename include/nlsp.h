@@ -220,9 +220,10 @@ NLSP_API nlsp_status nlsp_smooth_samples(nlsp_ctx* ctx, const nlsp_op* A, int K,
    NLSP_MIXED_FP32 samples agree with the FP64 stream to a few FP32 ulps):
    smooths them s1 times, takes
    the leading k left singular vectors of S as P (thin SVD via the Gram
-   matrix S^T S, a Jacobi eigensolver and, in FP64, iterative refinement),
-   then forms and factors A_c = P^T A P for the full rank k (call
-   nlsp_factor_coarse to truncate).  Requires 1 <= k <= K <= 128, K <= n,
+   matrix S^T S, a one-sided Jacobi eigensolver (K > 128: on a cluster of
+   two CTAs) and, in FP64, iterative refinement), then forms and factors
+   A_c = P^T A P for the full rank k (call nlsp_factor_coarse to
+   truncate).  Requires 1 <= k <= 128, k <= K <= 256, K <= n,
    nu1 = nu2 >= 1 (PCG needs a symmetric preconditioner) and
    0 < omega < 2.  Synchronises.  Errors: NLSP_ERR_INVALID, NLSP_ERR_NOT_SPD
    (rank-deficient samples), NLSP_ERR_OOM, NLSP_ERR_CUDA. */
@@ -234,7 +235,8 @@ NLSP_API nlsp_status nlsp_build_prolongation(nlsp_ctx* ctx, const nlsp_op* A, co
    S^T A S, so that P = S V_k Sigma_k^-1 satisfies P^T A P = I and A^{1/2} P
    spans the top-k left singular subspace of A^{1/2} S, the coarse space that
    minimises ||A^{1/2} (I - Pi_A(P)) S||_F^2.  The singular values reported
-   (nlsp_prec_copy_sigma) are those of A^{1/2} S.  Same arguments and errors. */
+   (nlsp_prec_copy_sigma) are those of A^{1/2} S.  Same arguments and errors,
+   except that K <= 128. */
 NLSP_API nlsp_status nlsp_build_prolongation_a_weighted(nlsp_ctx* ctx, const nlsp_op* A,
                                                         const nlsp_setup_params* params, const double* dev_S0,
                                                         nlsp_prec** M_out);
@@ -250,8 +252,8 @@ NLSP_API nlsp_status nlsp_build_prolongation_a_weighted(nlsp_ctx* ctx, const nls
    counter-based generator of nlsp_random_normal with params->seed and stream
    NLSP_STREAM_SKETCH (element (c, j) is normal number j K + c).  The
    singular values reported are those of B (l values, zeros beyond).
-   Requires 0 <= oversample, k + oversample <= K, 0 <= power_iters <= 16;
-   other arguments and errors as nlsp_build_prolongation (NLSP_ERR_NOT_SPD
+   Requires 0 <= oversample, k + oversample <= K <= 128, 0 <= power_iters <=
+   16; other arguments and errors as nlsp_build_prolongation (NLSP_ERR_NOT_SPD
    also when S Omega is rank deficient). */
 NLSP_API nlsp_status nlsp_build_prolongation_randomized(nlsp_ctx* ctx, const nlsp_op* A,
                                                         const nlsp_setup_params* params, const double* dev_S0,

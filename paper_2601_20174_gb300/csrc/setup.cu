@@ -821,19 +821,21 @@ __global__ void k_make_basis_coeffs(const double* __restrict__ evals, const doub
 // with its rows padded with zeros to ldm, a multiple of KC, so the product
 // loop needs no column test; it is read as 16-byte broadcasts.  The input
 // column loads are issued CU at a time ahead of their products.
+// This launch forms output columns [jlo, jlo + jw) (M's columns staged for
+// them only).
 template <typename T, int KC, int CU>
 __global__ void __launch_bounds__(NLSP_TILE) k_tile_times_small(const T* __restrict__ In, int ncin,
                                                                const T* __restrict__ Mg, int k, int64_t n_pad,
-                                                               T* __restrict__ Out) {
+                                                               T* __restrict__ Out, int jlo, int jw) {
   using V = typename Vec16<T>::type;
   constexpr int VN = Vec16<T>::N;
   static_assert(KC % VN == 0, "KC must be a multiple of the vector width");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* M = reinterpret_cast<T*>(smem_raw);
-  const int ldm = (k + KC - 1) / KC * KC;
+  const int ldm = (jw + KC - 1) / KC * KC;
   for (int e = threadIdx.x; e < ncin * ldm; e += blockDim.x) {
     const int c = e / ldm, j = e % ldm;
-    M[e] = j < k ? Mg[c * k + j] : T(0);
+    M[e] = j < jw ? Mg[c * k + jlo + j] : T(0);
   }
   __syncthreads();
   const int64_t ntiles = n_pad / NLSP_TILE;
@@ -841,7 +843,7 @@ __global__ void __launch_bounds__(NLSP_TILE) k_tile_times_small(const T* __restr
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const T* in = In + t * ncin * NLSP_TILE + w;
     T* out = Out + t * (int64_t)k * NLSP_TILE + w;
-    for (int j0 = 0; j0 < k; j0 += KC) {
+    for (int j0 = 0; j0 < jw; j0 += KC) {
       T acc[KC];
 #pragma unroll
       for (int j = 0; j < KC; ++j) acc[j] = T(0);
@@ -875,7 +877,7 @@ __global__ void __launch_bounds__(NLSP_TILE) k_tile_times_small(const T* __restr
       }
 #pragma unroll
       for (int j = 0; j < KC; ++j)
-        if (j0 + j < k) out[(int64_t)(j0 + j) * NLSP_TILE] = acc[j];
+        if (j0 + j < jw) out[(int64_t)(jlo + j0 + j) * NLSP_TILE] = acc[j];
     }
   }
 }
@@ -1134,20 +1136,31 @@ nlsp_status tile_times_small(nlsp_ctx* ctx, const T* In, int ncin, const T* M, i
   // register chunk: the smallest of 16 / 32 / 64 (FP64: 16 / 32) columns
   // that covers k, else the largest in several passes
   const int kc = k <= 16 ? 16 : (k <= 32 || sizeof(T) == 8) ? 32 : 64;
-  const size_t sm = (size_t)ncin * ((k + kc - 1) / kc * kc) * sizeof(T);
   const void* fn;
   if (kc == 16) fn = (const void*)k_tile_times_small<T, 16, 16>;
   else if (kc == 32) fn = (const void*)k_tile_times_small<T, 32, 16>;
   else fn = (const void*)k_tile_times_small<T, 64, 16>;
-  NLSP_TRY(set_smem(fn, sm));
+  // output columns per launch: all of them when M fits in shared memory,
+  // else chunks of whole kc (a wide FP64 M: K = 256, k = 128 is 256 KB)
+  const size_t limit = 200 * 1024;
+  int width = (k + kc - 1) / kc * kc;
+  while (width > kc && (size_t)ncin * width * sizeof(T) > limit) width -= kc;
+  if ((size_t)ncin * width * sizeof(T) > limit) return NLSP_ERR_INVALID;
+  NLSP_TRY(set_smem(fn, (size_t)ncin * width * sizeof(T)));
   const int64_t ntiles = n_pad / NLSP_TILE;
-  const int bt = NLSP_TILE;
   const int g = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 8);
-  if (kc == 16) k_tile_times_small<T, 16, 16><<<g, bt, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
-  else if (kc == 32) k_tile_times_small<T, 32, 16><<<g, bt, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
-  else k_tile_times_small<T, 64, 16><<<g, bt, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out);
-  NLSP_LAUNCH_CHECK();
-  count_launches(ctx, 1);
+  int launches = 0;
+  for (int jlo = 0; jlo < k; jlo += width) {
+    const int jw = std::min(width, k - jlo);
+    const size_t sm = (size_t)ncin * ((jw + kc - 1) / kc * kc) * sizeof(T);
+    if (kc == 16) k_tile_times_small<T, 16, 16><<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out, jlo, jw);
+    else if (kc == 32)
+      k_tile_times_small<T, 32, 16><<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out, jlo, jw);
+    else k_tile_times_small<T, 64, 16><<<g, NLSP_TILE, sm, ctx->stream>>>(In, ncin, M, k, n_pad, Out, jlo, jw);
+    NLSP_LAUNCH_CHECK();
+    ++launches;
+  }
+  count_launches(ctx, launches);
   return NLSP_OK;
 }
 
@@ -1176,7 +1189,7 @@ nlsp_status check_setup_params(const nlsp_op* A, const nlsp_setup_params* p, boo
   if (!A || !p) return NLSP_ERR_INVALID;
   if (p->precision < NLSP_FP64 || p->precision > NLSP_MIXED_TF32) return NLSP_ERR_INVALID;
   if (p->k < 1 || p->k > 128 || p->k > A->n) return NLSP_ERR_INVALID;
-  if (need_K && (p->K < p->k || p->K > 128 || p->K > A->n || p->s1 < 0)) return NLSP_ERR_INVALID;
+  if (need_K && (p->K < p->k || p->K > 256 || p->K > A->n || p->s1 < 0)) return NLSP_ERR_INVALID;
   if (p->nu1 < 1 || p->nu2 != p->nu1 || p->nu1 > 64) return NLSP_ERR_INVALID;
   if (!(p->omega > 0.0) || !(p->omega < 2.0)) return NLSP_ERR_INVALID;
   return NLSP_OK;
@@ -1656,6 +1669,10 @@ extern "C" nlsp_status nlsp_build_prolongation_a_weighted(nlsp_ctx* ctx, const n
   if (!ctx || !M_out) return NLSP_ERR_INVALID;
   *M_out = nullptr;
   NLSP_TRY(check_setup_params(A, params, true));
+  if (params->K > 128) {  // the wider (K <= 256) eigensolver path serves the exact-SVD basis only
+    nlsp_record_message("nlsp_build_prolongation_a_weighted: K <= 128");
+    return NLSP_ERR_INVALID;
+  }
   NLSP_CUDA(cudaSetDevice(ctx->device));
   const BasisChoice bc{1, 0, 0, nullptr, 0};
   if (params->precision == NLSP_FP64) return build_impl<double>(ctx, A, params, dev_S0, M_out, bc);
@@ -1669,6 +1686,10 @@ extern "C" nlsp_status nlsp_build_prolongation_randomized(nlsp_ctx* ctx, const n
   if (!ctx || !M_out) return NLSP_ERR_INVALID;
   *M_out = nullptr;
   NLSP_TRY(check_setup_params(A, params, true));
+  if (params->K > 128) {  // the wider (K <= 256) eigensolver path serves the exact-SVD basis only
+    nlsp_record_message("nlsp_build_prolongation_randomized: K <= 128");
+    return NLSP_ERR_INVALID;
+  }
   if (oversample < 0 || params->k + oversample > params->K || power_iters < 0 || power_iters > 16) {
     nlsp_record_message("nlsp_build_prolongation_randomized: need 0 <= oversample, k + oversample <= K, "
                         "0 <= power_iters <= 16");

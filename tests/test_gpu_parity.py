@@ -189,6 +189,54 @@ def test_setup_fp64_subspace_sigma_and_galerkin(ctx, name):
     assert np.max(np.abs(Lf @ Lf.T - Ac)) <= 1e-12 * np.max(np.abs(Ac))
 
 
+@pytest.mark.parametrize("K", [160, 256])
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_setup_wide_sample_blocks(ctx, K, precision):
+    # 128 < K <= 256: the Gram matrix in 128-column quadrants and its
+    # eigenvectors by one-sided Jacobi on a cluster of two CTAs (then the
+    # FP64 refinement in the FP64 path); sigma, span(P) and A_c against the
+    # oracle's SVD of the same smoothed samples
+    p = gen.grf_diffusion_2d(N=40, k=64, K=K, seed=31, tol=1e-8)
+    A = op.assemble(p)
+    ref = osetup.build(A, p.S0, p.k, p.omega, p.s1)
+    M = _api().Preconditioner.build(_api().Operator.from_problem(ctx, p), to_dev(p.S0), p.k, p.s1, p.nu, p.omega,
+                                    precision)
+    P, sig = to_np(M.basis()), to_np(M.sigma())
+    s_ref = ref["sigma"][: p.k + 1]
+    gap = (s_ref[p.k - 1] ** 2 - s_ref[p.k] ** 2) / s_ref[0] ** 2
+    if precision == FP64:
+        tol_s = 1e-9 * s_ref + 1e-13 * s_ref[0] ** 2 / s_ref
+        assert np.all(np.abs(sig[: p.k + 1] - s_ref) <= tol_s), (sig[: p.k + 1] - s_ref) / s_ref
+        assert projector_dist(P, ref["P"]) <= max(1e-8, 1e-13 / gap)
+        assert np.max(np.abs(P.T @ P - np.eye(p.k))) <= 1e-12
+        Ac, _ = (to_np(t) for t in M.coarse())
+        Ac_ref = osetup.galerkin(A, P)
+        assert np.max(np.abs(Ac - Ac_ref)) <= 1e-12 * np.max(np.abs(Ac_ref))
+    else:
+        assert np.all(np.abs(sig[: p.k + 1] - s_ref) <= 1e-4 * s_ref[0]), (sig[: p.k + 1] - s_ref)
+        Q = np.linalg.qr(P)[0]
+        assert projector_dist(Q, ref["P"]) <= max(1e-3, 1e-6 / gap)
+    b = p.f[:, 0]
+    x, res = M.solve(to_dev(b), tol=1e-8)
+    assert res[0].status == 0
+    assert np.linalg.norm(b - A @ to_np(x)) / np.linalg.norm(b) <= 1e-8 * 1.01
+
+
+def test_setup_wide_sample_blocks_limits(ctx):
+    # K <= 256 for the exact-SVD basis; the A-weighted and randomised bases
+    # keep K <= 128
+    api = _api()
+    p = gen.grf_diffusion_2d(N=24, k=8, K=160, seed=3, tol=1e-8)
+    Aop = api.Operator.from_problem(ctx, p)
+    with pytest.raises(api.L.NlspError):
+        api.Preconditioner.build(Aop, to_dev(p.S0), p.k, p.s1, p.nu, p.omega, FP64, a_weighted=True)
+    with pytest.raises(api.L.NlspError):
+        api.Preconditioner.build_randomized(Aop, to_dev(p.S0), p.k, 8, 1, None, p.s1, p.nu, p.omega, FP64)
+    q = gen.grf_diffusion_2d(N=24, k=8, K=257, seed=3, tol=1e-8)
+    with pytest.raises(api.L.NlspError):
+        api.Preconditioner.build(api.Operator.from_problem(ctx, q), to_dev(q.S0), q.k, q.s1, q.nu, q.omega, FP64)
+
+
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_setup_mixed_sigma_and_subspace(ctx, name):
     # FP32 preconditioner: the Gram matrix is decomposed in FP32 (pivoted
