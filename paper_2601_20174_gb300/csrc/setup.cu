@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(CE_THREADS) k_chol_jacobi_eig(const double* __
       r = j;
       break;
     }
-    const float sd = sqrtf(d), isd = 1.0f / sd, id = 1.0f / d;
+    const float isd = rsqrtf(d), sd = d * isd, id = isd * isd;
     const int t = tid >> 2, sub = tid & 3;  // four threads per trailing row
     const int i = j + 1 + t;
     if (i < K) {
@@ -490,13 +490,13 @@ __global__ void __launch_bounds__(CE_THREADS) k_chol_jacobi_eig(const double* __
         b += __shfl_xor_sync(0xffffffffu, b, off);
         c += __shfl_xor_sync(0xffffffffu, c, off);
       }
-      if (act && fabsf(c) > tol * sqrtf(a) * sqrtf(b)) {
+      if (act && fabsf(c) * rsqrtf(a) * rsqrtf(b) > tol) {  // (a zero column gives NaN: no rotation)
         // the rotation zeroing the pair's inner product (Rutishauser's
         // formulas); |zeta| is capped so that zeta^2 stays finite
         const float zeta = __fdividef(b - a, 2.0f * c);
         const float z = fminf(fabsf(zeta), 1e18f);
         const float w = fmaf(z, z, 1.0f);
-        const float tt = copysignf(__frcp_rn(z + w * rsqrtf(w)), zeta);
+        const float tt = copysignf(__fdividef(1.0f, z + w * rsqrtf(w)), zeta);
         const float cs = rsqrtf(fmaf(tt, tt, 1.0f)), sn = cs * tt;
         float4* xp = reinterpret_cast<float4*>(X + p * LDX) + g;
         float4* xq = reinterpret_cast<float4*>(X + q * LDX) + g;
@@ -676,11 +676,11 @@ __global__ void __launch_bounds__(CJ_THREADS, 1) k_cluster_jacobi_eig(const doub
         b += __shfl_xor_sync(0xffffffffu, b, off);
         c += __shfl_xor_sync(0xffffffffu, c, off);
       }
-      if (act && fabsf(c) > tol * sqrtf(a) * sqrtf(b)) {
+      if (act && fabsf(c) * rsqrtf(a) * rsqrtf(b) > tol) {  // (a zero column gives NaN: no rotation)
         const float zeta = __fdividef(b - a, 2.0f * c);
         const float z = fminf(fabsf(zeta), 1e18f);
         const float w = fmaf(z, z, 1.0f);
-        const float tt = copysignf(__frcp_rn(z + w * rsqrtf(w)), zeta);
+        const float tt = copysignf(__fdividef(1.0f, z + w * rsqrtf(w)), zeta);
         const float cs = rsqrtf(fmaf(tt, tt, 1.0f)), sn = cs * tt;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -1171,11 +1171,17 @@ nlsp_status smooth_tiled(nlsp_ctx* ctx, const nlsp_op* A, int K, int s1, double 
                          T** result) {
   T* src = a;
   T* dst = tmp;
-  constexpr int CPT = 8;  // 8: 67.8 us per sweep at 512^2, K = 128 (4: 77.4, 2: 108.8; 16 was slower)
-  const dim3 g((unsigned)div_up(n_pad, 256), (unsigned)div_up(K, CPT));
+  // columns per thread: 8 on large systems (67.8 us per sweep at 512^2, K =
+  // 128, against 77.4 with 4), 4 where 8 would leave too few threads
+  const bool wide = n_pad >= 65536;
+  const int cpt = wide ? 8 : 4;
+  const dim3 g((unsigned)div_up(n_pad, 256), (unsigned)div_up(K, cpt));
   for (int it = 0; it < s1; ++it) {
     NLSP_DISPATCH_KIND(A->kind, KD, {
-      k_smooth_sweep<KD, T, CPT><<<g, 256, 0, ctx->stream>>>(view_of<T>(A), (T)omega, K, (int)n_pad, src, dst);
+      if (wide)
+        k_smooth_sweep<KD, T, 8><<<g, 256, 0, ctx->stream>>>(view_of<T>(A), (T)omega, K, (int)n_pad, src, dst);
+      else
+        k_smooth_sweep<KD, T, 4><<<g, 256, 0, ctx->stream>>>(view_of<T>(A), (T)omega, K, (int)n_pad, src, dst);
     });
     NLSP_LAUNCH_CHECK();
     std::swap(src, dst);
