@@ -731,14 +731,20 @@ __global__ void __launch_bounds__(CJ_THREADS, 1) k_cluster_jacobi_eig(const doub
 // XtX = X^T X and S = X^T G X:  R = I - XtX, lambda_i = S_ii / (1 - R_ii),
 // E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i) when the gap exceeds
 // delta = 2 (||S - diag(lambda)|| + ||G|| ||R||), else R_ij / 2; E_ii = R_ii / 2.
-// Writes E and lambda; the caller forms X <- X + X E.  One block.
+// Writes E and lambda; the caller forms X <- X + X E.
+// One block per column j of E (K <= 256 blocks): every block forms lambda,
+// the two norms and max |lambda| itself (K^2 cheap reads), then divides only
+// its column, so the K^2 FP64 divisions are spread over K SMs.
 __global__ void k_oa_step(const double* __restrict__ XtX, const double* __restrict__ S, int K, double* __restrict__ E,
                           double* __restrict__ lam) {
   __shared__ double red[32];
+  __shared__ double lm[256];
+  __shared__ double mx;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < K; i += nt) {
     const double rii = 1.0 - XtX[(int64_t)i * K + i];
-    lam[i] = S[(int64_t)i * K + i] / (1.0 - rii);
+    lm[i] = S[(int64_t)i * K + i] / (1.0 - rii);
+    if (blockIdx.x == 0) lam[i] = lm[i];
   }
   __syncthreads();
   double so = 0.0, rr = 0.0, lmax = 0.0;
@@ -749,9 +755,9 @@ __global__ void k_oa_step(const double* __restrict__ XtX, const double* __restri
     if (i != j) so += S[e] * S[e];
   }
   for (int i = tid; i < K; i += nt) {
-    const double d = S[(int64_t)i * K + i] - lam[i];
+    const double d = S[(int64_t)i * K + i] - lm[i];
     so += d * d;
-    lmax = fmax(lmax, fabs(lam[i]));
+    lmax = fmax(lmax, fabs(lm[i]));
   }
   so = block_sum(so, red);
   rr = block_sum(rr, red);
@@ -759,7 +765,6 @@ __global__ void k_oa_step(const double* __restrict__ XtX, const double* __restri
   for (int off = 16; off > 0; off >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
   if ((tid & 31) == 0) red[tid >> 5] = lmax;
   __syncthreads();
-  __shared__ double mx;
   if (tid < 32) {
     double m = tid < (nt >> 5) ? red[tid] : 0.0;
     for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
@@ -767,12 +772,13 @@ __global__ void k_oa_step(const double* __restrict__ XtX, const double* __restri
   }
   __syncthreads();
   const double delta = 2.0 * (sqrt(so) + mx * sqrt(rr));
-  for (int e = tid; e < K * K; e += nt) {
-    const int i = e % K, j = e / K;
+  const int j = blockIdx.x;
+  for (int i = tid; i < K; i += nt) {
+    const int64_t e = (int64_t)j * K + i;
     const double r = (i == j ? 1.0 : 0.0) - XtX[e];
     double v;
     if (i == j) v = 0.5 * r;
-    else if (fabs(lam[j] - lam[i]) > delta) v = (S[e] + lam[j] * r) / (lam[j] - lam[i]);
+    else if (fabs(lm[j] - lm[i]) > delta) v = (S[e] + lm[j] * r) / (lm[j] - lm[i]);
     else v = 0.5 * r;
     E[e] = v;
   }
@@ -1323,7 +1329,7 @@ nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double
       mm(V, 1, V, XtX);
       mm(G, 0, V, GX);
       mm(V, 1, GX, S);
-      k_oa_step<<<1, 512, 0, s>>>(XtX, S, K, E, lam);
+      k_oa_step<<<K, 256, 0, s>>>(XtX, S, K, E, lam);
       mm(V, 0, E, XE);
       k_add<<<div_up((int64_t)K * K, 256), 256, 0, s>>>(V, XE, K * K);
       NLSP_LAUNCH_CHECK();
@@ -1332,7 +1338,7 @@ nlsp_status gram_eigen(nlsp_ctx* ctx, const double* G, int K, int refine, double
     mm(V, 1, V, XtX);
     mm(G, 0, V, GX);
     mm(V, 1, GX, S);
-    k_oa_step<<<1, 512, 0, s>>>(XtX, S, K, E, lam);
+    k_oa_step<<<K, 256, 0, s>>>(XtX, S, K, E, lam);
     NLSP_CUDA(cudaMemcpyAsync(vcopy, V, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
     k_sort_eig<<<1, 1024, 0, s>>>(lam, vcopy, K, evals, V);
     NLSP_LAUNCH_CHECK();
