@@ -1001,23 +1001,36 @@ inline size_t spd_inverse_smem(int m) { return sizeof(double) * ((size_t)m * (m 
 __global__ void __launch_bounds__(256) k_gemm_small(const double* __restrict__ A, int lda, int ta,
                                                     const double* __restrict__ B, int ldb, int tb,
                                                     double* __restrict__ C, int ldc, int m, int n, int kk) {
-  // one 16 x 16 tile of C per block; the inner dimension in chunks of 16,
-  // op(A) and op(B) chunks staged in shared memory
-  __shared__ double As[16][17], Bs[16][17];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // one 16 x 16 tile of C per block; the inner dimension in strips of up to
+  // 128 (one strip, i.e. one round of loads, for K <= 128), op(A) and op(B)
+  // strips staged in shared memory with loads coalesced along the stored
+  // dimension, then four interleaved FP64 FMA chains per output
+  constexpr int LC = 128;
+  __shared__ double As[LC][17];      // op(A)(i0 + ii, l0 + l) at As[l][ii]
+  __shared__ double Bs[16][LC + 1];  // op(B)(l0 + l, j0 + jj) at Bs[jj][l]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = blockIdx.x * 16, j0 = blockIdx.y * 16;
-  double acc = 0.0;
-  for (int l0 = 0; l0 < kk; l0 += 16) {
-    const int ai = i0 + tx, al = l0 + ty;  // op(A)(ai, al)
-    As[ty][tx] = (ai < m && al < kk) ? (ta ? A[(int64_t)ai * lda + al] : A[(int64_t)al * lda + ai]) : 0.0;
-    const int bl = l0 + tx, bj = j0 + ty;  // op(B)(bl, bj)
-    Bs[ty][tx] = (bl < kk && bj < n) ? (tb ? B[(int64_t)bl * ldb + bj] : B[(int64_t)bj * ldb + bl]) : 0.0;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  for (int l0 = 0; l0 < kk; l0 += LC) {
+    const int lw = min(LC, kk - l0);
+    for (int e = tid; e < 16 * LC; e += 256) {
+      const int ii = ta ? e / LC : e % 16, la = ta ? e % LC : e / 16;
+      const int ai = i0 + ii, al = l0 + la;
+      As[la][ii] = (ai < m && la < lw) ? (ta ? A[(int64_t)ai * lda + al] : A[(int64_t)al * lda + ai]) : 0.0;
+      const int jj = tb ? e % 16 : e / LC, lb = tb ? e / 16 : e % LC;
+      const int bj = j0 + jj, bl = l0 + lb;
+      Bs[jj][lb] = (bj < n && lb < lw) ? (tb ? B[(int64_t)bl * ldb + bj] : B[(int64_t)bj * ldb + bl]) : 0.0;
+    }
     __syncthreads();
-#pragma unroll
-    for (int t = 0; t < 16; ++t) acc = fma(As[t][tx], Bs[ty][t], acc);
+    for (int l = 0; l < lw; l += 4) {  // entries past lw are zero
+      a0 = fma(As[l][tx], Bs[ty][l], a0);
+      a1 = fma(As[l + 1][tx], Bs[ty][l + 1], a1);
+      a2 = fma(As[l + 2][tx], Bs[ty][l + 2], a2);
+      a3 = fma(As[l + 3][tx], Bs[ty][l + 3], a3);
+    }
     __syncthreads();
   }
-  if (i0 + tx < m && j0 + ty < n) C[(int64_t)(j0 + ty) * ldc + i0 + tx] = acc;
+  if (i0 + tx < m && j0 + ty < n) C[(int64_t)(j0 + ty) * ldc + i0 + tx] = (a0 + a1) + (a2 + a3);
 }
 
 // Coefficients of the randomised basis: M = X V[:, :k] (K x k, row-major
