@@ -1292,8 +1292,7 @@ nlsp_status cluster_jacobi_eig(cudaStream_t s, const double* G, int K, double* e
                    : nv == 7 ? (const void*)k_cluster_jacobi_eig<7>
                              : (const void*)k_cluster_jacobi_eig<8>;
   NLSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  cudaLaunchConfig_t cfg;
-  memset(&cfg, 0, sizeof(cfg));
+  cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CJ_RANKS);
   cfg.blockDim = dim3(CJ_THREADS);
   cfg.dynamicSmemBytes = sm;
@@ -1410,9 +1409,7 @@ nlsp_status orthonormalize_small(nlsp_ctx* ctx, nlsp_prec* M, const double* G, i
   double* H = WX + (size_t)K * l;    // l x l
   double* Lf = H + (size_t)l * l;
   double* Hinv = Lf + (size_t)l * l;
-  double* Lit = Hinv + (size_t)l * l;
-  double* Xn = Lit + (size_t)l * l;  // l x l scratch is enough for nothing else: X L^-T goes to WX
-  (void)Xn;
+  double* Lit = Hinv + (size_t)l * l;  // X L^-T goes to WX
   const double* WXp = X;
   if (G) {
     NLSP_TRY(gemm64(ctx, 0, 0, K, l, K, G, K, X, K, WX, K));
