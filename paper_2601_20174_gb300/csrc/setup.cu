@@ -155,6 +155,123 @@ __global__ void __launch_bounds__(256) k_smooth_sweep(StencilView<T> A, T omega,
   }
 }
 
+// The same sweep on the 2D grids, streamed along grid rows: thread x of a
+// block walks the rows j0 .. j0 + band - 1 of grid column x for one group of
+// CPT sample columns, holding the rows below, at and above the current one
+// in registers, so that every sample value is read from memory once per band
+// (plus the two rows around it) instead of once more for each vertical
+// neighbour.  East/west (and, for the 9-point stencil, diagonal) neighbours
+// are read from lines the warp itself has just loaded.  Grid: x over
+// SR_THREADS grid columns, y over bands, z over column groups; the first
+// block of each column group also zeroes the padding rows.  The neighbours
+// are visited in the order for_each_neighbour uses, so the sums are the same.
+constexpr int SR_THREADS = 128;
+
+template <int KIND, typename T, int CPT>
+__global__ void __launch_bounds__(SR_THREADS) k_smooth_rows(StencilView<T> A, T omega, int ncols, int n_pad, int band,
+                                                           const T* __restrict__ Sin, T* __restrict__ Sout) {
+  static_assert(KIND == ST_5PT || KIND == ST_9PT, "row streaming needs a 2D grid");
+  const int N = A.N;
+  const int cbase = blockIdx.z * CPT;
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    for (int64_t i = A.n + threadIdx.x; i < n_pad; i += SR_THREADS) {
+      const int64_t e0 = tiled_index(i, cbase, ncols);
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+        if (cbase + c < ncols) Sout[e0 + (int64_t)c * NLSP_TILE] = T(0);
+    }
+  }
+  const int x = blockIdx.x * SR_THREADS + threadIdx.x;
+  const int j0 = blockIdx.y * band;
+  if (x >= N || j0 >= N) return;
+  const int j1 = min(j0 + band, N);
+  // the CPT columns of node i (0 past ncols)
+  auto load = [&](int64_t i, T(&v)[CPT]) {
+    const int64_t e = tiled_index(i, cbase, ncols);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) v[c] = cbase + c < ncols ? Sin[e + (int64_t)c * NLSP_TILE] : T(0);
+  };
+  T rs[CPT], rc[CPT], rn[CPT], t[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) rs[c] = rn[c] = T(0);
+  if (j0 > 0) load((int64_t)(j0 - 1) * N + x, rs);
+  load((int64_t)j0 * N + x, rc);
+  T cys = T(0);  // 5-point: coupling of the current row to the row below
+  if (KIND == ST_5PT && j0 > 0) cys = A.cy[(int64_t)(j0 - 1) * N + x];
+  const bool w = x > 0, e = x < N - 1;
+  for (int j = j0; j < j1; ++j) {
+    const int64_t idx = (int64_t)j * N + x;
+    const bool so = j > 0, no = j < N - 1;
+    if (no) load(idx + N, rn);
+    T as[CPT];
+    T wd;
+    auto add = [&](T a, const T(&v)[CPT]) {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) as[c] += a * v[c];
+    };
+    if constexpr (KIND == ST_9PT) {
+      wd = omega * A.cdinv;
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) as[c] = A.c[0] * rc[c];
+      if (w) {
+        load(idx - 1, t);
+        add(A.c[1], t);
+      }
+      if (e) {
+        load(idx + 1, t);
+        add(A.c[1], t);
+      }
+      if (so) add(A.c[2], rs);
+      if (no) add(A.c[2], rn);
+      if (e && no) {
+        load(idx + N + 1, t);
+        add(A.c[3], t);
+      }
+      if (w && so) {
+        load(idx - N - 1, t);
+        add(A.c[3], t);
+      }
+      if (w && no) {
+        load(idx + N - 1, t);
+        add(A.c[4], t);
+      }
+      if (e && so) {
+        load(idx - N + 1, t);
+        add(A.c[4], t);
+      }
+    } else {
+      wd = omega * A.dinv[idx];
+      const T dg = A.diag[idx];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) as[c] = dg * rc[c];
+      if (w) {
+        const T a = -A.cx[idx - 1];
+        load(idx - 1, t);
+        add(a, t);
+      }
+      if (e) {
+        const T a = -A.cx[idx];
+        load(idx + 1, t);
+        add(a, t);
+      }
+      if (so) add(-cys, rs);
+      T cyn = T(0);
+      if (no) {
+        cyn = A.cy[idx];
+        add(-cyn, rn);
+      }
+      cys = cyn;
+    }
+    const int64_t e0 = tiled_index(idx, cbase, ncols);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      if (cbase + c < ncols) Sout[e0 + (int64_t)c * NLSP_TILE] = rc[c] - wd * as[c];
+      rs[c] = rc[c];
+      rc[c] = rn[c];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Tall-skinny products over node tiles: partial[b] = sum over the tiles of
 // block b of X_t^T Y_t (ncx x ncy block of the first ncx / ncy columns), with
@@ -1195,11 +1312,39 @@ nlsp_status smooth_tiled(nlsp_ctx* ctx, const nlsp_op* A, int K, int s1, double 
   const bool wide = n_pad >= 65536;
   const int cpt = wide ? 8 : 4;
   const dim3 g((unsigned)div_up(n_pad, 256), (unsigned)div_up(K, cpt));
+  // large 2D grids stream along rows in FP32 (62.8 against 69.7 us per sweep
+  // at 512^2, K = 128; 587 against 662 at 1024^2, 9-point, K = 256); the
+  // bands are as long as makes the grid one wave of resident blocks (equal
+  // work, no partial last wave).  The FP64 sweep is bound by the FP64 pipe,
+  // where the per-node kernel's lower register count keeps more warps busy
+  // (349 against 394 us at 512^2, K = 128).
+  const bool rows = wide && sizeof(T) == 4 && (A->kind == ST_5PT || A->kind == ST_9PT);
+  dim3 gr(1, 1, 1);
+  int band = 0;
+  if (rows) {
+    int per_sm = 0;
+    NLSP_DISPATCH_KIND(A->kind, KD, {
+      if constexpr ((KD == ST_5PT || KD == ST_9PT) && sizeof(T) == 4)
+        NLSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_rows<KD, T, 8>, SR_THREADS, 0));
+    });
+    const int strips = div_up(A->N, SR_THREADS) * div_up(K, 8);
+    const int bands = std::max(1, std::max(per_sm, 1) * ctx->num_sms / strips);
+    band = div_up(A->N, bands);
+    gr = dim3((unsigned)div_up(A->N, SR_THREADS), (unsigned)div_up(A->N, band), (unsigned)div_up(K, 8));
+  }
   for (int it = 0; it < s1; ++it) {
     NLSP_DISPATCH_KIND(A->kind, KD, {
-      if (wide)
+      bool done = false;
+      if constexpr ((KD == ST_5PT || KD == ST_9PT) && sizeof(T) == 4) {
+        if (rows) {
+          k_smooth_rows<KD, T, 8><<<gr, SR_THREADS, 0, ctx->stream>>>(view_of<T>(A), (T)omega, K, (int)n_pad, band,
+                                                                       src, dst);
+          done = true;
+        }
+      }
+      if (!done && wide)
         k_smooth_sweep<KD, T, 8><<<g, 256, 0, ctx->stream>>>(view_of<T>(A), (T)omega, K, (int)n_pad, src, dst);
-      else
+      else if (!done)
         k_smooth_sweep<KD, T, 4><<<g, 256, 0, ctx->stream>>>(view_of<T>(A), (T)omega, K, (int)n_pad, src, dst);
     });
     NLSP_LAUNCH_CHECK();
