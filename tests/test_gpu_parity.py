@@ -67,13 +67,16 @@ def test_smooth_samples(ctx, name, precision):
     assert rel(S, ref) <= tol
 
 
-@pytest.mark.parametrize("N,K,s1", [(37, 6, 1), (37, 6, 3), (29, 5, 7), (700, 3, 3)])
+@pytest.mark.parametrize("N,K,s1", [(37, 6, 1), (37, 6, 3), (29, 5, 7), (700, 3, 3), (300, 13, 2)])
 @pytest.mark.parametrize("kind", ["5pt", "9pt"])
 @pytest.mark.parametrize("precision", [FP64, MIXED])
 def test_smooth_samples_sweep_counts_and_shapes(ctx, N, K, s1, kind, precision):
     # odd and even sweep counts, sample counts that are not a multiple of the
-    # kernel's four columns per thread, grid rows that span node tiles and a
-    # 700-wide grid (n = 490000, ragged last tile), for both 2D stencils
+    # kernels' four or eight columns per thread, grid rows that span node
+    # tiles, and grids of 65536 nodes and more (700^2: n = 490000 with a
+    # ragged last tile; 300^2 with K = 13: two column groups, the second
+    # ragged), which the FP32 path sweeps by streaming along grid rows with a
+    # partial block of grid columns at the edge, for both 2D stencils
     p = gen.poisson_2d(N, 2, K, seed=5) if kind == "5pt" else gen.aniso_9pt_2d(N=N, k=2, K=K, m=1, seed=6)
     A = op.assemble(p)
     Aop = _api().Operator.from_problem(ctx, p)
